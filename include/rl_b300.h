@@ -1,0 +1,253 @@
+/*
+ * rl_b300.h -- C ABI of the B300 (sm_103a) hot path of massively parallel PPO for legged
+ * locomotion (Rudin, Hoeller, Reist, Hutter, "Learning to Walk in Minutes Using Massively
+ * Parallel Deep Reinforcement Learning", CoRL 2021).
+ *
+ * One training iteration (Sec. 2, Sec. 2.2) is: n_steps times { batched actor/critic
+ * inference (rl_policy_act) -> env-side tensor math for every robot (rl_env_step) }, then the
+ * critic's value of the last observation, GAE (rl_gae), and epochs x minibatches of the
+ * clipped-surrogate PPO update with the adaptive learning rate of Algorithm 1 and Adam
+ * (rl_ppo_update).  rl_train_iteration runs all of it on buffers the context owns, optionally
+ * as one CUDA graph.
+ *
+ * Conventions (all entry points):
+ *   - Status codes only; no exception crosses the ABI.  Arguments are validated on the host
+ *     before anything is launched; an invalid argument returns RL_ERR_INVALID_ARG (or
+ *     RL_ERR_ALIGNMENT) and launches nothing.
+ *   - Unless stated otherwise a pointer argument is a CUDA device pointer owned by the caller
+ *     and valid for the duration of the asynchronous work on `stream`.  Host pointers are
+ *     marked "host".  The library keeps no pointer to caller memory after a call returns.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream).  No entry point other than rl_create / rl_destroy /
+ *     rl_get_scalars / rl_train_iteration (when it copies stats to the host) synchronises.
+ *   - Device-side failures that are not CUDA errors (a bounded wait that ran out, an index
+ *     outside its buffer) are recorded in a device status word, read by
+ *     rl_last_device_status.
+ *   - Floating point: FP32 everywhere except the MLP GEMM operands in RL_BF16 precision
+ *     (bfloat16 operands, FP32 accumulation).
+ *   - Layouts: "[T][N]" means row-major, N contiguous; step t of a rollout is row t.
+ */
+#ifndef RL_B300_H
+#define RL_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rl_ctx rl_ctx;
+typedef int32_t rl_status;
+
+#define RL_OK 0
+#define RL_ERR_INVALID_ARG (-1)
+#define RL_ERR_ALIGNMENT (-2)
+#define RL_ERR_CUDA (-3)
+#define RL_ERR_TIMEOUT (-4)
+#define RL_ERR_STATE (-5)
+#define RL_ERR_OOM (-6)
+#define RL_ERR_UNSUPPORTED (-7)
+
+#define RL_FP32 0
+#define RL_BF16 1
+
+/* Env state layout (structure of arrays).  float state: [RL_NF][num_envs]; int state:
+ * [RL_NI][num_envs].  Rows: position relative to the spawn origin (x, y), base height z,
+ * heading (cos, sin), base-frame linear velocity (3), angular velocity (3), projected gravity
+ * (3), command (v*_x, v*_y, w*_z), feet air time (4), joint positions (12), joint velocities
+ * (12), previous actions (12); int rows: episode length, curriculum level, foot-contact bits. */
+#define RL_NF 57
+#define RL_NI 3
+#define RL_F_PX 0
+#define RL_F_PY 1
+#define RL_F_Z 2
+#define RL_F_HC 3
+#define RL_F_HS 4
+#define RL_F_VX 5
+#define RL_F_WX 8
+#define RL_F_GX 11
+#define RL_F_CMDX 14
+#define RL_F_TAIR 17
+#define RL_F_Q 21
+#define RL_F_QD 33
+#define RL_F_AP 45
+#define RL_I_EPLEN 0
+#define RL_I_LEVEL 1
+#define RL_I_CONTACT 2
+
+/* Number of floats of the device statistics vector written by rl_ppo_update / rl_train_iteration:
+ * [0] mean loss, [1] mean surrogate loss, [2] mean value loss, [3] entropy, [4] mean KL,
+ * [5] final learning rate alpha, [6] clip fraction, [7] mean reward of the rollout (train only),
+ * [8] mean advantage before normalisation, [9] its standard deviation, [10] number of resets,
+ * [11] mean curriculum level, [12..15] reserved. */
+#define RL_NSTATS 16
+
+/* Configuration.  Defaults (rl_config_default) follow Table 3 (PPO), Algorithm 1, Table 2,
+ * Table 4, Sec. 3.1 (8 m tiles), App. A.1.1 (50 Hz policy, 4 x 0.005 s substeps) and the
+ * rough-terrain workload (4096 robots x 24 steps, 235 observations, 512-256-128 ELU MLPs). */
+typedef struct rl_config {
+    int32_t num_envs;        /* robots N (Sec. 2.2.1) */
+    int32_t num_steps;       /* steps per robot and iteration T (Sec. 2.2.1) */
+    int32_t obs_dim;         /* 48 proprioceptive + grid_x * grid_y heights (Sec. 3.2) */
+    int32_t obs_pad;         /* row stride of observation buffers; multiple of 64, >= obs_dim */
+    int32_t act_dim;         /* 12 joint targets */
+    int32_t num_hidden;      /* hidden layers (1..4) */
+    int32_t hidden[4];       /* widths, each a multiple of 64, <= 1024 */
+    float gamma, lam, clip, entropy_coef, value_coef, kl_target, lr_init, lr_min, lr_max;
+    int32_t epochs, minibatches;
+    int32_t precision;       /* RL_FP32 or RL_BF16 (MLP GEMM operands) */
+    float kp, kd, action_scale, dt, sim_dt;
+    int32_t decimation, max_episode_len;
+    int32_t num_levels, num_cols;
+    float tile_size, hf_res;
+    int32_t grid_x, grid_y;
+    float grid_spacing;
+    int32_t noise_on, push_on, push_interval;
+    float push_vel;
+    float cmd_range[3];
+    uint32_t crash_threshold; /* stand-in physics: crash when a 32-bit draw is below this */
+    float q_def[12];          /* default joint positions */
+    int32_t reserved[2];      /* zero; keeps seed 8-byte aligned without implicit padding */
+    uint64_t seed;
+} rl_config;
+
+/* Fills *cfg with the defaults listed above.  Never fails. */
+void rl_config_default(rl_config* cfg);
+
+/* Number of parameters of the flat layout (actor then critic, see rl_get_params). */
+int64_t rl_param_count(const rl_config* cfg);
+
+/* Human-readable name of a status code (static string). */
+const char* rl_status_string(rl_status s);
+
+/* Creates a learner.  heightfield: host, fp32 [num_levels * c][num_cols * c] with
+ * c = tile_size / hf_res (x rows, y columns; Sec. 2.1 tiles all terrain levels and types in
+ * one mesh), may be NULL when grid_x * grid_y == 0.  init_params: host, flat fp32 parameters
+ * (layout of rl_get_params), required.  Allocates every buffer it will ever use (weights,
+ * Adam moments, rollout storage, workspaces); no later call allocates.  The env state is
+ * initialised as rl_env_reset_all describes.  Returns RL_ERR_INVALID_ARG for an inconsistent
+ * config, RL_ERR_OOM if device memory runs out, RL_ERR_CUDA on any other CUDA error. */
+rl_status rl_create(const rl_config* cfg, const float* heightfield, const float* init_params,
+                    rl_ctx** out);
+
+/* Frees everything the context owns.  Synchronises the device.  NULL is a no-op. */
+void rl_destroy(rl_ctx* ctx);
+
+/* Flat parameters (fp32), actor [W1, b1, ..., W_head, b_head, log_std] then critic
+ * [W1, b1, ..., W_head, b_head], W_l row-major [fan_out][fan_in], first fan_in = obs_dim. */
+rl_status rl_get_params(rl_ctx* ctx, float* params_out, void* stream);
+rl_status rl_set_params(rl_ctx* ctx, const float* params, void* stream);
+
+/* Host-visible learner scalars (synchronises): out[0] = alpha, out[1] = iteration counter,
+ * out[2] = Adam step count, out[3] = last minibatch KL. */
+rl_status rl_get_scalars(rl_ctx* ctx, double out[4]);
+/* Sets alpha, the iteration counter and the Adam step count (enqueued on stream). */
+rl_status rl_set_scalars(rl_ctx* ctx, double alpha, int64_t iteration, int64_t adam_step, void* stream);
+
+/* Env state access (layout above).  state_f: [RL_NF][num_envs] fp32, state_i: [RL_NI][num_envs]. */
+rl_status rl_env_get_state(rl_ctx* ctx, float* state_f, int32_t* state_i, void* stream);
+rl_status rl_env_set_state(rl_ctx* ctx, const float* state_f, const int32_t* state_i, void* stream);
+
+/* Spawns every robot on level 0 at the centre of its tile with a fresh command and a random
+ * episode length (Sec. 3.1), and writes the first observation to obs_out [num_envs][obs_pad]
+ * (fp32 for RL_FP32, bf16 for RL_BF16; may be NULL). */
+rl_status rl_env_reset_all(rl_ctx* ctx, void* obs_out, void* stream);
+
+/* One 50 Hz policy step of the env-side math for all robots (Sec. 3.2, App. A.1.1, Table 2,
+ * Sec. 2.2.2, Sec. 3.1, Sec. 3.3): 4 substeps of PD control (tau = Kp (q* - q) - Kd qd,
+ * q* = q_def + action_scale * a) each followed by the seeded physics stand-in, the nine
+ * Table 2 reward terms, crash / time-out, reward + gamma V on time-out, curriculum update and
+ * respawn of finished robots, then the observation with bilinear height samples and Table 4
+ * noise.  t: step index within the iteration (part of the random key).
+ *   actions [N][act_dim] fp32; values [N] fp32 = V(o_t) stored at act time;
+ *   obs_out [N][obs_pad] (fp32 or bf16 by precision; padding columns written as 0);
+ *   rew_out [N] fp32; done_out, timeout_out [N] uint8; level_out, terrain_idx_out [N] int32
+ *   (any output may be NULL except obs_out and rew_out). */
+rl_status rl_env_step(rl_ctx* ctx, int32_t t, const float* actions, const float* values,
+                      void* obs_out, float* rew_out, uint8_t* done_out, uint8_t* timeout_out,
+                      int32_t* level_out, int32_t* terrain_idx_out, void* stream);
+
+/* Batched policy inference (Sec. 2): mu = actor(obs), V = critic(obs) (ELU hidden layers,
+ * linear heads), a = mu + exp(log_std) * eps with eps ~ N(0, 1) drawn from the counter-based
+ * generator keyed by (seed, iteration, t, env), log pi(a) of the diagonal Gaussian.
+ *   obs [n][obs_pad] (fp32 or bf16 by precision), n <= num_envs;
+ *   actions, mu [n][act_dim] fp32; logp, values [n] fp32.  actions, mu and logp may all be
+ *   NULL, which runs the critic only (the last value of a rollout). */
+rl_status rl_policy_act(rl_ctx* ctx, int32_t t, int32_t n, const void* obs, float* actions,
+                        float* mu, float* logp, float* values, void* stream);
+
+/* Generalized advantage estimation (Sec. 2.2.1, Table 3) over [T][N] samples:
+ *   delta_t = r_t + gamma (1 - d_t) V_{t+1} - V_t,  A_t = delta_t + gamma lambda (1 - d_t) A_{t+1},
+ *   V_T = last_val, R_t = A_t + V_t.  Stateless.
+ * rew, val [T][N] fp32; last_val [N]; done [T][N] uint8; adv_out, ret_out [T][N] fp32.
+ * normalize != 0 replaces A by (A - mean) / (std + 1e-8) over all T*N samples (population std;
+ * R keeps the unnormalised A).  adv_stats_out (may be NULL): [2] = mean, std of A.
+ * workspace: device scratch of rl_gae_workspace_bytes(T, N) bytes, 16-byte aligned (may be
+ * NULL when normalize == 0 and adv_stats_out == NULL). */
+size_t rl_gae_workspace_bytes(int32_t T, int32_t N);
+rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val,
+                 const float* last_val, const uint8_t* done, float* adv_out, float* ret_out,
+                 int32_t normalize, float* adv_stats_out, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* PPO update (Sec. 2.2, Table 3, Algorithm 1) on B = num_envs * num_steps samples:
+ * for each of `epochs` epochs a fresh permutation (keyed by seed, iteration, epoch) splits
+ * the batch into `minibatches` minibatches; for each minibatch: forward, clipped surrogate,
+ * clipped value loss, entropy bonus, KL(pi_old || pi_new), alpha updated by Algorithm 1,
+ * hand-written backward, Adam step with the new alpha.  Increments the iteration counter.
+ *   obs [B][obs_pad] (fp32 / bf16 by precision); actions, mu_old [B][act_dim] fp32;
+ *   logp_old, val_old, adv (normalised), ret [B] fp32; stats_out: device [RL_NSTATS] or NULL.
+ * B must be divisible by minibatches. */
+rl_status rl_ppo_update(rl_ctx* ctx, const void* obs, const float* actions, const float* logp_old,
+                        const float* mu_old, const float* val_old, const float* adv,
+                        const float* ret, int32_t epochs, int32_t minibatches, float* stats_out,
+                        void* stream);
+
+/* Loss and gradient of one minibatch without a parameter step (the hand-written backward of
+ * rl_ppo_update, exposed for gradient checks).  Inputs are M contiguous rows (same layouts
+ * as rl_ppo_update); log_std_old [act_dim]; grad_out: flat layout of rl_get_params;
+ * stats_out [RL_NSTATS] (loss terms, KL).  M <= num_envs * num_steps / minibatches. */
+rl_status rl_ppo_loss_grad(rl_ctx* ctx, int32_t M, const void* obs, const float* actions,
+                           const float* logp_old, const float* mu_old, const float* log_std_old,
+                           const float* val_old, const float* adv, const float* ret,
+                           float* grad_out, float* stats_out, void* stream);
+
+/* One full training iteration on context-owned storage (rollout, last value, GAE with
+ * normalisation, update).  use_graph != 0 replays a CUDA graph of the whole iteration
+ * (captured on first use).  stats_host (host, may be NULL): RL_NSTATS floats copied back,
+ * which synchronises stream. */
+rl_status rl_train_iteration(rl_ctx* ctx, int32_t use_graph, float* stats_host, void* stream);
+
+/* Context-owned rollout storage (device pointers, valid until rl_destroy):
+ * 0 obs [T+1][N][obs_pad], 1 actions [T][N][A], 2 mu [T][N][A], 3 logp [T][N], 4 values [T][N],
+ * 5 rewards [T][N], 6 dones [T][N] u8, 7 timeouts [T][N] u8, 8 last values [N],
+ * 9 advantages [T][N], 10 returns [T][N], 11 levels [N] int32, 12 stats [RL_NSTATS]. */
+rl_status rl_get_storage(rl_ctx* ctx, int32_t which, void** ptr, size_t* bytes);
+
+/* Device status word: RL_OK, or the first device-side failure recorded (RL_ERR_TIMEOUT for a
+ * bounded wait that ran out, RL_ERR_STATE for an out-of-range index).  Synchronises. */
+rl_status rl_last_device_status(rl_ctx* ctx);
+
+/* Timing of the dominant kernel class inside rl_train_iteration: enable records CUDA events
+ * around every launch of class `kernel_class` (0 = update GEMMs) on the launching stream;
+ * read returns the summed event time in ms and the launch count of the last iteration and
+ * resets them.  Event recording is captured into the graph when the graph is built after
+ * enabling. */
+rl_status rl_profile_enable(rl_ctx* ctx, int32_t kernel_class, int32_t on);
+rl_status rl_profile_read(rl_ctx* ctx, float* total_ms, int32_t* launches);
+
+/* Diagnostic: C = A B^T with the library's tcgen05 BF16 tensor-core GEMM kernel (FP32
+ * accumulation), for checking the tensor-core path in isolation.  A [M][K] bf16, B [N][K] bf16
+ * (row-major, K contiguous), C [M][N] fp32.  K % 8 == 0 (16-byte rows), N % 64 == 0, pointers
+ * 16-byte aligned.  The paper has no counterpart; it is the GEMM behind rl_policy_act and
+ * rl_ppo_update in RL_BF16 precision. */
+rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream);
+
+/* Number of kernel launches one rl_train_iteration enqueues (host-side count). */
+int32_t rl_launches_per_iteration(rl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RL_B300_H */

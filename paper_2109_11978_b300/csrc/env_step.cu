@@ -1,0 +1,376 @@
+// Env-side tensor math of one 50 Hz policy step for all robots, fused in one kernel:
+// PD control over the simulation substeps with the seeded physics stand-in, the Table 2
+// reward, termination / time-out / bootstrap, the curriculum update and respawn, and the
+// observation with bilinear height samples and Table 4 noise.
+//
+// Layout: the env state is a structure of arrays in HBM ([57][N] fp32 + [3][N] int32), so
+// every state row is read and written with 128-byte coalesced accesses.  A block owns 32
+// robots.  Phase 1: warp 0, one robot per lane, runs the per-robot recurrence in registers
+// and leaves a 60-float record per robot in shared memory.  Phase 2: all 8 warps assemble the
+// observation rows (one robot per warp at a time, two adjacent columns per lane), so the row
+// of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height samples of a
+// robot are gathered by 32 lanes in parallel from the L2-resident heightfield.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rl {
+
+namespace {
+
+// Physics stand-in constants (dyadic, exact in fp32).  The stand-in is not the paper's
+// method: it replaces PhysX with a linear stochastic transition that both the CUDA path and
+// the oracle evaluate as the same fp32 recurrence, operation by operation.
+constexpr float A_Q = 0.96875f, INV_I = 2.0f, S_Q = 0.0625f;
+constexpr float RHO_V = 0.96875f, ONE_M_RHO_V = 0.03125f, S_V = 0.03125f;
+constexpr float RHO_W = 0.96875f, ONE_M_RHO_W = 0.03125f, S_W = 0.0625f;
+constexpr float RHO_G = 0.96875f, S_G = 0.0078125f;
+constexpr float RHO_Z = 0.96875f, ONE_M_RHO_Z = 0.03125f, S_Z = 0.00390625f;
+constexpr float Z_NOM0 = 0.5f, Z_NOM_PER_LEVEL = 0.0625f;
+
+// Table 2 weights (times dt) and phi(x) = exp(-|x|^2 / 0.25).
+constexpr float W_LIN = 1.0f, W_ANG = 0.5f, W_VZ = 4.0f, W_WXY = 0.05f, W_JOINT = 0.001f;
+constexpr float W_TAU = 0.00002f, W_RATE = 0.25f, W_COLL = 0.001f, W_AIR = 2.0f;
+constexpr float PHI_INV = 4.0f, AIR_TARGET = 0.5f;
+
+// Random-key slots.
+constexpr int SLOT_CRASH = 128, SLOT_COLL = 129, SLOT_LOOP = 130, SLOT_PUSH = 131;
+constexpr int SLOT_CMD = 133, SLOT_HEADING = 136, SLOT_EPLEN = 138, SLOT_OBS = 256;
+
+// Foot-contact schedule of the stand-in.
+constexpr int CONTACT_PERIOD = 40, CONTACT_DUTY = 20, CONTACT_ENV_STRIDE = 7;
+
+constexpr int ENVS = 32;        // robots per block
+constexpr int THREADS = 256;    // 8 warps
+constexpr int REC = 64;         // floats per robot record in shared memory
+
+// Record fields (after the 48 proprioceptive observations).
+constexpr int R_PX = 48, R_PY = 49, R_HC = 50, R_HS = 51, R_Z = 52, R_BX = 53, R_BY = 54;
+constexpr int R_KEYLO = 55, R_KEYHI = 56;
+
+#define FADD __fadd_rn
+#define FSUB __fsub_rn
+#define FMUL __fmul_rn
+
+__device__ __forceinline__ float znom(int level) {
+    return FADD(FMUL(__int2float_rn(level), Z_NOM_PER_LEVEL), Z_NOM0);
+}
+
+// Table 4 half-widths by observation column.
+__device__ __forceinline__ float noise_scale(int c) {
+    if (c < 3) return 0.01f;       // base linear velocity
+    if (c < 6) return 0.2f;        // base angular velocity
+    if (c < 9) return 0.05f;       // projected gravity
+    if (c < 12) return 0.0f;       // commands
+    if (c < 24) return 0.01f;      // joint positions
+    if (c < 36) return 1.5f;       // joint velocities
+    if (c < 48) return 0.0f;       // previous actions (not listed)
+    return 0.1f;                   // terrain heights
+}
+
+struct Respawn {
+    float hc, hs, cx, cy, cw;
+};
+
+// Fresh heading and command of a respawned robot (Sec. 3.1: commands are drawn at reset and
+// held for the episode).  The heading is a random direction normalised in fp32.
+__device__ __forceinline__ Respawn respawn_draw(uint64_t key, const EnvParams& p) {
+    Respawn r;
+    float hx = uniform_pm1(hi32(rng_word(key, SLOT_HEADING)));
+    float hy = uniform_pm1(hi32(rng_word(key, SLOT_HEADING + 1)));
+    float n2 = FADD(FMUL(hx, hx), FMUL(hy, hy));
+    bool ok = n2 > 9.5367431640625e-07f;   // 2^-20
+    float nn = __fsqrt_rn(ok ? n2 : 1.0f);
+    r.hc = ok ? __fdiv_rn(hx, nn) : 1.0f;
+    r.hs = ok ? __fdiv_rn(hy, nn) : 0.0f;
+    r.cx = FMUL(uniform_pm1(hi32(rng_word(key, SLOT_CMD))), p.cmd_range[0]);
+    r.cy = FMUL(uniform_pm1(hi32(rng_word(key, SLOT_CMD + 1))), p.cmd_range[1]);
+    r.cw = FMUL(uniform_pm1(hi32(rng_word(key, SLOT_CMD + 2))), p.cmd_range[2]);
+    return r;
+}
+
+// Bilinear terrain height at cell coordinate (ib + f) along each axis, clamped to the map.
+// ib is the integer cell of the tile centre, f the fp32 offset in cells (small magnitude,
+// so the split keeps sub-micrometre resolution anywhere on the 80 m x 160 m map).
+__device__ __forceinline__ float terrain_height(const float* __restrict__ hf, int nx, int ny, int ibx,
+                                               float fx, int iby, float fy) {
+    float flx = floorf(fx), fly = floorf(fy);
+    int i0 = ibx + (int)flx, j0 = iby + (int)fly;
+    float fu = fx - flx, fv = fy - fly;
+    if (i0 < 0) { i0 = 0; fu = 0.f; }
+    if (i0 >= nx - 1) { i0 = nx - 2; fu = 1.f; }
+    if (j0 < 0) { j0 = 0; fv = 0.f; }
+    if (j0 >= ny - 1) { j0 = ny - 2; fv = 1.f; }
+    const float* h = hf + (size_t)i0 * ny + j0;
+    float h00 = __ldg(h), h01 = __ldg(h + 1), h10 = __ldg(h + ny), h11 = __ldg(h + ny + 1);
+    return (1.f - fu) * (1.f - fv) * h00 + fu * (1.f - fv) * h10 + (1.f - fu) * fv * h01 + fu * fv * h11;
+}
+
+template <int MODE>   // 0 = policy step, 1 = spawn all robots (initial state)
+__global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
+    __shared__ float rec[ENVS][REC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int env0 = blockIdx.x * ENVS;
+    const int N = p.N;
+    const unsigned long long it = p.iteration ? *p.iteration : 0ull;
+
+    if (warp == 0) {
+        const int e = env0 + lane;
+        float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (reward, reset, level)
+        if (e < N) {
+            float* sf = p.sf;
+            int* si = p.si;
+            auto F = [&](int r) -> float& { return sf[(size_t)r * N + e]; };
+            float px = F(RL_F_PX), py = F(RL_F_PY), z = F(RL_F_Z), hc = F(RL_F_HC), hs = F(RL_F_HS);
+            float vx = F(5), vy = F(6), vz = F(7), wx = F(8), wy = F(9), wz = F(10);
+            float gx = F(11), gy = F(12), gz = F(13), cx = F(14), cy = F(15), cw = F(16);
+            float tair[4], q[12], qd[12], ap[12];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) tair[f] = F(RL_F_TAIR + f);
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                q[j] = F(RL_F_Q + j);
+                qd[j] = F(RL_F_QD + j);
+                ap[j] = F(RL_F_AP + j);
+            }
+            int eplen = si[(size_t)RL_I_EPLEN * N + e];
+            int level = si[(size_t)RL_I_LEVEL * N + e];
+            int contact = si[(size_t)RL_I_CONTACT * N + e];
+            uint64_t key;
+            if (MODE == 0) {
+                key = rng_key(p.seed, kStreamEnv, it, (uint64_t)p.t, (uint64_t)e);
+                float a[12], qstar[12], tau[12], qd_old[12];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    a[j] = __ldg(p.actions + (size_t)e * 12 + j);
+                    qd_old[j] = qd[j];
+                    qstar[j] = FADD(p.q_def[j], FMUL(p.ascale, a[j]));
+                }
+                // Pushes (Sec. 3.3): every push_interval steps of the episode, +-push_vel in x, y.
+                if (p.push_on && eplen > 0 && (eplen % p.push_interval) == 0) {
+                    vx = FADD(vx, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH)))));
+                    vy = FADD(vy, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH + 1)))));
+                }
+                const float zn = znom(level);
+                for (int k = 0; k < p.decimation; ++k) {
+                    const uint32_t base = 32u * (uint32_t)k;
+                    // PD torque (Sec. 3.2), recomputed every substep (App. A.1.1).
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) tau[j] = FSUB(FMUL(p.kp, FSUB(qstar[j], q[j])), FMUL(p.kd, qd[j]));
+                    // Physics stand-in substep (exact fp32 recurrence).
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        float xi = irwin_hall(rng_word(key, base + j));
+                        qd[j] = FADD(FADD(FMUL(A_Q, qd[j]), FMUL(p.sim_dt, FMUL(INV_I, tau[j]))), FMUL(S_Q, xi));
+                        q[j] = FADD(q[j], FMUL(p.sim_dt, qd[j]));
+                    }
+                    vx = FADD(FADD(FMUL(RHO_V, vx), FMUL(ONE_M_RHO_V, cx)), FMUL(S_V, irwin_hall(rng_word(key, base + 12))));
+                    vy = FADD(FADD(FMUL(RHO_V, vy), FMUL(ONE_M_RHO_V, cy)), FMUL(S_V, irwin_hall(rng_word(key, base + 13))));
+                    vz = FADD(FMUL(RHO_V, vz), FMUL(S_V, irwin_hall(rng_word(key, base + 14))));
+                    wx = FADD(FMUL(RHO_W, wx), FMUL(S_W, irwin_hall(rng_word(key, base + 15))));
+                    wy = FADD(FMUL(RHO_W, wy), FMUL(S_W, irwin_hall(rng_word(key, base + 16))));
+                    wz = FADD(FADD(FMUL(RHO_W, wz), FMUL(ONE_M_RHO_W, cw)), FMUL(S_W, irwin_hall(rng_word(key, base + 17))));
+                    const float w = FMUL(wz, p.sim_dt);
+                    const float c1 = FSUB(hc, FMUL(hs, w)), s1 = FADD(hs, FMUL(hc, w));
+                    const float nrm = __fsqrt_rn(FADD(FMUL(c1, c1), FMUL(s1, s1)));
+                    hc = __fdiv_rn(c1, nrm);
+                    hs = __fdiv_rn(s1, nrm);
+                    const float dx = FSUB(FMUL(hc, vx), FMUL(hs, vy)), dy = FADD(FMUL(hs, vx), FMUL(hc, vy));
+                    px = FADD(px, FMUL(p.sim_dt, dx));
+                    py = FADD(py, FMUL(p.sim_dt, dy));
+                    gx = FADD(FMUL(RHO_G, gx), FMUL(S_G, irwin_hall(rng_word(key, base + 18))));
+                    gy = FADD(FMUL(RHO_G, gy), FMUL(S_G, irwin_hall(rng_word(key, base + 19))));
+                    gz = -__fsqrt_rn(fmaxf(0.0f, FSUB(1.0f, FADD(FMUL(gx, gx), FMUL(gy, gy)))));
+                    z = FADD(FADD(FMUL(RHO_Z, z), FMUL(ONE_M_RHO_Z, zn)), FMUL(S_Z, irwin_hall(rng_word(key, base + 20))));
+                }
+                // Feet: contact schedule, air time (fp32, exact), first contacts.
+                const int eplen_new = eplen + 1;
+                const int off = (int)(((long long)e * CONTACT_ENV_STRIDE) % CONTACT_PERIOD);
+                int cbits = 0;
+                float r_air = 0.f;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const int ph = (f == 1 || f == 2) ? 20 : 0;
+                    const bool on = ((eplen_new + off + ph) % CONTACT_PERIOD) < CONTACT_DUTY;
+                    cbits |= (int)on << f;
+                    tair[f] = FADD(tair[f], p.dt);
+                    const bool first = on && !((contact >> f) & 1);
+                    if (first) r_air += tair[f] - AIR_TARGET;
+                    if (on) tair[f] = 0.f;
+                }
+                const bool crash = hi32(rng_word(key, SLOT_CRASH)) < p.crash_thr;
+                const float n_coll = (float)mulhi_n(hi32(rng_word(key, SLOT_COLL)), 3u);
+
+                // Reward: the nine Table 2 terms, each weight times dt.
+                float e2 = (cx - vx) * (cx - vx) + (cy - vy) * (cy - vy);
+                float ew = (cw - wz) * (cw - wz);
+                float sq_qdd = 0.f, sq_qd = 0.f, sq_tau = 0.f, sq_rate = 0.f;
+                const float inv_dt = 1.0f / p.dt;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    float qdd = (qd[j] - qd_old[j]) * inv_dt;
+                    sq_qdd += qdd * qdd;
+                    sq_qd += qd[j] * qd[j];
+                    sq_tau += tau[j] * tau[j];
+                    float da = a[j] - ap[j];
+                    sq_rate += da * da;
+                }
+                float r = W_LIN * expf(-e2 * PHI_INV) + W_ANG * expf(-ew * PHI_INV) - W_VZ * vz * vz -
+                          W_WXY * (wx * wx + wy * wy) - W_JOINT * (sq_qdd + sq_qd) - W_TAU * sq_tau -
+                          W_RATE * sq_rate - W_COLL * n_coll + W_AIR * r_air;
+                r *= p.dt;
+                // Termination (Sec. 3.2: base contact = crash; Sec. 2.2.1: 20 s time-out) and the
+                // time-out bootstrap r += gamma V(o_t) (Sec. 2.2.2).
+                const bool timeout = (eplen_new >= p.max_ep) && !crash;
+                const bool done = crash || timeout;
+                if (timeout) r += p.gamma * __ldg(p.values + e);
+
+                int level_new = level;
+                if (done) {
+                    // Curriculum (Sec. 3.1), decided in fp64 with one rounding per operation.
+                    const double dpx = px, dpy = py, dcx = cx, dcy = cy;
+                    const double d2 = __dadd_rn(__dmul_rn(dpx, dpx), __dmul_rn(dpy, dpy));
+                    const double half = __dmul_rn(0.5, (double)p.tile);
+                    const bool promote = d2 > __dmul_rn(half, half);
+                    const double vv = __dadd_rn(__dmul_rn(dcx, dcx), __dmul_rn(dcy, dcy));
+                    const double T = __dmul_rn((double)p.max_ep, (double)p.dt);
+                    const double thr = __dmul_rn(__dmul_rn(vv, __dmul_rn(T, T)), 0.25);
+                    const bool demote = d2 < thr;
+                    if (promote) {
+                        level_new = level + 1 >= p.L ? (int)mulhi_n(hi32(rng_word(key, SLOT_LOOP)), (uint32_t)p.L)
+                                                     : level + 1;
+                    } else if (demote) {
+                        level_new = level > 0 ? level - 1 : 0;
+                    }
+                }
+                if (p.rew) p.rew[e] = r;
+                if (p.done) p.done[e] = (uint8_t)done;
+                if (p.timeout) p.timeout[e] = (uint8_t)timeout;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) ap[j] = a[j];
+                eplen = eplen_new;
+                contact = cbits;
+                if (done) {
+                    level = level_new;
+                    Respawn rs = respawn_draw(key, p);
+                    px = 0.f; py = 0.f; z = znom(level);
+                    hc = rs.hc; hs = rs.hs;
+                    vx = vy = vz = wx = wy = wz = gx = gy = 0.f; gz = -1.f;
+                    cx = rs.cx; cy = rs.cy; cw = rs.cw;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) tair[f] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) { q[j] = p.q_def[j]; qd[j] = 0.f; ap[j] = 0.f; }
+                    eplen = 0;
+                    contact = 0;
+                }
+                st_r = r;
+                st_d = (float)done;
+                st_l = (float)level;
+            } else {
+                // Spawn (initial state): level 0, fresh heading and command, random episode length.
+                key = rng_key(p.seed, kStreamInit, 0ull, 0ull, (uint64_t)e);
+                level = 0;
+                Respawn rs = respawn_draw(key, p);
+                px = 0.f; py = 0.f; z = znom(0);
+                hc = rs.hc; hs = rs.hs;
+                vx = vy = vz = wx = wy = wz = gx = gy = 0.f; gz = -1.f;
+                cx = rs.cx; cy = rs.cy; cw = rs.cw;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) tair[f] = 0.f;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) { q[j] = p.q_def[j]; qd[j] = 0.f; ap[j] = 0.f; }
+                eplen = p.randomize_eplen ? (int)mulhi_n(hi32(rng_word(key, SLOT_EPLEN)), (uint32_t)p.max_ep) : 0;
+                contact = 0;
+            }
+            // Store the state.
+            F(RL_F_PX) = px; F(RL_F_PY) = py; F(RL_F_Z) = z; F(RL_F_HC) = hc; F(RL_F_HS) = hs;
+            F(5) = vx; F(6) = vy; F(7) = vz; F(8) = wx; F(9) = wy; F(10) = wz;
+            F(11) = gx; F(12) = gy; F(13) = gz; F(14) = cx; F(15) = cy; F(16) = cw;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) F(RL_F_TAIR + f) = tair[f];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) { F(RL_F_Q + j) = q[j]; F(RL_F_QD + j) = qd[j]; F(RL_F_AP + j) = ap[j]; }
+            si[(size_t)RL_I_EPLEN * N + e] = eplen;
+            si[(size_t)RL_I_LEVEL * N + e] = level;
+            si[(size_t)RL_I_CONTACT * N + e] = contact;
+            if (p.level_out) p.level_out[e] = level;
+            if (p.tidx_out) p.tidx_out[e] = level * p.C + (e % p.C);
+            // Record for the observation phase: the 48 proprioceptive values (Sec. 3.2 order),
+            // then the position / heading / height and the tile-centre cell.
+            float* R = rec[lane];
+            R[0] = vx; R[1] = vy; R[2] = vz; R[3] = wx; R[4] = wy; R[5] = wz;
+            R[6] = gx; R[7] = gy; R[8] = gz; R[9] = cx; R[10] = cy; R[11] = cw;
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                R[12 + j] = q[j] - p.q_def[j];
+                R[24 + j] = qd[j];
+                R[36 + j] = ap[j];
+            }
+            R[R_PX] = px; R[R_PY] = py; R[R_HC] = hc; R[R_HS] = hs; R[R_Z] = z;
+            R[R_BX] = __int_as_float(level * p.cpt + p.cpt / 2);
+            R[R_BY] = __int_as_float((e % p.C) * p.cpt + p.cpt / 2);
+            R[R_KEYLO] = __uint_as_float(lo32(key));
+            R[R_KEYHI] = __uint_as_float(hi32(key));
+        }
+        if (MODE == 0 && p.stats) {       // whole warp participates; lanes past N add zeros
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                st_r += __shfl_xor_sync(0xffffffffu, st_r, o);
+                st_d += __shfl_xor_sync(0xffffffffu, st_d, o);
+                st_l += __shfl_xor_sync(0xffffffffu, st_l, o);
+            }
+            if (lane == 0) { atomicAdd(p.stats + 0, st_r); atomicAdd(p.stats + 1, st_d); atomicAdd(p.stats + 2, st_l); }
+        }
+    }
+    __syncthreads();
+
+    // Phase 2: observation rows, one robot per warp at a time, two columns per lane.
+    for (int le = warp; le < ENVS; le += THREADS / 32) {
+        const int e = env0 + le;
+        if (e >= N) break;
+        const float* R = rec[le];
+        const uint64_t key = ((uint64_t)__float_as_uint(R[R_KEYHI]) << 32) | __float_as_uint(R[R_KEYLO]);
+        const float px = R[R_PX], py = R[R_PY], hc = R[R_HC], hs = R[R_HS], z = R[R_Z];
+        const int ibx = __float_as_int(R[R_BX]), iby = __float_as_int(R[R_BY]);
+        for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
+            float v[2];
+            uint64_t w = (p.noise_on && c0 < p.O) ? rng_word(key, SLOT_OBS + (c0 >> 1)) : 0ull;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + h;
+                float val = 0.f;
+                if (c < 48) {
+                    val = R[c];
+                } else if (c < p.O) {
+                    const int k = c - 48;
+                    const int ix = k % p.GX, iy = k / p.GX;
+                    const float gxo = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
+                    const float gyo = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+                    const float fx = (px + (hc * gxo - hs * gyo)) * p.inv_res;
+                    const float fy = (py + (hs * gxo + hc * gyo)) * p.inv_res;
+                    val = z - terrain_height(p.hf, p.nx, p.ny, ibx, fx, iby, fy);
+                }
+                if (p.noise_on && c < p.O) val += noise_scale(c) * uniform_pm1(h == 0 ? hi32(w) : lo32(w));
+                v[h] = val;
+            }
+            if (p.obs_bf16) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+                *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(p.obs) + (size_t)e * p.Op + c0) = b2;
+            } else {
+                *reinterpret_cast<float2*>(reinterpret_cast<float*>(p.obs) + (size_t)e * p.Op + c0) = make_float2(v[0], v[1]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
+    if (p.N <= 0) return cudaSuccess;
+    dim3 grid((p.N + ENVS - 1) / ENVS);
+    if (mode == 0) env_step_kernel<0><<<grid, THREADS, 0, s>>>(p);
+    else env_step_kernel<1><<<grid, THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace rl

@@ -1,0 +1,36 @@
+// Interface of the tcgen05 BF16 GEMM (see gemm_tc.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace rl {
+
+struct TcParams {
+    CUtensorMap tmA[2];        // A operand per batch entry: [M][K] bf16, box 64 x 128
+    CUtensorMap tmB[2];        // B operand per batch entry: [N][K] bf16, box 64 x bn
+    int M, N;                  // output rows / columns (N a multiple of bn)
+    int kblocks;               // K / 64 (K zero-padded by TMA beyond the tensor)
+    int kb_per_split, splits;  // split-K over blockIdx.z
+    int batch;                 // 1 or 2 (actor, critic share one launch)
+    int bn;                    // 64, 128 or 256
+    int epi;                   // EPI_STORE (fp32 split partials), EPI_BIAS_ELU, EPI_ELU_GRAD (bf16 out)
+    void* C[2];                // output per batch entry
+    int ldc;
+    void* Ct[2];               // optional transposed bf16 output [N][ldct]
+    int ldct;
+    const float* bias[2];      // EPI_BIAS_ELU
+    const void* H[2];          // EPI_ELU_GRAD: bf16 activation [M][ldh]
+    int ldh;
+    float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [M/128][N]
+    long long split_stride;    // EPI_STORE: elements between split slices
+    int* status;               // device status word
+};
+
+cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
+bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
+int tc_smem_bytes(int bn);
+cudaError_t tc_prepare();
+
+}  // namespace rl

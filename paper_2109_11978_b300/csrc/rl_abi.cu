@@ -1,0 +1,1056 @@
+// C ABI of the library: the learner context (every buffer allocated once, at creation), the
+// orchestration of the rollout step, GAE and the PPO update over the kernels, and the CUDA
+// graph of a whole training iteration.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm_tc.cuh"
+#include "kernels.cuh"
+
+using namespace rl;
+
+namespace {
+
+struct LayerInfo {
+    int in_log, in, out;   // fan-in (logical / padded), fan-out
+    long long w, b;        // offsets in the internal flat parameter vector
+};
+
+struct Seg {               // one tensor of the flat parameter layout
+    long long ioff, loff;  // internal / logical offset
+    int rows, cols_int, cols_log;
+};
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+struct rl_ctx {
+    rl_config cfg;
+    int N, T, O, Op, A, NH, hid[4], B, Mb, HL, rows;
+    bool bf16;
+    int device;
+    // parameters
+    long long P = 0, P_log = 0;
+    LayerInfo L[2][5];
+    long long logstd = 0;
+    std::vector<Seg> segs;
+    std::vector<void*> allocs;
+    float *params = nullptr, *am = nullptr, *av = nullptr, *grad_int = nullptr;
+    float* scal = nullptr;
+    unsigned long long* iter = nullptr;
+    unsigned int* counter = nullptr;
+    int* status = nullptr;
+    float *acc = nullptr, *stats = nullptr;
+    // env
+    float* hf = nullptr;
+    float* sf = nullptr;
+    int* si = nullptr;
+    int nx = 0, ny = 0, cpt = 0;
+    // rollout storage
+    void* obs = nullptr;
+    float *actions = nullptr, *mu = nullptr, *logp = nullptr, *values = nullptr, *rew = nullptr, *last_val = nullptr;
+    float *adv = nullptr, *ret = nullptr;
+    uint8_t *done = nullptr, *timeout = nullptr;
+    int* level = nullptr;
+    float* gae_ws = nullptr;
+    int gae_nparts = 0;
+    // update workspaces
+    int* perm = nullptr;
+    int* iota = nullptr;
+    float* logstd_old = nullptr;
+    void* X0 = nullptr;
+    void* X0t = nullptr;
+    void* H[2][4] = {};
+    void* Ht[2][4] = {};
+    void* dY[2][4] = {};
+    void* dYt[2][4] = {};
+    int ldt = 0;
+    float* gw[2][4] = {};
+    int S[4] = {}, kchunk[4] = {};
+    float* gb[2][4] = {};
+    int mtiles = 0;
+    float* head_part = nullptr;
+    int head_blocks = 0;
+    AdamParams adam;
+    // bf16 weights and tensor maps
+    void* wbf[2][4] = {};
+    void* wbft[2][4] = {};
+    int bn_fwd[4], bn_dx[4], bn_dw[4];
+    CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
+    CUtensorMap tm_x0;                           // gathered minibatch observations
+    CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
+    CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
+    // graph / profiling
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int launches = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    float prof_ms = 0.f;
+    int prof_n = 0;
+};
+
+namespace {
+
+#define CK(x)                                     \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) return err_of(e_); \
+    } while (0)
+
+rl_status err_of(cudaError_t e) {
+    if (e == cudaSuccess) return RL_OK;
+    if (e == cudaErrorMemoryAllocation) return RL_ERR_OOM;
+    if (e == cudaErrorInvalidValue) return RL_ERR_INVALID_ARG;
+    return RL_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc(rl_ctx* c, T** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    e = cudaMemset(q, 0, bytes < 16 ? 16 : bytes);
+    *p = reinterpret_cast<T*>(q);
+    return e;
+}
+
+size_t esize(const rl_ctx* c) { return c->bf16 ? 2 : 4; }
+
+bool config_ok(const rl_config* g) {
+    if (!g) return false;
+    if (g->num_envs < 1 || g->num_steps < 1 || g->act_dim != 12) return false;
+    if (g->grid_x < 0 || g->grid_y < 0 || g->obs_dim != 48 + g->grid_x * g->grid_y) return false;
+    if (g->obs_pad < g->obs_dim || g->obs_pad % 64) return false;
+    if (g->num_hidden < 1 || g->num_hidden > 4) return false;
+    for (int i = 0; i < g->num_hidden; ++i)
+        if (g->hidden[i] < 64 || g->hidden[i] % 64 || g->hidden[i] > 1024) return false;
+    const int hl = g->hidden[g->num_hidden - 1];
+    if (hl != 64 && hl != 128 && hl != 256) return false;
+    if (g->epochs < 1 || g->minibatches < 1) return false;
+    const long long B = (long long)g->num_envs * g->num_steps;
+    if (B % g->minibatches || (B / g->minibatches) % 64) return false;
+    if (B > (1ll << 30)) return false;
+    if (g->precision != RL_FP32 && g->precision != RL_BF16) return false;
+    if (g->decimation < 1 || g->max_episode_len < 1 || g->num_levels < 1 || g->num_cols < 1) return false;
+    if (!(g->hf_res > 0.f) || !(g->tile_size > 0.f)) return false;
+    const double cpt = (double)g->tile_size / (double)g->hf_res;
+    const long long icpt = llround(cpt);
+    if (std::fabs(cpt - (double)icpt) > 1e-4 || icpt < 2 || icpt % 2) return false;
+    if (g->push_on && g->push_interval < 1) return false;
+    return true;
+}
+
+// Host-side launch bookkeeping (launch counter, optional CUDA events around GEMMs).
+struct Enq {
+    rl_ctx* c;
+    cudaStream_t s;
+    bool profile;
+    cudaError_t gemm(const TcParams* tp, int epi, bool a_t, bool b_t, int M, int N, int K, int lda, int ldb, int ldc,
+                     int ldh, int batch, int splits, int kchunk, const GemmBatch* g) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (profile && c->ev_used + 2 <= c->ev.size()) {
+            e0 = c->ev[c->ev_used++];
+            e1 = c->ev[c->ev_used++];
+            cudaError_t e = cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = tp ? launch_tc_gemm(*tp, s)
+                           : launch_gemm_f32(epi, a_t, b_t, M, N, K, lda, ldb, ldc, ldh, batch, splits, kchunk, *g, s);
+        c->launches++;
+        if (e == cudaSuccess && e1) e = cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+        return e;
+    }
+};
+
+int pick_bn(int n) {
+    if (n % 128 == 0) return 128;
+    return 64;
+}
+
+// Forward through the hidden layers for `rows` rows starting at X (layer-0 input).
+// batch = 2 (actor + critic) or 1 with net = first (critic only).
+rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool transposed) {
+    for (int l = 0; l < c->NH; ++l) {
+        const LayerInfo& Li = c->L[0][l];
+        if (c->bf16) {
+            TcParams tp;
+            std::memset(&tp, 0, sizeof(tp));
+            for (int j = 0; j < nnets; ++j) {
+                const int n = net0 + j;
+                if (l == 0) {
+                    if (!make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)) return RL_ERR_CUDA;
+                } else {
+                    tp.tmA[j] = c->tm_fwdA[n][l];
+                }
+                tp.tmB[j] = c->tm_fwdB[n][l];
+                tp.C[j] = c->H[n][l];
+                tp.Ct[j] = transposed ? c->Ht[n][l] : nullptr;
+                tp.bias[j] = c->params + c->L[n][l].b;
+            }
+            tp.M = rows;
+            tp.N = Li.out;
+            tp.kblocks = Li.in / 64;
+            tp.kb_per_split = tp.kblocks;
+            tp.splits = 1;
+            tp.batch = nnets;
+            tp.bn = c->bn_fwd[l];
+            tp.epi = EPI_BIAS_ELU;
+            tp.ldc = Li.out;
+            tp.ldct = c->ldt;
+            tp.status = c->status;
+            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+        } else {
+            GemmBatch g;
+            std::memset(&g, 0, sizeof(g));
+            for (int j = 0; j < nnets; ++j) {
+                const int n = net0 + j;
+                g.A[j] = l == 0 ? reinterpret_cast<const float*>(X) : reinterpret_cast<const float*>(c->H[n][l - 1]);
+                g.B[j] = c->params + c->L[n][l].w;
+                g.C[j] = reinterpret_cast<float*>(c->H[n][l]);
+                g.bias[j] = c->params + c->L[n][l].b;
+            }
+            CK(q.gemm(nullptr, EPI_BIAS_ELU, false, false, rows, Li.out, Li.in, Li.in, Li.in, Li.out, 0, nnets, 1, Li.in, &g));
+        }
+    }
+    return RL_OK;
+}
+
+HeadParams head_common(rl_ctx* c, int rows) {
+    HeadParams h;
+    std::memset(&h, 0, sizeof(h));
+    const int l = c->NH - 1;
+    h.M = rows;
+    h.H = c->HL;
+    h.A = c->A;
+    h.bf16 = c->bf16 ? 1 : 0;
+    h.ha = c->H[0][l];
+    h.hc = c->H[1][l];
+    h.Wa = c->params + c->L[0][c->NH].w;
+    h.ba = c->params + c->L[0][c->NH].b;
+    h.log_std = c->params + c->logstd;
+    h.Wc = c->params + c->L[1][c->NH].w;
+    h.bc = c->params + c->L[1][c->NH].b;
+    h.seed = c->cfg.seed;
+    h.iteration = c->iter;
+    return h;
+}
+
+rl_status act_impl(rl_ctx* c, Enq& q, int t, int n, const void* obs, float* actions, float* mu, float* logp,
+                   float* values) {
+    const bool critic_only = !actions && !mu && !logp;
+    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2, false);
+    if (st != RL_OK) return st;
+    HeadParams h = head_common(c, n);
+    h.t = t;
+    h.actions = actions;
+    h.mu = mu;
+    h.logp = logp;
+    h.values = values;
+    CK(launch_act_head(h, q.s));
+    q.c->launches++;
+    return RL_OK;
+}
+
+EnvParams env_params(rl_ctx* c) {
+    EnvParams p;
+    std::memset(&p, 0, sizeof(p));
+    const rl_config& g = c->cfg;
+    p.N = c->N; p.O = c->O; p.Op = c->Op; p.GX = g.grid_x; p.GY = g.grid_y; p.decimation = g.decimation;
+    p.max_ep = g.max_episode_len; p.L = g.num_levels; p.C = g.num_cols; p.cpt = c->cpt; p.nx = c->nx; p.ny = c->ny;
+    p.push_interval = g.push_interval > 0 ? g.push_interval : 1; p.noise_on = g.noise_on; p.push_on = g.push_on;
+    p.randomize_eplen = 1;
+    p.kp = g.kp; p.kd = g.kd; p.ascale = g.action_scale; p.dt = g.dt; p.sim_dt = g.sim_dt; p.gamma = g.gamma;
+    p.push_vel = g.push_vel; p.grid_sp = g.grid_spacing; p.inv_res = 1.0f / g.hf_res; p.tile = g.tile_size;
+    for (int i = 0; i < 3; ++i) p.cmd_range[i] = g.cmd_range[i];
+    for (int i = 0; i < 12; ++i) p.q_def[i] = g.q_def[i];
+    p.crash_thr = g.crash_threshold;
+    p.seed = g.seed;
+    p.hf = c->hf;
+    p.sf = c->sf;
+    p.si = c->si;
+    p.iteration = c->iter;
+    p.obs_bf16 = c->bf16 ? 1 : 0;
+    return p;
+}
+
+// One minibatch: forward, loss head (+ Algorithm 1 when kl_target > 0), backward.
+// X0 must already hold the minibatch observations (and X0t its transpose for bf16).
+rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
+                            const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
+                            const float* ret, bool step) {
+    rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, true);
+    if (st != RL_OK) return st;
+    HeadParams h = head_common(c, M);
+    const int l = c->NH - 1;
+    h.idx = idx;
+    h.a_old = a_old;
+    h.logp_old = logp_old;
+    h.mu_old = mu_old;
+    h.log_std_old = log_std_old;
+    h.v_old = v_old;
+    h.adv = adv;
+    h.ret = ret;
+    h.clip = c->cfg.clip;
+    h.value_coef = c->cfg.value_coef;
+    h.entropy_coef = c->cfg.entropy_coef;
+    h.dya = c->dY[0][l];
+    h.dyc = c->dY[1][l];
+    h.dya_t = c->dYt[0][l];
+    h.dyc_t = c->dYt[1][l];
+    h.ldt = c->ldt;
+    h.part = c->head_part;
+    h.nblocks = c->head_blocks;
+    h.counter = c->counter;
+    h.scal = c->scal;
+    h.stats = step ? c->acc : nullptr;
+    h.kl_target = step ? c->cfg.kl_target : 0.f;
+    h.lr_min = c->cfg.lr_min;
+    h.lr_max = c->cfg.lr_max;
+    CK(launch_loss_head(h, q.s));
+    c->launches++;
+    // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums
+    for (int k = c->NH - 1; k >= 1; --k) {
+        const LayerInfo& Li = c->L[0][k];   // in = hid[k-1], out = hid[k]
+        if (c->bf16) {
+            TcParams tp;
+            std::memset(&tp, 0, sizeof(tp));
+            for (int n = 0; n < 2; ++n) {
+                tp.tmA[n] = c->tm_dxA[n][k];
+                tp.tmB[n] = c->tm_dxB[n][k];
+                tp.C[n] = c->dY[n][k - 1];
+                tp.Ct[n] = c->dYt[n][k - 1];
+                tp.H[n] = c->H[n][k - 1];
+                tp.colsum[n] = c->gb[n][k - 1];
+            }
+            tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
+            tp.batch = 2; tp.bn = c->bn_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldct = c->ldt; tp.ldh = Li.in;
+            tp.status = c->status;
+            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+        } else {
+            GemmBatch g;
+            std::memset(&g, 0, sizeof(g));
+            for (int n = 0; n < 2; ++n) {
+                g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
+                g.B[n] = c->params + c->L[n][k].w;
+                g.C[n] = reinterpret_cast<float*>(c->dY[n][k - 1]);
+                g.H[n] = reinterpret_cast<const float*>(c->H[n][k - 1]);
+                g.colsum[n] = c->gb[n][k - 1];
+            }
+            CK(q.gemm(nullptr, EPI_ELU_GRAD, false, true, M, Li.in, Li.out, Li.out, Li.in, Li.in, Li.in, 2, 1, Li.out, &g));
+        }
+    }
+    // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows
+    for (int k = 0; k < c->NH; ++k) {
+        const LayerInfo& Li = c->L[0][k];
+        if (c->bf16) {
+            TcParams tp;
+            std::memset(&tp, 0, sizeof(tp));
+            for (int n = 0; n < 2; ++n) {
+                tp.tmA[n] = c->tm_dwA[n][k];
+                tp.tmB[n] = c->tm_dwB[n][k];
+                tp.C[n] = c->gw[n][k];
+            }
+            tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
+            tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.epi = EPI_STORE; tp.ldc = Li.in;
+            tp.split_stride = (long long)Li.out * Li.in;
+            tp.status = c->status;
+            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+        } else {
+            GemmBatch g;
+            std::memset(&g, 0, sizeof(g));
+            for (int n = 0; n < 2; ++n) {
+                g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
+                g.B[n] = k == 0 ? reinterpret_cast<const float*>(c->X0) : reinterpret_cast<const float*>(c->H[n][k - 1]);
+                g.C[n] = c->gw[n][k];
+            }
+            g.split_stride = (long long)Li.out * Li.in;
+            CK(q.gemm(nullptr, EPI_STORE, true, true, Li.out, Li.in, M, Li.out, Li.in, Li.in, 0, 2, c->S[k], c->kchunk[k], &g));
+        }
+    }
+    return RL_OK;
+}
+
+// Builds the Adam segment table (gradient partial sources of every parameter tensor).
+void build_adam(rl_ctx* c) {
+    AdamParams& a = c->adam;
+    std::memset(&a, 0, sizeof(a));
+    a.p = c->params;
+    a.m = c->am;
+    a.v = c->av;
+    a.scal = c->scal;
+    const int PF = head_part_floats(c->A, c->HL);
+    const int O_WA = 0, O_BA = c->A * c->HL, O_LS = O_BA + c->A, O_WC = O_LS + c->A, O_BC = O_WC + c->HL,
+              O_DBA = O_BC + 1, O_DBC = O_DBA + c->HL;
+    int ns = 0, blocks = 0;
+    auto add = [&](long long off, long long size, const float* part, long long stride, int nsplit, void* wbf, void* wbft,
+                   int rows, int cols) {
+        AdamSeg& s = a.seg[ns];
+        s.offset = off;
+        s.size = size;
+        s.partials = part;
+        s.stride = stride;
+        s.nsplit = nsplit;
+        s.block_start = blocks;
+        a.wbf[ns] = wbf;
+        a.wbf_t[ns] = wbft;
+        a.rows[ns] = rows;
+        a.cols[ns] = cols;
+        blocks += (int)((size + ADAM_CHUNK - 1) / ADAM_CHUNK);
+        ++ns;
+    };
+    for (int n = 0; n < 2; ++n) {
+        for (int l = 0; l < c->NH; ++l) {
+            const LayerInfo& Li = c->L[n][l];
+            add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], c->wbft[n][l],
+                Li.out, Li.in);
+            if (l < c->NH - 1)
+                add(Li.b, Li.out, c->gb[n][l], Li.out, c->mtiles, nullptr, nullptr, 0, 0);
+            else
+                add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
+        }
+        const LayerInfo& Lh = c->L[n][c->NH];
+        add(Lh.w, (long long)Lh.out * Lh.in, c->head_part + (n == 0 ? O_WA : O_WC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
+        add(Lh.b, Lh.out, c->head_part + (n == 0 ? O_BA : O_BC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
+        if (n == 0) add(c->logstd, c->A, c->head_part + O_LS, PF, c->head_blocks, nullptr, nullptr, 0, 0);
+    }
+    a.nsegs = ns;
+    a.nblocks = blocks;
+}
+
+rl_status refresh_bf16(rl_ctx* c, cudaStream_t s) {
+    if (!c->bf16) return RL_OK;
+    for (int n = 0; n < 2; ++n)
+        for (int l = 0; l < c->NH; ++l) {
+            const LayerInfo& Li = c->L[n][l];
+            CK(launch_to_bf16(c->params + Li.w, Li.out, Li.in, c->wbf[n][l], c->wbft[n][l], s));
+        }
+    return RL_OK;
+}
+
+rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
+                      const float* val_old, const float* adv, const float* ret, int epochs, int minibatches, float* stats_out) {
+    const int B = c->B, Mb = B / minibatches;
+    if (Mb != c->Mb || epochs > c->cfg.epochs) return RL_ERR_INVALID_ARG;
+    cudaStream_t s = q.s;
+    CK(cudaMemcpyAsync(c->logstd_old, c->params + c->logstd, sizeof(float) * c->A, cudaMemcpyDeviceToDevice, s));
+    CK(launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s));
+    c->launches++;
+    for (int e = 0; e < epochs; ++e) {
+        for (int m = 0; m < minibatches; ++m) {
+            const int* idx = c->perm + (size_t)e * B + (size_t)m * Mb;
+            CK(launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, c->X0t, c->ldt, s));
+            c->launches++;
+            rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true);
+            if (st != RL_OK) return st;
+            c->adam.grad_out = nullptr;
+            CK(launch_adam(c->adam, s));
+            c->launches++;
+        }
+    }
+    CK(launch_small(SMALL_ITER_INC, c->scal, c->iter, nullptr, nullptr, 0.f, s));
+    c->launches++;
+    if (stats_out) {
+        CK(launch_small(SMALL_FINAL_STATS, c->scal, c->iter, c->acc, stats_out, (float)c->B, s));
+        c->launches++;
+    }
+    return RL_OK;
+}
+
+rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
+    Enq q{c, s, profile};
+    c->launches = 0;
+    c->ev_used = 0;
+    const size_t obs_step = (size_t)c->N * c->Op * esize(c);
+    uint8_t* obs = reinterpret_cast<uint8_t*>(c->obs);
+    CK(launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s));
+    c->launches++;
+    EnvParams ep = env_params(c);
+    ep.stats = c->acc + ACC_ENV;
+    for (int t = 0; t < c->T; ++t) {
+        const size_t o = (size_t)t * c->N;
+        rl_status st = act_impl(c, q, t, c->N, obs + t * obs_step, c->actions + o * c->A, c->mu + o * c->A, c->logp + o,
+                                c->values + o);
+        if (st != RL_OK) return st;
+        ep.t = t;
+        ep.actions = c->actions + o * c->A;
+        ep.values = c->values + o;
+        ep.obs = obs + (t + 1) * obs_step;
+        ep.rew = c->rew + o;
+        ep.done = c->done + o;
+        ep.timeout = c->timeout + o;
+        ep.level_out = c->level;
+        ep.tidx_out = nullptr;
+        CK(launch_env_step(ep, 0, s));
+        c->launches++;
+    }
+    rl_status st = act_impl(c, q, c->T, c->N, obs + c->T * obs_step, nullptr, nullptr, nullptr, c->last_val);
+    if (st != RL_OK) return st;
+    CK(launch_gae(c->T, c->N, c->cfg.gamma, c->cfg.lam, c->rew, c->values, c->last_val, c->done, c->adv, c->ret, 1,
+                  c->scal + SC_ADV_MEAN, c->gae_ws, c->gae_nparts, s));
+    c->launches += 2;
+    st = update_impl(c, q, c->obs, c->actions, c->logp, c->mu, c->values, c->adv, c->ret, c->cfg.epochs, c->cfg.minibatches,
+                     c->stats);
+    if (st != RL_OK) return st;
+    CK(cudaMemcpyAsync(obs, obs + c->T * obs_step, obs_step, cudaMemcpyDeviceToDevice, s));
+    return RL_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+void rl_config_default(rl_config* g) {
+    if (!g) return;
+    std::memset(g, 0, sizeof(*g));
+    g->num_envs = 4096;
+    g->num_steps = 24;
+    g->grid_x = 17;
+    g->grid_y = 11;
+    g->obs_dim = 48 + 17 * 11;
+    g->obs_pad = 256;
+    g->act_dim = 12;
+    g->num_hidden = 3;
+    g->hidden[0] = 512;
+    g->hidden[1] = 256;
+    g->hidden[2] = 128;
+    g->gamma = 0.99f;
+    g->lam = 0.95f;
+    g->clip = 0.2f;
+    g->entropy_coef = 0.01f;
+    g->value_coef = 1.0f;
+    g->kl_target = 0.01f;
+    g->lr_init = 1e-3f;
+    g->lr_min = 1e-5f;
+    g->lr_max = 1e-2f;
+    g->epochs = 5;
+    g->minibatches = 4;
+    g->precision = RL_BF16;
+    g->kp = 80.f;
+    g->kd = 2.f;
+    g->action_scale = 0.5f;
+    g->dt = 0.02f;
+    g->sim_dt = 0.005f;
+    g->decimation = 4;
+    g->max_episode_len = 1000;
+    g->num_levels = 10;
+    g->num_cols = 20;
+    g->tile_size = 8.f;
+    g->hf_res = 0.1f;
+    g->grid_spacing = 0.1f;
+    g->noise_on = 1;
+    g->push_on = 1;
+    g->push_interval = 500;
+    g->push_vel = 1.f;
+    g->cmd_range[0] = g->cmd_range[1] = g->cmd_range[2] = 1.f;
+    g->crash_threshold = 9170000u;
+    g->seed = 0;
+}
+
+int64_t rl_param_count(const rl_config* g) {
+    if (!g || g->num_hidden < 1 || g->num_hidden > 4) return -1;
+    int64_t total = 0;
+    for (int net = 0; net < 2; ++net) {
+        int in = g->obs_dim;
+        for (int l = 0; l < g->num_hidden; ++l) {
+            total += (int64_t)g->hidden[l] * in + g->hidden[l];
+            in = g->hidden[l];
+        }
+        const int out = net == 0 ? g->act_dim : 1;
+        total += (int64_t)out * in + out;
+        if (net == 0) total += g->act_dim;
+    }
+    return total;
+}
+
+const char* rl_status_string(rl_status s) {
+    switch (s) {
+        case RL_OK: return "ok";
+        case RL_ERR_INVALID_ARG: return "invalid argument";
+        case RL_ERR_ALIGNMENT: return "misaligned pointer";
+        case RL_ERR_CUDA: return "CUDA error";
+        case RL_ERR_TIMEOUT: return "device wait timed out";
+        case RL_ERR_STATE: return "invalid state";
+        case RL_ERR_OOM: return "out of device memory";
+        case RL_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+void rl_destroy(rl_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* init_params) {
+    const rl_config& g = c->cfg;
+    c->N = g.num_envs; c->T = g.num_steps; c->O = g.obs_dim; c->Op = g.obs_pad; c->A = g.act_dim; c->NH = g.num_hidden;
+    for (int i = 0; i < 4; ++i) c->hid[i] = g.hidden[i];
+    c->B = c->N * c->T;
+    c->Mb = c->B / g.minibatches;
+    c->HL = c->hid[c->NH - 1];
+    c->rows = std::max(c->N, c->Mb);
+    c->bf16 = g.precision == RL_BF16;
+    c->cpt = (int)llround((double)g.tile_size / (double)g.hf_res);
+    c->nx = g.num_levels * c->cpt;
+    c->ny = g.num_cols * c->cpt;
+    CK(cudaGetDevice(&c->device));
+    CK(tc_prepare());
+    heads_prepare();
+
+    // parameter layout (internal: first-layer weights padded to obs_pad columns)
+    long long off = 0, loff = 0;
+    for (int n = 0; n < 2; ++n) {
+        int in_log = c->O, in = c->Op;
+        for (int l = 0; l <= c->NH; ++l) {
+            const int out = l < c->NH ? c->hid[l] : (n == 0 ? c->A : 1);
+            LayerInfo& Li = c->L[n][l];
+            Li.in_log = in_log; Li.in = in; Li.out = out;
+            Li.w = off; off += (long long)out * in;
+            c->segs.push_back({Li.w, loff, out, in, in_log});
+            loff += (long long)out * in_log;
+            Li.b = off; off += out;
+            c->segs.push_back({Li.b, loff, 1, out, out});
+            loff += out;
+            in_log = out; in = out;
+        }
+        if (n == 0) {
+            c->logstd = off;
+            c->segs.push_back({off, loff, 1, c->A, c->A});
+            off += c->A;
+            loff += c->A;
+        }
+    }
+    c->P = off;
+    c->P_log = loff;
+    CK(dalloc(c, &c->params, sizeof(float) * c->P));
+    CK(dalloc(c, &c->am, sizeof(float) * c->P));
+    CK(dalloc(c, &c->av, sizeof(float) * c->P));
+    CK(dalloc(c, &c->grad_int, sizeof(float) * c->P));
+    CK(dalloc(c, &c->scal, sizeof(float) * SC_NSCAL));
+    CK(dalloc(c, &c->iter, sizeof(unsigned long long)));
+    CK(dalloc(c, &c->counter, sizeof(unsigned int)));
+    CK(dalloc(c, &c->status, sizeof(int)));
+    CK(dalloc(c, &c->acc, sizeof(float) * RL_NSTATS));
+    CK(dalloc(c, &c->stats, sizeof(float) * RL_NSTATS));
+    // env
+    if (g.grid_x * g.grid_y > 0) {
+        CK(dalloc(c, &c->hf, sizeof(float) * (size_t)c->nx * c->ny));
+        CK(cudaMemcpy(c->hf, heightfield, sizeof(float) * (size_t)c->nx * c->ny, cudaMemcpyHostToDevice));
+    }
+    CK(dalloc(c, &c->sf, sizeof(float) * (size_t)RL_NF * c->N));
+    CK(dalloc(c, &c->si, sizeof(int) * (size_t)RL_NI * c->N));
+    // rollout storage
+    const size_t NT = (size_t)c->N * c->T;
+    CK(dalloc(c, &c->obs, (size_t)(c->T + 1) * c->N * c->Op * esize(c)));
+    CK(dalloc(c, &c->actions, sizeof(float) * NT * c->A));
+    CK(dalloc(c, &c->mu, sizeof(float) * NT * c->A));
+    CK(dalloc(c, &c->logp, sizeof(float) * NT));
+    CK(dalloc(c, &c->values, sizeof(float) * NT));
+    CK(dalloc(c, &c->rew, sizeof(float) * NT));
+    CK(dalloc(c, &c->done, NT));
+    CK(dalloc(c, &c->timeout, NT));
+    CK(dalloc(c, &c->last_val, sizeof(float) * c->N));
+    CK(dalloc(c, &c->adv, sizeof(float) * NT));
+    CK(dalloc(c, &c->ret, sizeof(float) * NT));
+    CK(dalloc(c, &c->level, sizeof(int) * c->N));
+    c->gae_nparts = gae_num_partials(c->T, c->N);
+    CK(dalloc(c, &c->gae_ws, rl_gae_workspace_bytes(c->T, c->N)));
+    // update workspaces
+    CK(dalloc(c, &c->perm, sizeof(int) * (size_t)g.epochs * c->B));
+    CK(dalloc(c, &c->iota, sizeof(int) * (size_t)c->Mb));
+    {
+        std::vector<int> io(c->Mb);
+        for (int i = 0; i < c->Mb; ++i) io[i] = i;
+        CK(cudaMemcpy(c->iota, io.data(), sizeof(int) * c->Mb, cudaMemcpyHostToDevice));
+    }
+    CK(dalloc(c, &c->logstd_old, sizeof(float) * c->A));
+    c->ldt = (c->Mb + 63) / 64 * 64;
+    CK(dalloc(c, &c->X0, (size_t)c->rows * c->Op * esize(c)));
+    if (c->bf16) CK(dalloc(c, &c->X0t, (size_t)c->Op * c->ldt * 2));
+    for (int n = 0; n < 2; ++n)
+        for (int l = 0; l < c->NH; ++l) {
+            CK(dalloc(c, &c->H[n][l], (size_t)c->rows * c->hid[l] * esize(c)));
+            CK(dalloc(c, &c->dY[n][l], (size_t)c->rows * c->hid[l] * esize(c)));
+            if (c->bf16) {
+                CK(dalloc(c, &c->Ht[n][l], (size_t)c->hid[l] * c->ldt * 2));
+                CK(dalloc(c, &c->dYt[n][l], (size_t)c->hid[l] * c->ldt * 2));
+            }
+        }
+    // split-K of the weight-gradient GEMMs: enough CTAs for ~4 waves over 148 SMs
+    c->mtiles = (c->Mb + 127) / 128;
+    for (int l = 0; l < c->NH; ++l) {
+        const LayerInfo& Li = c->L[0][l];
+        const int bn = c->bf16 ? pick_bn(Li.in) : 64;
+        const long long tiles = (long long)((Li.out + 127) / 128) * (Li.in / bn) * 2;
+        int S = (int)std::max(1ll, std::min(32ll, (4ll * 148 + tiles - 1) / tiles));
+        const int unit = 64;
+        int kc = (c->Mb + S - 1) / S;
+        kc = (kc + unit - 1) / unit * unit;
+        S = (c->Mb + kc - 1) / kc;
+        c->S[l] = S;
+        c->kchunk[l] = kc;
+        c->bn_fwd[l] = pick_bn(Li.out);
+        c->bn_dx[l] = pick_bn(Li.in);
+        c->bn_dw[l] = bn;
+        for (int n = 0; n < 2; ++n) {
+            CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)S * Li.out * Li.in));
+            if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->mtiles * Li.out));
+        }
+    }
+    c->head_blocks = loss_head_blocks(c->Mb);
+    CK(dalloc(c, &c->head_part, sizeof(float) * (size_t)c->head_blocks * head_part_floats(c->A, c->HL)));
+    if (c->bf16) {
+        for (int n = 0; n < 2; ++n)
+            for (int l = 0; l < c->NH; ++l) {
+                const LayerInfo& Li = c->L[n][l];
+                CK(dalloc(c, &c->wbf[n][l], (size_t)Li.out * Li.in * 2));
+                CK(dalloc(c, &c->wbft[n][l], (size_t)Li.out * Li.in * 2));
+            }
+        bool ok = make_tmap_bf16(&c->tm_x0, c->X0, c->rows, c->Op, c->Op, 128);
+        for (int n = 0; n < 2; ++n)
+            for (int l = 0; l < c->NH; ++l) {
+                const LayerInfo& Li = c->L[n][l];
+                ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l]);
+                if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
+                else c->tm_fwdA[n][l] = c->tm_x0;
+                if (l > 0) {
+                    ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
+                    ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l]);
+                }
+                ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dYt[n][l], Li.out, c->Mb, c->ldt, 128);
+                const void* xb = l == 0 ? c->X0t : c->Ht[n][l - 1];
+                ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, Li.in, c->Mb, c->ldt, c->bn_dw[l]);
+            }
+        if (!ok) return RL_ERR_CUDA;
+    }
+    build_adam(c);
+    // parameters, learning rate, env state
+    std::vector<float> pi(c->P, 0.f);
+    for (const Seg& sg : c->segs)
+        for (int r = 0; r < sg.rows; ++r)
+            std::memcpy(&pi[sg.ioff + (long long)r * sg.cols_int], &init_params[sg.loff + (long long)r * sg.cols_log],
+                        sizeof(float) * sg.cols_log);
+    CK(cudaMemcpy(c->params, pi.data(), sizeof(float) * c->P, cudaMemcpyHostToDevice));
+    float sc[SC_NSCAL] = {};
+    sc[SC_ALPHA] = g.lr_init;
+    CK(cudaMemcpy(c->scal, sc, sizeof(sc), cudaMemcpyHostToDevice));
+    rl_status st = refresh_bf16(c, nullptr);
+    if (st != RL_OK) return st;
+    EnvParams ep = env_params(c);
+    ep.obs = c->obs;
+    ep.level_out = c->level;
+    CK(launch_env_step(ep, 1, nullptr));
+    CK(cudaDeviceSynchronize());
+    return RL_OK;
+}
+
+rl_status rl_create(const rl_config* cfg, const float* heightfield, const float* init_params, rl_ctx** out) {
+    if (!out) return RL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!config_ok(cfg) || !init_params) return RL_ERR_INVALID_ARG;
+    if (cfg->grid_x * cfg->grid_y > 0 && !heightfield) return RL_ERR_INVALID_ARG;
+    rl_ctx* c = new rl_ctx();
+    c->cfg = *cfg;
+    rl_status st = create_impl(c, heightfield, init_params);
+    if (st != RL_OK) {
+        rl_destroy(c);
+        cudaGetLastError();
+        return st;
+    }
+    *out = c;
+    return RL_OK;
+}
+
+static cudaStream_t S_(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+rl_status rl_get_params(rl_ctx* c, float* out, void* stream) {
+    if (!c || !out) return RL_ERR_INVALID_ARG;
+    for (const Seg& sg : c->segs)
+        CK(cudaMemcpy2DAsync(out + sg.loff, sizeof(float) * sg.cols_log, c->params + sg.ioff, sizeof(float) * sg.cols_int,
+                             sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_set_params(rl_ctx* c, const float* in, void* stream) {
+    if (!c || !in) return RL_ERR_INVALID_ARG;
+    for (const Seg& sg : c->segs)
+        CK(cudaMemcpy2DAsync(c->params + sg.ioff, sizeof(float) * sg.cols_int, in + sg.loff, sizeof(float) * sg.cols_log,
+                             sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, S_(stream)));
+    return refresh_bf16(c, S_(stream));
+}
+
+rl_status rl_get_scalars(rl_ctx* c, double out[4]) {
+    if (!c || !out) return RL_ERR_INVALID_ARG;
+    float sc[SC_NSCAL];
+    unsigned long long it = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&it, c->iter, sizeof(it), cudaMemcpyDeviceToHost));
+    out[0] = sc[SC_ALPHA];
+    out[1] = (double)it;
+    out[2] = sc[SC_STEP];
+    out[3] = sc[SC_KL];
+    return RL_OK;
+}
+
+rl_status rl_set_scalars(rl_ctx* c, double alpha, int64_t iteration, int64_t adam_step, void* stream) {
+    if (!c || iteration < 0 || adam_step < 0 || !(alpha > 0)) return RL_ERR_INVALID_ARG;
+    static thread_local float a;
+    static thread_local float st;
+    static thread_local unsigned long long it;
+    a = (float)alpha;
+    st = (float)adam_step;
+    it = (unsigned long long)iteration;
+    CK(cudaMemcpyAsync(c->scal + SC_ALPHA, &a, sizeof(float), cudaMemcpyHostToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(c->scal + SC_STEP, &st, sizeof(float), cudaMemcpyHostToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(c->iter, &it, sizeof(it), cudaMemcpyHostToDevice, S_(stream)));
+    CK(cudaStreamSynchronize(S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_env_get_state(rl_ctx* c, float* sf, int32_t* si, void* stream) {
+    if (!c || !sf || !si) return RL_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(sf, c->sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(si, c->si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_env_set_state(rl_ctx* c, const float* sf, const int32_t* si, void* stream) {
+    if (!c || !sf || !si) return RL_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->sf, sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(c->si, si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_env_reset_all(rl_ctx* c, void* obs_out, void* stream) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    if (obs_out && !aligned16(obs_out)) return RL_ERR_ALIGNMENT;
+    EnvParams ep = env_params(c);
+    ep.obs = obs_out ? obs_out : c->obs;
+    ep.level_out = c->level;
+    CK(launch_env_step(ep, 1, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_env_step(rl_ctx* c, int32_t t, const float* actions, const float* values, void* obs_out, float* rew_out,
+                      uint8_t* done_out, uint8_t* timeout_out, int32_t* level_out, int32_t* tidx_out, void* stream) {
+    if (!c || !actions || !values || !obs_out || !rew_out || t < 0) return RL_ERR_INVALID_ARG;
+    if (!aligned16(obs_out) || !aligned16(actions)) return RL_ERR_ALIGNMENT;
+    EnvParams ep = env_params(c);
+    ep.t = t;
+    ep.actions = actions;
+    ep.values = values;
+    ep.obs = obs_out;
+    ep.rew = rew_out;
+    ep.done = done_out;
+    ep.timeout = timeout_out;
+    ep.level_out = level_out;
+    ep.tidx_out = tidx_out;
+    CK(launch_env_step(ep, 0, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_policy_act(rl_ctx* c, int32_t t, int32_t n, const void* obs, float* actions, float* mu, float* logp,
+                        float* values, void* stream) {
+    if (!c || !obs || !values || n < 1 || n > c->rows || t < 0) return RL_ERR_INVALID_ARG;
+    if (!aligned16(obs)) return RL_ERR_ALIGNMENT;
+    const bool any = actions || mu || logp;
+    if (any && !(actions && mu && logp)) return RL_ERR_INVALID_ARG;
+    Enq q{c, S_(stream), false};
+    return act_impl(c, q, t, n, obs, actions, mu, logp, values);
+}
+
+size_t rl_gae_workspace_bytes(int32_t T, int32_t N) {
+    if (T <= 0 || N <= 0) return 0;
+    return (size_t)gae_num_partials(T, N) * 2 * sizeof(double);
+}
+
+rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val, const float* last_val,
+                 const uint8_t* done, float* adv_out, float* ret_out, int32_t normalize, float* adv_stats_out,
+                 void* workspace, size_t workspace_bytes, void* stream) {
+    if (T <= 0 || N <= 0 || !rew || !val || !last_val || !done || !adv_out || !ret_out) return RL_ERR_INVALID_ARG;
+    const bool need = normalize || adv_stats_out;
+    if (need && (!workspace || workspace_bytes < rl_gae_workspace_bytes(T, N))) return RL_ERR_INVALID_ARG;
+    if (!aligned16(adv_out) || (need && !aligned16(workspace))) return RL_ERR_ALIGNMENT;
+    CK(launch_gae(T, N, gamma, lam, rew, val, last_val, done, adv_out, ret_out, normalize, adv_stats_out,
+                  reinterpret_cast<float*>(workspace), gae_num_partials(T, N), S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_ppo_update(rl_ctx* c, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
+                        const float* val_old, const float* adv, const float* ret, int32_t epochs, int32_t minibatches,
+                        float* stats_out, void* stream) {
+    if (!c || !obs || !actions || !logp_old || !mu_old || !val_old || !adv || !ret) return RL_ERR_INVALID_ARG;
+    if (epochs < 1 || minibatches < 1 || c->B % minibatches || c->B / minibatches != c->Mb || epochs > c->cfg.epochs)
+        return RL_ERR_INVALID_ARG;
+    cudaStream_t s = S_(stream);
+    CK(launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s));
+    Enq q{c, s, false};
+    return update_impl(c, q, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out);
+}
+
+rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* actions, const float* logp_old,
+                           const float* mu_old, const float* log_std_old, const float* val_old, const float* adv,
+                           const float* ret, float* grad_out, float* stats_out, void* stream) {
+    if (!c || !obs || !actions || !logp_old || !mu_old || !log_std_old || !val_old || !adv || !ret || !grad_out)
+        return RL_ERR_INVALID_ARG;
+    if (M < 1 || M > c->Mb || M % 64) return RL_ERR_INVALID_ARG;
+    cudaStream_t s = S_(stream);
+    Enq q{c, s, false};
+    CK(launch_gather(obs, c->bf16 ? 1 : 0, c->iota, M, c->Op, c->X0, c->X0t, c->ldt, s));
+    for (int n = 0; n < 2; ++n)          // row tiles past M leave no bias-gradient partial
+        for (int l = 0; l + 1 < c->NH; ++l)
+            CK(cudaMemsetAsync(c->gb[n][l], 0, sizeof(float) * (size_t)c->mtiles * c->hid[l], s));
+    rl_status st = minibatch_fwd_bwd(c, q, M, nullptr, actions, logp_old, mu_old, log_std_old, val_old, adv, ret, false);
+    if (st != RL_OK) return st;
+    AdamParams a = c->adam;
+    a.grad_out = c->grad_int;
+    CK(launch_adam(a, s));
+    for (const Seg& sg : c->segs)
+        CK(cudaMemcpy2DAsync(grad_out + sg.loff, sizeof(float) * sg.cols_log, c->grad_int + sg.ioff,
+                             sizeof(float) * sg.cols_int, sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, s));
+    if (stats_out) {
+        // [0] loss, [1] surrogate, [2] value loss, [3] entropy, [4] KL, [6] clip fraction
+        CK(cudaMemsetAsync(stats_out, 0, sizeof(float) * RL_NSTATS, s));
+        CK(cudaMemcpyAsync(stats_out + 0, c->scal + SC_LOSS, sizeof(float) * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(stats_out + 4, c->scal + SC_KL, sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(stats_out + 6, c->scal + SC_CLIPFRAC, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    return RL_OK;
+}
+
+rl_status rl_train_iteration(rl_ctx* c, int32_t use_graph, float* stats_host, void* stream) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    cudaStream_t s = S_(stream);
+    if (use_graph) {
+        if (!c->gexec) {
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            rl_status st = train_enqueue(c, s, c->prof_on);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (st != RL_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            CK(e);
+            c->graph = graph;
+            CK(cudaGraphInstantiate(&c->gexec, graph, 0));
+        }
+        CK(cudaGraphLaunch(c->gexec, s));
+    } else {
+        rl_status st = train_enqueue(c, s, c->prof_on);
+        if (st != RL_OK) return st;
+    }
+    if (stats_host) {
+        CK(cudaMemcpyAsync(stats_host, c->stats, sizeof(float) * RL_NSTATS, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RL_OK;
+}
+
+rl_status rl_get_storage(rl_ctx* c, int32_t which, void** ptr, size_t* bytes) {
+    if (!c || !ptr) return RL_ERR_INVALID_ARG;
+    const size_t NT = (size_t)c->N * c->T;
+    void* p = nullptr;
+    size_t b = 0;
+    switch (which) {
+        case 0: p = c->obs; b = (size_t)(c->T + 1) * c->N * c->Op * esize(c); break;
+        case 1: p = c->actions; b = NT * c->A * 4; break;
+        case 2: p = c->mu; b = NT * c->A * 4; break;
+        case 3: p = c->logp; b = NT * 4; break;
+        case 4: p = c->values; b = NT * 4; break;
+        case 5: p = c->rew; b = NT * 4; break;
+        case 6: p = c->done; b = NT; break;
+        case 7: p = c->timeout; b = NT; break;
+        case 8: p = c->last_val; b = (size_t)c->N * 4; break;
+        case 9: p = c->adv; b = NT * 4; break;
+        case 10: p = c->ret; b = NT * 4; break;
+        case 11: p = c->level; b = (size_t)c->N * 4; break;
+        case 12: p = c->stats; b = RL_NSTATS * 4; break;
+        default: return RL_ERR_INVALID_ARG;
+    }
+    *ptr = p;
+    if (bytes) *bytes = b;
+    return RL_OK;
+}
+
+rl_status rl_last_device_status(rl_ctx* c) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    int st = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    return st;
+}
+
+rl_status rl_profile_enable(rl_ctx* c, int32_t kernel_class, int32_t on) {
+    if (!c || kernel_class != 0) return RL_ERR_INVALID_ARG;
+    c->prof_on = on != 0;
+    if (c->prof_on && c->ev.empty()) {
+        const size_t need = (size_t)2 * (c->cfg.epochs * c->cfg.minibatches * 3 * c->NH + 8 * (c->T + 1));
+        for (size_t i = 0; i < need; ++i) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev.push_back(e);
+        }
+    }
+    // a graph built without (or with) the event nodes is rebuilt on next use
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return RL_OK;
+}
+
+rl_status rl_profile_read(rl_ctx* c, float* total_ms, int32_t* launches) {
+    if (!c || !total_ms || !launches) return RL_ERR_INVALID_ARG;
+    float tot = 0.f;
+    int n = 0;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        CK(cudaEventSynchronize(c->ev[i + 1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+        tot += ms;
+        ++n;
+    }
+    *total_ms = tot;
+    *launches = n;
+    return RL_OK;
+}
+
+rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {
+    if (M < 1 || N < 64 || N % 64 || K < 8 || K % 8 || !A || !B || !C) return RL_ERR_INVALID_ARG;
+    if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
+    TcParams tp;
+    std::memset(&tp, 0, sizeof(tp));
+    const int bn = N % 128 == 0 ? 128 : 64;
+    if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
+    if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)) return RL_ERR_CUDA;
+    CK(tc_prepare());
+    tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
+    tp.bn = bn; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    CK(launch_tc_gemm(tp, S_(stream)));
+    return RL_OK;
+}
+
+int32_t rl_launches_per_iteration(rl_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+"""GPU parity (through the C ABI) of policy inference, the PPO loss/gradient, the update and a
+whole training iteration against the FP64 oracle.
+
+FP32 form: 1e-5 relative (norm-wise per tensor) for mu, V, log pi, actions, loss terms and every
+gradient tensor.  BF16 form (bf16 GEMM operands, FP32 accumulation): 2e-2.
+Adam after one step is -alpha g / (|g| + eps), i.e. alpha times the sign of g for all but the
+smallest gradients: elements whose oracle gradient exceeds 1e-3 of the tensor's largest must
+match to 1e-5 alpha, every other element must stay within the step bound alpha.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gae as OG
+from oracle import mlp as OM
+from oracle import ppo as OP
+from oracle.train import Learner as OLearner
+from paper_2109_11978_b300 import api, synth
+from tests.helpers import TOL_BF16, TOL_FP32, lib_config, obs_dims, oracle_env_config, oracle_ppo_config, rel_err, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(x):
+    return torch.as_tensor(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _setup(w):
+    cfg = lib_config(w)
+    O, Op = obs_dims(w)
+    params = synth.xavier_params(w["seed"] + 1, O, w["hidden"], 12, log_std=-0.3, bias_scale=0.1)
+    hf = synth.heightfield(w["seed"] + 2) if w["grid"][0] else None
+    return api.Learner(cfg, hf, params), params, O, Op
+
+
+def _obs(rows, O, Op, seed, bf16):
+    x = np.zeros((rows, Op), np.float32)
+    x[:, :O] = np.random.default_rng(seed).normal(size=(rows, O))
+    if bf16:
+        x = _bf16(x)
+        return x, torch.from_numpy(x).to(torch.bfloat16).cuda()
+    return x, torch.from_numpy(x).cuda()
+
+
+def _segments(dims):
+    """(name, size) of every tensor in the flat layout."""
+    O, hidden, A = dims
+    out = []
+    for net, od in (("actor", A), ("critic", 1)):
+        for l, (o, i) in enumerate(OM.layer_dims(O, hidden, od)):
+            out += [(f"{net}.W{l}", o * i), (f"{net}.b{l}", o)]
+        if net == "actor":
+            out.append(("log_std", A))
+    return out
+
+
+def _per_tensor_err(g, ref, dims):
+    errs, off = {}, 0
+    for name, n in _segments(dims):
+        errs[name] = rel_err(g[off:off + n], ref[off:off + n])
+        off += n
+    return errs
+
+
+@pytest.mark.parametrize("name,form,rows", [("tiny", "fp32", 64), ("rough", "fp32", 4096), ("tiny", "bf16", 64),
+                                            ("rough", "bf16", 4096), ("rough", "bf16", 1000)])
+def test_policy_act(name, form, rows):
+    prec = 1 if form == "bf16" else 0
+    w = workload(name, precision=prec)
+    L, params, O, Op = _setup(w)
+    x, xd = _obs(rows, O, Op, 3, prec == 1)
+    act = torch.empty((rows, 12), device="cuda")
+    mu = torch.empty((rows, 12), device="cuda")
+    lp = torch.empty(rows, device="cuda")
+    v = torch.empty(rows, device="cuda")
+    api.rl_policy_act(L.ctx, 3, xd, act, mu, lp, v)
+    v2 = torch.empty(rows, device="cuda")
+    api.rl_policy_act(L.ctx, 3, xd, None, None, None, v2)
+    torch.cuda.synchronize()
+    p = OM.unflatten(params, O, w["hidden"], 12)
+    ref = OM.act(p, x[:, :O], w["seed"], 0, 3)
+    tol = TOL_FP32 if prec == 0 else TOL_BF16
+    for k, got in (("mu", mu), ("values", v), ("actions", act), ("logp", lp)):
+        assert rel_err(got.cpu().numpy(), ref[k]) < tol, k
+    assert torch.equal(v, v2)
+    L.close()
+
+
+def _batch(M, O, Op, A, params, hidden, seed, bf16, kink_margin=False):
+    """A minibatch whose ratios straddle the clip range and whose values straddle the value clip.
+
+    kink_margin: keep every sample away from the clip kinks of the surrogate and the value loss
+    (log-ratio offsets either |x| < 0.05 or |x| > 0.45, value offsets |dv| < 0.05 or > 0.5, and
+    |u - w| > 10 % of max(u, w)), so that the bf16 rounding of the forward pass (a few 1e-2 in
+    log pi) cannot move a sample from one branch of the loss to the other; the gradient then
+    differs from the FP64 one only by rounding, which is what the BF16 tolerance bounds."""
+    rs = np.random.default_rng(seed)
+    x, xd = _obs(M, O, Op, seed, bf16)
+    p = OM.unflatten(params, O, hidden, A)
+    mu, _ = OM.forward(p["actor"], x[:, :O])
+    v, _ = OM.forward(p["critic"], x[:, :O])
+    a = (mu + np.exp(p["log_std"]) * rs.normal(size=mu.shape)).astype(np.float32)
+    off = 0.3 * rs.normal(size=M)
+    dvo = 0.3 * rs.normal(size=M)
+    ret = rs.normal(size=M)
+    if kink_margin:
+        inside = rs.random(M) < 0.5
+        off = np.where(inside, rs.uniform(-0.05, 0.05, M), np.sign(rs.normal(size=M)) * rs.uniform(0.45, 0.8, M))
+        inside_v = rs.random(M) < 0.5
+        dvo = np.where(inside_v, rs.uniform(-0.05, 0.05, M), np.sign(rs.normal(size=M)) * rs.uniform(0.5, 1.0, M))
+        vv, vo = v[:, 0], v[:, 0] - dvo
+        for _ in range(50):
+            vc = vo + np.clip(vv - vo, -0.2, 0.2)
+            u, w_ = (vv - ret) ** 2, (vc - ret) ** 2
+            bad = np.abs(u - w_) <= 0.1 * np.maximum(u, w_)
+            bad &= np.abs(dvo) > 0.2
+            if not bad.any():
+                break
+            ret[bad] = rs.normal(size=int(bad.sum())) * 2.0
+    logp = OM.log_prob(a, mu, p["log_std"])
+    b = {
+        "obs": x, "actions": a,
+        "logp_old": (logp - off).astype(np.float32),
+        "mu_old": (mu + 0.05 * rs.normal(size=mu.shape)).astype(np.float32),
+        "log_std_old": (p["log_std"] + 0.05).astype(np.float32),
+        "v_old": (v[:, 0] - dvo).astype(np.float32),
+        "adv": rs.normal(size=M).astype(np.float32), "ret": ret.astype(np.float32),
+    }
+    dev = {k: torch.from_numpy(np.ascontiguousarray(val)).cuda() for k, val in b.items() if k != "obs"}
+    dev["obs"] = xd
+    return b, dev
+
+
+@pytest.mark.parametrize("name,form", [("tiny", "fp32"), ("rough", "fp32"), ("tiny", "bf16"), ("rough", "bf16")])
+def test_ppo_loss_grad(name, form):
+    prec = 1 if form == "bf16" else 0
+    w = workload(name, precision=prec)
+    L, params, O, Op = _setup(w)
+    M = w["num_envs"] * w["num_steps"] // w["minibatches"]
+    b, d = _batch(M, O, Op, 12, params, w["hidden"], 21, prec == 1, kink_margin=prec == 1)
+    grad = torch.empty(L.n_params, device="cuda")
+    stats = torch.empty(16, device="cuda")
+    api.rl_ppo_loss_grad(L.ctx, d["obs"], d["actions"], d["logp_old"], d["mu_old"], d["log_std_old"], d["v_old"],
+                         d["adv"], d["ret"], grad, stats)
+    torch.cuda.synchronize()
+    p = OM.unflatten(params, O, w["hidden"], 12)
+    _, g, st = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
+                                b["v_old"], b["adv"], b["ret"])
+    gref = OP.flat_grad(g)
+    errs = _per_tensor_err(grad.cpu().numpy(), gref, (O, w["hidden"], 12))
+    tol = TOL_FP32 if prec == 0 else TOL_BF16
+    bad = {k: e for k, e in errs.items() if e >= tol}
+    assert not bad, (bad, errs)
+    s = stats.cpu().numpy()
+    for i, k in ((0, "loss"), (1, "surrogate"), (2, "value_loss"), (3, "entropy")):
+        assert abs(s[i] - st[k]) <= tol * max(1.0, abs(st[k])), (k, s[i], st[k])
+    assert abs(s[4] - st["kl"]) <= tol * max(st["kl"], 1e-3)
+    assert 0.05 < st["clip_frac"] < 0.95
+    L.close()
+
+
+def test_ppo_single_step_adam_and_alg1():
+    w = workload("tiny", epochs=1, minibatches=1)
+    L, params, O, Op = _setup(w)
+    B = w["num_envs"] * w["num_steps"]
+    b, d = _batch(B, O, Op, 12, params, w["hidden"], 5, False)
+    b["mu_old"][:] = OM.forward(OM.unflatten(params, O, w["hidden"], 12)["actor"], b["obs"][:, :O])[0]
+    d["mu_old"] = torch.from_numpy(b["mu_old"]).cuda()
+    api.rl_ppo_update(L.ctx, d["obs"], d["actions"], d["logp_old"], d["mu_old"], d["v_old"], d["adv"], d["ret"], 1, 1)
+    newp = L.params().cpu().numpy().astype(np.float64)
+    sc = api.rl_get_scalars(L.ctx)
+    assert sc["iteration"] == 1 and sc["adam_step"] == 1
+    assert sc["alpha"] == np.float32(np.float32(1e-3) * np.float32(1.5))    # KL ~ 0 < kl*/2 -> alpha * 1.5
+    p = OM.unflatten(params, O, w["hidden"], 12)
+    log_std_old = p["log_std"].copy()
+    _, g, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], log_std_old, b["v_old"],
+                               b["adv"], b["ret"])
+    gref = OP.flat_grad(g)
+    alpha = float(sc["alpha"])
+    dref = -alpha * gref / (np.abs(gref) + 1e-8)
+    dgot = newp - params.astype(np.float64)
+    ulp = 2 * np.spacing(np.abs(params).astype(np.float32)).astype(np.float64)   # fp32 rounding of p + dp
+    off = 0
+    for name, n in _segments((O, w["hidden"], 12)):
+        gs, dr, dg, u = gref[off:off + n], dref[off:off + n], dgot[off:off + n], ulp[off:off + n]
+        firm = np.abs(gs) > 1e-3 * np.abs(gs).max()
+        assert np.all(np.abs(dg[firm] - dr[firm]) <= TOL_FP32 * alpha + u[firm]), name
+        assert np.all(np.abs(dg) <= alpha * (1 + 1e-5) + u), name
+        off += n
+    L.close()
+
+
+def test_train_iteration_against_oracle_teacher_forced():
+    w = workload("tiny", epochs=2, minibatches=2, crash_threshold=2 ** 26)
+    L, params, O, Op = _setup(w)
+    ecfg, pcfg = oracle_env_config(w), oracle_ppo_config(w)
+    T, N = w["num_steps"], w["num_envs"]
+    L.train_iteration(use_graph=False)
+    torch.cuda.synchronize()
+    S = {k: L.storage(i).cpu().numpy() for i, k in L.STORAGE.items()}
+    ol = OLearner(ecfg, pcfg, w["hidden"], np.zeros((800, 1600), np.float32), params)
+    st = ol.rollout(T, actions_override=S["actions"].astype(np.float64))
+    # obs[t] for t >= 1 came from env step t - 1; obs[0] already holds the next iteration's first
+    # observation (copied from obs[T] at the end of the iteration)
+    assert rel_err(S["obs"][1:T, :, :O], st["obs"][1:]) < TOL_FP32
+    assert rel_err(S["obs"][0, :, :O], ol.obs) < TOL_FP32 and rel_err(S["obs"][T, :, :O], ol.obs) < TOL_FP32
+    assert rel_err(S["rewards"], st["reward"]) < TOL_FP32
+    assert np.array_equal(S["dones"], st["done"]) and np.array_equal(S["timeouts"], st["timeout"])
+    assert np.array_equal(S["levels"], st["level"][-1])
+    assert S["dones"].sum() > 0
+    for k_gpu, k_ref in (("mu", "mu"), ("values", "values"), ("logp", "logp")):
+        assert rel_err(S[k_gpu], st[k_ref]) < TOL_FP32, k_gpu
+    assert rel_err(S["last_values"], st["last_values"]) < TOL_FP32
+    # GAE on the GPU's rewards and values
+    A, R = OG.gae(S["rewards"], S["values"], S["last_values"], S["dones"], pcfg.gamma, pcfg.lam)
+    An, _, _ = OG.normalize(A)
+    assert rel_err(S["advantages"], An) < TOL_FP32 and rel_err(S["returns"], R) < TOL_FP32
+    # iteration counter, stats
+    sc = api.rl_get_scalars(L.ctx)
+    assert sc["iteration"] == 1 and sc["adam_step"] == pcfg.epochs * pcfg.minibatches
+    stats = S["stats"]
+    assert abs(stats[7] - S["rewards"].mean()) < 1e-5 * max(1.0, abs(S["rewards"].mean()))
+    assert stats[10] == S["dones"].sum()
+    L.close()
+
+
+def test_graph_replay_equals_eager():
+    w = workload("tiny", epochs=2, minibatches=2)
+    La, params, O, Op = _setup(w)
+    Lb, _, _, _ = _setup(w)
+    for _ in range(2):
+        La.train_iteration(use_graph=True)
+        Lb.train_iteration(use_graph=False)
+    torch.cuda.synchronize()
+    assert torch.equal(La.params(), Lb.params())
+    for i in (0, 1, 5, 6, 9):
+        assert torch.equal(La.storage(i), Lb.storage(i)), i
+    assert api.rl_last_device_status(La.ctx) == 0
+    La.close()
+    Lb.close()
