@@ -47,6 +47,22 @@ def dist_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def reduce_max_time(total_ms, device="cpu"):
+    """Max over ranks of the timed region (replicas finish when the slowest does)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, num_envs, num_steps, steps, total_ms):
+    """env-steps/s of all replicas together: every rank processed num_envs x num_steps x steps."""
+    return world * num_envs * num_steps * steps / (total_ms / 1000.0)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -160,8 +176,6 @@ def time_iterations(torch, L, steps, warmup, flush, profile=False):
 
 def cpu_baseline(seconds_budget=20.0, n_envs=256):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
-    from threadpoolctl import threadpool_info
-
     from oracle import config as OC
     from oracle.train import Learner
     from paper_2109_11978_b300 import synth
@@ -179,8 +193,12 @@ def cpu_baseline(seconds_budget=20.0, n_envs=256):
         if time.perf_counter() - t0 > seconds_budget * 0.5 or iters >= 4:
             break
     dt = time.perf_counter() - t0
-    threads = max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
     cores = len(os.sched_getaffinity(0))
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
+    except ImportError:          # numpy's BLAS defaults to one thread per available core
+        threads = int(os.environ.get("OMP_NUM_THREADS", cores))
     return {"value": n_envs * w["num_steps"] * iters / dt, "unit": "env-steps/s", "cores": min(cores, threads),
             "host_cores": cores, "blas_threads": threads, "kind": "oracle",
             "sample": f"{iters} full iteration(s) of the same workload at {n_envs} robots x 24 steps "
@@ -252,13 +270,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_time(sum(times), device="cuda")
     status = api.rl_last_device_status(L.ctx)
-    value = world * N * T * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, N, T, args.steps, total_ms)
 
     # dominant kernel: the tcgen05 GEMMs (sum of their in-graph event times)
     flops_iter = gemm_flops_per_iteration(w, O)

@@ -87,6 +87,8 @@ struct rl_ctx {
     CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
     CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
     // graph / profiling
+    cudaStream_t gstream = nullptr;              // capture / replay stream (never the legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
@@ -592,6 +594,9 @@ void rl_destroy(rl_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -609,6 +614,9 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     c->nx = g.num_levels * c->cpt;
     c->ny = g.num_cols * c->cpt;
     CK(cudaGetDevice(&c->device));
+    CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     CK(tc_prepare());
     heads_prepare();
 
@@ -938,11 +946,16 @@ rl_status rl_train_iteration(rl_ctx* c, int32_t use_graph, float* stats_host, vo
     if (!c) return RL_ERR_INVALID_ARG;
     cudaStream_t s = S_(stream);
     if (use_graph) {
+        // The graph is captured and replayed on the context's own stream (capture is not
+        // allowed on the legacy default stream), ordered after and before the caller's stream.
+        cudaStream_t g = c->gstream;
+        CK(cudaEventRecord(c->ev_in, s));
+        CK(cudaStreamWaitEvent(g, c->ev_in, 0));
         if (!c->gexec) {
-            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            rl_status st = train_enqueue(c, s, c->prof_on);
+            CK(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+            rl_status st = train_enqueue(c, g, c->prof_on);
             cudaGraph_t graph = nullptr;
-            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            cudaError_t e = cudaStreamEndCapture(g, &graph);
             if (st != RL_OK) {
                 if (graph) cudaGraphDestroy(graph);
                 return st;
@@ -951,7 +964,9 @@ rl_status rl_train_iteration(rl_ctx* c, int32_t use_graph, float* stats_host, vo
             c->graph = graph;
             CK(cudaGraphInstantiate(&c->gexec, graph, 0));
         }
-        CK(cudaGraphLaunch(c->gexec, s));
+        CK(cudaGraphLaunch(c->gexec, g));
+        CK(cudaEventRecord(c->ev_out, g));
+        CK(cudaStreamWaitEvent(s, c->ev_out, 0));
     } else {
         rl_status st = train_enqueue(c, s, c->prof_on);
         if (st != RL_OK) return st;
