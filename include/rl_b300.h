@@ -191,6 +191,26 @@ rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew,
                  int32_t normalize, float* adv_stats_out, void* workspace, size_t workspace_bytes,
                  void* stream);
 
+/* rl_gae without any allocation, for callers that cannot allocate device memory: a process
+ * whose GPU memory is reserved up front by another framework's allocator or a fixed budget, a
+ * plugin that is not allowed to call the CUDA allocator, or a latency-critical loop that must
+ * not pay for cudaMalloc and its implicit synchronisation.  The paper has no counterpart; this is
+ * a deployment convenience.  Same arguments, results and layouts as rl_gae, minus the workspace:
+ * the normalisation partial sums live in a file-scope device array of the library (64 KiB,
+ * 4096 partials), held by every GPU that loads the library until the process exits.
+ *   - N <= 262144 (4096 blocks of 64 robots); larger N returns RL_ERR_INVALID_ARG and
+ *     launches nothing.  T is unrestricted.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its partial sums there.  Each call
+ *     overwrites every slot it reads before reading it, so nothing has to start at zero, but
+ *     calls that overlap on the GPU (other streams, other host threads) race on the array and
+ *     must be serialised by the caller.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+rl_status rl_gae_noalloc(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val,
+                         const float* last_val, const uint8_t* done, float* adv_out, float* ret_out,
+                         int32_t normalize, float* adv_stats_out, void* stream);
+
 /* PPO update (Sec. 2.2, Table 3, Algorithm 1) on B = num_envs * num_steps samples:
  * for each of `epochs` epochs a fresh permutation (keyed by seed, iteration, epoch) splits
  * the batch into `minibatches` minibatches; for each minibatch: forward, clipped surrogate,

@@ -71,6 +71,7 @@ SIGNATURES = {
     "rl_policy_act": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rl_gae_workspace_bytes": (ctypes.c_size_t, [_i32, _i32]),
     "rl_gae": (_i32, [_i32, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, ctypes.c_size_t, _vp]),
+    "rl_gae_noalloc": (_i32, [_i32, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "rl_ppo_update": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "rl_ppo_loss_grad": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rl_train_iteration": (_i32, [_vp, _i32, _vp, _vp]),

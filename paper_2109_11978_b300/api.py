@@ -105,6 +105,15 @@ def rl_gae(gamma, lam, rew, val, last_val, done, adv_out, ret_out, normalize=Fal
                        _stream()), "rl_gae")
 
 
+def rl_gae_noalloc(gamma, lam, rew, val, last_val, done, adv_out, ret_out, normalize=False, adv_stats_out=None):
+    """rl_gae with its scratch in the library's static device array: no allocation anywhere
+    (for callers that cannot allocate device memory); N <= 262144, overlapping calls race."""
+    T, Nn = rew.shape
+    check(lib().rl_gae_noalloc(T, Nn, float(gamma), float(lam), _ptr(rew), _ptr(val), _ptr(last_val), _ptr(done),
+                               _ptr(adv_out), _ptr(ret_out), int(bool(normalize)), _ptr(adv_stats_out), _stream()),
+          "rl_gae_noalloc")
+
+
 def rl_ppo_update(ctx, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out=None):
     check(lib().rl_ppo_update(ctx, _ptr(obs), _ptr(actions), _ptr(logp_old), _ptr(mu_old), _ptr(val_old), _ptr(adv),
                               _ptr(ret), int(epochs), int(minibatches), _ptr(stats_out), _stream()), "rl_ppo_update")

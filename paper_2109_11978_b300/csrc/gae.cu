@@ -8,10 +8,19 @@
 // together.  Each block also leaves the fp64 sum and sum of squares of its advantages in a
 // scratch slot; the normalising kernel reduces those few hundred partials (every block
 // redundantly, which avoids a third launch) and rescales the advantages in place.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace rl {
+
+// Scratch of rl_gae_noalloc: the per-block fp64 (sum, sum of squares) pairs of the advantage
+// statistics, in a file-scope device array instead of caller- or library-allocated memory.
+// 4096 blocks of 64 robots = at most 262,144 robots; 64 KiB held by every device that loads
+// the library, until the process exits.
+constexpr int NOALLOC_MAX_PARTS = 4096;
+static __device__ __align__(256) double g_gae_noalloc_scratch[2 * NOALLOC_MAX_PARTS];
 
 namespace {
 
@@ -125,6 +134,29 @@ __global__ void gae_normalize_kernel(size_t total, int nparts, const double* __r
 }  // namespace
 
 int gae_num_partials(int T, int N) { return (N + GAE_THREADS - 1) / GAE_THREADS; }
+
+int gae_noalloc_max_envs() { return NOALLOC_MAX_PARTS * GAE_THREADS; }
+
+// Device address of the scratch array on the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+cudaError_t gae_noalloc_scratch(void** out) {
+    static std::mutex mu;
+    static void* addr[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_gae_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
 
 cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, const float* val,
                        const float* last_val, const uint8_t* done, float* adv, float* ret, int normalize,

@@ -36,6 +36,8 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
                        const float* last_val, const uint8_t* done, float* adv, float* ret,
                        int normalize, float* adv_stats, float* partials, int nparts, cudaStream_t s);
 int gae_num_partials(int T, int N);
+int gae_noalloc_max_envs();
+cudaError_t gae_noalloc_scratch(void** out);
 
 // ------------------------------------------------------------------ SIMT FP32 GEMM
 // C[m][n] = sum_k A(m,k) B(n,k);  A(m,k) = a_t ? A[k*lda+m] : A[m*lda+k];

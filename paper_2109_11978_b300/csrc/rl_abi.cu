@@ -900,6 +900,19 @@ rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew,
     return RL_OK;
 }
 
+rl_status rl_gae_noalloc(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val,
+                         const float* last_val, const uint8_t* done, float* adv_out, float* ret_out, int32_t normalize,
+                         float* adv_stats_out, void* stream) {
+    if (T <= 0 || N <= 0 || !rew || !val || !last_val || !done || !adv_out || !ret_out) return RL_ERR_INVALID_ARG;
+    if (N > gae_noalloc_max_envs()) return RL_ERR_INVALID_ARG;
+    if (!aligned16(adv_out)) return RL_ERR_ALIGNMENT;
+    void* scratch = nullptr;
+    CK(gae_noalloc_scratch(&scratch));
+    CK(launch_gae(T, N, gamma, lam, rew, val, last_val, done, adv_out, ret_out, normalize, adv_stats_out,
+                  reinterpret_cast<float*>(scratch), gae_num_partials(T, N), S_(stream)));
+    return RL_OK;
+}
+
 rl_status rl_ppo_update(rl_ctx* c, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
                         const float* val_old, const float* adv, const float* ret, int32_t epochs, int32_t minibatches,
                         float* stats_out, void* stream) {
