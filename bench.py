@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the grouped-learner and 16384-robot lines")
+    ap.add_argument("--sweep", action="store_true", help="HBM size sweep of the env-step and GAE kernels (one JSON line per size)")
     return ap.parse_args()
 
 
@@ -96,7 +98,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        out_dir = os.environ.get("BENCH_OUT_DIR") or __import__("tempfile").gettempdir()
+        self.path = os.path.join(out_dir, f"bench_clocks_gpu{gpu_index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -174,6 +177,117 @@ def time_iterations(torch, L, steps, warmup, flush, profile=False):
     return times, gemm_ms, gemm_n
 
 
+GROUP_SIZES = (512, 1024, 1536, 2048, 3072, 4096, 6144, 8192)
+
+
+def grouped_learners(torch, api, synth, steps=5, warmup=2):
+    """8 independent BF16 learners of uneven robot counts in one grouped CUDA graph."""
+    cfgs, hfs, params = [], [], []
+    for i, n in enumerate(GROUP_SIZES):
+        cfgs.append(api.default_config(num_envs=n, seed=30 + i, precision=api.RL_BF16))
+        hfs.append(synth.heightfield(32 + i))
+        params.append(synth.xavier_params(31 + i, 235, WORKLOAD["hidden"], 12))
+    g = api.rl_group_create(cfgs, hfs, params)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        api.rl_group_train_iteration(g, use_graph=True)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        api.rl_group_train_iteration(g, use_graph=True)
+        b.record(s)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    status = max(abs(api.rl_last_device_status(api.rl_group_learner(g, i))) for i in range(len(GROUP_SIZES)))
+    api.rl_group_destroy(g)
+    total = sum(GROUP_SIZES) * 24
+    return {"learners": list(GROUP_SIZES), "env_steps_per_iteration": total, "ms_per_step": sum(times) / len(times),
+            "env_steps_per_s": total * len(times) / (sum(times) / 1000.0), "device_status": -status,
+            "what": "8 independent BF16 learners (own weights, Adam, alpha, curriculum), obs 235, 512-256-128, "
+                    "24 steps, 5x4 update each, replayed as one CUDA graph with one branch per learner"}
+
+
+def large_config(torch, api, synth, steps=3, warmup=2):
+    """The full captured iteration at 16384 robots (B = 393216, minibatch 98304)."""
+    w = dict(WORKLOAD)
+    w["num_envs"] = 16384
+    L, O = make_learner(api, synth, api.RL_BF16, seed=40, w=w)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    L.train_iteration(use_graph=True)
+    times, _, _ = time_iterations(torch, L, steps, warmup, flush)
+    status = api.rl_last_device_status(L.ctx)
+    L.close()
+    return {"num_envs": 16384, "ms_per_step": sum(times) / len(times),
+            "env_steps_per_s": 16384 * 24 * len(times) / (sum(times) / 1000.0), "device_status": status}
+
+
+# Algorithmic bytes per robot-step of rl_env_step: fp32 state 57 x 4 + int state 3 x 4 read and
+# written, actions 48 + value 4 read, observation row (256 x 2 bf16 or x 4 fp32), reward 4,
+# done 1, time-out 1, level 4 written.
+ENV_BYTES = {"bf16": 2 * 240 + 52 + 256 * 2 + 10, "fp32": 2 * 240 + 52 + 256 * 4 + 10}
+GAE_BYTES_PER_SAMPLE = 17 + 8        # r, V, d read, A, R written + normalisation pass (read + write A)
+
+
+def sweep(torch, api, synth, reps=10):
+    """Achieved HBM bandwidth of the memory-bound kernels at sizes past the L2 (126 MB)."""
+    peaks, src = read_peaks()
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    lines = []
+    for n in (4096, 65536, 262144, 1048576):
+        for form in ("bf16", "fp32"):
+            cfg = api.default_config(num_envs=n, num_steps=1, minibatches=1, hidden=[64, 64],
+                                     precision=api.RL_BF16 if form == "bf16" else api.RL_FP32)
+            L = api.Learner(cfg, synth.heightfield(2), synth.xavier_params(1, 235, (64, 64), 12))
+            sf, si = synth.random_env_state(3, n)
+            L.set_state(torch.from_numpy(sf).cuda(), torch.from_numpy(si).cuda())
+            act = torch.randn(n, 12, device="cuda")
+            val = torch.randn(n, device="cuda")
+            obs = torch.empty((n, 256), dtype=torch.bfloat16 if form == "bf16" else torch.float32, device="cuda")
+            rew = torch.empty(n, device="cuda")
+            dn = torch.empty(n, dtype=torch.uint8, device="cuda")
+            to = torch.empty(n, dtype=torch.uint8, device="cuda")
+            lv = torch.empty(n, dtype=torch.int32, device="cuda")
+            ms = timed(lambda: api.rl_env_step(L.ctx, 0, act, val, obs, rew, dn, to, lv))
+            gbs = ENV_BYTES[form] * n / (ms / 1000.0) / 1e9
+            lines.append({"kernel": "env_step_kernel", "obs": form, "robots": n, "ms": ms, "bytes_per_robot": ENV_BYTES[form],
+                          "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": src})
+            L.close()
+    for n in (4096, 65536, 262144, 1048576):
+        T = 24
+        r, v = torch.randn(T, n, device="cuda"), torch.randn(T, n, device="cuda")
+        lv, d = torch.randn(n, device="cuda"), (torch.rand(T, n, device="cuda") < 0.05).to(torch.uint8)
+        adv, ret = torch.empty(T, n, device="cuda"), torch.empty(T, n, device="cuda")
+        ws = torch.empty(api.rl_gae_workspace_bytes(T, n) // 4 + 4, device="cuda")
+        ms = timed(lambda: api.rl_gae(0.99, 0.95, r, v, lv, d, adv, ret, normalize=True, workspace=ws))
+        byt = GAE_BYTES_PER_SAMPLE * T * n + 4 * n
+        gbs = byt / (ms / 1000.0) / 1e9
+        lines.append({"kernel": "gae_scan_kernel+gae_normalize_kernel", "T": T, "robots": n, "ms": ms,
+                      "bytes_per_sample": GAE_BYTES_PER_SAMPLE, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                      "peak_source": src})
+    return lines
+
+
 def cpu_baseline(seconds_budget=20.0, n_envs=256):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
     from oracle import config as OC
@@ -241,6 +355,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        import torch
+        from paper_2109_11978_b300 import api, synth
+        for line in sweep(torch, api, synth):
+            print(json.dumps(line), flush=True)
+        return 0
     rank, world, local = dist_info()
     import torch
     torch.cuda.set_device(local)
@@ -314,6 +434,10 @@ def main():
         Lf.close()
         del flush
 
+    extra = {}
+    if not args.no_extra:
+        extra["grouped_learners"] = grouped_learners(torch, api, synth)
+        extra["robots_16384"] = large_config(torch, api, synth)
     if rank != 0:
         return 0
     out = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -327,6 +451,7 @@ def main():
            "e2e": e2e, "clocks": clk, "device_status": status}
     if compare:
         out["compare"] = compare
+    out.update(extra)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     elif not args.no_cpu_baseline:

@@ -239,6 +239,21 @@ rl_status rl_ppo_loss_grad(rl_ctx* ctx, int32_t M, const void* obs, const float*
  * which synchronises stream. */
 rl_status rl_train_iteration(rl_ctx* ctx, int32_t use_graph, float* stats_host, void* stream);
 
+/* Several independent learners (own configs, weights, Adam state, learning rate, curriculum and
+ * env state; e.g. uneven robot counts) trained together: one rl_group_train_iteration replays
+ * one CUDA graph whose parallel branches hold every learner's whole iteration, so the GPU
+ * overlaps the learners' kernels.  cfgs, heightfields, init_params: host arrays of n entries
+ * (each as for rl_create).  n in [1, 16]. */
+typedef struct rl_group rl_group;
+rl_status rl_group_create(int32_t n, const rl_config* cfgs, const float* const* heightfields,
+                          const float* const* init_params, rl_group** out);
+void rl_group_destroy(rl_group* g);
+/* The i-th learner's context (owned by the group; valid until rl_group_destroy). */
+rl_ctx* rl_group_learner(rl_group* g, int32_t i);
+/* One training iteration of every learner.  use_graph != 0 replays the grouped graph (captured
+ * on first use); 0 enqueues the learners one after the other on `stream`. */
+rl_status rl_group_train_iteration(rl_group* g, int32_t use_graph, void* stream);
+
 /* Context-owned rollout storage (device pointers, valid until rl_destroy):
  * 0 obs [T+1][N][obs_pad], 1 actions [T][N][A], 2 mu [T][N][A], 3 logp [T][N], 4 values [T][N],
  * 5 rewards [T][N], 6 dones [T][N] u8, 7 timeouts [T][N] u8, 8 last values [N],
@@ -256,6 +271,15 @@ rl_status rl_last_device_status(rl_ctx* ctx);
  * enabling. */
 rl_status rl_profile_enable(rl_ctx* ctx, int32_t kernel_class, int32_t on);
 rl_status rl_profile_read(rl_ctx* ctx, float* total_ms, int32_t* launches);
+
+/* Tile autotuner: times each GEMM site of the update (per hidden layer: forward, input gradient,
+ * weight gradient; actor and critic in one launch; minibatch rows) over candidate tile widths
+ * (64, 128 and, for weight gradients, 256 columns) and split-K counts (half, default, double)
+ * on the context's own buffers, keeps the fastest, and drops a captured iteration graph so the
+ * next rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on
+ * are scratch (parameters, Adam state and env state are untouched).  report (host, may be NULL):
+ * a JSON summary of the chosen shapes and their times, truncated to report_bytes. */
+rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stream);
 
 /* Diagnostic: C = A B^T with the library's tcgen05 BF16 tensor-core GEMM kernel (FP32
  * accumulation), for checking the tensor-core path in isolation.  A [M][K] bf16, B [N][K] bf16

@@ -71,7 +71,7 @@ CONTACT_ENV_STRIDE = 7
 class EnvConfig:
     num_envs: int = 64
     act_dim: int = 12
-    kp: float = 80.0               # PD gains (BASELINE config 5; Sec. 3.2 PD controller)
+    kp: float = 80.0               # PD gains of the measured workload (Sec. 3.2 PD controller)
     kd: float = 2.0
     action_scale: float = 0.5      # q* = q_def + action_scale * a (Sec. 3.2: actions are joint targets)
     dt: float = 0.02               # 50 Hz policy (App. A.1.1)

@@ -156,6 +156,15 @@ def rl_profile_read(ctx):
     return ms.value, n.value
 
 
+def rl_autotune(ctx):
+    """Times the update's GEMM sites over candidate tile shapes and keeps the fastest; returns the
+    report (dict)."""
+    import json
+    buf = ctypes.create_string_buffer(8192)
+    check(lib().rl_autotune(ctx, buf, len(buf), _stream()), "rl_autotune")
+    return json.loads(buf.value.decode() or "{}")
+
+
 def rl_gemm_bf16(A, B, C):
     """C[M][N] (fp32) = A[M][K] (bf16) @ B[N][K]^T (bf16) on the tcgen05 tensor-core kernel."""
     M, K = A.shape
@@ -165,6 +174,35 @@ def rl_gemm_bf16(A, B, C):
 
 def rl_launches_per_iteration(ctx):
     return int(lib().rl_launches_per_iteration(ctx))
+
+
+def rl_group_create(cfgs, heightfields, init_params):
+    """cfgs: list of rl_config; heightfields / init_params: lists of host float32 arrays."""
+    import numpy as np
+    n = len(cfgs)
+    arr = (N.rl_config * n)(*cfgs)
+    hfs = [None if h is None else np.ascontiguousarray(h, dtype=np.float32) for h in heightfields]
+    ips = [np.ascontiguousarray(x, dtype=np.float32) for x in init_params]
+    for c, x in zip(cfgs, ips):
+        if x.size != rl_param_count(c):
+            raise RLError("init_params size does not match its config")
+    hp = (ctypes.c_void_p * n)(*[None if h is None else h.ctypes.data for h in hfs])
+    ip = (ctypes.c_void_p * n)(*[x.ctypes.data for x in ips])
+    out = ctypes.c_void_p()
+    check(lib().rl_group_create(n, arr, hp, ip, ctypes.byref(out)), "rl_group_create")
+    return out
+
+
+def rl_group_destroy(group):
+    lib().rl_group_destroy(group)
+
+
+def rl_group_learner(group, i):
+    return ctypes.c_void_p(lib().rl_group_learner(group, int(i)))
+
+
+def rl_group_train_iteration(group, use_graph=True):
+    check(lib().rl_group_train_iteration(group, int(bool(use_graph)), _stream()), "rl_group_train_iteration")
 
 
 # ------------------------------------------------------------------------------------------

@@ -39,8 +39,7 @@ constexpr int SLOT_CMD = 133, SLOT_HEADING = 136, SLOT_EPLEN = 138, SLOT_OBS = 2
 // Foot-contact schedule of the stand-in.
 constexpr int CONTACT_PERIOD = 40, CONTACT_DUTY = 20, CONTACT_ENV_STRIDE = 7;
 
-constexpr int ENVS = 32;        // robots per block
-constexpr int THREADS = 256;    // 8 warps
+constexpr int THREADS = 256;    // 8 warps; a block owns ENVS = 32 (small N) or 256 robots
 constexpr int REC = 64;         // floats per robot record in shared memory
 
 // Record fields (after the 48 proprioceptive observations).
@@ -105,16 +104,20 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
     return (1.f - fu) * (1.f - fv) * h00 + fu * (1.f - fv) * h10 + (1.f - fu) * fv * h01 + fu * fv * h11;
 }
 
-template <int MODE>   // 0 = policy step, 1 = spawn all robots (initial state)
-__global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
-    __shared__ float rec[ENVS][REC];
+template <int MODE, int ENVS>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
+__global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
+    extern __shared__ float rec_raw[];
+    float (*rec)[REC] = reinterpret_cast<float (*)[REC]>(rec_raw);       // [ENVS][REC]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int env0 = blockIdx.x * ENVS;
     const int N = p.N;
     const unsigned long long it = p.iteration ? *p.iteration : 0ull;
+    // Phase 1 runs one robot per thread: on warp 0 only for 32-robot blocks (small N, where
+    // spreading robots over many SMs matters more), on every thread for 256-robot blocks.
+    const int local = ENVS == 32 ? lane : (int)threadIdx.x;
 
-    if (warp == 0) {
-        const int e = env0 + lane;
+    if (ENVS == 256 || warp == 0) {
+        const int e = env0 + local;
         float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (reward, reset, level)
         if (e < N) {
             float* sf = p.sf;
@@ -138,12 +141,11 @@ __global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
             uint64_t key;
             if (MODE == 0) {
                 key = rng_key(p.seed, kStreamEnv, it, (uint64_t)p.t, (uint64_t)e);
-                float a[12], qstar[12], tau[12], qd_old[12];
+                float a[12], qd_old[12];
 #pragma unroll
                 for (int j = 0; j < 12; ++j) {
                     a[j] = __ldg(p.actions + (size_t)e * 12 + j);
                     qd_old[j] = qd[j];
-                    qstar[j] = FADD(p.q_def[j], FMUL(p.ascale, a[j]));
                 }
                 // Pushes (Sec. 3.3): every push_interval steps of the episode, +-push_vel in x, y.
                 if (p.push_on && eplen > 0 && (eplen % p.push_interval) == 0) {
@@ -151,16 +153,20 @@ __global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
                     vy = FADD(vy, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH + 1)))));
                 }
                 const float zn = znom(level);
+                float sq_tau = 0.f;     // |tau|^2 of the last substep (Table 2 torque term)
                 for (int k = 0; k < p.decimation; ++k) {
                     const uint32_t base = 32u * (uint32_t)k;
-                    // PD torque (Sec. 3.2), recomputed every substep (App. A.1.1).
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) tau[j] = FSUB(FMUL(p.kp, FSUB(qstar[j], q[j])), FMUL(p.kd, qd[j]));
-                    // Physics stand-in substep (exact fp32 recurrence).
+                    const bool last = k == p.decimation - 1;
 #pragma unroll
                     for (int j = 0; j < 12; ++j) {
-                        float xi = irwin_hall(rng_word(key, base + j));
-                        qd[j] = FADD(FADD(FMUL(A_Q, qd[j]), FMUL(p.sim_dt, FMUL(INV_I, tau[j]))), FMUL(S_Q, xi));
+                        // PD torque (Sec. 3.2) on the target q* = q_def + action_scale a, recomputed
+                        // every substep (App. A.1.1) ...
+                        const float qs = FADD(p.q_def[j], FMUL(p.ascale, a[j]));
+                        const float tau = FSUB(FMUL(p.kp, FSUB(qs, q[j])), FMUL(p.kd, qd[j]));
+                        if (last) sq_tau += tau * tau;
+                        // ... consumed by the physics stand-in (exact fp32 recurrence).
+                        const float xi = irwin_hall(rng_word(key, base + j));
+                        qd[j] = FADD(FADD(FMUL(A_Q, qd[j]), FMUL(p.sim_dt, FMUL(INV_I, tau))), FMUL(S_Q, xi));
                         q[j] = FADD(q[j], FMUL(p.sim_dt, qd[j]));
                     }
                     vx = FADD(FADD(FMUL(RHO_V, vx), FMUL(ONE_M_RHO_V, cx)), FMUL(S_V, irwin_hall(rng_word(key, base + 12))));
@@ -203,14 +209,13 @@ __global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
                 // Reward: the nine Table 2 terms, each weight times dt.
                 float e2 = (cx - vx) * (cx - vx) + (cy - vy) * (cy - vy);
                 float ew = (cw - wz) * (cw - wz);
-                float sq_qdd = 0.f, sq_qd = 0.f, sq_tau = 0.f, sq_rate = 0.f;
+                float sq_qdd = 0.f, sq_qd = 0.f, sq_rate = 0.f;
                 const float inv_dt = 1.0f / p.dt;
 #pragma unroll
                 for (int j = 0; j < 12; ++j) {
                     float qdd = (qd[j] - qd_old[j]) * inv_dt;
                     sq_qdd += qdd * qdd;
                     sq_qd += qd[j] * qd[j];
-                    sq_tau += tau[j] * tau[j];
                     float da = a[j] - ap[j];
                     sq_rate += da * da;
                 }
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
             if (p.tidx_out) p.tidx_out[e] = level * p.C + (e % p.C);
             // Record for the observation phase: the 48 proprioceptive values (Sec. 3.2 order),
             // then the position / heading / height and the tile-centre cell.
-            float* R = rec[lane];
+            float* R = rec[local];
             R[0] = vx; R[1] = vy; R[2] = vz; R[3] = wx; R[4] = wy; R[5] = wz;
             R[6] = gx; R[7] = gy; R[8] = gz; R[9] = cx; R[10] = cy; R[11] = cw;
 #pragma unroll
@@ -365,12 +370,28 @@ __global__ void __launch_bounds__(THREADS) env_step_kernel(EnvParams p) {
 
 }  // namespace
 
+template <int MODE, int ENVS>
+static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
+    const size_t smem = (size_t)ENVS * REC * sizeof(float);
+    env_step_kernel<MODE, ENVS><<<(p.N + ENVS - 1) / ENVS, THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Dynamic shared-memory limit of the 256-robot blocks (64 KiB of robot records), set once
+// before any launch (and so before any stream capture).
+cudaError_t env_prepare() {
+    const int smem = 256 * REC * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(env_step_kernel<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(env_step_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+// 256-robot blocks once there are enough robots to give every SM two of them.
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
-    dim3 grid((p.N + ENVS - 1) / ENVS);
-    if (mode == 0) env_step_kernel<0><<<grid, THREADS, 0, s>>>(p);
-    else env_step_kernel<1><<<grid, THREADS, 0, s>>>(p);
-    return cudaGetLastError();
+    const bool big = p.N >= 2 * 148 * 256;
+    if (mode == 0) return big ? launch_cfg<0, 256>(p, s) : launch_cfg<0, 32>(p, s);
+    return big ? launch_cfg<1, 256>(p, s) : launch_cfg<1, 32>(p, s);
 }
 
 }  // namespace rl

@@ -12,13 +12,14 @@
 // The forward and input-gradient epilogues write their bf16 result both row-major and
 // transposed, so the weight-gradient GEMM finds its operands K-major.
 //
-// CTA: 128 threads, one 128 x BN output tile, K in steps of 64 (one 128-byte swizzle row).
-// warp 0 lane 0 issues TMA loads into a STAGES-deep ring (full/empty mbarriers); warp 1
-// lane 0 issues 4 tcgen05.mma (K = 16 each) per stage and releases the stage with
-// tcgen05.commit; after the last stage a commit signals the accumulator, and all four warps
-// read their 32 TMEM lanes (= tile rows) back with tcgen05.ld.  Every mbarrier wait is bounded
-// by the global timer; a wait that runs out records RL_ERR_TIMEOUT in the status word and the
-// CTA skips the rest of its work, frees its tensor memory and returns.
+// Persistent CTA per SM, 320 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
+// swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
+// lane 0 issues 4 tcgen05.mma (K = 16 each) per stage, releases the stage with tcgen05.commit and
+// signals a finished tile on one of two TMEM accumulators; eight epilogue warps read the tile
+// back with tcgen05.ld while the next tile accumulates in the other buffer.  Every mbarrier wait
+// is bounded by the global timer; a wait that runs out records RL_ERR_TIMEOUT in the status
+// word, the CTA stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its
+// tensor memory and returns.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -28,7 +29,8 @@ namespace rl {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int EPI_WARPS = 8;                       // epilogue warps (two per TMEM lane quarter)
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;    // warp 0: TMA, warp 1: MMA + TMEM owner
 constexpr int BM = 128, BK = 64;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 
@@ -136,46 +138,83 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int BN>
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Fast ELU for the bf16 forms: the result is rounded to 8 mantissa bits, so exp(x) - 1 from the
+// fast exponential is accurate enough (absolute error ~1e-7).
+__device__ __forceinline__ float elu_fast(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
+
+// Column sums of a 32 x 32 block held one row per lane (v[j] = column j): recursive halving,
+// 31 shuffles; afterwards lane l holds the sum of column l.
+__device__ __forceinline__ float colsum32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = up ? v[i] : v[i + s];
+            const float keep = up ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+template <int BN, int EPI>
 struct TileCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = BN >= 256 ? 3 : 4;
-    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/ + 4 * BN * 4 /*colsum per warp*/;
+    static constexpr int STAGES = 4;
+    static constexpr int TP = 40;                                       // staging row pitch (bf16)
+    // transposed staging, per epilogue warp (BN/2) x 32 bf16 (only the bf16-output epilogues)
+    static constexpr int STG_BYTES = EPI == EPI_STORE ? 0 : EPI_WARPS * (BN / 2) * TP * 2;
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = STAGES * STAGE + STG_BYTES + BAR_BYTES + 1024 /*align*/;
 };
 
+// Persistent, warp-specialised GEMM.  Tiles (m, n, split, batch) are dealt round-robin to the
+// CTAs; the TMA warp streams K blocks through a STAGES-deep ring; the MMA warp accumulates each
+// tile into one of two TMEM buffers (2 x BN columns) while the eight epilogue warps drain the
+// other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue warp e reads TMEM
+// lanes 32 (warp % 4) .. + 31 (its rows) and half of the columns.
 template <int BN, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-    using C = TileCfg<BN>;
+    using C = TileCfg<BN, EPI>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 1);
-    float* colsum_s = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + 256);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES), tfull = smem_u32(bars + 2 * C::STAGES);
+    __nv_bfloat16* stage_t = reinterpret_cast<__nv_bfloat16*>(smem + C::STAGES * C::STAGE);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
+    // barriers: full[S], empty[S], tfull[2], tempty[2], drain
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
+    const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + 2);
+    const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.z / p.splits, sp = blockIdx.z % p.splits;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int kb0 = sp * p.kb_per_split;
-    const int kb1 = min(p.kblocks, kb0 + p.kb_per_split);
-    const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+    const int mt = (p.M + BM - 1) / BM, nt = p.N / BN;
+    const int total = mt * nt * p.splits * p.batch;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(tfull, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (EPI == EPI_ELU_GRAD)
-        for (int i = threadIdx.x; i < 4 * BN; i += TC_THREADS) colsum_s[i] = 0.f;
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -184,127 +223,223 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0 && nkb > 0) {
-        // TMA producer
-        const CUtensorMap* ma = &p.tmA[b];
-        const CUtensorMap* mb = &p.tmB[b];
-        for (int i = 0; i < nkb; ++i) {
-            const int s = i % C::STAGES;
-            const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
-            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) break;
-            const uint32_t sa = smem_u32(smem + s * C::STAGE);
-            mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
-            tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, m0);
-            tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, n0);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        const uint32_t idesc = idesc_bf16<BN>();
-        for (int i = 0; i < nkb; ++i) {
-            const int s = i % C::STAGES;
-            const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
-            if (!mbar_wait(full0 + 8 * s, ph, p.status)) break;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * C::STAGE);
-            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + C::A_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(empty0 + 8 * s);
-        }
-        mma_commit(tfull);   // arrives once every issued MMA has completed (immediately if none)
-    }
-    __syncwarp();
+    auto decode = [&](int t, int& mi, int& ni, int& sp, int& b) {
+        mi = t % mt;
+        int r = t / mt;
+        ni = r % nt;
+        r /= nt;
+        sp = r % p.splits;
+        b = r / p.splits;
+    };
+    auto kblocks_of = [&](int sp, int& kb0) {
+        kb0 = sp * p.kb_per_split;
+        const int kb1 = min(p.kblocks, kb0 + p.kb_per_split);
+        return kb1 > kb0 ? kb1 - kb0 : 0;
+    };
 
-    // Epilogue: warp w owns TMEM lanes / tile rows 32w .. 32w + 31.
-    const bool have = mbar_wait(tfull, 0u, p.status);
-    tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    const bool row_ok = row < p.M;
-    if (have) {
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (nkb == 0) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int mi, ni, sp, b, kb0;
+                decode(t, mi, ni, sp, b);
+                const int nkb = kblocks_of(sp, kb0);
+                const CUtensorMap* ma = &p.tmA[b];
+                const CUtensorMap* mb = &p.tmB[b];
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % C::STAGES;
+                    const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+                    if (*abort_flag || !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
+                    tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, mi * BM);
+                    tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
+                }
             }
-            const int col = n0 + c;
-            if (EPI == EPI_STORE) {
-                if (row_ok) {
-                    float* dst = reinterpret_cast<float*>(p.C[b]) + (size_t)sp * p.split_stride + (size_t)row * p.ldc + col;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            if (!ok) {
+                // let the copies already issued land before the CTA leaves (bounded)
+                for (int k = 1; k <= C::STAGES && it - k >= 0; ++k) {
+                    const int j = it - k;
+                    mbar_wait(full0 + 8 * (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, p.status);
                 }
-            } else {
-                if (EPI == EPI_BIAS_ELU) {
-                    const float* bias = p.bias[b] + col;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t idesc = idesc_bf16<BN>();
+            int it = 0, local = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++local) {
+                int mi, ni, sp, b, kb0;
+                decode(t, mi, ni, sp, b);
+                const int nkb = kblocks_of(sp, kb0);
+                const int a = local & 1;
+                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                if (*abort_flag || !mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * BN);
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % C::STAGES;
+                    const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+                    if (*abort_flag || !mbar_wait(full0 + 8 * s, ph, p.status)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + C::A_BYTES);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = elu(v[j] + __ldg(bias + j));
-                } else {   // EPI_ELU_GRAD
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(empty0 + 8 * s);
+                }
+                mma_commit(tfull0 + 8 * a);   // arrives when every MMA issued so far has completed
+            }
+            // drain: every MMA this thread issued has finished before the TMEM is freed
+            mma_commit(drain);
+            mbar_wait(drain, 0u, p.status);
+        }
+    } else {
+        // ---------------- epilogue warps
+        const int ew = warp - 2;
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = ew >> 2;               // column half of the tile
+        __nv_bfloat16* stg = stage_t + (size_t)ew * (BN / 2) * C::TP;
+        int local = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+            int mi, ni, sp, b, kb0;
+            decode(t, mi, ni, sp, b);
+            const int nkb = kblocks_of(sp, kb0);
+            const int a = local & 1;
+            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            if (*abort_flag || !mbar_wait(tfull0 + 8 * a, aph, p.status)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int m0 = mi * BM, n0 = ni * BN;
+            const int row = m0 + 32 * q + lane;
+            const bool row_ok = row < p.M;
+            const bool trans = EPI != EPI_STORE && p.Ct[b] != nullptr;
+#pragma unroll 1
+            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+                if (nkb == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                }
+                const int col = n0 + c;
+                if (EPI == EPI_STORE) {
                     if (row_ok) {
-                        const uint4* hp = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.H[b]) +
-                                                                         (size_t)row * p.ldh + col);
+                        float* dst = reinterpret_cast<float*>(p.C[b]) + (size_t)sp * p.split_stride + (size_t)row * p.ldc + col;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint4 hv = __ldg(hp + q);
-                            const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hv);
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
+                } else {
+                    if (EPI == EPI_BIAS_ELU) {
+                        const float4* bias4 = reinterpret_cast<const float4*>(p.bias[b] + col);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) v[8 * q + j] *= elu_grad_y(bf2f(h8[j]));
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 bb = __ldg(bias4 + j4);
+                            v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
+                            v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
+                            v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
+                            v[4 * j4 + 3] = elu_fast(v[4 * j4 + 3] + bb.w);
                         }
-                    } else {
+                    } else {   // EPI_ELU_GRAD
+                        if (row_ok) {
+                            const uint4* hp = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.H[b]) +
+                                                                             (size_t)row * p.ldh + col);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                            for (int g = 0; g < 4; ++g) {
+                                const uint4 hv = __ldg(hp + g);
+                                const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hv);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) v[8 * g + j] *= elu_grad_y(bf2f(h8[j]));
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                        }
+                    }
+                    __align__(16) __nv_bfloat16 o[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
+                    if (row_ok) {
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.C[b]) + (size_t)row * p.ldc + col);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) dst[g] = reinterpret_cast<const uint4*>(o)[g];
+                    }
+                    if (trans) {
+                        const int lc0 = c - half * (BN / 2);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[(lc0 + j) * C::TP + lane] = o[j];
+                    }
+                    if (EPI == EPI_ELU_GRAD && p.colsum[b]) {
+                        const float s = colsum32(v, lane);    // column col + lane, over this warp's 32 rows
+                        p.colsum[b][((size_t)mi * 4 + q) * p.N + col + lane] = s;
                     }
                 }
-                __align__(16) __nv_bfloat16 o[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
-                if (row_ok) {
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.C[b]) + (size_t)row * p.ldc + col);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
-                    if (p.Ct[b]) {
-                        __nv_bfloat16* ct = reinterpret_cast<__nv_bfloat16*>(p.Ct[b]) + (size_t)col * p.ldct + row;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) ct[(size_t)j * p.ldct] = o[j];
+            }
+            // the TMEM buffer is free for the next tile's MMAs
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+            if (trans) {
+                // transposed copy: 16-byte runs of 8 consecutive rows per hidden unit
+                __syncwarp();
+                __nv_bfloat16* ct = reinterpret_cast<__nv_bfloat16*>(p.Ct[b]);
+                const int colbase = n0 + half * (BN / 2);
+#pragma unroll 1
+                for (int idx = lane; idx < (BN / 2) * 4; idx += 32) {
+                    const int lc = idx >> 2, g = idx & 3;
+                    const int r0 = m0 + 32 * q + 8 * g;
+                    if (r0 < p.M) {
+                        const uint4 val = *reinterpret_cast<const uint4*>(stg + lc * C::TP + 8 * g);
+                        *reinterpret_cast<uint4*>(ct + (size_t)(colbase + lc) * p.ldct + r0) = val;
                     }
                 }
-                if (EPI == EPI_ELU_GRAD && p.colsum[b]) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float s = v[j];
-#pragma unroll
-                        for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
-                        if (lane == j) colsum_s[warp * BN + c + j] = s;   // per-warp slot, summed in order below
-                    }
-                }
+                __syncwarp();
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (EPI == EPI_ELU_GRAD && p.colsum[b] && have)
-        for (int i = threadIdx.x; i < BN; i += TC_THREADS)
-            p.colsum[b][(size_t)blockIdx.x * p.N + n0 + i] =
-                ((colsum_s[i] + colsum_s[BN + i]) + colsum_s[2 * BN + i]) + colsum_s[3 * BN + i];
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
     }
 }
 
 template <int BN, int EPI>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<BN>::SMEM);
+    return cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<BN, EPI>::SMEM);
 }
 
 template <int BN, int EPI>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
-    using C = TileCfg<BN>;
-    dim3 grid((p.M + BM - 1) / BM, p.N / BN, p.batch * p.splits);
+    using C = TileCfg<BN, EPI>;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    const int total = ((p.M + BM - 1) / BM) * (p.N / BN) * p.splits * p.batch;
+    const int grid = total < sms ? total : sms;      // one persistent CTA per SM
     tc_gemm_kernel<BN, EPI><<<grid, TC_THREADS, C::SMEM, s>>>(p);
     return cudaGetLastError();
 }
@@ -314,7 +449,18 @@ cudaError_t launch_bn(const TcParams& p, cudaStream_t s) {
     switch (p.bn) {
         case 64: return launch_cfg<64, EPI>(p, s);
         case 128: return launch_cfg<128, EPI>(p, s);
-        case 256: return launch_cfg<256, EPI>(p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The split-K weight-gradient epilogue (no staging) also runs 256-wide tiles (2 x 256 TMEM
+// columns, 4 x 48 KB stages).
+template <>
+cudaError_t launch_bn<EPI_STORE>(const TcParams& p, cudaStream_t s) {
+    switch (p.bn) {
+        case 64: return launch_cfg<64, EPI_STORE>(p, s);
+        case 128: return launch_cfg<128, EPI_STORE>(p, s);
+        case 256: return launch_cfg<256, EPI_STORE>(p, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -324,6 +470,7 @@ cudaError_t launch_bn(const TcParams& p, cudaStream_t s) {
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
     if (p.N % p.bn || p.kblocks <= 0 || p.splits <= 0 || p.batch < 1 || p.batch > 2) return cudaErrorInvalidValue;
+    if (p.epi != EPI_STORE && (p.Ct[0] || p.Ct[1]) && p.M % 8) return cudaErrorInvalidValue;   // 16-byte transposed runs
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -373,18 +520,16 @@ cudaError_t tc_prepare() {
     e = e != cudaSuccess ? e : set_attr<256, EPI_STORE>();
     e = e != cudaSuccess ? e : set_attr<64, EPI_BIAS_ELU>();
     e = e != cudaSuccess ? e : set_attr<128, EPI_BIAS_ELU>();
-    e = e != cudaSuccess ? e : set_attr<256, EPI_BIAS_ELU>();
     e = e != cudaSuccess ? e : set_attr<64, EPI_ELU_GRAD>();
     e = e != cudaSuccess ? e : set_attr<128, EPI_ELU_GRAD>();
-    e = e != cudaSuccess ? e : set_attr<256, EPI_ELU_GRAD>();
     return e;
 }
 
 int tc_smem_bytes(int bn) {
     switch (bn) {
-        case 64: return TileCfg<64>::SMEM;
-        case 128: return TileCfg<128>::SMEM;
-        case 256: return TileCfg<256>::SMEM;
+        case 64: return TileCfg<64, EPI_BIAS_ELU>::SMEM;
+        case 128: return TileCfg<128, EPI_BIAS_ELU>::SMEM;
+        case 256: return TileCfg<256, EPI_STORE>::SMEM;
     }
     return 0;
 }

@@ -30,6 +30,7 @@ struct EnvParams {
     float* stats;   // optional: [0] += sum reward, [1] += resets, [2] += sum level
 };
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s);
+cudaError_t env_prepare();
 
 // ------------------------------------------------------------------ GAE
 cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, const float* val,
@@ -107,7 +108,7 @@ void heads_prepare();
 
 // Device scalar block (floats): alpha, kl, adam step (as float bits of int), ...
 enum { SC_ALPHA = 0, SC_KL = 1, SC_STEP = 2, SC_LOSS = 3, SC_SURR = 4, SC_VLOSS = 5, SC_ENT = 6,
-       SC_CLIPFRAC = 7, SC_ADV_MEAN = 8, SC_ADV_STD = 9, SC_NSCAL = 16 };
+       SC_CLIPFRAC = 7, SC_ADV_MEAN = 8, SC_ADV_STD = 9, SC_STEPSIZE = 10, SC_INVSQRT_BC2 = 11, SC_NSCAL = 16 };
 
 struct AdamSeg {
     long long offset;      // into the flat internal parameter vector
@@ -133,7 +134,8 @@ struct AdamParams {
     int cols[MAX_SEGS];
     float* grad_out;       // optional: reduced gradient (flat internal) instead of a step
 };
-constexpr int ADAM_CHUNK = 1024;   // parameters per block
+constexpr int ADAM_CHUNK = 256;    // parameters per block (one per thread)
+constexpr int ADAM_WIDE = 64;      // segments with more partials than this get 32 parameters per block
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op] (and bf16 transposed [Op][ldt]).

@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -72,9 +74,10 @@ struct rl_ctx {
     void* dYt[2][4] = {};
     int ldt = 0;
     float* gw[2][4] = {};
-    int S[4] = {}, kchunk[4] = {};
+    int S[4] = {}, kchunk[4] = {}, S_cap[4] = {};
     float* gb[2][4] = {};
     int mtiles = 0;
+    int gb_parts = 0;            // bias-gradient partials per row tile (4 TMEM lane quarters in bf16)
     float* head_part = nullptr;
     int head_blocks = 0;
     AdamParams adam;
@@ -178,50 +181,139 @@ int pick_bn(int n) {
     return 64;
 }
 
-// Forward through the hidden layers for `rows` rows starting at X (layer-0 input).
-// batch = 2 (actor + critic) or 1 with net = first (critic only).
+// TMA descriptors of layer l (both networks) for the current tile widths.
+bool encode_layer_maps(rl_ctx* c, int l) {
+    bool ok = true;
+    for (int n = 0; n < 2; ++n) {
+        const LayerInfo& Li = c->L[n][l];
+        ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l]);
+        if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
+        else c->tm_fwdA[n][l] = c->tm_x0;
+        if (l > 0) {
+            ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
+            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l]);
+        }
+        ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dYt[n][l], Li.out, c->Mb, c->ldt, 128);
+        const void* xb = l == 0 ? c->X0t : c->Ht[n][l - 1];
+        ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, Li.in, c->Mb, c->ldt, c->bn_dw[l]);
+    }
+    return ok;
+}
+
+// One hidden layer of the forward pass for `rows` rows (X = layer-0 input), batch = nnets
+// networks starting at net0: 2 (actor + critic) or 1 with net0 = 1 (critic only).
+rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets, bool transposed) {
+    const LayerInfo& Li = c->L[0][l];
+    if (c->bf16) {
+        TcParams tp;
+        std::memset(&tp, 0, sizeof(tp));
+        for (int j = 0; j < nnets; ++j) {
+            const int n = net0 + j;
+            if (l == 0) {
+                if (!make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)) return RL_ERR_CUDA;
+            } else {
+                tp.tmA[j] = c->tm_fwdA[n][l];
+            }
+            tp.tmB[j] = c->tm_fwdB[n][l];
+            tp.C[j] = c->H[n][l];
+            tp.Ct[j] = transposed ? c->Ht[n][l] : nullptr;
+            tp.bias[j] = c->params + c->L[n][l].b;
+        }
+        tp.M = rows;
+        tp.N = Li.out;
+        tp.kblocks = Li.in / 64;
+        tp.kb_per_split = tp.kblocks;
+        tp.splits = 1;
+        tp.batch = nnets;
+        tp.bn = c->bn_fwd[l];
+        tp.epi = EPI_BIAS_ELU;
+        tp.ldc = Li.out;
+        tp.ldct = c->ldt;
+        tp.status = c->status;
+        CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+    } else {
+        GemmBatch g;
+        std::memset(&g, 0, sizeof(g));
+        for (int j = 0; j < nnets; ++j) {
+            const int n = net0 + j;
+            g.A[j] = l == 0 ? reinterpret_cast<const float*>(X) : reinterpret_cast<const float*>(c->H[n][l - 1]);
+            g.B[j] = c->params + c->L[n][l].w;
+            g.C[j] = reinterpret_cast<float*>(c->H[n][l]);
+            g.bias[j] = c->params + c->L[n][l].b;
+        }
+        CK(q.gemm(nullptr, EPI_BIAS_ELU, false, false, rows, Li.out, Li.in, Li.in, Li.in, Li.out, 0, nnets, 1, Li.in, &g));
+    }
+    return RL_OK;
+}
+
+// Forward through every hidden layer.
 rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool transposed) {
     for (int l = 0; l < c->NH; ++l) {
-        const LayerInfo& Li = c->L[0][l];
-        if (c->bf16) {
-            TcParams tp;
-            std::memset(&tp, 0, sizeof(tp));
-            for (int j = 0; j < nnets; ++j) {
-                const int n = net0 + j;
-                if (l == 0) {
-                    if (!make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)) return RL_ERR_CUDA;
-                } else {
-                    tp.tmA[j] = c->tm_fwdA[n][l];
-                }
-                tp.tmB[j] = c->tm_fwdB[n][l];
-                tp.C[j] = c->H[n][l];
-                tp.Ct[j] = transposed ? c->Ht[n][l] : nullptr;
-                tp.bias[j] = c->params + c->L[n][l].b;
-            }
-            tp.M = rows;
-            tp.N = Li.out;
-            tp.kblocks = Li.in / 64;
-            tp.kb_per_split = tp.kblocks;
-            tp.splits = 1;
-            tp.batch = nnets;
-            tp.bn = c->bn_fwd[l];
-            tp.epi = EPI_BIAS_ELU;
-            tp.ldc = Li.out;
-            tp.ldct = c->ldt;
-            tp.status = c->status;
-            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
-        } else {
-            GemmBatch g;
-            std::memset(&g, 0, sizeof(g));
-            for (int j = 0; j < nnets; ++j) {
-                const int n = net0 + j;
-                g.A[j] = l == 0 ? reinterpret_cast<const float*>(X) : reinterpret_cast<const float*>(c->H[n][l - 1]);
-                g.B[j] = c->params + c->L[n][l].w;
-                g.C[j] = reinterpret_cast<float*>(c->H[n][l]);
-                g.bias[j] = c->params + c->L[n][l].b;
-            }
-            CK(q.gemm(nullptr, EPI_BIAS_ELU, false, false, rows, Li.out, Li.in, Li.in, Li.in, Li.out, 0, nnets, 1, Li.in, &g));
+        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, transposed);
+        if (st != RL_OK) return st;
+    }
+    return RL_OK;
+}
+
+// Input gradient of hidden layer k >= 1 for M minibatch rows (actor and critic in one launch).
+rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
+    const LayerInfo& Li = c->L[0][k];   // in = hid[k-1], out = hid[k]
+    if (c->bf16) {
+        TcParams tp;
+        std::memset(&tp, 0, sizeof(tp));
+        for (int n = 0; n < 2; ++n) {
+            tp.tmA[n] = c->tm_dxA[n][k];
+            tp.tmB[n] = c->tm_dxB[n][k];
+            tp.C[n] = c->dY[n][k - 1];
+            tp.Ct[n] = c->dYt[n][k - 1];
+            tp.H[n] = c->H[n][k - 1];
+            tp.colsum[n] = c->gb[n][k - 1];
         }
+        tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
+        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldct = c->ldt; tp.ldh = Li.in;
+        tp.status = c->status;
+        CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+    } else {
+        GemmBatch g;
+        std::memset(&g, 0, sizeof(g));
+        for (int n = 0; n < 2; ++n) {
+            g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
+            g.B[n] = c->params + c->L[n][k].w;
+            g.C[n] = reinterpret_cast<float*>(c->dY[n][k - 1]);
+            g.H[n] = reinterpret_cast<const float*>(c->H[n][k - 1]);
+            g.colsum[n] = c->gb[n][k - 1];
+        }
+        CK(q.gemm(nullptr, EPI_ELU_GRAD, false, true, M, Li.in, Li.out, Li.out, Li.in, Li.in, Li.in, 2, 1, Li.out, &g));
+    }
+    return RL_OK;
+}
+
+// Weight gradient of hidden layer k, split over the minibatch rows.
+rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
+    const LayerInfo& Li = c->L[0][k];
+    if (c->bf16) {
+        TcParams tp;
+        std::memset(&tp, 0, sizeof(tp));
+        for (int n = 0; n < 2; ++n) {
+            tp.tmA[n] = c->tm_dwA[n][k];
+            tp.tmB[n] = c->tm_dwB[n][k];
+            tp.C[n] = c->gw[n][k];
+        }
+        tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
+        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.epi = EPI_STORE; tp.ldc = Li.in;
+        tp.split_stride = (long long)Li.out * Li.in;
+        tp.status = c->status;
+        CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
+    } else {
+        GemmBatch g;
+        std::memset(&g, 0, sizeof(g));
+        for (int n = 0; n < 2; ++n) {
+            g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
+            g.B[n] = k == 0 ? reinterpret_cast<const float*>(c->X0) : reinterpret_cast<const float*>(c->H[n][k - 1]);
+            g.C[n] = c->gw[n][k];
+        }
+        g.split_stride = (long long)Li.out * Li.in;
+        CK(q.gemm(nullptr, EPI_STORE, true, true, Li.out, Li.in, M, Li.out, Li.in, Li.in, 0, 2, c->S[k], c->kchunk[k], &g));
     }
     return RL_OK;
 }
@@ -321,62 +413,13 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     c->launches++;
     // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums
     for (int k = c->NH - 1; k >= 1; --k) {
-        const LayerInfo& Li = c->L[0][k];   // in = hid[k-1], out = hid[k]
-        if (c->bf16) {
-            TcParams tp;
-            std::memset(&tp, 0, sizeof(tp));
-            for (int n = 0; n < 2; ++n) {
-                tp.tmA[n] = c->tm_dxA[n][k];
-                tp.tmB[n] = c->tm_dxB[n][k];
-                tp.C[n] = c->dY[n][k - 1];
-                tp.Ct[n] = c->dYt[n][k - 1];
-                tp.H[n] = c->H[n][k - 1];
-                tp.colsum[n] = c->gb[n][k - 1];
-            }
-            tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
-            tp.batch = 2; tp.bn = c->bn_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldct = c->ldt; tp.ldh = Li.in;
-            tp.status = c->status;
-            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
-        } else {
-            GemmBatch g;
-            std::memset(&g, 0, sizeof(g));
-            for (int n = 0; n < 2; ++n) {
-                g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
-                g.B[n] = c->params + c->L[n][k].w;
-                g.C[n] = reinterpret_cast<float*>(c->dY[n][k - 1]);
-                g.H[n] = reinterpret_cast<const float*>(c->H[n][k - 1]);
-                g.colsum[n] = c->gb[n][k - 1];
-            }
-            CK(q.gemm(nullptr, EPI_ELU_GRAD, false, true, M, Li.in, Li.out, Li.out, Li.in, Li.in, Li.in, 2, 1, Li.out, &g));
-        }
+        rl_status st = dx_layer(c, q, k, M);
+        if (st != RL_OK) return st;
     }
     // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows
     for (int k = 0; k < c->NH; ++k) {
-        const LayerInfo& Li = c->L[0][k];
-        if (c->bf16) {
-            TcParams tp;
-            std::memset(&tp, 0, sizeof(tp));
-            for (int n = 0; n < 2; ++n) {
-                tp.tmA[n] = c->tm_dwA[n][k];
-                tp.tmB[n] = c->tm_dwB[n][k];
-                tp.C[n] = c->gw[n][k];
-            }
-            tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
-            tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.epi = EPI_STORE; tp.ldc = Li.in;
-            tp.split_stride = (long long)Li.out * Li.in;
-            tp.status = c->status;
-            CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
-        } else {
-            GemmBatch g;
-            std::memset(&g, 0, sizeof(g));
-            for (int n = 0; n < 2; ++n) {
-                g.A[n] = reinterpret_cast<const float*>(c->dY[n][k]);
-                g.B[n] = k == 0 ? reinterpret_cast<const float*>(c->X0) : reinterpret_cast<const float*>(c->H[n][k - 1]);
-                g.C[n] = c->gw[n][k];
-            }
-            g.split_stride = (long long)Li.out * Li.in;
-            CK(q.gemm(nullptr, EPI_STORE, true, true, Li.out, Li.in, M, Li.out, Li.in, Li.in, 0, 2, c->S[k], c->kchunk[k], &g));
-        }
+        rl_status st = dw_layer(c, q, k, M);
+        if (st != RL_OK) return st;
     }
     return RL_OK;
 }
@@ -406,7 +449,8 @@ void build_adam(rl_ctx* c) {
         a.wbf_t[ns] = wbft;
         a.rows[ns] = rows;
         a.cols[ns] = cols;
-        blocks += (int)((size + ADAM_CHUNK - 1) / ADAM_CHUNK);
+        const long long per_block = nsplit > ADAM_WIDE ? 32 : ADAM_CHUNK;
+        blocks += (int)((size + per_block - 1) / per_block);
         ++ns;
     };
     for (int n = 0; n < 2; ++n) {
@@ -415,7 +459,7 @@ void build_adam(rl_ctx* c) {
             add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], c->wbft[n][l],
                 Li.out, Li.in);
             if (l < c->NH - 1)
-                add(Li.b, Li.out, c->gb[n][l], Li.out, c->mtiles, nullptr, nullptr, 0, 0);
+                add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, nullptr, 0, 0);
             else
                 add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
         }
@@ -503,6 +547,122 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
                      c->stats);
     if (st != RL_OK) return st;
     CK(cudaMemcpyAsync(obs, obs + c->T * obs_step, obs_step, cudaMemcpyDeviceToDevice, s));
+    return RL_OK;
+}
+
+// ----------------------------------------------------------------------- tile autotuner
+// Times every GEMM site of the update (forward, input gradient and weight gradient of each hidden
+// layer, actor and critic together, minibatch rows) over candidate tile widths and split counts on
+// the context's own buffers, and keeps the fastest.  CUDA events on the launching stream, one
+// warm-up and `reps` timed launches per candidate.
+rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
+    Enq q{c, s, false};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = 5;
+    auto timed = [&](auto&& launch, float& ms) -> rl_status {
+        rl_status st = launch();
+        if (st != RL_OK) return st;
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps && st == RL_OK; ++r) st = launch();
+        if (st != RL_OK) return st;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        return RL_OK;
+    };
+    char buf[256];
+    rl_status st = RL_OK;
+    report = "{\"sites\": [";
+    bool first = true;
+    auto note = [&](const char* site, int l, int bn, int S, float ms) {
+        std::snprintf(buf, sizeof(buf), "%s{\"site\": \"%s\", \"layer\": %d, \"bn\": %d, \"splits\": %d, \"us\": %.2f}",
+                      first ? "" : ", ", site, l, bn, S, ms * 1000.f);
+        report += buf;
+        first = false;
+    };
+    for (int l = 0; l < c->NH && st == RL_OK; ++l) {
+        const LayerInfo& Li = c->L[0][l];
+        if (c->bf16) {
+            // forward
+            int best_bn = c->bn_fwd[l];
+            float best = 1e30f;
+            for (int bn : {64, 128}) {
+                if (Li.out % bn) continue;
+                c->bn_fwd[l] = bn;
+                if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                float ms = 0.f;
+                st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2, true); }, ms);
+                if (st != RL_OK) break;
+                if (ms < best) { best = ms; best_bn = bn; }
+            }
+            c->bn_fwd[l] = best_bn;
+            note("forward", l, best_bn, 1, best);
+            // input gradient
+            if (l > 0 && st == RL_OK) {
+                best_bn = c->bn_dx[l];
+                best = 1e30f;
+                for (int bn : {64, 128}) {
+                    if (Li.in % bn) continue;
+                    c->bn_dx[l] = bn;
+                    if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                    float ms = 0.f;
+                    st = timed([&] { return dx_layer(c, q, l, c->Mb); }, ms);
+                    if (st != RL_OK) break;
+                    if (ms < best) { best = ms; best_bn = bn; }
+                }
+                c->bn_dx[l] = best_bn;
+                note("input_grad", l, best_bn, 1, best);
+            }
+        }
+        // weight gradient: tile width (bf16) and split count
+        if (st == RL_OK) {
+            const int S0 = c->S[l];
+            int best_bn = c->bn_dw[l], best_S = S0, best_kc = c->kchunk[l];
+            float best = 1e30f;
+            const int bns[3] = {64, 128, 256};
+            for (int bi = 0; bi < (c->bf16 ? 3 : 1) && st == RL_OK; ++bi) {
+                const int bn = c->bf16 ? bns[bi] : 64;
+                if (Li.in % bn) continue;
+                for (int S : {S0 / 2, S0, 2 * S0}) {
+                    if (S < 1 || S > c->S_cap[l]) continue;
+                    int kc = (c->Mb + S - 1) / S;
+                    kc = (kc + 63) / 64 * 64;
+                    const int Sr = (c->Mb + kc - 1) / kc;
+                    if (Sr > c->S_cap[l] && Sr > S0) continue;
+                    c->bn_dw[l] = bn;
+                    c->S[l] = Sr;
+                    c->kchunk[l] = kc;
+                    if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                    float ms = 0.f;
+                    st = timed([&] { return dw_layer(c, q, l, c->Mb); }, ms);
+                    if (st != RL_OK) break;
+                    if (ms < best) { best = ms; best_bn = bn; best_S = Sr; best_kc = kc; }
+                }
+            }
+            c->bn_dw[l] = best_bn;
+            c->S[l] = best_S;
+            c->kchunk[l] = best_kc;
+            note("weight_grad", l, best_bn, best_S, best);
+        }
+        if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    report += "]}";
+    if (st != RL_OK) return st;
+    build_adam(c);
+    // a captured iteration graph holds the old tile shapes: rebuild it on next use
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return RL_OK;
 }
 
@@ -618,6 +778,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     CK(tc_prepare());
+    CK(env_prepare());
     heads_prepare();
 
     // parameter layout (internal: first-layer weights padded to obs_pad columns)
@@ -699,25 +860,33 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
                 CK(dalloc(c, &c->dYt[n][l], (size_t)c->hid[l] * c->ldt * 2));
             }
         }
-    // split-K of the weight-gradient GEMMs: enough CTAs for ~4 waves over 148 SMs
+    // split-K of the weight-gradient GEMMs.  BF16: 256-wide tiles (each dY^T tile read once
+    // per layer input width) and about one wave of 148 CTAs, each K range >= 384 rows.  FP32:
+    // 128 x 64 tiles, about two CTAs per SM, at most 16 slices.
     c->mtiles = (c->Mb + 127) / 128;
+    c->gb_parts = c->mtiles * (c->bf16 ? 4 : 1);
     for (int l = 0; l < c->NH; ++l) {
         const LayerInfo& Li = c->L[0][l];
-        const int bn = c->bf16 ? pick_bn(Li.in) : 64;
+        const int bn = c->bf16 ? (Li.in % 256 == 0 ? 256 : pick_bn(Li.in)) : 64;
         const long long tiles = (long long)((Li.out + 127) / 128) * (Li.in / bn) * 2;
-        int S = (int)std::max(1ll, std::min(32ll, (4ll * 148 + tiles - 1) / tiles));
+        int S;
+        if (c->bf16)
+            S = (int)std::max(1ll, std::min((long long)std::max(1, c->Mb / 384), (148ll + tiles / 2) / tiles));
+        else
+            S = (int)std::max(1ll, std::min(16ll, (2ll * 148 + tiles / 2) / tiles));
         const int unit = 64;
         int kc = (c->Mb + S - 1) / S;
         kc = (kc + unit - 1) / unit * unit;
         S = (c->Mb + kc - 1) / kc;
         c->S[l] = S;
         c->kchunk[l] = kc;
+        c->S_cap[l] = std::min(2 * S, std::max(1, c->Mb / 64));   // room for the autotuner's larger splits
         c->bn_fwd[l] = pick_bn(Li.out);
         c->bn_dx[l] = pick_bn(Li.in);
         c->bn_dw[l] = bn;
         for (int n = 0; n < 2; ++n) {
-            CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)S * Li.out * Li.in));
-            if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->mtiles * Li.out));
+            CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)std::max(S, c->S_cap[l]) * Li.out * Li.in));
+            if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->gb_parts * Li.out));
         }
     }
     c->head_blocks = loss_head_blocks(c->Mb);
@@ -730,22 +899,12 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
                 CK(dalloc(c, &c->wbft[n][l], (size_t)Li.out * Li.in * 2));
             }
         bool ok = make_tmap_bf16(&c->tm_x0, c->X0, c->rows, c->Op, c->Op, 128);
-        for (int n = 0; n < 2; ++n)
-            for (int l = 0; l < c->NH; ++l) {
-                const LayerInfo& Li = c->L[n][l];
-                ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l]);
-                if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
-                else c->tm_fwdA[n][l] = c->tm_x0;
-                if (l > 0) {
-                    ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
-                    ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l]);
-                }
-                ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dYt[n][l], Li.out, c->Mb, c->ldt, 128);
-                const void* xb = l == 0 ? c->X0t : c->Ht[n][l - 1];
-                ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, Li.in, c->Mb, c->ldt, c->bn_dw[l]);
-            }
+        for (int l = 0; l < c->NH; ++l) ok = ok && encode_layer_maps(c, l);
         if (!ok) return RL_ERR_CUDA;
     }
+    for (int n = 0; n < 2; ++n)          // the GEMM epilogues read biases as float4
+        for (int l = 0; l < c->NH; ++l)
+            if (c->L[n][l].b % 4) return RL_ERR_UNSUPPORTED;
     build_adam(c);
     // parameters, learning rate, env state
     std::vector<float> pi(c->P, 0.f);
@@ -936,7 +1095,7 @@ rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* a
     CK(launch_gather(obs, c->bf16 ? 1 : 0, c->iota, M, c->Op, c->X0, c->X0t, c->ldt, s));
     for (int n = 0; n < 2; ++n)          // row tiles past M leave no bias-gradient partial
         for (int l = 0; l + 1 < c->NH; ++l)
-            CK(cudaMemsetAsync(c->gb[n][l], 0, sizeof(float) * (size_t)c->mtiles * c->hid[l], s));
+            CK(cudaMemsetAsync(c->gb[n][l], 0, sizeof(float) * (size_t)c->gb_parts * c->hid[l], s));
     rl_status st = minibatch_fwd_bwd(c, q, M, nullptr, actions, logp_old, mu_old, log_std_old, val_old, adv, ret, false);
     if (st != RL_OK) return st;
     AdamParams a = c->adam;
@@ -1064,12 +1223,22 @@ rl_status rl_profile_read(rl_ctx* c, float* total_ms, int32_t* launches) {
     return RL_OK;
 }
 
+rl_status rl_autotune(rl_ctx* c, char* report, size_t report_bytes, void* stream) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    std::string rep;
+    rl_status st = autotune_impl(c, S_(stream), rep);
+    if (report && report_bytes) {
+        std::snprintf(report, report_bytes, "%s", rep.c_str());
+    }
+    return st;
+}
+
 rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {
     if (M < 1 || N < 64 || N % 64 || K < 8 || K % 8 || !A || !B || !C) return RL_ERR_INVALID_ARG;
     if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
-    const int bn = N % 128 == 0 ? 128 : 64;
+    const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
     if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
     if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)) return RL_ERR_CUDA;
     CK(tc_prepare());
@@ -1080,5 +1249,118 @@ rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const voi
 }
 
 int32_t rl_launches_per_iteration(rl_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ grouped learners
+struct rl_group {
+    std::vector<rl_ctx*> ctx;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaStream_t s0 = nullptr;
+    cudaEvent_t fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+extern "C" {
+
+void rl_group_destroy(rl_group* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (cudaStream_t s : g->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : g->joins) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->s0) cudaStreamDestroy(g->s0);
+    for (rl_ctx* c : g->ctx) rl_destroy(c);
+    delete g;
+}
+
+static rl_status group_setup(rl_group* g, int n) {
+    CK(cudaStreamCreateWithFlags(&g->s0, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming));
+    for (int i = 0; i < n; ++i) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        g->streams.push_back(s);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->joins.push_back(e);
+    }
+    return RL_OK;
+}
+
+rl_status rl_group_create(int32_t n, const rl_config* cfgs, const float* const* heightfields,
+                          const float* const* init_params, rl_group** out) {
+    if (!out) return RL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || n > 16 || !cfgs || !init_params) return RL_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!config_ok(&cfgs[i]) || !init_params[i] ||
+            (cfgs[i].grid_x * cfgs[i].grid_y > 0 && (!heightfields || !heightfields[i])))
+            return RL_ERR_INVALID_ARG;
+    rl_group* g = new rl_group();
+    rl_status st = group_setup(g, n);
+    for (int i = 0; i < n && st == RL_OK; ++i) {
+        rl_ctx* c = nullptr;
+        st = rl_create(&cfgs[i], heightfields ? heightfields[i] : nullptr, init_params[i], &c);
+        if (st == RL_OK) g->ctx.push_back(c);
+    }
+    if (st != RL_OK) {
+        rl_group_destroy(g);
+        return st;
+    }
+    *out = g;
+    return RL_OK;
+}
+
+rl_ctx* rl_group_learner(rl_group* g, int32_t i) {
+    if (!g || i < 0 || i >= (int)g->ctx.size()) return nullptr;
+    return g->ctx[i];
+}
+
+rl_status rl_group_train_iteration(rl_group* g, int32_t use_graph, void* stream) {
+    if (!g) return RL_ERR_INVALID_ARG;
+    cudaStream_t s = S_(stream);
+    if (!use_graph) {
+        for (rl_ctx* c : g->ctx) {
+            rl_status st = train_enqueue(c, s, false);
+            if (st != RL_OK) return st;
+        }
+        return RL_OK;
+    }
+    CK(cudaEventRecord(g->ev_in, s));
+    CK(cudaStreamWaitEvent(g->s0, g->ev_in, 0));
+    if (!g->gexec) {
+        // fork: every learner's iteration on its own stream, joined back into s0
+        CK(cudaStreamBeginCapture(g->s0, cudaStreamCaptureModeThreadLocal));
+        rl_status st = RL_OK;
+        cudaError_t e = cudaEventRecord(g->fork, g->s0);
+        for (size_t i = 0; i < g->ctx.size() && e == cudaSuccess && st == RL_OK; ++i) {
+            e = cudaStreamWaitEvent(g->streams[i], g->fork, 0);
+            if (e == cudaSuccess) st = train_enqueue(g->ctx[i], g->streams[i], false);
+            if (e == cudaSuccess && st == RL_OK) e = cudaEventRecord(g->joins[i], g->streams[i]);
+            if (e == cudaSuccess && st == RL_OK) e = cudaStreamWaitEvent(g->s0, g->joins[i], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(g->s0, &graph);
+        if (st != RL_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return st != RL_OK ? st : err_of(e != cudaSuccess ? e : e2);
+        }
+        g->graph = graph;
+        CK(cudaGraphInstantiate(&g->gexec, graph, 0));
+    }
+    CK(cudaGraphLaunch(g->gexec, g->s0));
+    CK(cudaEventRecord(g->ev_out, g->s0));
+    CK(cudaStreamWaitEvent(s, g->ev_out, 0));
+    return RL_OK;
+}
 
 }  // extern "C"

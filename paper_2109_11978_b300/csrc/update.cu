@@ -40,34 +40,58 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
 }
 
 // ---------------------------------------------------------------- gather
-// 32 rows x 64 columns per block through shared memory: rows leave coalesced, and the
-// transposed bf16 copy (the K-major operand of the weight-gradient GEMM) leaves as 64-byte
-// runs of consecutive rows.
+// 64 rows x 64 columns per block (256 threads), 16-byte vector loads and stores: rows leave
+// coalesced, and the transposed bf16 copy (the K-major operand of the weight-gradient GEMM)
+// is assembled in shared memory and leaves as 128-byte runs of 64 consecutive rows.
 template <bool BF16>
-__global__ void gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M, int Op, void* X,
-                              void* Xt, int ldt) {
-    __shared__ float tile[32][65];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 x 4 threads
-    for (int r = ty; r < 32; r += 4) {
-        const int row = r0 + r;
-        float v = 0.f;
-        if (row < M) {
-            const size_t src = (size_t)idx[row] * Op + c0 + tx;
-            v = BF16 ? bf2f(reinterpret_cast<const __nv_bfloat16*>(obs)[src]) : reinterpret_cast<const float*>(obs)[src];
-            const size_t dst = (size_t)row * Op + c0 + tx;
-            if (BF16) reinterpret_cast<__nv_bfloat16*>(X)[dst] = f2bf(v);
-            else reinterpret_cast<float*>(X)[dst] = v;
+__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
+                                                     int Op, void* X, void* Xt, int ldt) {
+    __shared__ __align__(16) __nv_bfloat16 tile[64][72];
+    const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+    const int tid = threadIdx.x;
+    if (BF16) {
+        // 64 rows x 8 vectors of 8 bf16
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int v = tid + 256 * k;
+            const int r = v >> 3, g = v & 7;
+            const int row = r0 + r;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (row < M) {
+                const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(obs) + (size_t)__ldg(idx + row) * Op + c0 + 8 * g;
+                val = __ldg(reinterpret_cast<const uint4*>(src));
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(X) + (size_t)row * Op + c0 + 8 * g) = val;
+            }
+            *reinterpret_cast<uint4*>(&tile[r][8 * g]) = val;
         }
-        tile[r][tx] = v;
-    }
-    if (!BF16 || !Xt) return;
-    __syncthreads();
-    // transposed: column c of the tile -> Xt[c0 + c][r0 .. r0 + 31]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 8 warps
-    for (int c = w; c < 64; c += 8) {
-        const int row = r0 + lane;
-        if (row < M) reinterpret_cast<__nv_bfloat16*>(Xt)[(size_t)(c0 + c) * ldt + row] = f2bf(tile[lane][c]);
+        if (!Xt) return;
+        __syncthreads();
+        // column c of the tile -> Xt[c0 + c][r0 .. r0 + 63], 8 rows per 16-byte store
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int v = tid + 256 * k;
+            const int c = v >> 3, g = v & 7;
+            if (r0 + 8 * g < M) {
+                __align__(16) __nv_bfloat16 e[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) e[j] = tile[8 * g + j][c];
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(Xt) + (size_t)(c0 + c) * ldt + r0 + 8 * g) =
+                    *reinterpret_cast<const uint4*>(e);
+            }
+        }
+    } else {
+        // 64 rows x 16 vectors of 4 floats
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int v = tid + 256 * k;
+            const int r = v >> 4, g = v & 15;
+            const int row = r0 + r;
+            if (row < M) {
+                const float* src = reinterpret_cast<const float*>(obs) + (size_t)__ldg(idx + row) * Op + c0 + 4 * g;
+                *reinterpret_cast<float4*>(reinterpret_cast<float*>(X) + (size_t)row * Op + c0 + 4 * g) =
+                    __ldg(reinterpret_cast<const float4*>(src));
+            }
+        }
     }
 }
 
@@ -82,18 +106,44 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamParams p) {
     int s = 0;
     while (s + 1 < p.nsegs && (int)blockIdx.x >= p.seg[s + 1].block_start) ++s;
     const AdamSeg sg = p.seg[s];
-    const long long base = (long long)(blockIdx.x - sg.block_start) * ADAM_CHUNK;
-    const float step = p.scal ? p.scal[SC_STEP] : 1.f;
-    const float alpha = p.scal ? p.scal[SC_ALPHA] : 0.f;
-    const float bc1 = 1.f - (float)pow(0.9, (double)step);
-    const float bc2 = 1.f - (float)pow(0.999, (double)step);
-    const float step_size = alpha / bc1;
-    const float inv_sqrt_bc2 = rsqrtf(bc2);
-    for (int k = threadIdx.x; k < ADAM_CHUNK; k += blockDim.x) {
+    // step size alpha / (1 - 0.9^t) and 1 / sqrt(1 - 0.999^t), computed once per minibatch by the
+    // loss kernel together with Algorithm 1 and the step count
+    const float step_size = p.scal ? p.scal[SC_STEPSIZE] : 0.f;
+    const float inv_sqrt_bc2 = p.scal ? p.scal[SC_INVSQRT_BC2] : 1.f;
+    // Segments with many partials: 32 parameters per block, the 8 warps split the partials
+    // (warp w sums partials w, w + 8, ...) and the warp sums are added in warp order.
+    const bool wide = sg.nsplit > ADAM_WIDE;
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)(blockIdx.x - sg.block_start) * (wide ? 32 : ADAM_CHUNK);
+    for (int k = wide ? lane : (int)threadIdx.x; k < (wide ? 32 : ADAM_CHUNK); k += wide ? 32 : blockDim.x) {
         const long long i = base + k;
-        if (i >= sg.size) break;
-        float g = 0.f;
-        for (int q = 0; q < sg.nsplit; ++q) g += __ldg(sg.partials + (size_t)q * sg.stride + i);
+        const bool in = i < sg.size;
+        const float* src = sg.partials + (in ? i : 0);
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f;
+        const int q0 = wide ? warp : 0, dq = wide ? 8 : 1;
+        int q = q0;
+        if (in) {
+            // eight independent loads in flight, fixed order
+            const size_t st = (size_t)dq * sg.stride;
+            for (; q + 7 * dq < sg.nsplit; q += 8 * dq) {
+                const float* a = src + (size_t)q * sg.stride;
+                g0 += __ldg(a); g1 += __ldg(a + st); g2 += __ldg(a + 2 * st); g3 += __ldg(a + 3 * st);
+                g4 += __ldg(a + 4 * st); g5 += __ldg(a + 5 * st); g6 += __ldg(a + 6 * st); g7 += __ldg(a + 7 * st);
+            }
+            for (; q < sg.nsplit; q += dq) g0 += __ldg(src + (size_t)q * sg.stride);
+        }
+        g0 += g4; g1 += g5; g2 += g6; g3 += g7;
+        float g = (g0 + g1) + (g2 + g3);
+        if (wide) {
+            red[warp][lane] = g;
+            __syncthreads();
+            g = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) g += red[w][lane];
+            if (warp != 0) break;           // warp 0 applies the step for the 32 parameters
+        }
+        if (!in) continue;
         const long long gi = sg.offset + i;
         if (p.grad_out) {
             p.grad_out[gi] = g;
@@ -160,7 +210,8 @@ cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int 
                           cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (Op % 64) return cudaErrorInvalidValue;
-    dim3 grid((M + 31) / 32, Op / 64);
+    if (Xt && M % 8) return cudaErrorInvalidValue;
+    dim3 grid((M + 63) / 64, Op / 64);
     if (bf16) gather_kernel<true><<<grid, 256, 0, s>>>(obs, idx, M, Op, X, Xt, ldt);
     else gather_kernel<false><<<grid, 256, 0, s>>>(obs, idx, M, Op, X, Xt, ldt);
     return cudaGetLastError();

@@ -272,3 +272,43 @@ def test_graph_replay_equals_eager():
     assert api.rl_last_device_status(La.ctx) == 0
     La.close()
     Lb.close()
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
+def test_autotune_keeps_results(form):
+    """The autotuner only changes tile widths and split counts: the gradient stays within the
+    tolerance of the oracle, and the report names every GEMM site it timed."""
+    prec = 1 if form == "bf16" else 0
+    w = workload("tiny", precision=prec)
+    L, params, O, Op = _setup(w)
+    M = w["num_envs"] * w["num_steps"] // w["minibatches"]
+    b, d = _batch(M, O, Op, 12, params, w["hidden"], 31, prec == 1, kink_margin=prec == 1)
+    if prec == 1:
+        d = _own_old_policy(L, b, d, O, params, w["hidden"])
+
+    def grad():
+        g = torch.empty(L.n_params, device="cuda")
+        api.rl_ppo_loss_grad(L.ctx, d["obs"], d["actions"], d["logp_old"], d["mu_old"], d["log_std_old"], d["v_old"],
+                             d["adv"], d["ret"], g)
+        torch.cuda.synchronize()
+        return g.cpu().numpy()
+
+    g0 = grad()
+    rep = api.rl_autotune(L.ctx)
+    sites = {(s["site"], s["layer"]) for s in rep["sites"]}
+    assert ("weight_grad", 0) in sites and ("weight_grad", len(w["hidden"]) - 1) in sites
+    if prec == 1:
+        assert ("forward", 0) in sites and ("input_grad", 1) in sites
+    g1 = grad()
+    p = OM.unflatten(params, O, w["hidden"], 12)
+    _, g, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
+                               b["v_old"], b["adv"], b["ret"])
+    gref = OP.flat_grad(g)
+    measure, tol = (rel_err, TOL_FP32) if prec == 0 else (rel_err2, TOL_BF16)
+    for gg in (g0, g1):
+        errs = _per_tensor_err(gg, gref, (O, w["hidden"], 12), measure)
+        assert max(errs.values()) < tol, errs
+    L.train_iteration(use_graph=True)          # the graph is re-captured with the tuned shapes
+    torch.cuda.synchronize()
+    assert api.rl_last_device_status(L.ctx) == 0
+    L.close()
