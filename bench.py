@@ -374,6 +374,7 @@ def main():
 
     # --- BF16 form: the headline --------------------------------------------------------
     L, O = make_learner(api, synth, api.RL_BF16, seed=1000 * rank)
+    tuned = api.rl_autotune(L.ctx)          # tile widths / split counts of every update GEMM site
     api.rl_profile_enable(L.ctx, 0, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     # untimed: build the graph once and count the launches of one iteration
@@ -448,6 +449,7 @@ def main():
                       "l2": "flushed (256 MB write) between timed iterations", "graph": "one CUDA graph per iteration",
                       "per_step_ms": [round(t, 4) for t in times]},
            "roofline": roof, "gpu_launches": launches * args.steps, "launches_per_step": launches,
+           "autotune": tuned,
            "e2e": e2e, "clocks": clk, "device_status": status}
     if compare:
         out["compare"] = compare

@@ -12,10 +12,10 @@
 // The forward and input-gradient epilogues write their bf16 result both row-major and
 // transposed, so the weight-gradient GEMM finds its operands K-major.
 //
-// Persistent CTA per SM, 320 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
+// Persistent CTA per SM, 576 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
 // swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
 // lane 0 issues 4 tcgen05.mma (K = 16 each) per stage, releases the stage with tcgen05.commit and
-// signals a finished tile on one of two TMEM accumulators; eight epilogue warps read the tile
+// signals a finished tile on one of two TMEM accumulators; sixteen epilogue warps read the tile
 // back with tcgen05.ld while the next tile accumulates in the other buffer.  Every mbarrier wait
 // is bounded by the global timer; a wait that runs out records RL_ERR_TIMEOUT in the status
 // word, the CTA stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its
@@ -29,7 +29,7 @@ namespace rl {
 
 namespace {
 
-constexpr int EPI_WARPS = 8;                       // epilogue warps (two per TMEM lane quarter)
+constexpr int EPI_WARPS = 16;                      // epilogue warps (four per TMEM lane quarter)
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;    // warp 0: TMA, warp 1: MMA + TMEM owner
 constexpr int BM = 128, BK = 64;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
@@ -169,17 +169,20 @@ struct TileCfg {
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = 4;
     static constexpr int TP = 40;                                       // staging row pitch (bf16)
-    // transposed staging, per epilogue warp (BN/2) x 32 bf16 (only the bf16-output epilogues)
-    static constexpr int STG_BYTES = EPI == EPI_STORE ? 0 : EPI_WARPS * (BN / 2) * TP * 2;
+    // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
+    static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
+    static constexpr int SLICE_COLS = BN / SLICES;
+    // transposed staging, per epilogue warp SLICE_COLS x 32 bf16 (only the bf16-output epilogues)
+    static constexpr int STG_BYTES = EPI == EPI_STORE ? 0 : EPI_WARPS * SLICE_COLS * TP * 2;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM = STAGES * STAGE + STG_BYTES + BAR_BYTES + 1024 /*align*/;
 };
 
 // Persistent, warp-specialised GEMM.  Tiles (m, n, split, batch) are dealt round-robin to the
 // CTAs; the TMA warp streams K blocks through a STAGES-deep ring; the MMA warp accumulates each
-// tile into one of two TMEM buffers (2 x BN columns) while the eight epilogue warps drain the
+// tile into one of two TMEM buffers (2 x BN columns) while the sixteen epilogue warps drain the
 // other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue warp e reads TMEM
-// lanes 32 (warp % 4) .. + 31 (its rows) and half of the columns.
+// lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
 template <int BN, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = TileCfg<BN, EPI>;
@@ -314,8 +317,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         // ---------------- epilogue warps
         const int ew = warp - 2;
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = ew >> 2;               // column half of the tile
-        __nv_bfloat16* stg = stage_t + (size_t)ew * (BN / 2) * C::TP;
+        const int slice = ew >> 2;              // column slice of the tile (slice >= SLICES: idle)
+        const bool busy = slice < C::SLICES;
+        __nv_bfloat16* stg = stage_t + (size_t)ew * C::SLICE_COLS * C::TP;
         int local = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
             int mi, ni, sp, b, kb0;
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const bool row_ok = row < p.M;
             const bool trans = EPI != EPI_STORE && p.Ct[b] != nullptr;
 #pragma unroll 1
-            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+            for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
                 if (nkb == 0) {
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         for (int g = 0; g < 4; ++g) dst[g] = reinterpret_cast<const uint4*>(o)[g];
                     }
                     if (trans) {
-                        const int lc0 = c - half * (BN / 2);
+                        const int lc0 = c - slice * C::SLICE_COLS;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) stg[(lc0 + j) * C::TP + lane] = o[j];
                     }
@@ -398,13 +402,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * a);
-            if (trans) {
+            if (trans && busy) {
                 // transposed copy: 16-byte runs of 8 consecutive rows per hidden unit
                 __syncwarp();
                 __nv_bfloat16* ct = reinterpret_cast<__nv_bfloat16*>(p.Ct[b]);
-                const int colbase = n0 + half * (BN / 2);
+                const int colbase = n0 + slice * C::SLICE_COLS;
 #pragma unroll 1
-                for (int idx = lane; idx < (BN / 2) * 4; idx += 32) {
+                for (int idx = lane; idx < C::SLICE_COLS * 4; idx += 32) {
                     const int lc = idx >> 2, g = idx & 3;
                     const int r0 = m0 + 32 * q + 8 * g;
                     if (r0 < p.M) {

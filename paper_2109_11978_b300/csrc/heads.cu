@@ -9,6 +9,8 @@
 // warp in registers, then per block in shared memory, then as one partial per block; the
 // last block to finish (a counter, no spin-wait) reduces the statistics, takes the KL mean and
 // applies Algorithm 1 to the device-side learning rate before Adam runs.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -81,259 +83,313 @@ __global__ void __launch_bounds__(HEAD_WARPS * 32) act_head_kernel(HeadParams p)
     }
 }
 
-// Loss head: 4 warps per block, each warp owns chunks of 16 consecutive minibatch rows, whose
-// per-sample data (old actions, old means, log pi_old, advantage, V_old, return) it gathers into
-// shared memory once per chunk with independent loads.  The
-// gradient rows leave row-major straight from the lanes; in the bf16 form they are also staged
-// in shared memory and written transposed (the K-major operand of the weight-gradient GEMM)
-// as 64-byte runs, one per hidden unit.
-constexpr int LH_WARPS = 4;
-constexpr int LH_ROWS = 16;
-constexpr int LH_SD = 28;           // per-row sample record: a_old[12], mu_old[12], logp_old, adv, v_old, ret
+// Loss head: four threads per minibatch row, LR rows per block.  The rows' last hidden
+// activations (actor and critic) are staged in shared memory with a padded pitch (reads across
+// the rows of a warp are then conflict-free); each of a row's four threads takes a quarter of
+// the hidden units for the head outputs and for the backward into the hidden layer, and the
+// quarter sums are combined in a fixed order by the row's first thread, which computes the
+// per-sample loss terms and their gradients.  The head weight gradients are computed by
+// (hidden unit, row range) threads whose partials are combined in a fixed order, the gradient
+// rows are written back from shared memory with whole warps: row-major, and (bf16 form)
+// transposed for the weight-gradient GEMM as 256-byte runs of 128 consecutive rows.  Every
+// reduction runs in a fixed order, so the result does not depend on scheduling.
+template <typename T>
+struct Tile;
+template <>
+struct Tile<float> {
+    static constexpr int PAD = 1;       // words
+    __device__ static float ld(const float* t, int i) { return t[i]; }
+    __device__ static void st(float* t, int i, float v) { t[i] = v; }
+};
+template <>
+struct Tile<__nv_bfloat16> {
+    static constexpr int PAD = 2;       // elements (one word)
+    __device__ static float ld(const __nv_bfloat16* t, int i) { return bf2f(t[i]); }
+    __device__ static void st(__nv_bfloat16* t, int i, float v) { t[i] = f2bf(v); }
+};
 
-template <bool BF16, int NK>
-__global__ void __launch_bounds__(LH_WARPS * 32) loss_head_kernel(HeadParams p) {
-    extern __shared__ float sm[];
-    const int A = p.A, H = p.H;
-    float* Wa = sm;                       // [A][H]
-    float* Wc = Wa + A * H;               // [H]
-    float* cst = Wc + H;                  // [4][16]: log sigma, 1 / sigma^2, sigma_old^2, log sigma_old
-    const int PF = head_part_floats(A, H);
-    float* accw = cst + 64;               // per-warp partial records [LH_WARPS][PF]
-    float* sdat = accw + LH_WARPS * PF;   // per-warp sample records [LH_WARPS][LH_ROWS][LH_SD]
-    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(sdat + LH_WARPS * LH_ROWS * LH_SD);   // [LH_WARPS][2][LH_ROWS][H + 2]
-    const int SP = H + 2;
-    for (int i = threadIdx.x; i < A * H; i += blockDim.x) Wa[i] = p.Wa[i];
-    for (int i = threadIdx.x; i < H; i += blockDim.x) Wc[i] = p.Wc[i];
-    if (threadIdx.x < A) {
-        const float ls = p.log_std[threadIdx.x], lso = p.log_std_old[threadIdx.x];
-        cst[threadIdx.x] = ls;
-        cst[16 + threadIdx.x] = expf(-2.f * ls);
-        cst[32 + threadIdx.x] = expf(2.f * lso);
-        cst[48 + threadIdx.x] = lso;
+constexpr int LH_TPR = 4;           // threads per row (each owns H / 4 hidden units of the row)
+constexpr int LH_GP = 13;           // pitch of the [12 g_mu, g_v] rows (odd: conflict-free)
+constexpr int LH_RP = 17;           // pitch of the per-row records (surr, vloss, kl, clip, g_ls[12])
+
+template <int H, int LR>
+struct LossShape {
+    static constexpr int NT = LR * LH_TPR;         // threads
+    static constexpr int QW = NT / H;              // threads per hidden unit in the weight gradient
+    static constexpr int FWD = (LH_TPR - 1) * LR * LH_GP;   // forward partials of quarters 1..3
+    static constexpr int WG = (QW - 1) * H * LH_GP;          // weight-gradient partials of ranges 1..
+    static constexpr int LAST = 4 * NT;                      // last block's statistics
+    static constexpr int SCR = FWD > WG ? (FWD > LAST ? FWD : LAST) : (WG > LAST ? WG : LAST);
+    // floats: WaT, Wc, constants, g rows, records, scratch
+    static constexpr int FLOATS = H * MAX_A + H + 64 + LR * LH_GP + LR * LH_RP + SCR;
+    static_assert(NT % H == 0 && QW >= 1 && LR % QW == 0, "loss head shape");
+};
+
+template <bool BF16, int H, int LR>
+__global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p) {
+    using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
+    using S = LossShape<H, LR>;
+    constexpr int SP = H + Tile<T>::PAD;           // tile pitch (elements)
+    constexpr int NT = S::NT;
+    constexpr int HQ = H / LH_TPR;                 // hidden units per thread of a row
+    constexpr int QW = S::QW;
+    constexpr int RQ = LR / QW;                    // rows per weight-gradient range
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int A = p.A;
+    float* WaT = reinterpret_cast<float*>(sm_raw);          // [H][12] (transposed head weights)
+    float* Wc = WaT + H * MAX_A;                            // [H]
+    float* cst = Wc + H;                                    // [64]
+    float* gmu_s = cst + 64;                                // [LR][13]: g_mu (12) and g_v
+    float* recs = gmu_s + LR * LH_GP;                       // [LR][17]
+    float* scr = recs + LR * LH_RP;                         // scratch (partials)
+    T* ta = reinterpret_cast<T*>(scr + S::SCR);             // [LR][SP] actor h rows, then d/dh
+    T* tc = ta + LR * SP;                                   // [LR][SP] critic
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = tid % LR, part = tid / LR;                // row of the block, quarter of the units
+    const int m0 = blockIdx.x * LR;
+    const int rows = max(0, min(LR, p.M - m0));   // blocks past M leave zero records
+    for (int i = tid; i < H * MAX_A; i += NT) {
+        const int k = i / MAX_A, j = i % MAX_A;
+        WaT[i] = j < A ? p.Wa[j * H + k] : 0.f;
+    }
+    for (int i = tid; i < H; i += NT) Wc[i] = p.Wc[i];
+    if (tid < A) {
+        const float ls = p.log_std[tid], lso = p.log_std_old[tid];
+        cst[tid] = ls;
+        cst[16 + tid] = expf(-2.f * ls);
+        cst[32 + tid] = expf(2.f * lso);
+        cst[48 + tid] = lso;
+    }
+    // stage the rows (coalesced 4-byte words)
+    {
+        const T* ga = reinterpret_cast<const T*>(p.ha) + (size_t)m0 * H;
+        const T* gc = reinterpret_cast<const T*>(p.hc) + (size_t)m0 * H;
+        constexpr int EPW = 4 / sizeof(T);                  // elements per word
+        for (int w = tid; w < rows * (H / EPW); w += NT) {
+            const int rr = w / (H / EPW), c = (w % (H / EPW)) * EPW;
+            if (BF16) {
+                *reinterpret_cast<uint32_t*>(ta + rr * SP + c) = *reinterpret_cast<const uint32_t*>(ga + (size_t)rr * H + c);
+                *reinterpret_cast<uint32_t*>(tc + rr * SP + c) = *reinterpret_cast<const uint32_t*>(gc + (size_t)rr * H + c);
+            } else {
+                ta[rr * SP + c] = ga[(size_t)rr * H + c];
+                tc[rr * SP + c] = gc[(size_t)rr * H + c];
+            }
+        }
+    }
+    const bool live = r < rows;
+    __syncthreads();
+
+    // ---- forward of the heads over this thread's quarter of the hidden units
+    float mu[MAX_A], v = 0.f;
+#pragma unroll
+    for (int j = 0; j < MAX_A; ++j) mu[j] = 0.f;
+    if (live) {
+        const T* hr = ta + r * SP;
+        const T* cr = tc + r * SP;
+#pragma unroll 4
+        for (int k = part * HQ; k < (part + 1) * HQ; ++k) {
+            const float h = Tile<T>::ld(hr, k);
+            const float4* w4 = reinterpret_cast<const float4*>(WaT + k * MAX_A);
+            const float4 w0 = w4[0], w1 = w4[1], w2 = w4[2];
+            mu[0] += h * w0.x; mu[1] += h * w0.y; mu[2] += h * w0.z; mu[3] += h * w0.w;
+            mu[4] += h * w1.x; mu[5] += h * w1.y; mu[6] += h * w1.z; mu[7] += h * w1.w;
+            mu[8] += h * w2.x; mu[9] += h * w2.y; mu[10] += h * w2.z; mu[11] += h * w2.w;
+            v += Tile<T>::ld(cr, k) * Wc[k];
+        }
+    }
+    if (part > 0) {
+        float* d = scr + ((size_t)(part - 1) * LR + r) * LH_GP;
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) d[j] = mu[j];
+        d[12] = v;
     }
     __syncthreads();
+    // ---- per row (the row's first thread): loss terms and gradients w.r.t. mu and V
+    if (part == 0) {
+        const int m = m0 + r;
+        const int s = live ? (p.idx ? __ldg(p.idx + m) : m) : 0;
+        // quarter sums in order 0, 1, 2, 3, then the bias
+#pragma unroll
+        for (int q = 1; q < LH_TPR; ++q) {
+            const float* d = scr + ((size_t)(q - 1) * LR + r) * LH_GP;
+#pragma unroll
+            for (int j = 0; j < MAX_A; ++j) mu[j] += d[j];
+            v += d[12];
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) mu[j] += j < A ? p.ba[j] : 0.f;
+        v += p.bc[0];
+        float logp = 0.f, kl = 0.f, diff[MAX_A];
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) {
+            diff[j] = 0.f;
+            if (j < A && live) {
+                const float ls = cst[j], iv = cst[16 + j];
+                diff[j] = __ldg(p.a_old + (size_t)s * A + j) - mu[j];
+                logp += -0.5f * diff[j] * diff[j] * iv - ls - HALF_LOG_2PI;
+                const float dm = __ldg(p.mu_old + (size_t)s * A + j) - mu[j];
+                kl += ls - cst[48 + j] + 0.5f * (cst[32 + j] + dm * dm) * iv - 0.5f;
+            }
+        }
+        const float lpo = live ? __ldg(p.logp_old + s) : 0.f;
+        const float adv = live ? __ldg(p.adv + s) : 0.f;
+        const float vo = live ? __ldg(p.v_old + s) : 0.f;
+        const float R = live ? __ldg(p.ret + s) : 0.f;
+        const float inv_M = 1.0f / (float)p.M;
+        const float ratio = expf(logp - lpo);
+        const float s1 = ratio * adv;
+        const float s2 = fminf(fmaxf(ratio, 1.f - p.clip), 1.f + p.clip) * adv;
+        const float g_logp = -(s1 <= s2 ? adv : 0.f) * inv_M * ratio;
+        const float dv = v - vo;
+        const float vclip = vo + fminf(fmaxf(dv, -p.clip), p.clip);
+        const float u = (v - R) * (v - R), w = (vclip - R) * (vclip - R);
+        float g_v = p.value_coef * inv_M * (u >= w ? 2.f * (v - R) : ((dv > -p.clip && dv < p.clip) ? 2.f * (vclip - R) : 0.f));
+        if (!live) g_v = 0.f;
+        float* rc = recs + r * LH_RP;
+        rc[0] = live ? fminf(s1, s2) : 0.f;
+        rc[1] = live ? fmaxf(u, w) : 0.f;
+        rc[2] = live ? kl : 0.f;
+        rc[3] = (live && fabsf(ratio - 1.f) > p.clip) ? 1.f : 0.f;
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) {
+            const float iv = j < A ? cst[16 + j] : 0.f;
+            gmu_s[r * LH_GP + j] = (live && j < A) ? g_logp * diff[j] * iv : 0.f;
+            rc[4 + j] = (live && j < A) ? g_logp * (diff[j] * diff[j] * iv - 1.f) : 0.f;
+        }
+        gmu_s[r * LH_GP + 12] = g_v;
+    }
+    __syncthreads();
+
+    // ---- head weight gradients: thread (unit k, row range q); ranges combined by q = 0 in order
+    const int PF = head_part_floats(A, H);
     const int O_WA = 0, O_BA = A * H, O_LS = O_BA + A, O_WC = O_LS + A, O_BC = O_WC + H, O_DBA = O_BC + 1,
               O_DBC = O_DBA + H, O_ST = O_DBC + H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float inv_M = 1.0f / (float)p.M;
-    float gWa[MAX_A][NK], gWc[NK], dba[NK], dbc[NK];
+    float* out = p.part + (size_t)blockIdx.x * PF;
+    const int k = tid % H, q = tid / H;
+    float acc[MAX_A], accc = 0.f;
 #pragma unroll
-    for (int i = 0; i < NK; ++i) {
-        gWc[i] = dba[i] = dbc[i] = 0.f;
+    for (int j = 0; j < MAX_A; ++j) acc[j] = 0.f;
+    for (int rr = q * RQ; rr < min(rows, (q + 1) * RQ); ++rr) {
+        const float h = Tile<T>::ld(ta + rr * SP, k);
+        const float* g = gmu_s + rr * LH_GP;
 #pragma unroll
-        for (int j = 0; j < MAX_A; ++j) gWa[j][i] = 0.f;
+        for (int j = 0; j < MAX_A; ++j) acc[j] += g[j] * h;
+        accc += g[12] * Tile<T>::ld(tc + rr * SP, k);
     }
-    float gba = 0.f, gls = 0.f, gbc = 0.f;     // lane j < A owns action dim j
-    float st_surr = 0.f, st_vl = 0.f, st_kl = 0.f, st_clip = 0.f;
-    __nv_bfloat16* stA = stage + (size_t)warp * 2 * LH_ROWS * SP;
-    __nv_bfloat16* stC = stA + LH_ROWS * SP;
-
-    float* sd = sdat + (size_t)warp * LH_ROWS * LH_SD;
-    const int nchunks = (p.M + LH_ROWS - 1) / LH_ROWS;
-    for (int ch = blockIdx.x * LH_WARPS + warp; ch < nchunks; ch += gridDim.x * LH_WARPS) {
-        const int m0 = ch * LH_ROWS;
-        const int rows = min(LH_ROWS, p.M - m0);
-        // the chunk's per-sample data, gathered once (two lanes per row, independent loads)
-        __syncwarp();
-        {
-            const int r = lane >> 1, h = lane & 1;
-            if (r < rows) {
-                const int s = p.idx ? __ldg(p.idx + m0 + r) : m0 + r;
-                float* d = sd + r * LH_SD;
-                const float* src = h ? p.mu_old : p.a_old;
+    if (q > 0) {
+        float* d = scr + ((size_t)(q - 1) * H + k) * LH_GP;
 #pragma unroll
-                for (int j = 0; j < MAX_A; ++j)
-                    if (j < A) d[h * 12 + j] = __ldg(src + (size_t)s * A + j);
-                if (h == 0) {
-                    d[24] = __ldg(p.logp_old + s);
-                    d[25] = __ldg(p.adv + s);
-                } else {
-                    d[26] = __ldg(p.v_old + s);
-                    d[27] = __ldg(p.ret + s);
-                }
-            }
-        }
-        __syncwarp();
-        for (int r = 0; r < rows; ++r) {
-            const int m = m0 + r;
-            const float* d = sd + r * LH_SD;
-            float ha[NK], hc[NK];
-            float v = 0.f;
-#pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                ha[i] = ld_act<BF16>(p.ha, (size_t)m * H + lane + 32 * i);
-                hc[i] = ld_act<BF16>(p.hc, (size_t)m * H + lane + 32 * i);
-                v += hc[i] * Wc[lane + 32 * i];
-            }
-            float mu[MAX_A];
-#pragma unroll
-            for (int j = 0; j < MAX_A; ++j) {
-                float t = 0.f;
-                if (j < A) {
-#pragma unroll
-                    for (int i = 0; i < NK; ++i) t += ha[i] * Wa[j * H + lane + 32 * i];
-                }
-                mu[j] = t;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-#pragma unroll
-                for (int j = 0; j < MAX_A; ++j) mu[j] += __shfl_xor_sync(0xffffffffu, mu[j], o);
-            }
-            v += p.bc[0];
-            // per-sample loss terms (every lane computes the same scalars)
-            float logp = 0.f, kl = 0.f;
-#pragma unroll
-            for (int j = 0; j < MAX_A; ++j) {
-                if (j < A) {
-                    mu[j] += p.ba[j];
-                    const float ls = cst[j], iv = cst[16 + j];
-                    const float diff = d[j] - mu[j];
-                    logp += -0.5f * diff * diff * iv - ls - HALF_LOG_2PI;
-                    const float dm = d[12 + j] - mu[j];
-                    kl += ls - cst[48 + j] + 0.5f * (cst[32 + j] + dm * dm) * iv - 0.5f;
-                    mu[j] = diff;          // keep a - mu for the gradient
-                }
-            }
-            const float ratio = expf(logp - d[24]);
-            const float adv = d[25];
-            const float s1 = ratio * adv;
-            const float s2 = fminf(fmaxf(ratio, 1.f - p.clip), 1.f + p.clip) * adv;
-            const float g_logp = -(s1 <= s2 ? adv : 0.f) * inv_M * ratio;
-            const float vo = d[26], R = d[27];
-            const float dv = v - vo;
-            const float vclip = vo + fminf(fmaxf(dv, -p.clip), p.clip);
-            const float u = (v - R) * (v - R), w = (vclip - R) * (vclip - R);
-            const float g_v = p.value_coef * inv_M *
-                              (u >= w ? 2.f * (v - R) : ((dv > -p.clip && dv < p.clip) ? 2.f * (vclip - R) : 0.f));
-            if (lane == 0) {
-                st_surr += fminf(s1, s2);
-                st_vl += fmaxf(u, w);
-                st_kl += kl;
-                st_clip += fabsf(ratio - 1.f) > p.clip ? 1.f : 0.f;
-                gbc += g_v;
-            }
-            float gmu[MAX_A];
-#pragma unroll
-            for (int j = 0; j < MAX_A; ++j) {
-                gmu[j] = 0.f;
-                if (j < A) {
-                    const float iv = cst[16 + j];
-                    gmu[j] = g_logp * mu[j] * iv;
-                    if (lane == j) {
-                        gba += gmu[j];
-                        gls += g_logp * (mu[j] * mu[j] * iv - 1.f);
-                    }
-                }
-            }
-            // backward into the last hidden layer and the head weight gradients
-#pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                const int k = lane + 32 * i;
-                float da = 0.f;
-#pragma unroll
-                for (int j = 0; j < MAX_A; ++j) {
-                    if (j < A) {
-                        da += gmu[j] * Wa[j * H + k];
-                        gWa[j][i] += gmu[j] * ha[i];
-                    }
-                }
-                da *= elu_grad_y(ha[i]);
-                const float dc = g_v * Wc[k] * elu_grad_y(hc[i]);
-                gWc[i] += g_v * hc[i];
-                dba[i] += da;
-                dbc[i] += dc;
-                if (BF16) {
-                    const __nv_bfloat16 ba16 = f2bf(da), bc16 = f2bf(dc);
-                    reinterpret_cast<__nv_bfloat16*>(p.dya)[(size_t)m * H + k] = ba16;
-                    reinterpret_cast<__nv_bfloat16*>(p.dyc)[(size_t)m * H + k] = bc16;
-                    stA[r * SP + k] = ba16;
-                    stC[r * SP + k] = bc16;
-                } else {
-                    reinterpret_cast<float*>(p.dya)[(size_t)m * H + k] = da;
-                    reinterpret_cast<float*>(p.dyc)[(size_t)m * H + k] = dc;
-                }
-            }
-        }
-        if (BF16) {
-            // transposed copies: hidden unit k -> rows m0 .. m0 + rows - 1, 64 contiguous bytes
-            __syncwarp();
-            __nv_bfloat16* ta = reinterpret_cast<__nv_bfloat16*>(p.dya_t);
-            __nv_bfloat16* tc = reinterpret_cast<__nv_bfloat16*>(p.dyc_t);
-            if (lane < rows) {
-                for (int k = 0; k < H; ++k) {
-                    ta[(size_t)k * p.ldt + m0 + lane] = stA[lane * SP + k];
-                    tc[(size_t)k * p.ldt + m0 + lane] = stC[lane * SP + k];
-                }
-            }
-            __syncwarp();
-        }
-    }
-    // warp -> shared record of this warp (every slot written exactly once)
-    float* acc = accw + (size_t)warp * PF;
-#pragma unroll
-    for (int i = 0; i < NK; ++i) {
-        const int k = lane + 32 * i;
-#pragma unroll
-        for (int j = 0; j < MAX_A; ++j)
-            if (j < A) acc[O_WA + j * H + k] = gWa[j][i];
-        acc[O_WC + k] = gWc[i];
-        acc[O_DBA + k] = dba[i];
-        acc[O_DBC + k] = dbc[i];
-    }
-    if (lane < A) {
-        acc[O_BA + lane] = gba;
-        acc[O_LS + lane] = gls;
-    }
-    if (lane == 0) {
-        acc[O_BC] = gbc;
-        acc[O_ST + 0] = st_surr;
-        acc[O_ST + 1] = st_vl;
-        acc[O_ST + 2] = st_kl;
-        acc[O_ST + 3] = st_clip;
-        for (int i = 4; i < 8; ++i) acc[O_ST + i] = 0.f;
+        for (int j = 0; j < MAX_A; ++j) d[j] = acc[j];
+        d[12] = accc;
     }
     __syncthreads();
-    // block record = sum of the warp records in warp order (deterministic)
-    float* out = p.part + (size_t)blockIdx.x * PF;
-    for (int i = threadIdx.x; i < PF; i += blockDim.x) {
-        float v = 0.f;
+    if (q == 0) {
+        for (int qq = 1; qq < QW; ++qq) {
+            const float* d = scr + ((size_t)(qq - 1) * H + k) * LH_GP;
 #pragma unroll
-        for (int w = 0; w < LH_WARPS; ++w) v += accw[(size_t)w * PF + i];
-        if (blockIdx.x == 0 && i >= O_LS && i < O_LS + A) v -= p.entropy_coef;   // d(-c_e H)/d log sigma
-        out[i] = v;
+            for (int j = 0; j < MAX_A; ++j) acc[j] += d[j];
+            accc += d[12];
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j)
+            if (j < A) out[O_WA + j * H + k] = acc[j];
+        out[O_WC + k] = accc;
+    }
+
+    // ---- backward into the last hidden layer (in place in the tiles)
+    if (live) {
+        T* hr = ta + r * SP;
+        T* cr = tc + r * SP;
+        float gmu[MAX_A];
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) gmu[j] = gmu_s[r * LH_GP + j];
+        const float g_v = gmu_s[r * LH_GP + 12];
+#pragma unroll 4
+        for (int kk = part * HQ; kk < (part + 1) * HQ; ++kk) {
+            const float4* w4 = reinterpret_cast<const float4*>(WaT + kk * MAX_A);
+            const float4 w0 = w4[0], w1 = w4[1], w2 = w4[2];
+            float da = gmu[0] * w0.x + gmu[1] * w0.y + gmu[2] * w0.z + gmu[3] * w0.w + gmu[4] * w1.x + gmu[5] * w1.y +
+                       gmu[6] * w1.z + gmu[7] * w1.w + gmu[8] * w2.x + gmu[9] * w2.y + gmu[10] * w2.z + gmu[11] * w2.w;
+            da *= elu_grad_y(Tile<T>::ld(hr, kk));
+            const float dc = g_v * Wc[kk] * elu_grad_y(Tile<T>::ld(cr, kk));
+            Tile<T>::st(hr, kk, da);
+            Tile<T>::st(cr, kk, dc);
+        }
+    }
+    __syncthreads();
+
+    // ---- bias gradient of the last hidden layer (column sums) and the block's statistics:
+    // items [0, H) actor columns, [H, 2H) critic columns, [2H, 2H + 29) record columns
+    for (int i = tid; i < 2 * H + 29; i += NT) {
+        if (i < 2 * H) {
+            const T* t = i < H ? ta : tc;
+            const int kk = i < H ? i : i - H;
+            float sum = 0.f;
+            for (int rr = 0; rr < rows; ++rr) sum += Tile<T>::ld(t + rr * SP, kk);
+            out[(i < H ? O_DBA : O_DBC) + kk] = sum;
+        } else {
+            // record column c: 0..3 loss terms, 4 g_v, 5..16 g_mu, 17..28 g_log_std
+            const int c = i - 2 * H;
+            const float* col = c < 4 ? recs + c : c == 4 ? gmu_s + 12 : c < 17 ? gmu_s + (c - 5) : recs + 4 + (c - 17);
+            const int pitch = (c >= 4 && c < 17) ? LH_GP : LH_RP;
+            float sum = 0.f;
+            for (int rr = 0; rr < LR; ++rr) sum += col[rr * pitch];
+            if (c < 4) out[O_ST + c] = sum;
+            else if (c == 4) out[O_BC] = sum;
+            else if (c < 17) { if (c - 5 < A) out[O_BA + c - 5] = sum; }
+            else if (c - 17 < A) out[O_LS + c - 17] = sum - (blockIdx.x == 0 ? p.entropy_coef : 0.f);
+        }
+    }
+    if (tid >= 4 && tid < 8) out[O_ST + tid] = 0.f;
+    // ---- gradient rows out: row-major, and transposed (bf16) as 256-byte runs
+    {
+        T* gda = reinterpret_cast<T*>(p.dya);
+        T* gdc = reinterpret_cast<T*>(p.dyc);
+        for (int rr = warp; rr < rows; rr += NT / 32)
+            for (int kk = lane; kk < H; kk += 32) {
+                gda[(size_t)(m0 + rr) * H + kk] = ta[rr * SP + kk];
+                gdc[(size_t)(m0 + rr) * H + kk] = tc[rr * SP + kk];
+            }
+        if (BF16 && p.dya_t) {
+            __nv_bfloat16* xa = reinterpret_cast<__nv_bfloat16*>(p.dya_t);
+            __nv_bfloat16* xc = reinterpret_cast<__nv_bfloat16*>(p.dyc_t);
+            const __nv_bfloat16* ba = reinterpret_cast<const __nv_bfloat16*>(ta);
+            const __nv_bfloat16* bc = reinterpret_cast<const __nv_bfloat16*>(tc);
+            for (int kk = warp; kk < H; kk += NT / 32)
+                for (int rr = lane; rr < rows; rr += 32) {
+                    xa[(size_t)kk * p.ldt + m0 + rr] = ba[rr * SP + kk];
+                    xc[(size_t)kk * p.ldt + m0 + rr] = bc[rr * SP + kk];
+                }
+        }
     }
 
     // Last block: statistics, KL mean and Algorithm 1 on the device learning rate.
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
+    if (tid == 0) last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // all threads of the last block sum the per-block statistics (strided, then in thread order)
-    __shared__ float red[4][LH_WARPS * 32];
-    {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            const float* q = p.part + (size_t)b * PF + O_ST;
-            a0 += __ldcg(q); a1 += __ldcg(q + 1); a2 += __ldcg(q + 2); a3 += __ldcg(q + 3);
-        }
-        red[0][threadIdx.x] = a0; red[1][threadIdx.x] = a1; red[2][threadIdx.x] = a2; red[3][threadIdx.x] = a3;
+    // One warp: each lane sums every 32nd block's statistics, then a fixed xor tree (float64
+    // adds are slow on this part, so the chain is kept short: ceil(blocks / 32) + 5 adds).
+    if (warp != 0) return;
+    double st[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+        const float* q = p.part + (size_t)b * PF + O_ST;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[i] += (double)__ldcg(q + i);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double su = 0.0, vl = 0.0, klsum = 0.0, cl = 0.0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            su += red[0][t]; vl += red[1][t]; klsum += red[2][t]; cl += red[3][t];
-        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[i] += __shfl_xor_sync(0xffffffffu, st[i], o);
+    if (lane == 0) {
+        const float inv_M = 1.0f / (float)p.M;
         float ent = 0.f;
         for (int j = 0; j < A; ++j) ent += cst[j] + HALF_LOG_2PI + 0.5f;
-        const float kl = (float)(klsum / p.M);
-        const float surr = (float)(-su / p.M), vloss = (float)(vl / p.M);
+        const float kl = (float)st[2] * inv_M;
+        const float surr = -(float)st[0] * inv_M, vloss = (float)st[1] * inv_M;
         const float loss = surr + p.value_coef * vloss - p.entropy_coef * ent;
         float* sc = p.scal;
         sc[SC_KL] = kl;
@@ -341,20 +397,22 @@ __global__ void __launch_bounds__(LH_WARPS * 32) loss_head_kernel(HeadParams p) 
         sc[SC_SURR] = surr;
         sc[SC_VLOSS] = vloss;
         sc[SC_ENT] = ent;
-        sc[SC_CLIPFRAC] = (float)(cl / p.M);
+        sc[SC_CLIPFRAC] = (float)st[3] * inv_M;
+        float alpha = sc[SC_ALPHA];
         if (p.kl_target > 0.f) {
-            // Algorithm 1 (App. A.4), then the Adam step count for the step that follows.
-            float alpha = sc[SC_ALPHA];
+            // Algorithm 1 (App. A.4)
             if (kl > 2.f * p.kl_target) alpha = fmaxf(p.lr_min, alpha / 1.5f);
             else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
             sc[SC_ALPHA] = alpha;
-            const float t = sc[SC_STEP] + 1.f;
-            sc[SC_STEP] = t;
-            // Adam's bias corrections for this step, once (float64 is slow on this part):
-            // step size alpha / (1 - 0.9^t) and 1 / sqrt(1 - 0.999^t)
-            sc[SC_STEPSIZE] = (float)((double)alpha / (1.0 - pow(0.9, (double)t)));
-            sc[SC_INVSQRT_BC2] = (float)(1.0 / sqrt(1.0 - pow(0.999, (double)t)));
         }
+        // Adam step count and bias corrections for the step that follows, once per minibatch:
+        // 1 - beta^t = -expm1(t log1p(-(1 - beta))), accurate to a few ulp for every t
+        const float t = sc[SC_STEP] + 1.f;
+        sc[SC_STEP] = t;
+        const float bc1 = -expm1f(t * log1pf(-0.1f));      // beta1 = 0.9
+        const float bc2 = -expm1f(t * log1pf(-0.001f));    // beta2 = 0.999
+        sc[SC_STEPSIZE] = alpha / bc1;
+        sc[SC_INVSQRT_BC2] = 1.0f / sqrtf(bc2);
         if (p.stats) {
             p.stats[0] += loss; p.stats[1] += surr; p.stats[2] += vloss; p.stats[3] = ent;
             p.stats[4] += kl; p.stats[5] = sc[SC_ALPHA]; p.stats[6] += sc[SC_CLIPFRAC]; p.stats[12] += 1.f;
@@ -364,12 +422,6 @@ __global__ void __launch_bounds__(LH_WARPS * 32) loss_head_kernel(HeadParams p) 
 }
 
 }  // namespace
-
-int loss_head_blocks(int M) {
-    const int chunks = (M + LH_ROWS - 1) / LH_ROWS;
-    int b = (chunks + LH_WARPS - 1) / LH_WARPS;
-    return b < 1 ? 1 : (b > 3 * 148 ? 3 * 148 : b);
-}
 
 template <bool BF16, int NK>
 static cudaError_t act_dispatch(const HeadParams& p, int blocks, size_t smem, cudaStream_t s) {
@@ -394,42 +446,52 @@ cudaError_t launch_act_head(const HeadParams& p, cudaStream_t s) {
     return act_dispatch<false, 8>(p, blocks, smem, s);
 }
 
-template <bool BF16, int NK>
-static cudaError_t loss_dispatch(const HeadParams& p, size_t smem, cudaStream_t s) {
-    loss_head_kernel<BF16, NK><<<p.nblocks, LH_WARPS * 32, smem, s>>>(p);
+template <bool BF16, int H, int LR>
+static size_t loss_head_smem_t() {
+    using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
+    return (size_t)LossShape<H, LR>::FLOATS * sizeof(float) + (size_t)2 * LR * (H + Tile<T>::PAD) * sizeof(T);
+}
+
+template <bool BF16, int H, int LR>
+static cudaError_t loss_dispatch(const HeadParams& p, cudaStream_t s) {
+    loss_head_kernel<BF16, H, LR><<<p.nblocks, LR * LH_TPR, loss_head_smem_t<BF16, H, LR>(), s>>>(p);
     return cudaGetLastError();
 }
 
-static size_t loss_head_smem(int A, int H, bool bf16) {
-    return (size_t)(A * H + H + 64 + LH_WARPS * head_part_floats(A, H) + LH_WARPS * LH_ROWS * LH_SD) * sizeof(float) +
-           (bf16 ? (size_t)LH_WARPS * 2 * LH_ROWS * (H + 2) * 2 : 0);
+template <bool BF16, int H, int LR>
+static void loss_prepare() {
+    cudaFuncSetAttribute(loss_head_kernel<BF16, H, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)loss_head_smem_t<BF16, H, LR>());
 }
 
-// Largest dynamic shared memory of the loss head (A = 12, H = 256), set once before any
-// launch (and so before any stream capture).
+// Dynamic shared-memory limits of every loss-head instantiation, set once before any launch
+// (and so before any stream capture).
 void heads_prepare() {
-    const int smem = (int)loss_head_smem(12, 256, true);
-    cudaFuncSetAttribute(loss_head_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(loss_head_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(loss_head_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(loss_head_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(loss_head_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(loss_head_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    loss_prepare<true, 64, 128>();
+    loss_prepare<true, 128, 128>();
+    loss_prepare<true, 256, 64>();
+    loss_prepare<false, 64, 128>();
+    loss_prepare<false, 128, 128>();
+    loss_prepare<false, 256, 64>();
 }
+
+// 128 rows per block (64 when the last hidden layer is 256 wide, to fit the tiles).
+int loss_head_rows(int H) { return H >= 256 ? 64 : 128; }
+
+int loss_head_blocks(int M, int H) { return (M + loss_head_rows(H) - 1) / loss_head_rows(H); }
 
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
     if (p.A > MAX_A || !(p.H == 64 || p.H == 128 || p.H == 256)) return cudaErrorInvalidValue;
-    const size_t smem = loss_head_smem(p.A, p.H, p.bf16 != 0);
-    const int nk = p.H / 32;
+    if (p.nblocks < loss_head_blocks(p.M, p.H)) return cudaErrorInvalidValue;
     if (p.bf16) {
-        if (nk == 2) return loss_dispatch<true, 2>(p, smem, s);
-        if (nk == 4) return loss_dispatch<true, 4>(p, smem, s);
-        return loss_dispatch<true, 8>(p, smem, s);
+        if (p.H == 64) return loss_dispatch<true, 64, 128>(p, s);
+        if (p.H == 128) return loss_dispatch<true, 128, 128>(p, s);
+        return loss_dispatch<true, 256, 64>(p, s);
     }
-    if (nk == 2) return loss_dispatch<false, 2>(p, smem, s);
-    if (nk == 4) return loss_dispatch<false, 4>(p, smem, s);
-    return loss_dispatch<false, 8>(p, smem, s);
+    if (p.H == 64) return loss_dispatch<false, 64, 128>(p, s);
+    if (p.H == 128) return loss_dispatch<false, 128, 128>(p, s);
+    return loss_dispatch<false, 256, 64>(p, s);
 }
 
 }  // namespace rl

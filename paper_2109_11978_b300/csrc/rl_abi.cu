@@ -889,7 +889,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
             if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->gb_parts * Li.out));
         }
     }
-    c->head_blocks = loss_head_blocks(c->Mb);
+    c->head_blocks = loss_head_blocks(c->Mb, c->HL);
     CK(dalloc(c, &c->head_part, sizeof(float) * (size_t)c->head_blocks * head_part_floats(c->A, c->HL)));
     if (c->bf16) {
         for (int n = 0; n < 2; ++n)
