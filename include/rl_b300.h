@@ -274,12 +274,22 @@ rl_status rl_profile_read(rl_ctx* ctx, float* total_ms, int32_t* launches);
 
 /* Tile autotuner: times each GEMM site of the update (per hidden layer: forward, input gradient,
  * weight gradient; actor and critic in one launch; minibatch rows) over candidate tile widths
- * (64, 128 and, for weight gradients, 256 columns) and split-K counts (half, default, double)
- * on the context's own buffers, keeps the fastest, and drops a captured iteration graph so the
- * next rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on
- * are scratch (parameters, Adam state and env state are untouched).  report (host, may be NULL):
- * a JSON summary of the chosen shapes and their times, truncated to report_bytes. */
+ * (64, 128, 256 output columns), cluster sizes (1 or 2 CTAs sharing one weight/B tile through
+ * TMA multicast) and, for weight gradients, split-K counts (half, default, double) on the
+ * context's own buffers, keeps the fastest, and drops a captured iteration graph so the next
+ * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
+ * scratch (parameters, Adam state and env state are untouched).  report (host, may be NULL): a
+ * JSON summary of the chosen shapes and their times, truncated to report_bytes. */
 rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stream);
+
+/* Pins the tile shape of one GEMM site of a BF16 context (no counterpart in the paper: a tuning
+ * control of this implementation).  site: 0 forward, 1 input gradient (layer >= 1), 2 weight
+ * gradient; layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the
+ * site's output width; cluster: 1 or 2 (2 needs at least two 128-row tiles at the site);
+ * splits: weight-gradient split-K count (1 .. twice the default, rounded so every slice is a
+ * multiple of 64 rows), ignored for the other sites.  Drops a captured iteration graph.
+ * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
+rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits);
 
 /* Diagnostic: C = A B^T with the library's tcgen05 BF16 tensor-core GEMM kernel (FP32
  * accumulation), for checking the tensor-core path in isolation.  A [M][K] bf16, B [N][K] bf16
@@ -287,6 +297,12 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * 16-byte aligned.  The paper has no counterpart; it is the GEMM behind rl_policy_act and
  * rl_ppo_update in RL_BF16 precision. */
 rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream);
+
+/* Diagnostic, the weight-gradient form: C = At^T Bt, i.e. C[m][n] = sum_k At[k][m] Bt[k][n],
+ * with At [K][M] bf16 and Bt [K][N] bf16 row-major (the operands read MN-major, as the
+ * weight-gradient GEMM reads the row-major activations and gradients), C [M][N] fp32.
+ * M % 8 == 0, N % 64 == 0, K >= 1, pointers 16-byte aligned.  No counterpart in the paper. */
+rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const void* Bt, float* C, void* stream);
 
 /* Number of kernel launches one rl_train_iteration enqueues (host-side count). */
 int32_t rl_launches_per_iteration(rl_ctx* ctx);

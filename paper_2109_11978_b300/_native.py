@@ -81,7 +81,9 @@ SIGNATURES = {
     "rl_profile_read": (_i32, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_i32)]),
     "rl_launches_per_iteration": (_i32, [_vp]),
     "rl_autotune": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t, _vp]),
+    "rl_set_gemm_tiles": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "rl_gemm_bf16": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "rl_gemm_bf16_tn": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rl_group_create": (_i32, [_i32, ctypes.POINTER(rl_config), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "rl_group_destroy": (None, [_vp]),
     "rl_group_learner": (_vp, [_vp, _i32]),

@@ -165,11 +165,23 @@ def rl_autotune(ctx):
     return json.loads(buf.value.decode() or "{}")
 
 
+def rl_set_gemm_tiles(ctx, site, layer, bn, cluster=1, splits=1):
+    """Pins one GEMM site's tile shape (site 0 forward, 1 input gradient, 2 weight gradient)."""
+    check(lib().rl_set_gemm_tiles(ctx, int(site), int(layer), int(bn), int(cluster), int(splits)), "rl_set_gemm_tiles")
+
+
 def rl_gemm_bf16(A, B, C):
     """C[M][N] (fp32) = A[M][K] (bf16) @ B[N][K]^T (bf16) on the tcgen05 tensor-core kernel."""
     M, K = A.shape
     Nn = B.shape[0]
     check(lib().rl_gemm_bf16(int(M), int(Nn), int(K), _ptr(A), _ptr(B), _ptr(C), _stream()), "rl_gemm_bf16")
+
+
+def rl_gemm_bf16_tn(At, Bt, C):
+    """C[M][N] (fp32) = At[K][M]^T (bf16) @ Bt[K][N] (bf16), operands read MN-major."""
+    K, M = At.shape
+    Nn = Bt.shape[1]
+    check(lib().rl_gemm_bf16_tn(int(M), int(Nn), int(K), _ptr(At), _ptr(Bt), _ptr(C), _stream()), "rl_gemm_bf16_tn")
 
 
 def rl_launches_per_iteration(ctx):

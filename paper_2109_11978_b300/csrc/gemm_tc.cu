@@ -5,12 +5,12 @@
 //
 //   D[m][n] = sum_k A[m][k] * B[n][k]     A: [M][K] bf16, B: [N][K] bf16, both K contiguous
 //
-// Every MLP product is cast into this K-major form by keeping transposed copies where needed:
+// The MLP products map onto it as
 //   forward  H_l = ELU(H_{l-1} W_l^T + b_l):    A = H_{l-1} [rows][in],  B = W_l [out][in]
 //   input    dY_{l-1} = (dY_l W_l) * ELU'(H):   A = dY_l [rows][out],    B = W_l^T [in][out]
-//   weight   dW_l = dY_l^T H_{l-1}:             A = dY_l^T [out][rows],  B = H_{l-1}^T [in][rows]
-// The forward and input-gradient epilogues write their bf16 result both row-major and
-// transposed, so the weight-gradient GEMM finds its operands K-major.
+//   weight   dW_l = dY_l^T H_{l-1}:             A^T = dY_l [rows][out],  B^T = H_{l-1} [rows][in]
+// the weight gradient reading both operands MN-major (the row-major activations and gradients
+// as they are, K = the minibatch rows), so no transposed copy of any activation is kept.
 //
 // Persistent CTA per SM, 576 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
 // swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
@@ -21,6 +21,8 @@
 // word, the CTA stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its
 // tensor memory and returns.
 #include <cuda.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "gemm_tc.cuh"
@@ -100,11 +102,28 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor, MN-major operand with 128-byte swizzle: an atom is 64
+// consecutive M (or N) elements (one 128-byte row) x 8 K rows, 1024 bytes; atoms follow each
+// other every 1024 bytes along K (stride byte offset) and every 8192 bytes along M/N (leading
+// byte offset: one TMA box of 64 x 64 holds eight atoms stacked along K).  A K16 step is two
+// atoms further along K (2048 bytes).
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(8192u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
-// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-template <int N>
+// A and B K-major (bits 15, 16 clear) or both MN-major (set), N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+template <int N, bool MN>
 __device__ __forceinline__ uint32_t idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (MN ? (1u << 15) | (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -118,6 +137,54 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Multicast form: the box lands at the same shared-memory offset in every CTA of the cluster
+// named by `mask`, and completes bytes on the mbarrier at the same offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+
+// Arrives on the mbarrier at the same offset in every CTA of `mask` once this thread's MMAs
+// issued so far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"(mask)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t nclusters_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -167,28 +234,41 @@ struct TileCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = 4;
-    static constexpr int TP = 40;                                       // staging row pitch (bf16)
+    // row-major staging pitch in bytes (a 32-column row of bf16 or fp32 plus 16 bytes: the
+    // 16-byte writes of eight consecutive rows fall in distinct banks)
+    static constexpr int RP = EPI == EPI_STORE ? 144 : 80;
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
-    // transposed staging, per epilogue warp SLICE_COLS x 32 bf16 (only the bf16-output epilogues)
-    static constexpr int STG_BYTES = EPI == EPI_STORE ? 0 : EPI_WARPS * SLICE_COLS * TP * 2;
+    // per epilogue warp one 32 x 32 block of the output
+    static constexpr int STG_WARP = 32 * RP;
+    static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
     static constexpr int BAR_BYTES = 256;
-    static constexpr int SMEM = STAGES * STAGE + STG_BYTES + BAR_BYTES + 1024 /*align*/;
+    static constexpr int FIXED = STG_BYTES + BAR_BYTES + 1024 /*align*/;
+    static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3;
+    static constexpr int SMEM = STAGES * STAGE + FIXED;
 };
 
-// Persistent, warp-specialised GEMM.  Tiles (m, n, split, batch) are dealt round-robin to the
-// CTAs; the TMA warp streams K blocks through a STAGES-deep ring; the MMA warp accumulates each
-// tile into one of two TMEM buffers (2 x BN columns) while the sixteen epilogue warps drain the
-// other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue warp e reads TMEM
-// lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
-template <int BN, int EPI>
+// Persistent, warp-specialised GEMM.  Output tiles are grouped into cluster tiles of CM
+// vertically adjacent 128 x BN tiles (same columns, same B tile); cluster tiles are dealt
+// round-robin to the clusters, and CTA r of a cluster computes row tile CM * i + r.  In every K
+// step each CTA loads its own A tile and 1/CM of the shared B tile, multicast to the whole
+// cluster, so the B operand is read from L2 once per cluster instead of once per CTA.  A stage
+// is refilled only after all CM CTAs' MMAs have released it (the MMA commit arrives on every
+// CTA's "empty" barrier).  The TMA warp streams K blocks through a STAGES-deep ring; the MMA warp
+// accumulates each tile into one of two TMEM buffers (2 x BN columns) while the sixteen epilogue
+// warps drain the other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue
+// warp e reads TMEM lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
+template <int BN, int EPI, int CM, bool MN>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = TileCfg<BN, EPI>;
+    constexpr int B_SLICE_ROWS = BN / CM;
+    constexpr int B_BOXES = MN ? BN / 64 / CM : 1;          // MN-major: 64-wide boxes per CTA
+    static_assert(!MN || (BN / 64) % CM == 0, "MN-major B tile must split into whole boxes");
+    constexpr uint16_t MC_MASK = (uint16_t)((1u << CM) - 1u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __nv_bfloat16* stage_t = reinterpret_cast<__nv_bfloat16*>(smem + C::STAGES * C::STAGE);
+    uint8_t* stage_t = smem + C::STAGES * C::STAGE;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
     // barriers: full[S], empty[S], tfull[2], tempty[2], drain
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
@@ -197,14 +277,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+    // a multicast instantiation launched without its cluster shape would address CTAs that do
+    // not exist: refuse before touching any barrier
+    if (CM > 1 && cluster_size() != (uint32_t)CM) {
+        if (threadIdx.x == 0) set_status(p.status, RL_ERR_STATE);
+        return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = (p.M + BM - 1) / BM, nt = p.N / BN;
-    const int total = mt * nt * p.splits * p.batch;
+    const int mct = (mt + CM - 1) / CM;                     // cluster tiles along M
+    const int total = mct * nt * p.splits * p.batch;
+    const int rank = CM > 1 ? (int)cluster_rank() : 0;
+    const int cid = CM > 1 ? (int)cluster_id_x() : (int)blockIdx.x;
+    const int ncl = CM > 1 ? (int)nclusters_x() : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, CM);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -223,12 +313,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     tc_fence_before();
     __syncthreads();
+    if (CM > 1) cluster_sync_all();    // every CTA's barriers exist before any multicast lands
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     auto decode = [&](int t, int& mi, int& ni, int& sp, int& b) {
-        mi = t % mt;
-        int r = t / mt;
+        mi = (t % mct) * CM + rank;
+        int r = t / mct;
         ni = r % nt;
         r /= nt;
         sp = r % p.splits;
@@ -245,12 +336,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             // ---------------- TMA producer
             int it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            for (int t = cid; t < total && ok; t += ncl) {
                 int mi, ni, sp, b, kb0;
                 decode(t, mi, ni, sp, b);
                 const int nkb = kblocks_of(sp, kb0);
                 const CUtensorMap* ma = &p.tmA[b];
                 const CUtensorMap* mb = &p.tmB[b];
+                // a row tile past M (the last cluster tile of a ragged M) reloads the last valid
+                // rows; its results are never stored
+                const int ay = min(mi, mt - 1) * BM;
                 for (int i = 0; i < nkb; ++i, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
@@ -261,8 +355,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
                     mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
-                    tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, mi * BM);
-                    tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
+                    if (!MN) {
+                        tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, ay);
+                        if (CM == 1)
+                            tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
+                        else
+                            tma_load_2d_mc(sa + C::A_BYTES + rank * B_SLICE_ROWS * BK * 2, mb, full0 + 8 * s,
+                                           (kb0 + i) * BK, ni * BN + rank * B_SLICE_ROWS, MC_MASK);
+                    } else {
+                        // [K][M] and [K][N] sources: boxes of 64 M (N) columns x 64 K rows
+                        tma_load_2d(sa, ma, full0 + 8 * s, ay, (kb0 + i) * BK);
+                        tma_load_2d(sa + 8192, ma, full0 + 8 * s, ay + 64, (kb0 + i) * BK);
+#pragma unroll
+                        for (int j = 0; j < B_BOXES; ++j) {
+                            const int box = rank * B_BOXES + j;
+                            if (CM == 1)
+                                tma_load_2d(sa + C::A_BYTES + 8192 * box, mb, full0 + 8 * s, ni * BN + 64 * box, (kb0 + i) * BK);
+                            else
+                                tma_load_2d_mc(sa + C::A_BYTES + 8192 * box, mb, full0 + 8 * s, ni * BN + 64 * box,
+                                               (kb0 + i) * BK, MC_MASK);
+                        }
+                    }
                 }
             }
             if (!ok) {
@@ -271,15 +384,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     const int j = it - k;
                     mbar_wait(full0 + 8 * (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, p.status);
                 }
+            } else if (CM > 1) {
+                // every CTA of the cluster has released the last use of each stage: no copy or
+                // MMA-completion arrival of this cluster can still target this CTA's memory
+                for (int k = 1; k <= C::STAGES && it - k >= 0; ++k) {
+                    const int j = it - k;
+                    if (!mbar_wait(empty0 + 8 * (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, p.status)) break;
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t idesc = idesc_bf16<BN>();
+            const uint32_t idesc = idesc_bf16<BN, MN>();
             int it = 0, local = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++local) {
+            for (int t = cid; t < total && ok; t += ncl, ++local) {
                 int mi, ni, sp, b, kb0;
                 decode(t, mi, ni, sp, b);
                 const int nkb = kblocks_of(sp, kb0);
@@ -301,11 +421,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + C::A_BYTES);
+                    const uint64_t ad = MN ? sw128_desc_mn(sa) : sw128_desc(sa);
+                    const uint64_t bd = MN ? sw128_desc_mn(sa + C::A_BYTES) : sw128_desc(sa + C::A_BYTES);
+                    // K16 step: 32 bytes along the swizzled row (K-major), two 8-row atoms (MN-major)
+                    constexpr uint64_t KSTEP = MN ? (2048 >> 4) : (32 >> 4);
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
-                        mma_bf16(d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    mma_commit(empty0 + 8 * s);
+                        mma_bf16(d, ad + KSTEP * kk, bd + KSTEP * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    if (CM == 1) mma_commit(empty0 + 8 * s);
+                    else mma_commit_mc(empty0 + 8 * s, MC_MASK);
                 }
                 mma_commit(tfull0 + 8 * a);   // arrives when every MMA issued so far has completed
             }
@@ -319,9 +443,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int slice = ew >> 2;              // column slice of the tile (slice >= SLICES: idle)
         const bool busy = slice < C::SLICES;
-        __nv_bfloat16* stg = stage_t + (size_t)ew * C::SLICE_COLS * C::TP;
+        uint8_t* stg_raw = stage_t + (size_t)ew * C::STG_WARP;
         int local = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+        for (int t = cid; t < total; t += ncl, ++local) {
             int mi, ni, sp, b, kb0;
             decode(t, mi, ni, sp, b);
             const int nkb = kblocks_of(sp, kb0);
@@ -335,7 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const int m0 = mi * BM, n0 = ni * BN;
             const int row = m0 + 32 * q + lane;
             const bool row_ok = row < p.M;
-            const bool trans = EPI != EPI_STORE && p.Ct[b] != nullptr;
+            const bool tile_ok = mi < mt;
 #pragma unroll 1
             for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
@@ -346,12 +470,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 const int col = n0 + c;
                 if (EPI == EPI_STORE) {
-                    if (row_ok) {
-                        float* dst = reinterpret_cast<float*>(p.C[b]) + (size_t)sp * p.split_stride + (size_t)row * p.ldc + col;
+                    // through shared memory, so that eight lanes write one row's 128 bytes
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4*>(stg_raw + lane * C::RP + 4 * j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    __syncwarp();
+                    float* dst = reinterpret_cast<float*>(p.C[b]) + (size_t)sp * p.split_stride + col;
+#pragma unroll
+                    for (int idx = lane; idx < 256; idx += 32) {
+                        const int r = idx >> 3, g = idx & 7;
+                        const int rr = m0 + 32 * q + r;
+                        const float4 val = *reinterpret_cast<const float4*>(stg_raw + r * C::RP + 16 * g);
+                        if (rr < p.M) *reinterpret_cast<float4*>(dst + (size_t)rr * p.ldc + 4 * g) = val;
                     }
+                    __syncwarp();
                 } else {
                     if (EPI == EPI_BIAS_ELU) {
                         const float4* bias4 = reinterpret_cast<const float4*>(p.bias[b] + col);
@@ -382,19 +514,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
-                    if (row_ok) {
-                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.C[b]) + (size_t)row * p.ldc + col);
+                    {
+                        // row-major copy through shared memory: four lanes write one row's 64 bytes
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) dst[g] = reinterpret_cast<const uint4*>(o)[g];
-                    }
-                    if (trans) {
-                        const int lc0 = c - slice * C::SLICE_COLS;
+                        for (int g = 0; g < 4; ++g)
+                            *reinterpret_cast<uint4*>(stg_raw + lane * C::RP + 16 * g) = reinterpret_cast<const uint4*>(o)[g];
+                        __syncwarp();
+                        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) stg[(lc0 + j) * C::TP + lane] = o[j];
+                        for (int idx = lane; idx < 128; idx += 32) {
+                            const int r = idx >> 2, g = idx & 3;
+                            const int rr = m0 + 32 * q + r;
+                            const uint4 val = *reinterpret_cast<const uint4*>(stg_raw + r * C::RP + 16 * g);
+                            if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
+                        }
+                        __syncwarp();
                     }
                     if (EPI == EPI_ELU_GRAD && p.colsum[b]) {
                         const float s = colsum32(v, lane);    // column col + lane, over this warp's 32 rows
-                        p.colsum[b][((size_t)mi * 4 + q) * p.N + col + lane] = s;
+                        if (tile_ok) p.colsum[b][((size_t)mi * 4 + q) * p.N + col + lane] = s;
                     }
                 }
             }
@@ -402,22 +540,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * a);
-            if (trans && busy) {
-                // transposed copy: 16-byte runs of 8 consecutive rows per hidden unit
-                __syncwarp();
-                __nv_bfloat16* ct = reinterpret_cast<__nv_bfloat16*>(p.Ct[b]);
-                const int colbase = n0 + slice * C::SLICE_COLS;
-#pragma unroll 1
-                for (int idx = lane; idx < C::SLICE_COLS * 4; idx += 32) {
-                    const int lc = idx >> 2, g = idx & 3;
-                    const int r0 = m0 + 32 * q + 8 * g;
-                    if (r0 < p.M) {
-                        const uint4 val = *reinterpret_cast<const uint4*>(stg + lc * C::TP + 8 * g);
-                        *reinterpret_cast<uint4*>(ct + (size_t)(colbase + lc) * p.ldct + r0) = val;
-                    }
-                }
-                __syncwarp();
-            }
         }
     }
     tc_fence_before();
@@ -428,53 +550,125 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
 }
 
-template <int BN, int EPI>
-cudaError_t set_attr() {
-    return cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<BN, EPI>::SMEM);
+// Clusters of CM CTAs that fit on the device at once (one CTA per SM), per instantiation;
+// measured once in tc_prepare (before any stream capture) and used to size the persistent grid.
+struct ClusterFit {
+    int clusters[3][3][3];    // [bn 64/128/256][epi][cm 1/2/4]
+};
+static ClusterFit g_fit[64];
+
+static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 2 : -1; }
+static int cm_index(int cm) { return cm == 1 ? 0 : cm == 2 ? 1 : cm == 4 ? 2 : -1; }
+
+template <int BN, int EPI, int CM, bool MN>
+cudaError_t set_attr(int dev) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TileCfg<BN, EPI>::SMEM);
+    if (e != cudaSuccess) return e;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int n = sms / CM;
+    if (CM > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CM;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(n * CM));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = TileCfg<BN, EPI>::SMEM;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int fit = 0;
+        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MN>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (fit > 0 && fit < n) n = fit;
+    }
+    if (dev >= 0 && dev < 64) g_fit[dev].clusters[bn_index(BN)][EPI][cm_index(CM)] = n > 0 ? n : 1;
+    return cudaSuccess;
+}
+
+template <int BN, int EPI, int CM, bool MN>
+cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
+    using C = TileCfg<BN, EPI>;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int fit = (dev >= 0 && dev < 64) ? g_fit[dev].clusters[bn_index(BN)][EPI][cm_index(CM)] : 0;
+    if (fit <= 0) return cudaErrorNotReady;        // tc_prepare has not run on this device
+    const int mct = ((p.M + BM - 1) / BM + CM - 1) / CM;
+    const int total = mct * (p.N / BN) * p.splits * p.batch;
+    const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
+    if (CM == 1) {
+        tc_gemm_kernel<BN, EPI, 1, MN><<<clusters, TC_THREADS, C::SMEM, s>>>(p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(clusters * CM));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MN>, p);
 }
 
 template <int BN, int EPI>
-cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
-    using C = TileCfg<BN, EPI>;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+cudaError_t launch_cm(const TcParams& p, cudaStream_t s) {
+    if (p.mn) {
+        // MN-major operands: the split-K weight-gradient epilogue only
+        if (EPI != EPI_STORE) return cudaErrorInvalidValue;
+        if (p.cm == 1) return launch_cfg<BN, EPI_STORE, 1, true>(p, s);
+        if (p.cm == 2 && BN >= 128) return launch_cfg<BN >= 128 ? BN : 128, EPI_STORE, 2, true>(p, s);
+        return cudaErrorInvalidValue;
     }
-    const int total = ((p.M + BM - 1) / BM) * (p.N / BN) * p.splits * p.batch;
-    const int grid = total < sms ? total : sms;      // one persistent CTA per SM
-    tc_gemm_kernel<BN, EPI><<<grid, TC_THREADS, C::SMEM, s>>>(p);
-    return cudaGetLastError();
+    switch (p.cm) {
+        case 1: return launch_cfg<BN, EPI, 1, false>(p, s);
+        case 2: return launch_cfg<BN, EPI, 2, false>(p, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int EPI>
 cudaError_t launch_bn(const TcParams& p, cudaStream_t s) {
     switch (p.bn) {
-        case 64: return launch_cfg<64, EPI>(p, s);
-        case 128: return launch_cfg<128, EPI>(p, s);
+        case 64: return launch_cm<64, EPI>(p, s);
+        case 128: return launch_cm<128, EPI>(p, s);
+        case 256: return launch_cm<256, EPI>(p, s);
     }
     return cudaErrorInvalidValue;
 }
 
-// The split-K weight-gradient epilogue (no staging) also runs 256-wide tiles (2 x 256 TMEM
-// columns, 4 x 48 KB stages).
-template <>
-cudaError_t launch_bn<EPI_STORE>(const TcParams& p, cudaStream_t s) {
-    switch (p.bn) {
-        case 64: return launch_cfg<64, EPI_STORE>(p, s);
-        case 128: return launch_cfg<128, EPI_STORE>(p, s);
-        case 256: return launch_cfg<256, EPI_STORE>(p, s);
+template <int EPI>
+cudaError_t prepare_epi(int dev) {
+    cudaError_t e = cudaSuccess;
+    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<64, EPI, 2, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 1, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, false>(dev);
+    if (EPI == EPI_STORE) {
+        e = e != cudaSuccess ? e : set_attr<64, EPI_STORE, 1, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<128, EPI_STORE, 1, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<128, EPI_STORE, 2, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<256, EPI_STORE, 1, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<256, EPI_STORE, 2, true>(dev);
     }
-    return cudaErrorInvalidValue;
+    return e;
 }
 
 }  // namespace
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
-    if (p.N % p.bn || p.kblocks <= 0 || p.splits <= 0 || p.batch < 1 || p.batch > 2) return cudaErrorInvalidValue;
-    if (p.epi != EPI_STORE && (p.Ct[0] || p.Ct[1]) && p.M % 8) return cudaErrorInvalidValue;   // 16-byte transposed runs
+    if (p.bn <= 0 || p.N % p.bn || p.kblocks <= 0 || p.splits <= 0 || p.batch < 1 || p.batch > 2) return cudaErrorInvalidValue;
+    if (p.cm != 1 && p.cm != 2) return cudaErrorInvalidValue;
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -515,25 +709,30 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
     return r == CUDA_SUCCESS;
 }
 
-// Sets the dynamic shared-memory limit of every instantiation; called once per device before
-// the first launch (and so before any stream capture).
+// Sets the dynamic shared-memory limit of every instantiation and measures how many clusters
+// of each fit at once; called once per device before the first launch (and so before any
+// stream capture).
 cudaError_t tc_prepare() {
-    cudaError_t e = cudaSuccess;
-    e = e != cudaSuccess ? e : set_attr<64, EPI_STORE>();
-    e = e != cudaSuccess ? e : set_attr<128, EPI_STORE>();
-    e = e != cudaSuccess ? e : set_attr<256, EPI_STORE>();
-    e = e != cudaSuccess ? e : set_attr<64, EPI_BIAS_ELU>();
-    e = e != cudaSuccess ? e : set_attr<128, EPI_BIAS_ELU>();
-    e = e != cudaSuccess ? e : set_attr<64, EPI_ELU_GRAD>();
-    e = e != cudaSuccess ? e : set_attr<128, EPI_ELU_GRAD>();
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    e = prepare_epi<EPI_STORE>(dev);
+    e = e != cudaSuccess ? e : prepare_epi<EPI_BIAS_ELU>(dev);
+    e = e != cudaSuccess ? e : prepare_epi<EPI_ELU_GRAD>(dev);
+    if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-int tc_smem_bytes(int bn) {
+int tc_smem_bytes(int bn, int epi) {
     switch (bn) {
-        case 64: return TileCfg<64, EPI_BIAS_ELU>::SMEM;
-        case 128: return TileCfg<128, EPI_BIAS_ELU>::SMEM;
-        case 256: return TileCfg<256, EPI_STORE>::SMEM;
+        case 64: return epi == EPI_STORE ? TileCfg<64, EPI_STORE>::SMEM : TileCfg<64, EPI_BIAS_ELU>::SMEM;
+        case 128: return epi == EPI_STORE ? TileCfg<128, EPI_STORE>::SMEM : TileCfg<128, EPI_BIAS_ELU>::SMEM;
+        case 256: return epi == EPI_STORE ? TileCfg<256, EPI_STORE>::SMEM : TileCfg<256, EPI_BIAS_ELU>::SMEM;
     }
     return 0;
 }

@@ -8,18 +8,19 @@
 namespace rl {
 
 struct TcParams {
-    CUtensorMap tmA[2];        // A operand per batch entry: [M][K] bf16, box 64 x 128
-    CUtensorMap tmB[2];        // B operand per batch entry: [N][K] bf16, box 64 x bn
+    CUtensorMap tmA[2];        // A operand per batch entry: [M][K] bf16, box 64 x 128 (see mn)
+    CUtensorMap tmB[2];        // B operand per batch entry: [N][K] bf16, box 64 x (bn / cm)
     int M, N;                  // output rows / columns (N a multiple of bn)
     int kblocks;               // K / 64 (K zero-padded by TMA beyond the tensor)
     int kb_per_split, splits;  // split-K over blockIdx.z
     int batch;                 // 1 or 2 (actor, critic share one launch)
     int bn;                    // 64, 128 or 256
+    int cm;                    // CTAs per cluster along M sharing (multicasting) the B tile: 1 or 2
+    int mn;                    // 1: operands MN-major, A^T [K][M] and B^T [K][N] (boxes 64 x 64),
+                               //    EPI_STORE only; 0: K-major A [M][K], B [N][K]
     int epi;                   // EPI_STORE (fp32 split partials), EPI_BIAS_ELU, EPI_ELU_GRAD (bf16 out)
     void* C[2];                // output per batch entry
     int ldc;
-    void* Ct[2];               // optional transposed bf16 output [N][ldct]
-    int ldct;
     const float* bias[2];      // EPI_BIAS_ELU
     const void* H[2];          // EPI_ELU_GRAD: bf16 activation [M][ldh]
     int ldh;
@@ -30,7 +31,7 @@ struct TcParams {
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
-int tc_smem_bytes(int bn);
+int tc_smem_bytes(int bn, int epi);
 cudaError_t tc_prepare();
 
 }  // namespace rl

@@ -89,10 +89,9 @@ __global__ void __launch_bounds__(HEAD_WARPS * 32) act_head_kernel(HeadParams p)
 // the hidden units for the head outputs and for the backward into the hidden layer, and the
 // quarter sums are combined in a fixed order by the row's first thread, which computes the
 // per-sample loss terms and their gradients.  The head weight gradients are computed by
-// (hidden unit, row range) threads whose partials are combined in a fixed order, the gradient
-// rows are written back from shared memory with whole warps: row-major, and (bf16 form)
-// transposed for the weight-gradient GEMM as 256-byte runs of 128 consecutive rows.  Every
-// reduction runs in a fixed order, so the result does not depend on scheduling.
+// (hidden unit, row range) threads whose partials are combined in a fixed order, and the
+// gradient rows are written back from shared memory by whole warps.  Every reduction runs in a
+// fixed order, so the result does not depend on scheduling.
 template <typename T>
 struct Tile;
 template <>
@@ -341,7 +340,7 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
         }
     }
     if (tid >= 4 && tid < 8) out[O_ST + tid] = 0.f;
-    // ---- gradient rows out: row-major, and transposed (bf16) as 256-byte runs
+    // ---- gradient rows out (row-major)
     {
         T* gda = reinterpret_cast<T*>(p.dya);
         T* gdc = reinterpret_cast<T*>(p.dyc);
@@ -350,17 +349,6 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
                 gda[(size_t)(m0 + rr) * H + kk] = ta[rr * SP + kk];
                 gdc[(size_t)(m0 + rr) * H + kk] = tc[rr * SP + kk];
             }
-        if (BF16 && p.dya_t) {
-            __nv_bfloat16* xa = reinterpret_cast<__nv_bfloat16*>(p.dya_t);
-            __nv_bfloat16* xc = reinterpret_cast<__nv_bfloat16*>(p.dyc_t);
-            const __nv_bfloat16* ba = reinterpret_cast<const __nv_bfloat16*>(ta);
-            const __nv_bfloat16* bc = reinterpret_cast<const __nv_bfloat16*>(tc);
-            for (int kk = warp; kk < H; kk += NT / 32)
-                for (int rr = lane; rr < rows; rr += 32) {
-                    xa[(size_t)kk * p.ldt + m0 + rr] = ba[rr * SP + kk];
-                    xc[(size_t)kk * p.ldt + m0 + rr] = bc[rr * SP + kk];
-                }
-        }
     }
 
     // Last block: statistics, KL mean and Algorithm 1 on the device learning rate.

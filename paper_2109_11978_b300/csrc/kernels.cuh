@@ -89,9 +89,6 @@ struct HeadParams {
     float clip, value_coef, entropy_coef;
     void* dya;                   // actor d loss / d h_L, row-major [M][H] (fp32 or bf16)
     void* dyc;                   // critic
-    void* dya_t;                 // bf16 transposed copies [H][ldt] (bf16 path only)
-    void* dyc_t;
-    int ldt;
     float* part;                 // per-block partials, layout HEAD_PART_* below
     int nblocks;
     unsigned int* counter;       // last-block counter (zero at rest)
@@ -138,9 +135,8 @@ constexpr int ADAM_CHUNK = 256;    // parameters per block (one per thread)
 constexpr int ADAM_WIDE = 64;      // segments with more partials than this get 32 parameters per block
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
-// Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op] (and bf16 transposed [Op][ldt]).
-cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, void* Xt,
-                          int ldt, cudaStream_t s);
+// Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
+cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, cudaStream_t s);
 // Minibatch indices: permutation of [0, B) by a cycle-walking Feistel network keyed by
 // (seed, iteration, epoch); idx [epochs][B].
 cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned long long* iteration,

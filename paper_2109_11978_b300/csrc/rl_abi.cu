@@ -67,12 +67,8 @@ struct rl_ctx {
     int* iota = nullptr;
     float* logstd_old = nullptr;
     void* X0 = nullptr;
-    void* X0t = nullptr;
     void* H[2][4] = {};
-    void* Ht[2][4] = {};
     void* dY[2][4] = {};
-    void* dYt[2][4] = {};
-    int ldt = 0;
     float* gw[2][4] = {};
     int S[4] = {}, kchunk[4] = {}, S_cap[4] = {};
     float* gb[2][4] = {};
@@ -85,6 +81,7 @@ struct rl_ctx {
     void* wbf[2][4] = {};
     void* wbft[2][4] = {};
     int bn_fwd[4], bn_dx[4], bn_dw[4];
+    int cm_fwd[4], cm_dx[4], cm_dw[4];     // cluster size along M (B tile multicast)
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
     CUtensorMap tm_x0;                           // gathered minibatch observations
     CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
@@ -186,23 +183,24 @@ bool encode_layer_maps(rl_ctx* c, int l) {
     bool ok = true;
     for (int n = 0; n < 2; ++n) {
         const LayerInfo& Li = c->L[n][l];
-        ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l]);
+        ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l] / c->cm_fwd[l]);
         if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
             ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
-            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l]);
+            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l] / c->cm_dx[l]);
         }
-        ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dYt[n][l], Li.out, c->Mb, c->ldt, 128);
-        const void* xb = l == 0 ? c->X0t : c->Ht[n][l - 1];
-        ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, Li.in, c->Mb, c->ldt, c->bn_dw[l]);
+        // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in], 64 x 64 boxes
+        ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 64);
+        const void* xb = l == 0 ? c->X0 : c->H[n][l - 1];
+        ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, c->Mb, Li.in, Li.in, 64);
     }
     return ok;
 }
 
 // One hidden layer of the forward pass for `rows` rows (X = layer-0 input), batch = nnets
 // networks starting at net0: 2 (actor + critic) or 1 with net0 = 1 (critic only).
-rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets, bool transposed) {
+rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets) {
     const LayerInfo& Li = c->L[0][l];
     if (c->bf16) {
         TcParams tp;
@@ -216,7 +214,6 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
             }
             tp.tmB[j] = c->tm_fwdB[n][l];
             tp.C[j] = c->H[n][l];
-            tp.Ct[j] = transposed ? c->Ht[n][l] : nullptr;
             tp.bias[j] = c->params + c->L[n][l].b;
         }
         tp.M = rows;
@@ -226,9 +223,9 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.splits = 1;
         tp.batch = nnets;
         tp.bn = c->bn_fwd[l];
+        tp.cm = c->cm_fwd[l];
         tp.epi = EPI_BIAS_ELU;
         tp.ldc = Li.out;
-        tp.ldct = c->ldt;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -247,9 +244,9 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
 }
 
 // Forward through every hidden layer.
-rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool transposed) {
+rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets) {
     for (int l = 0; l < c->NH; ++l) {
-        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, transposed);
+        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets);
         if (st != RL_OK) return st;
     }
     return RL_OK;
@@ -265,12 +262,11 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.tmA[n] = c->tm_dxA[n][k];
             tp.tmB[n] = c->tm_dxB[n][k];
             tp.C[n] = c->dY[n][k - 1];
-            tp.Ct[n] = c->dYt[n][k - 1];
             tp.H[n] = c->H[n][k - 1];
             tp.colsum[n] = c->gb[n][k - 1];
         }
         tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
-        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldct = c->ldt; tp.ldh = Li.in;
+        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.cm = c->cm_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -300,7 +296,8 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.C[n] = c->gw[n][k];
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
-        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.epi = EPI_STORE; tp.ldc = Li.in;
+        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.cm = c->cm_dw[k]; tp.mn = 1; tp.epi = EPI_STORE;
+        tp.ldc = Li.in;
         tp.split_stride = (long long)Li.out * Li.in;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
@@ -341,7 +338,7 @@ HeadParams head_common(rl_ctx* c, int rows) {
 rl_status act_impl(rl_ctx* c, Enq& q, int t, int n, const void* obs, float* actions, float* mu, float* logp,
                    float* values) {
     const bool critic_only = !actions && !mu && !logp;
-    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2, false);
+    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, n);
     h.t = t;
@@ -377,11 +374,11 @@ EnvParams env_params(rl_ctx* c) {
 }
 
 // One minibatch: forward, loss head (+ Algorithm 1 when kl_target > 0), backward.
-// X0 must already hold the minibatch observations (and X0t its transpose for bf16).
+// X0 must already hold the minibatch observations.
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
                             const float* ret, bool step) {
-    rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, true);
+    rl_status st = forward_hidden(c, q, c->X0, M, 0, 2);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
     const int l = c->NH - 1;
@@ -398,9 +395,6 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.entropy_coef = c->cfg.entropy_coef;
     h.dya = c->dY[0][l];
     h.dyc = c->dY[1][l];
-    h.dya_t = c->dYt[0][l];
-    h.dyc_t = c->dYt[1][l];
-    h.ldt = c->ldt;
     h.part = c->head_part;
     h.nblocks = c->head_blocks;
     h.counter = c->counter;
@@ -493,7 +487,7 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
     for (int e = 0; e < epochs; ++e) {
         for (int m = 0; m < minibatches; ++m) {
             const int* idx = c->perm + (size_t)e * B + (size_t)m * Mb;
-            CK(launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, c->X0t, c->ldt, s));
+            CK(launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, s));
             c->launches++;
             rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true);
             if (st != RL_OK) return st;
@@ -555,6 +549,18 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
 // layer, actor and critic together, minibatch rows) over candidate tile widths and split counts on
 // the context's own buffers, and keeps the fastest.  CUDA events on the launching stream, one
 // warm-up and `reps` timed launches per candidate.
+// A captured iteration graph holds the tile shapes it was built with: rebuild it on next use.
+void drop_graph(rl_ctx* c) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+}
+
 rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     Enq q{c, s, false};
     cudaEvent_t e0, e1;
@@ -577,75 +583,88 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     rl_status st = RL_OK;
     report = "{\"sites\": [";
     bool first = true;
-    auto note = [&](const char* site, int l, int bn, int S, float ms) {
-        std::snprintf(buf, sizeof(buf), "%s{\"site\": \"%s\", \"layer\": %d, \"bn\": %d, \"splits\": %d, \"us\": %.2f}",
-                      first ? "" : ", ", site, l, bn, S, ms * 1000.f);
+    auto note = [&](const char* site, int l, int bn, int cm, int S, float ms) {
+        std::snprintf(buf, sizeof(buf),
+                      "%s{\"site\": \"%s\", \"layer\": %d, \"bn\": %d, \"cluster\": %d, \"splits\": %d, \"us\": %.2f}",
+                      first ? "" : ", ", site, l, bn, cm, S, ms * 1000.f);
         report += buf;
         first = false;
     };
+    const int bns[3] = {64, 128, 256};
+    const int cms[2] = {1, 2};
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
+        const int row_tiles = (c->Mb + 127) / 128;
         if (c->bf16) {
-            // forward
-            int best_bn = c->bn_fwd[l];
+            // forward: tile width x cluster size
+            int best_bn = c->bn_fwd[l], best_cm = c->cm_fwd[l];
             float best = 1e30f;
-            for (int bn : {64, 128}) {
-                if (Li.out % bn) continue;
-                c->bn_fwd[l] = bn;
-                if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
-                float ms = 0.f;
-                st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2, true); }, ms);
-                if (st != RL_OK) break;
-                if (ms < best) { best = ms; best_bn = bn; }
-            }
+            for (int bn : bns)
+                for (int cm : cms) {
+                    if (Li.out % bn || (cm > 1 && row_tiles < cm) || st != RL_OK) continue;
+                    c->bn_fwd[l] = bn;
+                    c->cm_fwd[l] = cm;
+                    if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                    float ms = 0.f;
+                    st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2); }, ms);
+                    if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; }
+                }
             c->bn_fwd[l] = best_bn;
-            note("forward", l, best_bn, 1, best);
+            c->cm_fwd[l] = best_cm;
+            note("forward", l, best_bn, best_cm, 1, best);
             // input gradient
             if (l > 0 && st == RL_OK) {
                 best_bn = c->bn_dx[l];
+                best_cm = c->cm_dx[l];
                 best = 1e30f;
-                for (int bn : {64, 128}) {
-                    if (Li.in % bn) continue;
-                    c->bn_dx[l] = bn;
-                    if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
-                    float ms = 0.f;
-                    st = timed([&] { return dx_layer(c, q, l, c->Mb); }, ms);
-                    if (st != RL_OK) break;
-                    if (ms < best) { best = ms; best_bn = bn; }
-                }
+                for (int bn : bns)
+                    for (int cm : cms) {
+                        if (Li.in % bn || (cm > 1 && row_tiles < cm) || st != RL_OK) continue;
+                        c->bn_dx[l] = bn;
+                        c->cm_dx[l] = cm;
+                        if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                        float ms = 0.f;
+                        st = timed([&] { return dx_layer(c, q, l, c->Mb); }, ms);
+                        if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; }
+                    }
                 c->bn_dx[l] = best_bn;
-                note("input_grad", l, best_bn, 1, best);
+                c->cm_dx[l] = best_cm;
+                note("input_grad", l, best_bn, best_cm, 1, best);
             }
         }
-        // weight gradient: tile width (bf16) and split count
+        // weight gradient: tile width and cluster size (bf16) and split count
         if (st == RL_OK) {
             const int S0 = c->S[l];
-            int best_bn = c->bn_dw[l], best_S = S0, best_kc = c->kchunk[l];
+            int best_bn = c->bn_dw[l], best_cm = c->cm_dw[l], best_S = S0, best_kc = c->kchunk[l];
             float best = 1e30f;
-            const int bns[3] = {64, 128, 256};
+            const int out_tiles = (Li.out + 127) / 128;
             for (int bi = 0; bi < (c->bf16 ? 3 : 1) && st == RL_OK; ++bi) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
-                for (int S : {S0 / 2, S0, 2 * S0}) {
-                    if (S < 1 || S > c->S_cap[l]) continue;
-                    int kc = (c->Mb + S - 1) / S;
-                    kc = (kc + 63) / 64 * 64;
-                    const int Sr = (c->Mb + kc - 1) / kc;
-                    if (Sr > c->S_cap[l] && Sr > S0) continue;
-                    c->bn_dw[l] = bn;
-                    c->S[l] = Sr;
-                    c->kchunk[l] = kc;
-                    if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
-                    float ms = 0.f;
-                    st = timed([&] { return dw_layer(c, q, l, c->Mb); }, ms);
-                    if (st != RL_OK) break;
-                    if (ms < best) { best = ms; best_bn = bn; best_S = Sr; best_kc = kc; }
+                for (int cm : cms) {
+                    if (cm > 1 && (!c->bf16 || out_tiles < cm || bn < 128)) continue;   // whole 64-wide B boxes per CTA
+                    for (int S : {S0 / 2, S0, 2 * S0}) {
+                        if (S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
+                        int kc = (c->Mb + S - 1) / S;
+                        kc = (kc + 63) / 64 * 64;
+                        const int Sr = (c->Mb + kc - 1) / kc;
+                        if (Sr > c->S_cap[l] && Sr > S0) continue;
+                        c->bn_dw[l] = bn;
+                        c->cm_dw[l] = cm;
+                        c->S[l] = Sr;
+                        c->kchunk[l] = kc;
+                        if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                        float ms = 0.f;
+                        st = timed([&] { return dw_layer(c, q, l, c->Mb); }, ms);
+                        if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; best_S = Sr; best_kc = kc; }
+                    }
                 }
             }
             c->bn_dw[l] = best_bn;
+            c->cm_dw[l] = best_cm;
             c->S[l] = best_S;
             c->kchunk[l] = best_kc;
-            note("weight_grad", l, best_bn, best_S, best);
+            note("weight_grad", l, best_bn, best_cm, best_S, best);
         }
         if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
     }
@@ -654,15 +673,44 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     report += "]}";
     if (st != RL_OK) return st;
     build_adam(c);
-    // a captured iteration graph holds the old tile shapes: rebuild it on next use
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
+    drop_graph(c);
+    return RL_OK;
+}
+
+rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
+    if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 2 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 2)) return RL_ERR_INVALID_ARG;
+    const LayerInfo& Li = c->L[0][l];
+    const int width = site == 0 ? Li.out : Li.in;
+    const int row_tiles = site == 2 ? (Li.out + 127) / 128 : (c->Mb + 127) / 128;
+    if (width % bn || row_tiles < cm) return RL_ERR_INVALID_ARG;
+    if (site == 2 && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;     // whole 64-wide B boxes per CTA
+    int kc = c->kchunk[l], Sr = c->S[l];
+    if (site == 2) {
+        if (splits < 1 || splits > c->S_cap[l]) return RL_ERR_INVALID_ARG;
+        kc = (c->Mb + splits - 1) / splits;
+        kc = (kc + 63) / 64 * 64;
+        Sr = (c->Mb + kc - 1) / kc;
     }
-    if (c->graph) {
-        cudaGraphDestroy(c->graph);
-        c->graph = nullptr;
+    const int old_bn = site == 0 ? c->bn_fwd[l] : site == 1 ? c->bn_dx[l] : c->bn_dw[l];
+    const int old_cm = site == 0 ? c->cm_fwd[l] : site == 1 ? c->cm_dx[l] : c->cm_dw[l];
+    auto assign = [&](int b, int m) {
+        if (site == 0) { c->bn_fwd[l] = b; c->cm_fwd[l] = m; }
+        else if (site == 1) { c->bn_dx[l] = b; c->cm_dx[l] = m; }
+        else { c->bn_dw[l] = b; c->cm_dw[l] = m; }
+    };
+    assign(bn, cm);
+    if (!encode_layer_maps(c, l)) {
+        assign(old_bn, old_cm);
+        encode_layer_maps(c, l);
+        return RL_ERR_CUDA;
     }
+    if (site == 2) {
+        c->S[l] = Sr;
+        c->kchunk[l] = kc;
+        build_adam(c);
+    }
+    drop_graph(c);
     return RL_OK;
 }
 
@@ -848,17 +896,11 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         CK(cudaMemcpy(c->iota, io.data(), sizeof(int) * c->Mb, cudaMemcpyHostToDevice));
     }
     CK(dalloc(c, &c->logstd_old, sizeof(float) * c->A));
-    c->ldt = (c->Mb + 63) / 64 * 64;
     CK(dalloc(c, &c->X0, (size_t)c->rows * c->Op * esize(c)));
-    if (c->bf16) CK(dalloc(c, &c->X0t, (size_t)c->Op * c->ldt * 2));
     for (int n = 0; n < 2; ++n)
         for (int l = 0; l < c->NH; ++l) {
             CK(dalloc(c, &c->H[n][l], (size_t)c->rows * c->hid[l] * esize(c)));
             CK(dalloc(c, &c->dY[n][l], (size_t)c->rows * c->hid[l] * esize(c)));
-            if (c->bf16) {
-                CK(dalloc(c, &c->Ht[n][l], (size_t)c->hid[l] * c->ldt * 2));
-                CK(dalloc(c, &c->dYt[n][l], (size_t)c->hid[l] * c->ldt * 2));
-            }
         }
     // split-K of the weight-gradient GEMMs.  BF16: 256-wide tiles (each dY^T tile read once
     // per layer input width) and about one wave of 148 CTAs, each K range >= 384 rows.  FP32:
@@ -884,6 +926,9 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         c->bn_fwd[l] = pick_bn(Li.out);
         c->bn_dx[l] = pick_bn(Li.in);
         c->bn_dw[l] = bn;
+        // B-tile multicast across pairs of row tiles wherever there are at least two row tiles
+        c->cm_fwd[l] = c->cm_dx[l] = (c->bf16 && c->Mb > 128) ? 2 : 1;
+        c->cm_dw[l] = (c->bf16 && Li.out > 128 && bn >= 128) ? 2 : 1;
         for (int n = 0; n < 2; ++n) {
             CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)std::max(S, c->S_cap[l]) * Li.out * Li.in));
             if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->gb_parts * Li.out));
@@ -1092,7 +1137,7 @@ rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* a
     if (M < 1 || M > c->Mb || M % 64) return RL_ERR_INVALID_ARG;
     cudaStream_t s = S_(stream);
     Enq q{c, s, false};
-    CK(launch_gather(obs, c->bf16 ? 1 : 0, c->iota, M, c->Op, c->X0, c->X0t, c->ldt, s));
+    CK(launch_gather(obs, c->bf16 ? 1 : 0, c->iota, M, c->Op, c->X0, s));
     for (int n = 0; n < 2; ++n)          // row tiles past M leave no bias-gradient partial
         for (int l = 0; l + 1 < c->NH; ++l)
             CK(cudaMemsetAsync(c->gb[n][l], 0, sizeof(float) * (size_t)c->gb_parts * c->hid[l], s));
@@ -1233,17 +1278,39 @@ rl_status rl_autotune(rl_ctx* c, char* report, size_t report_bytes, void* stream
     return st;
 }
 
+rl_status rl_set_gemm_tiles(rl_ctx* c, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    return set_tiles_impl(c, site, layer, bn, cluster, splits);
+}
+
 rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {
     if (M < 1 || N < 64 || N % 64 || K < 8 || K % 8 || !A || !B || !C) return RL_ERR_INVALID_ARG;
     if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
     const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
+    const int cm = M > 128 ? 2 : 1;    // pairs of row tiles share the B tile (multicast)
     if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
-    if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)) return RL_ERR_CUDA;
+    if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)(bn / cm))) return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    tp.bn = bn; tp.cm = cm; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    CK(launch_tc_gemm(tp, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const void* Bt, float* C, void* stream) {
+    if (M < 8 || M % 8 || N < 64 || N % 64 || K < 1 || !At || !Bt || !C) return RL_ERR_INVALID_ARG;
+    if (!aligned16(At) || !aligned16(Bt) || !aligned16(C)) return RL_ERR_ALIGNMENT;
+    TcParams tp;
+    std::memset(&tp, 0, sizeof(tp));
+    const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
+    const int cm = (M > 128 && bn >= 128) ? 2 : 1;
+    if (!make_tmap_bf16(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)) return RL_ERR_CUDA;
+    if (!make_tmap_bf16(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
+    CK(tc_prepare());
+    tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
+    tp.bn = bn; tp.cm = cm; tp.mn = 1; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }

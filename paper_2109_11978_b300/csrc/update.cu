@@ -40,59 +40,18 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
 }
 
 // ---------------------------------------------------------------- gather
-// 64 rows x 64 columns per block (256 threads), 16-byte vector loads and stores: rows leave
-// coalesced, and the transposed bf16 copy (the K-major operand of the weight-gradient GEMM)
-// is assembled in shared memory and leaves as 128-byte runs of 64 consecutive rows.
+// One warp per minibatch row: the sampled row of the rollout observations is copied with
+// 16-byte vector loads and stores (Op * element size is a multiple of 128 bytes).
 template <bool BF16>
 __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
-                                                     int Op, void* X, void* Xt, int ldt) {
-    __shared__ __align__(16) __nv_bfloat16 tile[64][72];
-    const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
-    const int tid = threadIdx.x;
-    if (BF16) {
-        // 64 rows x 8 vectors of 8 bf16
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int v = tid + 256 * k;
-            const int r = v >> 3, g = v & 7;
-            const int row = r0 + r;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (row < M) {
-                const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(obs) + (size_t)__ldg(idx + row) * Op + c0 + 8 * g;
-                val = __ldg(reinterpret_cast<const uint4*>(src));
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(X) + (size_t)row * Op + c0 + 8 * g) = val;
-            }
-            *reinterpret_cast<uint4*>(&tile[r][8 * g]) = val;
-        }
-        if (!Xt) return;
-        __syncthreads();
-        // column c of the tile -> Xt[c0 + c][r0 .. r0 + 63], 8 rows per 16-byte store
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int v = tid + 256 * k;
-            const int c = v >> 3, g = v & 7;
-            if (r0 + 8 * g < M) {
-                __align__(16) __nv_bfloat16 e[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) e[j] = tile[8 * g + j][c];
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(Xt) + (size_t)(c0 + c) * ldt + r0 + 8 * g) =
-                    *reinterpret_cast<const uint4*>(e);
-            }
-        }
-    } else {
-        // 64 rows x 16 vectors of 4 floats
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int v = tid + 256 * k;
-            const int r = v >> 4, g = v & 15;
-            const int row = r0 + r;
-            if (row < M) {
-                const float* src = reinterpret_cast<const float*>(obs) + (size_t)__ldg(idx + row) * Op + c0 + 4 * g;
-                *reinterpret_cast<float4*>(reinterpret_cast<float*>(X) + (size_t)row * Op + c0 + 4 * g) =
-                    __ldg(reinterpret_cast<const float4*>(src));
-            }
-        }
-    }
+                                                     int Op, void* X) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= M) return;
+    constexpr int E = BF16 ? 2 : 4;
+    const int nvec = Op * E / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(obs) + (size_t)__ldg(idx + row) * Op * E);
+    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(X) + (size_t)row * Op * E);
+    for (int v = lane; v < nvec; v += 32) dst[v] = __ldg(src + v);
 }
 
 // ---------------------------------------------------------------- Adam
@@ -206,14 +165,12 @@ cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, void* Xt, int ldt,
-                          cudaStream_t s) {
+cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (Op % 64) return cudaErrorInvalidValue;
-    if (Xt && M % 8) return cudaErrorInvalidValue;
-    dim3 grid((M + 63) / 64, Op / 64);
-    if (bf16) gather_kernel<true><<<grid, 256, 0, s>>>(obs, idx, M, Op, X, Xt, ldt);
-    else gather_kernel<false><<<grid, 256, 0, s>>>(obs, idx, M, Op, X, Xt, ldt);
+    const int grid = (M + 7) / 8;
+    if (bf16) gather_kernel<true><<<grid, 256, 0, s>>>(obs, idx, M, Op, X);
+    else gather_kernel<false><<<grid, 256, 0, s>>>(obs, idx, M, Op, X);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,24 @@ def test_tc_gemm_matches_fp64(M, N, K):
     assert err < 2e-6, err
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (64, 128, 1000), (512, 256, 24576), (256, 512, 3000),
+                                   (136, 192, 72), (8, 64, 5)])
+def test_tc_gemm_mn_major_matches_fp64(M, N, K):
+    """The weight-gradient form (both operands MN-major: K rows of M and N contiguous values),
+    ragged in M (not a multiple of 128) and K (not a multiple of 64)."""
+    g = torch.Generator().manual_seed(7 * M + N + K)
+    At = torch.randn(K, M, generator=g).to(torch.bfloat16)
+    Bt = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    api.rl_gemm_bf16_tn(At.cuda(), Bt.cuda(), C)
+    torch.cuda.synchronize()
+    ref = At.double().numpy().T @ Bt.double().numpy()
+    err = np.abs(C.cpu().double().numpy() - ref).max() / np.abs(ref).max()
+    # FP32 accumulation in tensor memory, one rounding per 16-product block: the error of a sum
+    # of K random products grows like sqrt(K)
+    assert err < max(2e-6, 5e-7 * np.sqrt(K)), err
+
+
 def _learner(w, hf=None, params=None):
     cfg = lib_config(w)
     O, _ = obs_dims(w)

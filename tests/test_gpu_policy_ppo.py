@@ -312,3 +312,62 @@ def test_autotune_keeps_results(form):
     torch.cuda.synchronize()
     assert api.rl_last_device_status(L.ctx) == 0
     L.close()
+
+
+@pytest.mark.parametrize("bn,cm,splits", [(64, 1, "one"), (64, 2, "most"), (128, 1, "most"), (128, 2, "one"),
+                                          (256, 1, "one"), (256, 2, "most")])
+def test_gemm_tile_shapes_keep_results(bn, cm, splits):
+    """Every tile width and cluster size of the tensor-core GEMM (cluster 2: pairs of row tiles
+    share the weight tile through TMA multicast), pinned at every site where it is valid, gives
+    the oracle's gradient within the BF16 tolerance.  2880 minibatch rows = 23 row tiles: the last
+    pair of a cluster has one tile past the rows, and the last row tile is ragged."""
+    w = workload("rough", num_envs=480, precision=1)
+    L, params, O, Op = _setup(w)
+    M = w["num_envs"] * w["num_steps"] // w["minibatches"]
+    assert M == 2880
+    hidden = w["hidden"]
+    widths = {0: hidden, 1: [Op] + list(hidden[:-1])}     # output width of forward / input-gradient sites
+    pinned = 0
+    for layer in range(len(hidden)):
+        for site in (0, 1, 2):
+            if site == 1 and layer == 0:
+                continue
+            width = hidden[layer] if site == 0 else widths[1][layer]
+            out_tiles = -(-hidden[layer] // 128)
+            if width % bn or (site == 2 and out_tiles < cm):
+                continue
+            choices = [1] if splits == "one" else [64, 48, 32, 24, 16, 12, 8, 6, 4, 3, 2]
+            for s_ in choices:
+                try:
+                    api.rl_set_gemm_tiles(L.ctx, site, layer, bn, cm, s_)
+                    pinned += 1
+                    break
+                except api.RLError:
+                    continue
+    assert pinned >= 3
+    b, d = _batch(M, O, Op, 12, params, hidden, 41, True, kink_margin=True)
+    d = _own_old_policy(L, b, d, O, params, hidden)
+    g = torch.empty(L.n_params, device="cuda")
+    api.rl_ppo_loss_grad(L.ctx, d["obs"], d["actions"], d["logp_old"], d["mu_old"], d["log_std_old"], d["v_old"],
+                         d["adv"], d["ret"], g)
+    torch.cuda.synchronize()
+    assert api.rl_last_device_status(L.ctx) == 0
+    p = OM.unflatten(params, O, hidden, 12)
+    _, gr, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
+                                b["v_old"], b["adv"], b["ret"])
+    errs = _per_tensor_err(g.cpu().numpy(), OP.flat_grad(gr), (O, hidden, 12), rel_err2)
+    assert max(errs.values()) < TOL_BF16, errs
+    L.train_iteration(use_graph=True)
+    torch.cuda.synchronize()
+    assert api.rl_last_device_status(L.ctx) == 0
+    L.close()
+
+
+def test_set_gemm_tiles_rejects_invalid():
+    w = workload("tiny", precision=1)
+    L, _, _, _ = _setup(w)
+    for args in ((3, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 4, 1), (0, 9, 64, 1, 1),
+                 (2, 0, 64, 1, 0)):
+        with pytest.raises(api.RLError):
+            api.rl_set_gemm_tiles(L.ctx, *args)
+    L.close()
