@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the grouped-learner and 16384-robot lines")
     ap.add_argument("--sweep", action="store_true", help="HBM size sweep of the env-step and GAE kernels (one JSON line per size)")
+    ap.add_argument("--tiles-out", default=None, help="write the full autotune report (every trial) to this JSON file")
+    ap.add_argument("--tiles", default=None,
+                    help="apply the GEMM tile shapes of a saved autotune report instead of autotuning (for profiler runs, "
+                         "where serialised launches would distort the autotuner's timings)")
     return ap.parse_args()
 
 
@@ -351,6 +355,24 @@ def run_reference(args):
     return 0
 
 
+def select_tiles(api, L, args):
+    """Autotune the update's GEMM sites (default) or apply the shapes of a saved report."""
+    site_id = {"forward": 0, "input_grad": 1, "weight_grad": 2}
+    if args.tiles:
+        with open(args.tiles) as f:
+            rep = json.load(f)
+        rep = rep.get("autotune", rep)
+        for s in rep["sites"]:
+            api.rl_set_gemm_tiles(L.ctx, site_id[s["site"]], s["layer"], s["bn"], s.get("cluster", 1), s["splits"])
+        return {"sites": rep["sites"], "source": f"applied from {os.path.basename(args.tiles)}"}
+    rep = api.rl_autotune(L.ctx)
+    rep["source"] = "autotuned in this run"
+    if args.tiles_out:
+        with open(args.tiles_out, "w") as f:
+            json.dump(rep, f, indent=1)
+    return rep
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -374,7 +396,7 @@ def main():
 
     # --- BF16 form: the headline --------------------------------------------------------
     L, O = make_learner(api, synth, api.RL_BF16, seed=1000 * rank)
-    tuned = api.rl_autotune(L.ctx)          # tile widths / split counts of every update GEMM site
+    tuned = select_tiles(api, L, args)      # tile widths / clusters / split counts of every update GEMM site
     api.rl_profile_enable(L.ctx, 0, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     # untimed: build the graph once and count the launches of one iteration
@@ -449,7 +471,7 @@ def main():
                       "l2": "flushed (256 MB write) between timed iterations", "graph": "one CUDA graph per iteration",
                       "per_step_ms": [round(t, 4) for t in times]},
            "roofline": roof, "gpu_launches": launches * args.steps, "launches_per_step": launches,
-           "autotune": tuned,
+           "autotune": {k: tuned[k] for k in ("sites", "clusters_of_2_resident", "source") if k in tuned},
            "e2e": e2e, "clocks": clk, "device_status": status}
     if compare:
         out["compare"] = compare

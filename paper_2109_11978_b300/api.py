@@ -160,7 +160,7 @@ def rl_autotune(ctx):
     """Times the update's GEMM sites over candidate tile shapes and keeps the fastest; returns the
     report (dict)."""
     import json
-    buf = ctypes.create_string_buffer(8192)
+    buf = ctypes.create_string_buffer(65536)
     check(lib().rl_autotune(ctx, buf, len(buf), _stream()), "rl_autotune")
     return json.loads(buf.value.decode() or "{}")
 

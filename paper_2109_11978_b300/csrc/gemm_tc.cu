@@ -728,6 +728,14 @@ cudaError_t tc_prepare() {
     return e;
 }
 
+int tc_cluster_fit(int bn, int epi, int cm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const int bi = bn_index(bn), ci = cm_index(cm);
+    if (bi < 0 || ci < 0 || epi < 0 || epi > 2) return 0;
+    return g_fit[dev].clusters[bi][epi][ci];
+}
+
 int tc_smem_bytes(int bn, int epi) {
     switch (bn) {
         case 64: return epi == EPI_STORE ? TileCfg<64, EPI_STORE>::SMEM : TileCfg<64, EPI_BIAS_ELU>::SMEM;

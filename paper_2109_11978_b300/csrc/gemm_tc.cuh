@@ -32,6 +32,7 @@ struct TcParams {
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 int tc_smem_bytes(int bn, int epi);
+int tc_cluster_fit(int bn, int epi, int cm);   // clusters resident at once (after tc_prepare)
 cudaError_t tc_prepare();
 
 }  // namespace rl

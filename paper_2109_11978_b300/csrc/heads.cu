@@ -455,9 +455,7 @@ static void loss_prepare() {
 // Dynamic shared-memory limits of every loss-head instantiation, set once before any launch
 // (and so before any stream capture).
 void heads_prepare() {
-    loss_prepare<true, 64, 128>();
-    loss_prepare<true, 128, 128>();
-    loss_prepare<true, 256, 64>();
+    loss_mma_prepare();
     loss_prepare<false, 64, 128>();
     loss_prepare<false, 128, 128>();
     loss_prepare<false, 256, 64>();
@@ -466,17 +464,16 @@ void heads_prepare() {
 // 128 rows per block (64 when the last hidden layer is 256 wide, to fit the tiles).
 int loss_head_rows(int H) { return H >= 256 ? 64 : 128; }
 
-int loss_head_blocks(int M, int H) { return (M + loss_head_rows(H) - 1) / loss_head_rows(H); }
+int loss_head_blocks(int M, int H, int bf16) {
+    const int rows = bf16 ? loss_mma_rows() : loss_head_rows(H);
+    return (M + rows - 1) / rows;
+}
 
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
     if (p.A > MAX_A || !(p.H == 64 || p.H == 128 || p.H == 256)) return cudaErrorInvalidValue;
-    if (p.nblocks < loss_head_blocks(p.M, p.H)) return cudaErrorInvalidValue;
-    if (p.bf16) {
-        if (p.H == 64) return loss_dispatch<true, 64, 128>(p, s);
-        if (p.H == 128) return loss_dispatch<true, 128, 128>(p, s);
-        return loss_dispatch<true, 256, 64>(p, s);
-    }
+    if (p.nblocks != loss_head_blocks(p.M, p.H, p.bf16)) return cudaErrorInvalidValue;
+    if (p.bf16) return launch_loss_mma(p, s);    // tensor-core form (loss_mma.cu)
     if (p.H == 64) return loss_dispatch<false, 64, 128>(p, s);
     if (p.H == 128) return loss_dispatch<false, 128, 128>(p, s);
     return loss_dispatch<false, 256, 64>(p, s);

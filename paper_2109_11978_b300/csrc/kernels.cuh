@@ -100,7 +100,11 @@ struct HeadParams {
 __host__ __device__ inline int head_part_floats(int A, int H) { return A * H + 2 * A + H + 1 + 2 * H + 8; }
 cudaError_t launch_act_head(const HeadParams& p, cudaStream_t s);
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s);
-int loss_head_blocks(int M, int H);
+int loss_head_blocks(int M, int H, int bf16);   // blocks (= partial slots) of one loss-head launch
+// BF16 loss head on warp-level tensor-core MMAs (loss_mma.cu)
+int loss_mma_rows();
+cudaError_t loss_mma_prepare();
+cudaError_t launch_loss_mma(const HeadParams& p, cudaStream_t s);
 void heads_prepare();
 
 // Device scalar block (floats): alpha, kl, adam step (as float bits of int), ...

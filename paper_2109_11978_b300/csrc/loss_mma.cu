@@ -1,0 +1,500 @@
+// BF16 form of the loss head (Sec. 2.2, Table 3, Algorithm 1): the heads' forward, the
+// per-sample clipped-surrogate / clipped-value loss, and the backward through the heads, with
+// the three small products on the warp-level tensor-core MMA
+// (mma.sync m16n8k16, bf16 operands, fp32 accumulation), 64 rows per block (4 warps x 16):
+//
+//   mu  = H_a Wa^T + ba        [64 x 12]    (actor; V = H_c Wc^T + bc the same way, one column)
+//   dWa = G^T H_a              [12 x H]     G = d loss / d mu, per row
+//   dH_a = (G Wa) * ELU'(H_a)  [64 x H]     (critic: dH_c = g_v Wc * ELU'(H_c), elementwise)
+//
+// The last hidden activations are bf16 already; the fp32 operands (head weights, G) are split
+// into a bf16 high part and a bf16 remainder, and the products hi*hi + hi*lo + lo*hi (weights:
+// hi + lo against exact bf16 activations) carry about 16 bits of each operand, which keeps the
+// result at fp32 level.  Per-row work (log pi, ratio, clipping, KL) runs one thread per row in
+// fp32.  The per-block partials and the last block's statistics / Algorithm 1 step follow the
+// same layout and order as the FP32 kernel.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rl {
+
+namespace {
+
+constexpr int MAX_A = 12;
+constexpr float HALF_LOG_2PI = 0.91893853320467274f;
+constexpr int ROWS = 64;                  // rows per block (4 warps x 16)
+constexpr int THREADS = 128;
+constexpr int NW = THREADS / 32;
+constexpr int GP = 24;                    // bf16 pitch of the [row][16] G tiles and [H][16] WaT tiles
+constexpr int FP = 17;                    // fp32 pitch of the [row][16] mu / G tiles
+constexpr int RP = 17;                    // per-row records: surr, vloss, kl, clip, g_ls[12]
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x2(const void* p, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+
+// D += A B, A 16 x 16 (row-major fragments), B 16 x 8 (column-major fragments), fp32 accumulators.
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes 0 fills the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// fp32 -> bf16 high part and bf16 remainder (x - hi rounded again)
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+template <int H>
+struct Smem {
+    static constexpr int HP = H + 8;                          // bf16 pitch of the [row][H] tiles
+    // bf16 regions (element offsets)
+    static constexpr int HA = 0;                              // [ROWS][HP] actor h, then dY_a
+    static constexpr int HC = HA + ROWS * HP;                 // [ROWS][HP] critic h, then dY_c
+    static constexpr int WA_HI = HC + ROWS * HP;              // [16][HP] Wa (rows j >= A zero)
+    static constexpr int WA_LO = WA_HI + 16 * HP;
+    static constexpr int WC_HI = WA_LO + 16 * HP;             // [8][HP] Wc in row 0
+    static constexpr int WC_LO = WC_HI + 8 * HP;
+    static constexpr int WAT_HI = WC_LO + 8 * HP;             // [H][GP] Wa^T
+    static constexpr int WAT_LO = WAT_HI + H * GP;
+    static constexpr int G_HI = WAT_LO + H * GP;              // [ROWS][GP] G
+    static constexpr int G_LO = G_HI + ROWS * GP;
+    static constexpr int BF16_END = G_LO + ROWS * GP;
+    // fp32 regions (float offsets from the end of the bf16 part, 16-byte aligned)
+    static constexpr int F0 = (BF16_END * 2 + 15) / 16 * 4;
+    // mu / V rows and the per-row records share one [ROWS][17] area: the row's thread reads
+    // its mu row before it writes its record row
+    static constexpr int MU = F0;                             // [ROWS][FP]: mu (12) and V at 12
+    static constexpr int REC = MU;                            // [ROWS][RP]
+    static constexpr int G = MU + ROWS * FP;                  // [ROWS][FP]: g_mu (12) and g_v at 12
+    // fp32 copies of Wa [A][H] and Wc [H] as loaded, split into the bf16 tiles before the mu /
+    // G rows are first written (they share the area)
+    static constexpr int WST = MU;
+    static constexpr int WST_END = WST + (2 * ROWS * FP > 13 * H ? 2 * ROWS * FP : 13 * H);
+    static constexpr int WCF = WST_END;                       // [H] Wc fp32
+    static constexpr int CST = WCF + H;                       // [64] log-std constants
+    static constexpr int FLOATS = CST + 64;
+    static constexpr int BYTES = FLOATS * 4;
+};
+
+template <int H>
+__global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
+    using S = Smem<H>;
+    constexpr int HP = S::HP;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(sm_raw);
+    float* sf = reinterpret_cast<float*>(sm_raw);
+    __nv_bfloat16* ha = sb + S::HA;
+    __nv_bfloat16* hc = sb + S::HC;
+    float* mu_s = sf + S::MU;
+    float* g_s = sf + S::G;
+    float* recs = sf + S::REC;
+    float* wcf = sf + S::WCF;
+    float* cst = sf + S::CST;
+    const int A = p.A;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;                  // mma fragment row group / column pair
+    const int m0 = blockIdx.x * ROWS;
+    const int rows = max(0, min(ROWS, p.M - m0));
+
+    // ---- per-row inputs of the loss, issued first (their latency overlaps the staging)
+    const bool row_thread = tid < ROWS;
+    const bool live = row_thread && tid < rows;
+    float aold[MAX_A], muold[MAX_A], lpo = 0.f, adv = 0.f, vo = 0.f, R = 0.f;
+#pragma unroll
+    for (int j = 0; j < MAX_A; ++j) aold[j] = muold[j] = 0.f;
+    if (live) {
+        const int m = m0 + tid;
+        const int s = p.idx ? __ldg(p.idx + m) : m;
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j)
+            if (j < A) {
+                aold[j] = __ldg(p.a_old + (size_t)s * A + j);
+                muold[j] = __ldg(p.mu_old + (size_t)s * A + j);
+            }
+        lpo = __ldg(p.logp_old + s);
+        adv = __ldg(p.adv + s);
+        vo = __ldg(p.v_old + s);
+        R = __ldg(p.ret + s);
+    }
+    // ---- stage (asynchronous 16-byte copies): h tiles (zeros past M), fp32 head weights
+    {
+        const __nv_bfloat16* ga = reinterpret_cast<const __nv_bfloat16*>(p.ha) + (size_t)m0 * H;
+        const __nv_bfloat16* gc = reinterpret_cast<const __nv_bfloat16*>(p.hc) + (size_t)m0 * H;
+        constexpr int VPR = H / 8;                            // 16-byte vectors per row
+        for (int v = tid; v < ROWS * VPR; v += THREADS) {
+            const int r = v / VPR, c = (v % VPR) * 8;
+            const int rr = r < rows ? r : 0;                  // a valid address; zero-filled
+            cp_async16(ha + r * HP + c, ga + (size_t)rr * H + c, r < rows ? 16 : 0);
+            cp_async16(hc + r * HP + c, gc + (size_t)rr * H + c, r < rows ? 16 : 0);
+        }
+        float* wst = sf + S::WST;
+        for (int v = tid; v < A * H / 4; v += THREADS) cp_async16(wst + 4 * v, p.Wa + 4 * v, 16);
+        for (int v = tid; v < H / 4; v += THREADS) cp_async16(wcf + 4 * v, p.Wc + 4 * v, 16);
+    }
+    if (tid < A) {
+        const float ls = p.log_std[tid], lso = p.log_std_old[tid];
+        cst[tid] = ls;
+        cst[16 + tid] = expf(-2.f * ls);
+        cst[32 + tid] = expf(2.f * lso);
+        cst[48 + tid] = lso;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // weights -> bf16 hi / lo tiles (Wa rows j >= A and Wc rows 1..7 zero)
+    {
+        const float* wst = sf + S::WST;
+        for (int i = tid; i < 16 * H; i += THREADS) {
+            const int j = i / H, k = i % H;
+            const float w = j < A ? wst[j * H + k] : 0.f;
+            __nv_bfloat16 hi, lo;
+            split_bf16(w, hi, lo);
+            sb[S::WA_HI + j * HP + k] = hi;
+            sb[S::WA_LO + j * HP + k] = lo;
+            sb[S::WAT_HI + k * GP + j] = hi;
+            sb[S::WAT_LO + k * GP + j] = lo;
+        }
+        for (int i = tid; i < 8 * H; i += THREADS) {
+            const int j = i / H, k = i % H;
+            const float w = j == 0 ? wcf[k] : 0.f;
+            __nv_bfloat16 hi, lo;
+            split_bf16(w, hi, lo);
+            sb[S::WC_HI + j * HP + k] = hi;
+            sb[S::WC_LO + j * HP + k] = lo;
+        }
+    }
+    __syncthreads();
+
+    static_assert(FP == RP, "mu rows and records share their rows");
+    // ---- heads forward: warp w owns rows 16 w .. 16 w + 15
+    {
+        const int r0 = 16 * warp;
+        float acc[2][4] = {}, accv[4] = {};
+#pragma unroll
+        for (int ks = 0; ks < H / 16; ++ks) {
+            const int k0 = 16 * ks;
+            uint32_t a[4], c[4];
+            ldsm_x4(ha + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), a[0], a[1], a[2], a[3]);
+            ldsm_x4(hc + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), c[0], c[1], c[2], c[3]);
+            // B = Wa^T: fragment rows are Wa rows j (n), columns k
+            const int bn = (lane & 7) + 8 * (lane >> 4), bk = k0 + 8 * ((lane >> 3) & 1);
+            uint32_t bh[4], bl[4];
+            ldsm_x4(sb + S::WA_HI + bn * HP + bk, bh[0], bh[1], bh[2], bh[3]);
+            ldsm_x4(sb + S::WA_LO + bn * HP + bk, bl[0], bl[1], bl[2], bl[3]);
+            mma16816(acc[0], a, bh[0], bh[1]);
+            mma16816(acc[0], a, bl[0], bl[1]);
+            mma16816(acc[1], a, bh[2], bh[3]);
+            mma16816(acc[1], a, bl[2], bl[3]);
+            uint32_t ch0, ch1, cl0, cl1;
+            const int cn = lane & 7, ck = k0 + 8 * ((lane >> 3) & 1);
+            ldsm_x2(sb + S::WC_HI + cn * HP + ck, ch0, ch1);
+            ldsm_x2(sb + S::WC_LO + cn * HP + ck, cl0, cl1);
+            mma16816(accv, c, ch0, ch1);
+            mma16816(accv, c, cl0, cl1);
+        }
+        // fragments -> [row][16] fp32 (mu columns 0..15, V from column 0 of the critic tile)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int r = r0 + gq + 8 * h2;
+                mu_s[r * FP + 8 * nt + 2 * tq] = acc[nt][2 * h2];
+                mu_s[r * FP + 8 * nt + 2 * tq + 1] = acc[nt][2 * h2 + 1];
+            }
+        if (tq == 0) {
+            mu_s[(r0 + gq) * FP + 12] = accv[0];
+            mu_s[(r0 + gq + 8) * FP + 12] = accv[2];
+        }
+    }
+    __syncthreads();
+
+    // ---- per row: loss terms, d loss / d mu and d loss / d V
+    if (row_thread) {
+        const int r = tid;
+        float mu[MAX_A];
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) mu[j] = mu_s[r * FP + j] + (j < A ? p.ba[j] : 0.f);
+        const float v = mu_s[r * FP + 12] + p.bc[0];
+        float logp = 0.f, kl = 0.f, diff[MAX_A];
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j) {
+            diff[j] = 0.f;
+            if (j < A && live) {
+                const float ls = cst[j], iv = cst[16 + j];
+                diff[j] = aold[j] - mu[j];
+                logp += -0.5f * diff[j] * diff[j] * iv - ls - HALF_LOG_2PI;
+                const float dm = muold[j] - mu[j];
+                kl += ls - cst[48 + j] + 0.5f * (cst[32 + j] + dm * dm) * iv - 0.5f;
+            }
+        }
+        const float inv_M = 1.0f / (float)p.M;
+        const float ratio = expf(logp - lpo);
+        const float s1 = ratio * adv;
+        const float s2 = fminf(fmaxf(ratio, 1.f - p.clip), 1.f + p.clip) * adv;
+        const float g_logp = -(s1 <= s2 ? adv : 0.f) * inv_M * ratio;
+        const float dv = v - vo;
+        const float vclip = vo + fminf(fmaxf(dv, -p.clip), p.clip);
+        const float u = (v - R) * (v - R), w = (vclip - R) * (vclip - R);
+        float g_v = p.value_coef * inv_M * (u >= w ? 2.f * (v - R) : ((dv > -p.clip && dv < p.clip) ? 2.f * (vclip - R) : 0.f));
+        if (!live) g_v = 0.f;
+        float* rc = recs + r * RP;
+        rc[0] = live ? fminf(s1, s2) : 0.f;
+        rc[1] = live ? fmaxf(u, w) : 0.f;
+        rc[2] = live ? kl : 0.f;
+        rc[3] = (live && fabsf(ratio - 1.f) > p.clip) ? 1.f : 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float g = 0.f;
+            if (j < MAX_A) {
+                const float iv = j < A ? cst[16 + j] : 0.f;
+                g = (live && j < A) ? g_logp * diff[j] * iv : 0.f;
+                rc[4 + j] = (live && j < A) ? g_logp * (diff[j] * diff[j] * iv - 1.f) : 0.f;
+            }
+            if (j < 12) g_s[r * FP + j] = g;
+            __nv_bfloat16 hi, lo;
+            split_bf16(g, hi, lo);
+            sb[S::G_HI + r * GP + j] = hi;
+            sb[S::G_LO + r * GP + j] = lo;
+        }
+        g_s[r * FP + 12] = g_v;
+    }
+    __syncthreads();
+
+    // ---- head weight gradients: dWa = G^T H_a (MMA), dWc = g_v^T H_c, head bias gradients
+    const int PF = head_part_floats(A, H);
+    const int O_WA = 0, O_BA = A * H, O_LS = O_BA + A, O_WC = O_LS + A, O_BC = O_WC + H, O_DBA = O_BC + 1,
+              O_DBC = O_DBA + H, O_ST = O_DBC + H;
+    float* out = p.part + (size_t)blockIdx.x * PF;
+    {
+        // warp w: output columns [H/NW * w, H/NW * (w + 1)), two n-tiles of 8 per step
+        static_assert((H / NW) % 16 == 0, "whole n-tile pairs per warp");
+#pragma unroll
+        for (int np = 0; np < H / NW / 16; ++np) {
+            const int n0 = (H / NW) * warp + 16 * np;
+            float acc[2][4] = {};
+#pragma unroll
+            for (int ks = 0; ks < ROWS / 16; ++ks) {
+                const int k0 = 16 * ks;                       // rows
+                // A = G^T [j][row]: 8 x 8 blocks of G [row][j] loaded transposed; matrices
+                // (j 0-7, rows 0-7), (j 8-15, rows 0-7), (j 0-7, rows 8-15), (j 8-15, rows 8-15)
+                const int ar = k0 + (lane & 7) + 8 * (lane >> 4), aj = 8 * ((lane >> 3) & 1);
+                uint32_t ah[4], al[4];
+                ldsm_x4_t(sb + S::G_HI + ar * GP + aj, ah[0], ah[1], ah[2], ah[3]);
+                ldsm_x4_t(sb + S::G_LO + ar * GP + aj, al[0], al[1], al[2], al[3]);
+                // B = H_a [row][col], transposed 8 x 8 loads: (rows 0-7, cols 0-7), (rows 8-15,
+                // cols 0-7), (rows 0-7, cols 8-15), (rows 8-15, cols 8-15)
+                const int br = k0 + (lane & 7) + 8 * ((lane >> 3) & 1), bc = n0 + 8 * (lane >> 4);
+                uint32_t b[4];
+                ldsm_x4_t(ha + br * HP + bc, b[0], b[1], b[2], b[3]);
+                mma16816(acc[0], ah, b[0], b[1]);
+                mma16816(acc[0], al, b[0], b[1]);
+                mma16816(acc[1], ah, b[2], b[3]);
+                mma16816(acc[1], al, b[2], b[3]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int j = gq + 8 * h2;
+                    const int col = n0 + 8 * nt + 2 * tq;
+                    if (j < A) {
+                        out[O_WA + j * H + col] = acc[nt][2 * h2];
+                        out[O_WA + j * H + col + 1] = acc[nt][2 * h2 + 1];
+                    }
+                }
+        }
+    }
+    // critic head weight gradient: column k = sum over rows of g_v h_c[row][k]
+    for (int k = tid; k < H; k += THREADS) {
+        float a = 0.f;
+        for (int r = 0; r < ROWS; ++r) a += g_s[r * FP + 12] * __bfloat162float(hc[r * HP + k]);
+        out[O_WC + k] = a;
+    }
+    __syncthreads();
+
+    // ---- backward into the last hidden layer, in place: dY_a = (G Wa) * ELU'(H_a)
+    {
+        const int r0 = 16 * warp;
+        uint32_t gh[4], gl[4];
+        ldsm_x4(sb + S::G_HI + (r0 + (lane & 15)) * GP + 8 * (lane >> 4), gh[0], gh[1], gh[2], gh[3]);
+        ldsm_x4(sb + S::G_LO + (r0 + (lane & 15)) * GP + 8 * (lane >> 4), gl[0], gl[1], gl[2], gl[3]);
+#pragma unroll 2
+        for (int np = 0; np < H / 16; ++np) {
+            const int n0 = 16 * np;
+            // B = Wa [j][col]: column-major fragments over j, i.e. rows of Wa^T [col][j]
+            const int bn = n0 + (lane & 7) + 8 * (lane >> 4), bk = 8 * ((lane >> 3) & 1);
+            uint32_t wh[4], wl[4];
+            ldsm_x4(sb + S::WAT_HI + bn * GP + bk, wh[0], wh[1], wh[2], wh[3]);
+            ldsm_x4(sb + S::WAT_LO + bn * GP + bk, wl[0], wl[1], wl[2], wl[3]);
+            float acc[2][4] = {};
+            mma16816(acc[0], gh, wh[0], wh[1]);
+            mma16816(acc[0], gh, wl[0], wl[1]);
+            mma16816(acc[0], gl, wh[0], wh[1]);
+            mma16816(acc[1], gh, wh[2], wh[3]);
+            mma16816(acc[1], gh, wl[2], wl[3]);
+            mma16816(acc[1], gl, wh[2], wh[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int r = r0 + gq + 8 * h2;
+                    const int col = n0 + 8 * nt + 2 * tq;
+                    __nv_bfloat162* e = reinterpret_cast<__nv_bfloat162*>(ha + r * HP + col);
+                    const float2 hv = __bfloat1622float2(*e);
+                    *e = __floats2bfloat162_rn(acc[nt][2 * h2] * elu_grad_y(hv.x), acc[nt][2 * h2 + 1] * elu_grad_y(hv.y));
+                }
+        }
+    }
+    // critic: dY_c = g_v Wc * ELU'(H_c), two columns per thread step
+    for (int e2 = tid; e2 < ROWS * H / 2; e2 += THREADS) {
+        const int r = e2 / (H / 2), k = (e2 % (H / 2)) * 2;
+        const float gv = g_s[r * FP + 12];
+        __nv_bfloat162* e = reinterpret_cast<__nv_bfloat162*>(hc + r * HP + k);
+        const float2 hv = __bfloat1622float2(*e);
+        *e = __floats2bfloat162_rn(gv * wcf[k] * elu_grad_y(hv.x), gv * wcf[k + 1] * elu_grad_y(hv.y));
+    }
+    __syncthreads();
+
+    // ---- hidden bias gradients (column sums of the bf16 dY rows) and the block's statistics:
+    // items [0, H) actor columns, [H, 2H) critic columns, [2H, 2H + 29) record columns
+    for (int i = tid; i < 2 * H + 29; i += THREADS) {
+        if (i < 2 * H) {
+            const __nv_bfloat16* t = i < H ? ha : hc;
+            const int k = i < H ? i : i - H;
+            float sum = 0.f;
+            for (int r = 0; r < rows; ++r) sum += __bfloat162float(t[r * HP + k]);
+            out[(i < H ? O_DBA : O_DBC) + k] = sum;
+        } else {
+            // record column c: 0..3 loss terms, 4 g_v, 5..16 g_mu, 17..28 g_log_std
+            const int c = i - 2 * H;
+            const float* col = c < 4 ? recs + c : c == 4 ? g_s + 12 : c < 17 ? g_s + (c - 5) : recs + 4 + (c - 17);
+            const int pitch = (c >= 4 && c < 17) ? FP : RP;
+            float sum = 0.f;
+            for (int r = 0; r < ROWS; ++r) sum += col[r * pitch];
+            if (c < 4) out[O_ST + c] = sum;
+            else if (c == 4) out[O_BC] = sum;
+            else if (c < 17) { if (c - 5 < A) out[O_BA + c - 5] = sum; }
+            else if (c - 17 < A) out[O_LS + c - 17] = sum - (blockIdx.x == 0 ? p.entropy_coef : 0.f);
+        }
+    }
+    if (tid >= 4 && tid < 8) out[O_ST + tid] = 0.f;
+    // ---- gradient rows out (16-byte vectors)
+    {
+        constexpr int VPR = H / 8;
+        uint4* da = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.dya) + (size_t)m0 * H);
+        uint4* dc = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.dyc) + (size_t)m0 * H);
+        for (int v = tid; v < rows * VPR; v += THREADS) {
+            const int r = v / VPR, c = (v % VPR) * 8;
+            da[(size_t)r * VPR + c / 8] = *reinterpret_cast<const uint4*>(ha + r * HP + c);
+            dc[(size_t)r * VPR + c / 8] = *reinterpret_cast<const uint4*>(hc + r * HP + c);
+        }
+    }
+
+    // ---- last block: statistics, KL mean, Algorithm 1, Adam step count and bias corrections
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (warp != 0) return;
+    double st[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+        const float* q = p.part + (size_t)b * PF + O_ST;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[i] += (double)__ldcg(q + i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[i] += __shfl_xor_sync(0xffffffffu, st[i], o);
+    if (lane == 0) {
+        const float inv_M = 1.0f / (float)p.M;
+        float ent = 0.f;
+        for (int j = 0; j < A; ++j) ent += cst[j] + HALF_LOG_2PI + 0.5f;
+        const float kl = (float)st[2] * inv_M;
+        const float surr = -(float)st[0] * inv_M, vloss = (float)st[1] * inv_M;
+        const float loss = surr + p.value_coef * vloss - p.entropy_coef * ent;
+        float* sc = p.scal;
+        sc[SC_KL] = kl;
+        sc[SC_LOSS] = loss;
+        sc[SC_SURR] = surr;
+        sc[SC_VLOSS] = vloss;
+        sc[SC_ENT] = ent;
+        sc[SC_CLIPFRAC] = (float)st[3] * inv_M;
+        float alpha = sc[SC_ALPHA];
+        if (p.kl_target > 0.f) {
+            if (kl > 2.f * p.kl_target) alpha = fmaxf(p.lr_min, alpha / 1.5f);
+            else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
+            sc[SC_ALPHA] = alpha;
+        }
+        const float t = sc[SC_STEP] + 1.f;
+        sc[SC_STEP] = t;
+        const float bc1 = -expm1f(t * log1pf(-0.1f));
+        const float bc2 = -expm1f(t * log1pf(-0.001f));
+        sc[SC_STEPSIZE] = alpha / bc1;
+        sc[SC_INVSQRT_BC2] = 1.0f / sqrtf(bc2);
+        if (p.stats) {
+            p.stats[0] += loss; p.stats[1] += surr; p.stats[2] += vloss; p.stats[3] = ent;
+            p.stats[4] += kl; p.stats[5] = sc[SC_ALPHA]; p.stats[6] += sc[SC_CLIPFRAC]; p.stats[12] += 1.f;
+        }
+        *p.counter = 0u;
+    }
+}
+
+template <int H>
+cudaError_t mma_dispatch(const HeadParams& p, cudaStream_t s) {
+    loss_mma_kernel<H><<<p.nblocks, THREADS, Smem<H>::BYTES, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int loss_mma_rows() { return ROWS; }
+
+cudaError_t loss_mma_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(loss_mma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<64>::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(loss_mma_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(loss_mma_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::BYTES);
+    return e;
+}
+
+cudaError_t launch_loss_mma(const HeadParams& p, cudaStream_t s) {
+    // 16-byte copies of the head weights and of the h rows
+    if ((reinterpret_cast<uintptr_t>(p.Wa) | reinterpret_cast<uintptr_t>(p.Wc) | reinterpret_cast<uintptr_t>(p.ha) |
+         reinterpret_cast<uintptr_t>(p.hc)) & 15u)
+        return cudaErrorMisalignedAddress;
+    if ((p.A * p.H) % 4) return cudaErrorInvalidValue;
+    if (p.H == 64) return mma_dispatch<64>(p, s);
+    if (p.H == 128) return mma_dispatch<128>(p, s);
+    if (p.H == 256) return mma_dispatch<256>(p, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rl

@@ -583,12 +583,18 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     rl_status st = RL_OK;
     report = "{\"sites\": [";
     bool first = true;
+    std::string trials;
     auto note = [&](const char* site, int l, int bn, int cm, int S, float ms) {
         std::snprintf(buf, sizeof(buf),
                       "%s{\"site\": \"%s\", \"layer\": %d, \"bn\": %d, \"cluster\": %d, \"splits\": %d, \"us\": %.2f}",
                       first ? "" : ", ", site, l, bn, cm, S, ms * 1000.f);
         report += buf;
         first = false;
+    };
+    auto trial = [&](const char* site, int l, int bn, int cm, int S, float ms) {
+        std::snprintf(buf, sizeof(buf), "%s[\"%s\", %d, %d, %d, %d, %.2f]", trials.empty() ? "" : ", ", site, l, bn, cm, S,
+                      ms * 1000.f);
+        trials += buf;
     };
     const int bns[3] = {64, 128, 256};
     const int cms[2] = {1, 2};
@@ -607,6 +613,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                     if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
                     float ms = 0.f;
                     st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2); }, ms);
+                    if (st == RL_OK) trial("forward", l, bn, cm, 1, ms);
                     if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; }
                 }
             c->bn_fwd[l] = best_bn;
@@ -625,6 +632,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
                         float ms = 0.f;
                         st = timed([&] { return dx_layer(c, q, l, c->Mb); }, ms);
+                        if (st == RL_OK) trial("input_grad", l, bn, cm, 1, ms);
                         if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; }
                     }
                 c->bn_dx[l] = best_bn;
@@ -656,6 +664,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                         if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
                         float ms = 0.f;
                         st = timed([&] { return dw_layer(c, q, l, c->Mb); }, ms);
+                        if (st == RL_OK) trial("weight_grad", l, bn, cm, Sr, ms);
                         if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; best_S = Sr; best_kc = kc; }
                     }
                 }
@@ -670,7 +679,12 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    report += "]}";
+    report += "], \"trials_site_layer_bn_cluster_splits_us\": [" + trials + "]";
+    if (c->bf16) {
+        std::snprintf(buf, sizeof(buf), ", \"clusters_of_2_resident\": %d", tc_cluster_fit(256, EPI_BIAS_ELU, 2));
+        report += buf;
+    }
+    report += "}";
     if (st != RL_OK) return st;
     build_adam(c);
     drop_graph(c);
@@ -934,7 +948,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
             if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->gb_parts * Li.out));
         }
     }
-    c->head_blocks = loss_head_blocks(c->Mb, c->HL);
+    c->head_blocks = loss_head_blocks(c->Mb, c->HL, c->bf16 ? 1 : 0);
     CK(dalloc(c, &c->head_part, sizeof(float) * (size_t)c->head_blocks * head_part_floats(c->A, c->HL)));
     if (c->bf16) {
         for (int n = 0; n < 2; ++n)
