@@ -155,15 +155,13 @@ def make_learner(api, synth, precision, seed, w=WORKLOAD):
     return api.Learner(cfg, hf, params), O
 
 
-def time_iterations(torch, L, steps, warmup, flush, profile=False):
+def time_iterations(torch, L, steps, warmup, flush):
     """Per-iteration CUDA-event time (ms) of `steps` graph replays after `warmup`, with an L2
     flush (a 256 MB write) between iterations outside the timed events."""
-    from paper_2109_11978_b300 import api
     s = torch.cuda.current_stream()
     for _ in range(warmup):
         L.train_iteration(use_graph=True)
     torch.cuda.synchronize()
-    times, gemm_ms, gemm_n = [], 0.0, 0
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for i in range(steps):
@@ -171,14 +169,28 @@ def time_iterations(torch, L, steps, warmup, flush, profile=False):
         e0[i].record(s)
         L.train_iteration(use_graph=True)
         e1[i].record(s)
-        if profile:
-            e1[i].synchronize()
-            ms, n = api.rl_profile_read(L.ctx)
-            gemm_ms += ms
-            gemm_n += n
     torch.cuda.synchronize()
-    times = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    return times, gemm_ms, gemm_n
+    return [a.elapsed_time(b) for a, b in zip(e0, e1)]
+
+
+def profile_iterations(torch, api, L, steps, flush):
+    """In-graph CUDA-event time per kernel class (ms per iteration, launches per iteration) over
+    `steps` replays of the graph rebuilt with event nodes around every launch; a separate run from
+    the timed one, since the events themselves cost time."""
+    api.rl_profile_enable(L.ctx, api.RL_PROF_ALL, True)
+    L.train_iteration(use_graph=True)          # capture the graph with the event nodes
+    torch.cuda.synchronize()
+    acc = {name: [0.0, 0] for name in api.RL_PROF_NAMES}
+    for _ in range(steps):
+        flush.zero_()
+        L.train_iteration(use_graph=True)
+        torch.cuda.synchronize()
+        for cls, name in enumerate(api.RL_PROF_NAMES):
+            ms, n = api.rl_profile_read_class(L.ctx, cls)
+            acc[name][0] += ms
+            acc[name][1] += n
+    api.rl_profile_enable(L.ctx, api.RL_PROF_ALL, False)
+    return {name: {"ms_per_iteration": v[0] / steps, "launches_per_iteration": v[1] / steps} for name, v in acc.items()}
 
 
 GROUP_SIZES = (512, 1024, 1536, 2048, 3072, 4096, 6144, 8192)
@@ -222,7 +234,7 @@ def large_config(torch, api, synth, steps=3, warmup=2):
     L, O = make_learner(api, synth, api.RL_BF16, seed=40, w=w)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     L.train_iteration(use_graph=True)
-    times, _, _ = time_iterations(torch, L, steps, warmup, flush)
+    times = time_iterations(torch, L, steps, warmup, flush)
     status = api.rl_last_device_status(L.ctx)
     L.close()
     return {"num_envs": 16384, "ms_per_step": sum(times) / len(times),
@@ -397,7 +409,6 @@ def main():
     # --- BF16 form: the headline --------------------------------------------------------
     L, O = make_learner(api, synth, api.RL_BF16, seed=1000 * rank)
     tuned = select_tiles(api, L, args)      # tile widths / clusters / split counts of every update GEMM site
-    api.rl_profile_enable(L.ctx, 0, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     # untimed: build the graph once and count the launches of one iteration
     L.train_iteration(use_graph=True)
@@ -408,7 +419,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    times, gemm_ms, gemm_n = time_iterations(torch, L, args.steps, args.warmup, flush, profile=True)
+    times = time_iterations(torch, L, args.steps, args.warmup, flush)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -417,15 +428,18 @@ def main():
     status = api.rl_last_device_status(L.ctx)
     value = whole_job_rate(world, N, T, args.steps, total_ms)
 
-    # dominant kernel: the tcgen05 GEMMs (sum of their in-graph event times)
+    # per-class in-graph kernel times (separate, profiled run); dominant kernel: the tcgen05 GEMMs
+    breakdown = profile_iterations(torch, api, L, min(args.steps, 5), flush)
+    gemm_ms = breakdown["gemm"]["ms_per_iteration"]
+    gemm_n = breakdown["gemm"]["launches_per_iteration"]
     flops_iter = gemm_flops_per_iteration(w, O)
-    achieved = flops_iter * args.steps / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else None
+    achieved = flops_iter / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else None
     peak = peaks.get("bf16_tflops_sustained", 1400.0)
     roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (all MLP GEMM launches of the iteration)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": f"bf16_tflops_sustained ({peak_src})", "gemm_launches_per_iteration": gemm_n / max(args.steps, 1),
-            "gemm_share_of_step": gemm_ms / total_ms if total_ms else None,
+            "peak_source": f"bf16_tflops_sustained ({peak_src})", "gemm_launches_per_iteration": gemm_n,
+            "gemm_share_of_step": gemm_ms / (total_ms / args.steps) if total_ms else None,
             "algorithmic_flops_per_iteration": flops_iter}
 
     # --- end to end through the public API: stats read back to pinned host memory each step
@@ -449,7 +463,7 @@ def main():
         Lf, _ = make_learner(api, synth, api.RL_FP32, seed=1000 * rank)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         Lf.train_iteration(use_graph=True)
-        ft, _, _ = time_iterations(torch, Lf, args.fp32_steps, 1, flush)
+        ft = time_iterations(torch, Lf, args.fp32_steps, 1, flush)
         fv = N * T * len(ft) / (sum(ft) / 1000.0)
         compare = {"fp32_env_steps_per_s": fv, "fp32_ms_per_step": sum(ft) / len(ft), "bf16_over_fp32": value / world / fv,
                    "note": "same workload, FP32 CUDA-core GEMMs; both forms pass their oracle tolerances "
@@ -470,7 +484,8 @@ def main():
                       "minibatch": N * T // w["minibatches"], "parallelism": f"replicas x{world}",
                       "l2": "flushed (256 MB write) between timed iterations", "graph": "one CUDA graph per iteration",
                       "per_step_ms": [round(t, 4) for t in times]},
-           "roofline": roof, "gpu_launches": launches * args.steps, "launches_per_step": launches,
+           "roofline": roof, "kernel_breakdown_in_graph": breakdown,
+           "gpu_launches": launches * args.steps, "launches_per_step": launches,
            "autotune": {k: tuned[k] for k in ("sites", "clusters_of_2_resident", "source") if k in tuned},
            "e2e": e2e, "clocks": clk, "device_status": status}
     if compare:

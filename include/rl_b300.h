@@ -264,13 +264,26 @@ rl_status rl_get_storage(rl_ctx* ctx, int32_t which, void** ptr, size_t* bytes);
  * bounded wait that ran out, RL_ERR_STATE for an out-of-range index).  Synchronises. */
 rl_status rl_last_device_status(rl_ctx* ctx);
 
-/* Timing of the dominant kernel class inside rl_train_iteration: enable records CUDA events
- * around every launch of class `kernel_class` (0 = update GEMMs) on the launching stream;
- * read returns the summed event time in ms and the launch count of the last iteration and
- * resets them.  Event recording is captured into the graph when the graph is built after
- * enabling. */
+/* In-graph timing of the kernels of rl_train_iteration, by class: RL_PROF_GEMM (every MLP GEMM,
+ * rollout and update), RL_PROF_LOSS (loss head), RL_PROF_ADAM, RL_PROF_ENV (env step),
+ * RL_PROF_ACT (action head), RL_PROF_GATHER (minibatch gather), RL_PROF_OTHER (GAE,
+ * permutation, bookkeeping); RL_PROF_ALL selects every class.  enable (on != 0) adds the class
+ * to the recorded set, on == 0 removes it; CUDA events are then recorded around each launch of
+ * a recorded class on the launching stream (captured into the graph, which is rebuilt on next
+ * use).  Events perturb the timing they measure, so time throughput with profiling off.
+ * rl_profile_read: summed event time (ms) and launch count over every recorded class, for the
+ * last iteration; rl_profile_read_class: the same for one class.  Both synchronise. */
+#define RL_PROF_GEMM 0
+#define RL_PROF_LOSS 1
+#define RL_PROF_ADAM 2
+#define RL_PROF_ENV 3
+#define RL_PROF_ACT 4
+#define RL_PROF_GATHER 5
+#define RL_PROF_OTHER 6
+#define RL_PROF_ALL 7
 rl_status rl_profile_enable(rl_ctx* ctx, int32_t kernel_class, int32_t on);
 rl_status rl_profile_read(rl_ctx* ctx, float* total_ms, int32_t* launches);
+rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_ms, int32_t* launches);
 
 /* Tile autotuner: times each GEMM site of the update (per hidden layer: forward, input gradient,
  * weight gradient; actor and critic in one launch; minibatch rows) over candidate tile widths

@@ -19,6 +19,8 @@ RL_ERR_OOM = -6
 RL_ERR_UNSUPPORTED = -7
 RL_FP32 = 0
 RL_BF16 = 1
+RL_PROF_GEMM, RL_PROF_LOSS, RL_PROF_ADAM, RL_PROF_ENV, RL_PROF_ACT, RL_PROF_GATHER, RL_PROF_OTHER, RL_PROF_ALL = range(8)
+RL_PROF_NAMES = ("gemm", "loss_head", "adam", "env_step", "act_head", "gather", "other")
 RL_NF = 57
 RL_NI = 3
 RL_NSTATS = 16
@@ -79,6 +81,7 @@ SIGNATURES = {
     "rl_last_device_status": (_i32, [_vp]),
     "rl_profile_enable": (_i32, [_vp, _i32, _i32]),
     "rl_profile_read": (_i32, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_i32)]),
+    "rl_profile_read_class": (_i32, [_vp, _i32, ctypes.POINTER(_f32), ctypes.POINTER(_i32)]),
     "rl_launches_per_iteration": (_i32, [_vp]),
     "rl_autotune": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t, _vp]),
     "rl_set_gemm_tiles": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),

@@ -11,6 +11,8 @@ import torch
 
 from . import _native as N
 from ._native import RLError, check, default_config, lib  # noqa: F401
+from ._native import (RL_PROF_ACT, RL_PROF_ADAM, RL_PROF_ALL, RL_PROF_ENV, RL_PROF_GATHER, RL_PROF_GEMM,  # noqa: F401
+                      RL_PROF_LOSS, RL_PROF_NAMES, RL_PROF_OTHER)
 
 RL_FP32, RL_BF16, RL_NF, RL_NI, RL_NSTATS = N.RL_FP32, N.RL_BF16, N.RL_NF, N.RL_NI, N.RL_NSTATS
 
@@ -148,6 +150,12 @@ def rl_last_device_status(ctx):
 
 def rl_profile_enable(ctx, kernel_class=0, on=True):
     check(lib().rl_profile_enable(ctx, int(kernel_class), int(bool(on))), "rl_profile_enable")
+
+
+def rl_profile_read_class(ctx, kernel_class):
+    ms, n = ctypes.c_float(), ctypes.c_int32()
+    check(lib().rl_profile_read_class(ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)), "rl_profile_read_class")
+    return ms.value, n.value
 
 
 def rl_profile_read(ctx):

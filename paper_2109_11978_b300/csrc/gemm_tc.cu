@@ -7,10 +7,10 @@
 //
 // The MLP products map onto it as
 //   forward  H_l = ELU(H_{l-1} W_l^T + b_l):    A = H_{l-1} [rows][in],  B = W_l [out][in]
-//   input    dY_{l-1} = (dY_l W_l) * ELU'(H):   A = dY_l [rows][out],    B = W_l^T [in][out]
+//   input    dY_{l-1} = (dY_l W_l) * ELU'(H):   A = dY_l [rows][out],    B^T = W_l [out][in]
 //   weight   dW_l = dY_l^T H_{l-1}:             A^T = dY_l [rows][out],  B^T = H_{l-1} [rows][in]
-// the weight gradient reading both operands MN-major (the row-major activations and gradients
-// as they are, K = the minibatch rows), so no transposed copy of any activation is kept.
+// where a transposed operand is read MN-major (the tensor-core descriptors take either form), so
+// every operand is used as it is stored and no transposed copy of any matrix is kept.
 //
 // Persistent CTA per SM, 576 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
 // swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
@@ -118,12 +118,12 @@ __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
-// A and B K-major (bits 15, 16 clear) or both MN-major (set), N >> 3 at bits 17-22, M >> 4 at
+// A MN-major at bit 15, B MN-major at bit 16 (clear: K-major), N >> 3 at bits 17-22, M >> 4 at
 // bits 24-28.
-template <int N, bool MN>
+template <int N, bool A_MN, bool B_MN>
 __device__ __forceinline__ uint32_t idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (MN ? (1u << 15) | (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (A_MN ? (1u << 15) : 0u) | (B_MN ? (1u << 16) : 0u) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -259,12 +259,14 @@ struct TileCfg {
 // accumulates each tile into one of two TMEM buffers (2 x BN columns) while the sixteen epilogue
 // warps drain the other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue
 // warp e reads TMEM lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
-template <int BN, int EPI, int CM, bool MN>
+template <int BN, int EPI, int CM, int MJ>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = TileCfg<BN, EPI>;
+    constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
+    constexpr bool B_MN = MJ != MAJ_K;                      // B^T [K][N] in memory
     constexpr int B_SLICE_ROWS = BN / CM;
-    constexpr int B_BOXES = MN ? BN / 64 / CM : 1;          // MN-major: 64-wide boxes per CTA
-    static_assert(!MN || (BN / 64) % CM == 0, "MN-major B tile must split into whole boxes");
+    constexpr int B_BOXES = B_MN ? BN / 64 / CM : 1;        // MN-major: 64-wide boxes per CTA
+    static_assert(!B_MN || (BN / 64) % CM == 0, "MN-major B tile must split into whole boxes");
     constexpr uint16_t MC_MASK = (uint16_t)((1u << CM) - 1u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -355,17 +357,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
                     mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
-                    if (!MN) {
+                    if (!A_MN) {
                         tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, ay);
+                    } else {
+                        // [K][M] source: two boxes of 64 M columns x 64 K rows
+                        tma_load_2d(sa, ma, full0 + 8 * s, ay, (kb0 + i) * BK);
+                        tma_load_2d(sa + 8192, ma, full0 + 8 * s, ay + 64, (kb0 + i) * BK);
+                    }
+                    if (!B_MN) {
                         if (CM == 1)
                             tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
                         else
                             tma_load_2d_mc(sa + C::A_BYTES + rank * B_SLICE_ROWS * BK * 2, mb, full0 + 8 * s,
                                            (kb0 + i) * BK, ni * BN + rank * B_SLICE_ROWS, MC_MASK);
                     } else {
-                        // [K][M] and [K][N] sources: boxes of 64 M (N) columns x 64 K rows
-                        tma_load_2d(sa, ma, full0 + 8 * s, ay, (kb0 + i) * BK);
-                        tma_load_2d(sa + 8192, ma, full0 + 8 * s, ay + 64, (kb0 + i) * BK);
+                        // [K][N] source: boxes of 64 N columns x 64 K rows, this CTA's share
 #pragma unroll
                         for (int j = 0; j < B_BOXES; ++j) {
                             const int box = rank * B_BOXES + j;
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t idesc = idesc_bf16<BN, MN>();
+            const uint32_t idesc = idesc_bf16<BN, A_MN, B_MN>();
             int it = 0, local = 0;
             bool ok = true;
             for (int t = cid; t < total && ok; t += ncl, ++local) {
@@ -421,13 +427,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    const uint64_t ad = MN ? sw128_desc_mn(sa) : sw128_desc(sa);
-                    const uint64_t bd = MN ? sw128_desc_mn(sa + C::A_BYTES) : sw128_desc(sa + C::A_BYTES);
+                    const uint64_t ad = A_MN ? sw128_desc_mn(sa) : sw128_desc(sa);
+                    const uint64_t bd = B_MN ? sw128_desc_mn(sa + C::A_BYTES) : sw128_desc(sa + C::A_BYTES);
                     // K16 step: 32 bytes along the swizzled row (K-major), two 8-row atoms (MN-major)
-                    constexpr uint64_t KSTEP = MN ? (2048 >> 4) : (32 >> 4);
+                    constexpr uint64_t KSTEP_A = A_MN ? (2048 >> 4) : (32 >> 4);
+                    constexpr uint64_t KSTEP_B = B_MN ? (2048 >> 4) : (32 >> 4);
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
-                        mma_bf16(d, ad + KSTEP * kk, bd + KSTEP * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
                     if (CM == 1) mma_commit(empty0 + 8 * s);
                     else mma_commit_mc(empty0 + 8 * s, MC_MASK);
                 }
@@ -560,9 +567,9 @@ static ClusterFit g_fit[64];
 static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 2 : -1; }
 static int cm_index(int cm) { return cm == 1 ? 0 : cm == 2 ? 1 : cm == 4 ? 2 : -1; }
 
-template <int BN, int EPI, int CM, bool MN>
+template <int BN, int EPI, int CM, int MJ>
 cudaError_t set_attr(int dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TileCfg<BN, EPI>::SMEM);
     if (e != cudaSuccess) return e;
     int sms = 148;
@@ -581,7 +588,7 @@ cudaError_t set_attr(int dev) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int fit = 0;
-        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MN>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MJ>, &cfg);
         if (e != cudaSuccess) return e;
         if (fit > 0 && fit < n) n = fit;
     }
@@ -589,7 +596,7 @@ cudaError_t set_attr(int dev) {
     return cudaSuccess;
 }
 
-template <int BN, int EPI, int CM, bool MN>
+template <int BN, int EPI, int CM, int MJ>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     using C = TileCfg<BN, EPI>;
     int dev = 0;
@@ -600,7 +607,7 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     const int total = mct * (p.N / BN) * p.splits * p.batch;
     const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
     if (CM == 1) {
-        tc_gemm_kernel<BN, EPI, 1, MN><<<clusters, TC_THREADS, C::SMEM, s>>>(p);
+        tc_gemm_kernel<BN, EPI, 1, MJ><<<clusters, TC_THREADS, C::SMEM, s>>>(p);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -615,21 +622,30 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MN>, p);
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ>, p);
+}
+
+// Instantiated operand forms: forward (EPI_BIAS_ELU) both K-major; input gradient
+// (EPI_ELU_GRAD) A K-major, B = W read MN-major; split-K weight gradient and the diagnostic
+// GEMMs (EPI_STORE) both K-major or both MN-major.  A cluster of 2 with an MN-major B needs
+// whole 64-column boxes per CTA (BN >= 128).
+
+template <int BN, int EPI, int MJ>
+cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
+    if (p.cm == 1) return launch_cfg<BN, EPI, 1, MJ>(p, s);
+    if (p.cm == 2 && (MJ == MAJ_K || BN >= 128)) return launch_cfg<BN, EPI, 2, (MJ == MAJ_K || BN >= 128) ? MJ : MAJ_K>(p, s);
+    return cudaErrorInvalidValue;
 }
 
 template <int BN, int EPI>
 cudaError_t launch_cm(const TcParams& p, cudaStream_t s) {
-    if (p.mn) {
-        // MN-major operands: the split-K weight-gradient epilogue only
-        if (EPI != EPI_STORE) return cudaErrorInvalidValue;
-        if (p.cm == 1) return launch_cfg<BN, EPI_STORE, 1, true>(p, s);
-        if (p.cm == 2 && BN >= 128) return launch_cfg<BN >= 128 ? BN : 128, EPI_STORE, 2, true>(p, s);
-        return cudaErrorInvalidValue;
-    }
-    switch (p.cm) {
-        case 1: return launch_cfg<BN, EPI, 1, false>(p, s);
-        case 2: return launch_cfg<BN, EPI, 2, false>(p, s);
+    if constexpr (EPI == EPI_BIAS_ELU) {
+        if (p.mn == MAJ_K) return launch_cm_mj<BN, EPI, MAJ_K>(p, s);
+    } else if constexpr (EPI == EPI_ELU_GRAD) {
+        if (p.mn == MAJ_B_MN) return launch_cm_mj<BN, EPI, MAJ_B_MN>(p, s);
+    } else {
+        if (p.mn == MAJ_K) return launch_cm_mj<BN, EPI, MAJ_K>(p, s);
+        if (p.mn == MAJ_MN) return launch_cm_mj<BN, EPI, MAJ_MN>(p, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -644,22 +660,15 @@ cudaError_t launch_bn(const TcParams& p, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-template <int EPI>
-cudaError_t prepare_epi(int dev) {
+template <int EPI, int MJ>
+cudaError_t prepare_form(int dev) {
     cudaError_t e = cudaSuccess;
-    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<64, EPI, 2, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<256, EPI, 1, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, false>(dev);
-    if (EPI == EPI_STORE) {
-        e = e != cudaSuccess ? e : set_attr<64, EPI_STORE, 1, true>(dev);
-        e = e != cudaSuccess ? e : set_attr<128, EPI_STORE, 1, true>(dev);
-        e = e != cudaSuccess ? e : set_attr<128, EPI_STORE, 2, true>(dev);
-        e = e != cudaSuccess ? e : set_attr<256, EPI_STORE, 1, true>(dev);
-        e = e != cudaSuccess ? e : set_attr<256, EPI_STORE, 2, true>(dev);
-    }
+    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ>(dev);
+    if (MJ == MAJ_K) e = e != cudaSuccess ? e : set_attr<64, EPI, 2, MAJ_K>(dev);
     return e;
 }
 
@@ -669,6 +678,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
     if (p.bn <= 0 || p.N % p.bn || p.kblocks <= 0 || p.splits <= 0 || p.batch < 1 || p.batch > 2) return cudaErrorInvalidValue;
     if (p.cm != 1 && p.cm != 2) return cudaErrorInvalidValue;
+    if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -709,6 +719,7 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
     return r == CUDA_SUCCESS;
 }
 
+
 // Sets the dynamic shared-memory limit of every instantiation and measures how many clusters
 // of each fit at once; called once per device before the first launch (and so before any
 // stream capture).
@@ -721,9 +732,10 @@ cudaError_t tc_prepare() {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
-    e = prepare_epi<EPI_STORE>(dev);
-    e = e != cudaSuccess ? e : prepare_epi<EPI_BIAS_ELU>(dev);
-    e = e != cudaSuccess ? e : prepare_epi<EPI_ELU_GRAD>(dev);
+    e = prepare_form<EPI_STORE, MAJ_K>(dev);
+    e = e != cudaSuccess ? e : prepare_form<EPI_STORE, MAJ_MN>(dev);
+    e = e != cudaSuccess ? e : prepare_form<EPI_BIAS_ELU, MAJ_K>(dev);
+    e = e != cudaSuccess ? e : prepare_form<EPI_ELU_GRAD, MAJ_B_MN>(dev);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }

@@ -7,6 +7,8 @@
 
 namespace rl {
 
+enum { MAJ_K = 0, MAJ_MN = 1, MAJ_B_MN = 2 };
+
 struct TcParams {
     CUtensorMap tmA[2];        // A operand per batch entry: [M][K] bf16, box 64 x 128 (see mn)
     CUtensorMap tmB[2];        // B operand per batch entry: [N][K] bf16, box 64 x (bn / cm)
@@ -16,8 +18,9 @@ struct TcParams {
     int batch;                 // 1 or 2 (actor, critic share one launch)
     int bn;                    // 64, 128 or 256
     int cm;                    // CTAs per cluster along M sharing (multicasting) the B tile: 1 or 2
-    int mn;                    // 1: operands MN-major, A^T [K][M] and B^T [K][N] (boxes 64 x 64),
-                               //    EPI_STORE only; 0: K-major A [M][K], B [N][K]
+    int mn;                    // operand forms: MAJ_K (A [M][K], B [N][K]), MAJ_MN (A^T [K][M],
+                               // B^T [K][N], EPI_STORE), MAJ_B_MN (A [M][K], B^T [K][N],
+                               // EPI_ELU_GRAD); MN-major operands use 64 x 64 boxes
     int epi;                   // EPI_STORE (fp32 split partials), EPI_BIAS_ELU, EPI_ELU_GRAD (bf16 out)
     void* C[2];                // output per batch entry
     int ldc;

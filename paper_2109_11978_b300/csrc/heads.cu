@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
     __syncthreads();
 
     // ---- head weight gradients: thread (unit k, row range q); ranges combined by q = 0 in order
-    const int PF = head_part_floats(A, H);
-    const int O_WA = 0, O_BA = A * H, O_LS = O_BA + A, O_WC = O_LS + A, O_BC = O_WC + H, O_DBA = O_BC + 1,
-              O_DBC = O_DBA + H, O_ST = O_DBC + H;
+    const HeadPart hp = head_part(A, H);
+    const int PF = hp.PF, O_WA = hp.WA, O_BA = hp.BA, O_LS = hp.LS, O_WC = hp.WC, O_BC = hp.BC, O_DBA = hp.DBA,
+              O_DBC = hp.DBC, O_ST = hp.ST;
     float* out = p.part + (size_t)blockIdx.x * PF;
     const int k = tid % H, q = tid / H;
     float acc[MAX_A], accc = 0.f;

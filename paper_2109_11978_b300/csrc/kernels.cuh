@@ -96,8 +96,27 @@ struct HeadParams {
     float* stats;                // [RL_NSTATS] accumulators (optional)
     float kl_target, lr_min, lr_max;
 };
-// partial layout per block: [Wa grad A*H][ba A][log_std A][Wc grad H][bc 1][db_a H][db_c H][stats 8]
-__host__ __device__ inline int head_part_floats(int A, int H) { return A * H + 2 * A + H + 1 + 2 * H + 8; }
+// Per-block partial layout of the loss head (floats): Wa grad [A*H], ba [A], log_std [A], Wc grad
+// [H], bc [1], db_a [H], db_c [H], stats [8]; every field starts on a 16-byte boundary so Adam
+// reads the partials as float4 (A * H and H are multiples of 4).
+struct HeadPart {
+    int WA, BA, LS, WC, BC, DBA, DBC, ST, PF;
+};
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline HeadPart head_part(int A, int H) {
+    HeadPart o;
+    o.WA = 0;
+    o.BA = pad4(A * H);
+    o.LS = o.BA + pad4(A);
+    o.WC = o.LS + pad4(A);
+    o.BC = o.WC + pad4(H);
+    o.DBA = o.BC + 4;
+    o.DBC = o.DBA + pad4(H);
+    o.ST = o.DBC + pad4(H);
+    o.PF = o.ST + 8;
+    return o;
+}
+__host__ __device__ inline int head_part_floats(int A, int H) { return head_part(A, H).PF; }
 cudaError_t launch_act_head(const HeadParams& p, cudaStream_t s);
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s);
 int loss_head_blocks(int M, int H, int bf16);   // blocks (= partial slots) of one loss-head launch
@@ -118,6 +137,7 @@ struct AdamSeg {
     long long stride;
     int nsplit;
     int block_start;       // first block of this segment
+    int vec;               // 1: offset, size, stride multiples of 4 and partials 16-byte aligned
 };
 constexpr int MAX_SEGS = 40;
 struct AdamParams {
@@ -128,15 +148,16 @@ struct AdamParams {
     int nsegs;
     int nblocks;
     AdamSeg seg[MAX_SEGS];
-    // bf16 weight copies (optional): for segment s, wbf[s] [rows][cols] and wbf_t[s] [cols][rows]
+    // bf16 weight copies (optional): for segment s, wbf[s] has the segment's layout
     void* wbf[MAX_SEGS];
-    void* wbf_t[MAX_SEGS];
-    int rows[MAX_SEGS];
-    int cols[MAX_SEGS];
     float* grad_out;       // optional: reduced gradient (flat internal) instead of a step
 };
-constexpr int ADAM_CHUNK = 256;    // parameters per block (one per thread)
-constexpr int ADAM_WIDE = 64;      // segments with more partials than this get 32 parameters per block
+constexpr int ADAM_THREADS = 256;
+constexpr int ADAM_WIDE = 64;      // segments with more partials than this: 8 warps split the partials
+// parameters per block: one (scalar) or four (vec) per thread, per lane for wide segments
+__host__ __device__ inline long long adam_per_block(int nsplit, int vec) {
+    return (long long)(nsplit > ADAM_WIDE ? 32 : ADAM_THREADS) * (vec ? 4 : 1);
+}
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
@@ -154,7 +175,7 @@ constexpr int ACC_ENV = 13;
 enum { SMALL_ITER_INC = 0, SMALL_ZERO_STATS = 1, SMALL_FINAL_STATS = 2 };
 
 // Convert fp32 [rows][cols] -> bf16 (row-major copy and transposed copy).
-cudaError_t launch_to_bf16(const float* src, int rows, int cols, void* dst, void* dst_t, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t s);
 
 // ------------------------------------------------------------------ tcgen05 BF16 GEMM
 struct TcGemm;   // defined in gemm_tc.cu

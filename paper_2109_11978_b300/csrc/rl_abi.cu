@@ -79,7 +79,6 @@ struct rl_ctx {
     AdamParams adam;
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
-    void* wbft[2][4] = {};
     int bn_fwd[4], bn_dx[4], bn_dw[4];
     int cm_fwd[4], cm_dx[4], cm_dw[4];     // cluster size along M (B tile multicast)
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
@@ -92,7 +91,8 @@ struct rl_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
-    bool prof_on = false;
+    unsigned prof_mask = 0;                      // recorded kernel classes (bit RL_PROF_*)
+    std::vector<int> ev_cls;                     // class of each recorded event pair
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     float prof_ms = 0.f;
@@ -151,25 +151,34 @@ bool config_ok(const rl_config* g) {
     return true;
 }
 
-// Host-side launch bookkeeping (launch counter, optional CUDA events around GEMMs).
+// Host-side launch bookkeeping: the launch counter and, for the recorded kernel classes, CUDA
+// events around each launch.
 struct Enq {
     rl_ctx* c;
     cudaStream_t s;
     bool profile;
-    cudaError_t gemm(const TcParams* tp, int epi, bool a_t, bool b_t, int M, int N, int K, int lda, int ldb, int ldc,
-                     int ldh, int batch, int splits, int kchunk, const GemmBatch* g) {
+    template <class F>
+    cudaError_t run(int cls, int nlaunch, F&& launch) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (profile && c->ev_used + 2 <= c->ev.size()) {
-            e0 = c->ev[c->ev_used++];
-            e1 = c->ev[c->ev_used++];
+        if (profile && ((c->prof_mask >> cls) & 1u) && c->ev_used + 2 <= c->ev.size()) {
+            e0 = c->ev[c->ev_used];
+            e1 = c->ev[c->ev_used + 1];
+            c->ev_cls[c->ev_used / 2] = cls;
+            c->ev_used += 2;
             cudaError_t e = cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
             if (e != cudaSuccess) return e;
         }
-        cudaError_t e = tp ? launch_tc_gemm(*tp, s)
-                           : launch_gemm_f32(epi, a_t, b_t, M, N, K, lda, ldb, ldc, ldh, batch, splits, kchunk, *g, s);
-        c->launches++;
+        cudaError_t e = launch();
+        c->launches += nlaunch;
         if (e == cudaSuccess && e1) e = cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
         return e;
+    }
+    cudaError_t gemm(const TcParams* tp, int epi, bool a_t, bool b_t, int M, int N, int K, int lda, int ldb, int ldc,
+                     int ldh, int batch, int splits, int kchunk, const GemmBatch* g) {
+        return run(RL_PROF_GEMM, 1, [&] {
+            return tp ? launch_tc_gemm(*tp, s)
+                      : launch_gemm_f32(epi, a_t, b_t, M, N, K, lda, ldb, ldc, ldh, batch, splits, kchunk, *g, s);
+        });
     }
 };
 
@@ -188,7 +197,8 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
             ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
-            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbft[n][l], Li.in, Li.out, Li.out, c->bn_dx[l] / c->cm_dx[l]);
+            // input gradient, B read MN-major: W_l [out][in] as it is stored, 64 x 64 boxes
+            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, 64);
         }
         // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in], 64 x 64 boxes
         ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 64);
@@ -266,7 +276,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.colsum[n] = c->gb[n][k - 1];
         }
         tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
-        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.cm = c->cm_dx[k]; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
+        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.cm = c->cm_dx[k]; tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -296,7 +306,7 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.C[n] = c->gw[n][k];
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
-        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.cm = c->cm_dw[k]; tp.mn = 1; tp.epi = EPI_STORE;
+        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.cm = c->cm_dw[k]; tp.mn = MAJ_MN; tp.epi = EPI_STORE;
         tp.ldc = Li.in;
         tp.split_stride = (long long)Li.out * Li.in;
         tp.status = c->status;
@@ -346,8 +356,7 @@ rl_status act_impl(rl_ctx* c, Enq& q, int t, int n, const void* obs, float* acti
     h.mu = mu;
     h.logp = logp;
     h.values = values;
-    CK(launch_act_head(h, q.s));
-    q.c->launches++;
+    CK(q.run(RL_PROF_ACT, 1, [&] { return launch_act_head(h, q.s); }));
     return RL_OK;
 }
 
@@ -403,8 +412,7 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.kl_target = step ? c->cfg.kl_target : 0.f;
     h.lr_min = c->cfg.lr_min;
     h.lr_max = c->cfg.lr_max;
-    CK(launch_loss_head(h, q.s));
-    c->launches++;
+    CK(q.run(RL_PROF_LOSS, 1, [&] { return launch_loss_head(h, q.s); }));
     // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums
     for (int k = c->NH - 1; k >= 1; --k) {
         rl_status st = dx_layer(c, q, k, M);
@@ -426,12 +434,12 @@ void build_adam(rl_ctx* c) {
     a.m = c->am;
     a.v = c->av;
     a.scal = c->scal;
-    const int PF = head_part_floats(c->A, c->HL);
-    const int O_WA = 0, O_BA = c->A * c->HL, O_LS = O_BA + c->A, O_WC = O_LS + c->A, O_BC = O_WC + c->HL,
-              O_DBA = O_BC + 1, O_DBC = O_DBA + c->HL;
+    const HeadPart hp = head_part(c->A, c->HL);
+    const int PF = hp.PF, O_WA = hp.WA, O_BA = hp.BA, O_LS = hp.LS, O_WC = hp.WC, O_BC = hp.BC, O_DBA = hp.DBA,
+              O_DBC = hp.DBC;
     int ns = 0, blocks = 0;
-    auto add = [&](long long off, long long size, const float* part, long long stride, int nsplit, void* wbf, void* wbft,
-                   int rows, int cols) {
+    auto add = [&](long long off, long long size, const float* part, long long stride, int nsplit, void* wbf, int rows,
+                   int cols) {
         AdamSeg& s = a.seg[ns];
         s.offset = off;
         s.size = size;
@@ -440,27 +448,29 @@ void build_adam(rl_ctx* c) {
         s.nsplit = nsplit;
         s.block_start = blocks;
         a.wbf[ns] = wbf;
-        a.wbf_t[ns] = wbft;
-        a.rows[ns] = rows;
-        a.cols[ns] = cols;
-        const long long per_block = nsplit > ADAM_WIDE ? 32 : ADAM_CHUNK;
+        (void)rows;
+        (void)cols;
+        s.vec = (off % 4 == 0 && size % 4 == 0 && stride % 4 == 0 && (reinterpret_cast<uintptr_t>(part) & 15u) == 0 &&
+                 (reinterpret_cast<uintptr_t>(wbf) & 7u) == 0)
+                    ? 1
+                    : 0;
+        const long long per_block = adam_per_block(nsplit, s.vec);
         blocks += (int)((size + per_block - 1) / per_block);
         ++ns;
     };
     for (int n = 0; n < 2; ++n) {
         for (int l = 0; l < c->NH; ++l) {
             const LayerInfo& Li = c->L[n][l];
-            add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], c->wbft[n][l],
-                Li.out, Li.in);
+            add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], Li.out, Li.in);
             if (l < c->NH - 1)
-                add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, nullptr, 0, 0);
+                add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, 0, 0);
             else
-                add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
+                add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, 0, 0);
         }
         const LayerInfo& Lh = c->L[n][c->NH];
-        add(Lh.w, (long long)Lh.out * Lh.in, c->head_part + (n == 0 ? O_WA : O_WC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
-        add(Lh.b, Lh.out, c->head_part + (n == 0 ? O_BA : O_BC), PF, c->head_blocks, nullptr, nullptr, 0, 0);
-        if (n == 0) add(c->logstd, c->A, c->head_part + O_LS, PF, c->head_blocks, nullptr, nullptr, 0, 0);
+        add(Lh.w, (long long)Lh.out * Lh.in, c->head_part + (n == 0 ? O_WA : O_WC), PF, c->head_blocks, nullptr, 0, 0);
+        add(Lh.b, Lh.out, c->head_part + (n == 0 ? O_BA : O_BC), PF, c->head_blocks, nullptr, 0, 0);
+        if (n == 0) add(c->logstd, c->A, c->head_part + O_LS, PF, c->head_blocks, nullptr, 0, 0);
     }
     a.nsegs = ns;
     a.nblocks = blocks;
@@ -471,7 +481,7 @@ rl_status refresh_bf16(rl_ctx* c, cudaStream_t s) {
     for (int n = 0; n < 2; ++n)
         for (int l = 0; l < c->NH; ++l) {
             const LayerInfo& Li = c->L[n][l];
-            CK(launch_to_bf16(c->params + Li.w, Li.out, Li.in, c->wbf[n][l], c->wbft[n][l], s));
+            CK(launch_to_bf16(c->params + Li.w, Li.out, Li.in, c->wbf[n][l], s));
         }
     return RL_OK;
 }
@@ -482,26 +492,21 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
     if (Mb != c->Mb || epochs > c->cfg.epochs) return RL_ERR_INVALID_ARG;
     cudaStream_t s = q.s;
     CK(cudaMemcpyAsync(c->logstd_old, c->params + c->logstd, sizeof(float) * c->A, cudaMemcpyDeviceToDevice, s));
-    CK(launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s));
-    c->launches++;
+    CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s); }));
     for (int e = 0; e < epochs; ++e) {
         for (int m = 0; m < minibatches; ++m) {
             const int* idx = c->perm + (size_t)e * B + (size_t)m * Mb;
-            CK(launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, s));
-            c->launches++;
+            CK(q.run(RL_PROF_GATHER, 1, [&] { return launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, s); }));
             rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true);
             if (st != RL_OK) return st;
             c->adam.grad_out = nullptr;
-            CK(launch_adam(c->adam, s));
-            c->launches++;
+            CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
         }
     }
-    CK(launch_small(SMALL_ITER_INC, c->scal, c->iter, nullptr, nullptr, 0.f, s));
-    c->launches++;
-    if (stats_out) {
-        CK(launch_small(SMALL_FINAL_STATS, c->scal, c->iter, c->acc, stats_out, (float)c->B, s));
-        c->launches++;
-    }
+    CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_small(SMALL_ITER_INC, c->scal, c->iter, nullptr, nullptr, 0.f, s); }));
+    if (stats_out)
+        CK(q.run(RL_PROF_OTHER, 1,
+                 [&] { return launch_small(SMALL_FINAL_STATS, c->scal, c->iter, c->acc, stats_out, (float)c->B, s); }));
     return RL_OK;
 }
 
@@ -511,8 +516,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
     c->ev_used = 0;
     const size_t obs_step = (size_t)c->N * c->Op * esize(c);
     uint8_t* obs = reinterpret_cast<uint8_t*>(c->obs);
-    CK(launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s));
-    c->launches++;
+    CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s); }));
     EnvParams ep = env_params(c);
     ep.stats = c->acc + ACC_ENV;
     for (int t = 0; t < c->T; ++t) {
@@ -529,14 +533,14 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
         ep.timeout = c->timeout + o;
         ep.level_out = c->level;
         ep.tidx_out = nullptr;
-        CK(launch_env_step(ep, 0, s));
-        c->launches++;
+        CK(q.run(RL_PROF_ENV, 1, [&] { return launch_env_step(ep, 0, s); }));
     }
     rl_status st = act_impl(c, q, c->T, c->N, obs + c->T * obs_step, nullptr, nullptr, nullptr, c->last_val);
     if (st != RL_OK) return st;
-    CK(launch_gae(c->T, c->N, c->cfg.gamma, c->cfg.lam, c->rew, c->values, c->last_val, c->done, c->adv, c->ret, 1,
-                  c->scal + SC_ADV_MEAN, c->gae_ws, c->gae_nparts, s));
-    c->launches += 2;
+    CK(q.run(RL_PROF_OTHER, 2, [&] {
+        return launch_gae(c->T, c->N, c->cfg.gamma, c->cfg.lam, c->rew, c->values, c->last_val, c->done, c->adv, c->ret, 1,
+                          c->scal + SC_ADV_MEAN, c->gae_ws, c->gae_nparts, s);
+    }));
     st = update_impl(c, q, c->obs, c->actions, c->logp, c->mu, c->values, c->adv, c->ret, c->cfg.epochs, c->cfg.minibatches,
                      c->stats);
     if (st != RL_OK) return st;
@@ -626,7 +630,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 best = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.in % bn || (cm > 1 && row_tiles < cm) || st != RL_OK) continue;
+                        if (Li.in % bn || (cm > 1 && (row_tiles < cm || bn < 128)) || st != RL_OK) continue;
                         c->bn_dx[l] = bn;
                         c->cm_dx[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -698,7 +702,7 @@ rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits)
     const int width = site == 0 ? Li.out : Li.in;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : (c->Mb + 127) / 128;
     if (width % bn || row_tiles < cm) return RL_ERR_INVALID_ARG;
-    if (site == 2 && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;     // whole 64-wide B boxes per CTA
+    if (site >= 1 && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;     // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
     if (site == 2) {
         if (splits < 1 || splits > c->S_cap[l]) return RL_ERR_INVALID_ARG;
@@ -941,7 +945,8 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         c->bn_dx[l] = pick_bn(Li.in);
         c->bn_dw[l] = bn;
         // B-tile multicast across pairs of row tiles wherever there are at least two row tiles
-        c->cm_fwd[l] = c->cm_dx[l] = (c->bf16 && c->Mb > 128) ? 2 : 1;
+        c->cm_fwd[l] = (c->bf16 && c->Mb > 128) ? 2 : 1;
+        c->cm_dx[l] = (c->bf16 && c->Mb > 128 && c->bn_dx[l] >= 128) ? 2 : 1;
         c->cm_dw[l] = (c->bf16 && Li.out > 128 && bn >= 128) ? 2 : 1;
         for (int n = 0; n < 2; ++n) {
             CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)std::max(S, c->S_cap[l]) * Li.out * Li.in));
@@ -955,7 +960,6 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
             for (int l = 0; l < c->NH; ++l) {
                 const LayerInfo& Li = c->L[n][l];
                 CK(dalloc(c, &c->wbf[n][l], (size_t)Li.out * Li.in * 2));
-                CK(dalloc(c, &c->wbft[n][l], (size_t)Li.out * Li.in * 2));
             }
         bool ok = make_tmap_bf16(&c->tm_x0, c->X0, c->rows, c->Op, c->Op, 128);
         for (int l = 0; l < c->NH; ++l) ok = ok && encode_layer_maps(c, l);
@@ -1184,7 +1188,7 @@ rl_status rl_train_iteration(rl_ctx* c, int32_t use_graph, float* stats_host, vo
         CK(cudaStreamWaitEvent(g, c->ev_in, 0));
         if (!c->gexec) {
             CK(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
-            rl_status st = train_enqueue(c, g, c->prof_on);
+            rl_status st = train_enqueue(c, g, c->prof_mask != 0);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(g, &graph);
             if (st != RL_OK) {
@@ -1199,7 +1203,7 @@ rl_status rl_train_iteration(rl_ctx* c, int32_t use_graph, float* stats_host, vo
         CK(cudaEventRecord(c->ev_out, g));
         CK(cudaStreamWaitEvent(s, c->ev_out, 0));
     } else {
-        rl_status st = train_enqueue(c, s, c->prof_on);
+        rl_status st = train_enqueue(c, s, c->prof_mask != 0);
         if (st != RL_OK) return st;
     }
     if (stats_host) {
@@ -1244,33 +1248,30 @@ rl_status rl_last_device_status(rl_ctx* c) {
 }
 
 rl_status rl_profile_enable(rl_ctx* c, int32_t kernel_class, int32_t on) {
-    if (!c || kernel_class != 0) return RL_ERR_INVALID_ARG;
-    c->prof_on = on != 0;
-    if (c->prof_on && c->ev.empty()) {
-        const size_t need = (size_t)2 * (c->cfg.epochs * c->cfg.minibatches * 3 * c->NH + 8 * (c->T + 1));
-        for (size_t i = 0; i < need; ++i) {
+    if (!c || kernel_class < 0 || kernel_class > RL_PROF_ALL) return RL_ERR_INVALID_ARG;
+    const unsigned bits = kernel_class == RL_PROF_ALL ? 0x7Fu : (1u << kernel_class);
+    c->prof_mask = on ? (c->prof_mask | bits) : (c->prof_mask & ~bits);
+    if (c->prof_mask && c->ev.empty()) {
+        // one event pair per launch of an iteration, every class recorded
+        const size_t launches = (size_t)(c->T + 1) * (c->NH + 2) + (size_t)c->cfg.epochs * c->cfg.minibatches * (3 * c->NH + 4) + 16;
+        for (size_t i = 0; i < 2 * launches; ++i) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
             c->ev.push_back(e);
         }
+        c->ev_cls.assign(launches, -1);
     }
     // a graph built without (or with) the event nodes is rebuilt on next use
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
-    if (c->graph) {
-        cudaGraphDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graph(c);
     return RL_OK;
 }
 
-rl_status rl_profile_read(rl_ctx* c, float* total_ms, int32_t* launches) {
+static rl_status profile_sum(rl_ctx* c, int cls, float* total_ms, int32_t* launches) {
     if (!c || !total_ms || !launches) return RL_ERR_INVALID_ARG;
     float tot = 0.f;
     int n = 0;
     for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        if (cls >= 0 && c->ev_cls[i / 2] != cls) continue;
         CK(cudaEventSynchronize(c->ev[i + 1]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
@@ -1280,6 +1281,13 @@ rl_status rl_profile_read(rl_ctx* c, float* total_ms, int32_t* launches) {
     *total_ms = tot;
     *launches = n;
     return RL_OK;
+}
+
+rl_status rl_profile_read(rl_ctx* c, float* total_ms, int32_t* launches) { return profile_sum(c, -1, total_ms, launches); }
+
+rl_status rl_profile_read_class(rl_ctx* c, int32_t kernel_class, float* total_ms, int32_t* launches) {
+    if (kernel_class < 0 || kernel_class >= RL_PROF_ALL) return RL_ERR_INVALID_ARG;
+    return profile_sum(c, kernel_class, total_ms, launches);
 }
 
 rl_status rl_autotune(rl_ctx* c, char* report, size_t report_bytes, void* stream) {
@@ -1324,7 +1332,7 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
     if (!make_tmap_bf16(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.cm = cm; tp.mn = 1; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    tp.bn = bn; tp.cm = cm; tp.mn = MAJ_MN; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }

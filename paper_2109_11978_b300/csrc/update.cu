@@ -59,9 +59,118 @@ __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ ob
 // p -= alpha m_hat / (sqrt(v_hat) + eps).  alpha and the step count come from the device
 // scalars (Algorithm 1 has already updated alpha for this minibatch).  The gradient of each
 // parameter is the sum of its partials (split-K slices or per-block head partials), read
-// coalesced; bf16 copies of the GEMM weights (and their transposes) are refreshed in the
-// same pass.
-__global__ void __launch_bounds__(256) adam_kernel(AdamParams p) {
+// coalesced, four parameters per thread (float4) wherever the segment allows it, with eight
+// loads in flight and the parameter's own state (p, m, v) fetched before the partial sums; bf16
+// copies of the GEMM weights are refreshed in the same pass.
+template <int V>
+struct Vec;
+template <>
+struct Vec<4> {
+    using T = float4;
+    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static T ld(const float* a) { return __ldg(reinterpret_cast<const float4*>(a)); }
+    __device__ static T ld_rw(const float* a) { return *reinterpret_cast<const float4*>(a); }
+    __device__ static void st(float* a, T v) { *reinterpret_cast<float4*>(a) = v; }
+    __device__ static void add(T& a, T b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+    __device__ static float get(const T& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+    __device__ static void set(T& v, int c, float x) {
+        if (c == 0) v.x = x; else if (c == 1) v.y = x; else if (c == 2) v.z = x; else v.w = x;
+    }
+};
+template <>
+struct Vec<1> {
+    using T = float;
+    __device__ static T zero() { return 0.f; }
+    __device__ static T ld(const float* a) { return __ldg(a); }
+    __device__ static T ld_rw(const float* a) { return *a; }
+    __device__ static void st(float* a, T v) { *a = v; }
+    __device__ static void add(T& a, T b) { a += b; }
+    __device__ static float get(const T& v, int) { return v; }
+    __device__ static void set(T& v, int, float x) { v = x; }
+};
+
+template <int V>
+__device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg& sg, int s, float step_size,
+                                             float inv_sqrt_bc2, float (*red)[32 * 4]) {
+    using O = Vec<V>;
+    using T = typename O::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool wide = sg.nsplit > ADAM_WIDE;
+    const long long base = (long long)(blockIdx.x - sg.block_start) * adam_per_block(sg.nsplit, V == 4);
+    const long long i = base + (long long)(wide ? lane : (int)threadIdx.x) * V;
+    const bool in = i < sg.size;
+    const bool owner = in && (!wide || warp == 0);          // the thread that applies the step
+    const long long gi = sg.offset + i;
+    T m = O::zero(), v = O::zero(), w = O::zero();
+    if (owner && !p.grad_out) {
+        m = O::ld_rw(p.m + gi);
+        v = O::ld_rw(p.v + gi);
+        w = O::ld_rw(p.p + gi);
+    }
+    // partial sums: eight independent accumulators, combined in a fixed order
+    T g0 = O::zero(), g1 = g0, g2 = g0, g3 = g0, g4 = g0, g5 = g0, g6 = g0, g7 = g0;
+    if (in) {
+        const int dq = wide ? 8 : 1;
+        int q = wide ? warp : 0;
+        const float* src = sg.partials + i;
+        const size_t st = (size_t)dq * sg.stride;
+        for (; q + 7 * dq < sg.nsplit; q += 8 * dq) {
+            const float* a = src + (size_t)q * sg.stride;
+            O::add(g0, O::ld(a)); O::add(g1, O::ld(a + st)); O::add(g2, O::ld(a + 2 * st)); O::add(g3, O::ld(a + 3 * st));
+            O::add(g4, O::ld(a + 4 * st)); O::add(g5, O::ld(a + 5 * st)); O::add(g6, O::ld(a + 6 * st));
+            O::add(g7, O::ld(a + 7 * st));
+        }
+        for (; q < sg.nsplit; q += dq) O::add(g0, O::ld(src + (size_t)q * sg.stride));
+    }
+    O::add(g0, g4); O::add(g1, g5); O::add(g2, g6); O::add(g3, g7);
+    O::add(g0, g1); O::add(g2, g3); O::add(g0, g2);
+    T g = g0;
+    if (wide) {
+#pragma unroll
+        for (int c = 0; c < V; ++c) red[warp][lane * V + c] = O::get(g, c);
+        __syncthreads();
+        if (warp != 0) return;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) acc += red[ww][lane * V + c];
+            O::set(g, c, acc);
+        }
+    }
+    if (!owner) return;
+    if (p.grad_out) {
+        O::st(p.grad_out + gi, g);
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        const float gc = O::get(g, c);
+        const float mc = 0.9f * O::get(m, c) + 0.1f * gc;
+        const float vc = 0.999f * O::get(v, c) + 0.001f * gc * gc;
+        O::set(m, c, mc);
+        O::set(v, c, vc);
+        O::set(w, c, O::get(w, c) - step_size * mc / (sqrtf(vc) * inv_sqrt_bc2 + 1e-8f));
+    }
+    O::st(p.m + gi, m);
+    O::st(p.v + gi, v);
+    O::st(p.p + gi, w);
+    if (p.wbf[s]) {
+        __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(p.wbf[s]) + i;
+        if (V == 4) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(O::get(w, 0), O::get(w, 1));
+            __nv_bfloat162 hi = __floats2bfloat162_rn(O::get(w, 2), O::get(w, 3));
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t*>(&lo);
+            pk.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(d) = pk;
+        } else {
+            d[0] = f2bf(O::get(w, 0));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ADAM_THREADS) adam_kernel(AdamParams p) {
     int s = 0;
     while (s + 1 < p.nsegs && (int)blockIdx.x >= p.seg[s + 1].block_start) ++s;
     const AdamSeg sg = p.seg[s];
@@ -69,59 +178,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamParams p) {
     // loss kernel together with Algorithm 1 and the step count
     const float step_size = p.scal ? p.scal[SC_STEPSIZE] : 0.f;
     const float inv_sqrt_bc2 = p.scal ? p.scal[SC_INVSQRT_BC2] : 1.f;
-    // Segments with many partials: 32 parameters per block, the 8 warps split the partials
-    // (warp w sums partials w, w + 8, ...) and the warp sums are added in warp order.
-    const bool wide = sg.nsplit > ADAM_WIDE;
-    __shared__ float red[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long base = (long long)(blockIdx.x - sg.block_start) * (wide ? 32 : ADAM_CHUNK);
-    for (int k = wide ? lane : (int)threadIdx.x; k < (wide ? 32 : ADAM_CHUNK); k += wide ? 32 : blockDim.x) {
-        const long long i = base + k;
-        const bool in = i < sg.size;
-        const float* src = sg.partials + (in ? i : 0);
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f;
-        const int q0 = wide ? warp : 0, dq = wide ? 8 : 1;
-        int q = q0;
-        if (in) {
-            // eight independent loads in flight, fixed order
-            const size_t st = (size_t)dq * sg.stride;
-            for (; q + 7 * dq < sg.nsplit; q += 8 * dq) {
-                const float* a = src + (size_t)q * sg.stride;
-                g0 += __ldg(a); g1 += __ldg(a + st); g2 += __ldg(a + 2 * st); g3 += __ldg(a + 3 * st);
-                g4 += __ldg(a + 4 * st); g5 += __ldg(a + 5 * st); g6 += __ldg(a + 6 * st); g7 += __ldg(a + 7 * st);
-            }
-            for (; q < sg.nsplit; q += dq) g0 += __ldg(src + (size_t)q * sg.stride);
-        }
-        g0 += g4; g1 += g5; g2 += g6; g3 += g7;
-        float g = (g0 + g1) + (g2 + g3);
-        if (wide) {
-            red[warp][lane] = g;
-            __syncthreads();
-            g = 0.f;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) g += red[w][lane];
-            if (warp != 0) break;           // warp 0 applies the step for the 32 parameters
-        }
-        if (!in) continue;
-        const long long gi = sg.offset + i;
-        if (p.grad_out) {
-            p.grad_out[gi] = g;
-            continue;
-        }
-        const float m = 0.9f * p.m[gi] + 0.1f * g;
-        const float v = 0.999f * p.v[gi] + 0.001f * g * g;
-        p.m[gi] = m;
-        p.v[gi] = v;
-        const float w = p.p[gi] - step_size * m / (sqrtf(v) * inv_sqrt_bc2 + 1e-8f);
-        p.p[gi] = w;
-        if (p.wbf[s]) {
-            const int cols = p.cols[s];
-            const int r = (int)(i / cols), c = (int)(i % cols);
-            const __nv_bfloat16 b = f2bf(w);
-            reinterpret_cast<__nv_bfloat16*>(p.wbf[s])[i] = b;
-            if (p.wbf_t[s]) reinterpret_cast<__nv_bfloat16*>(p.wbf_t[s])[(size_t)c * p.rows[s] + r] = b;
-        }
-    }
+    __shared__ float red[8][32 * 4];
+    if (sg.vec) adam_segment<4>(p, sg, s, step_size, inv_sqrt_bc2, red);
+    else adam_segment<1>(p, sg, s, step_size, inv_sqrt_bc2, red);
 }
 
 __global__ void small_kernel(int op, float* scal, unsigned long long* iteration, const float* src, float* dst,
@@ -145,13 +204,9 @@ __global__ void small_kernel(int op, float* scal, unsigned long long* iteration,
     }
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ src, int rows, int cols, __nv_bfloat16* dst, __nv_bfloat16* dst_t) {
-    const long long n = (long long)rows * cols;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const __nv_bfloat16 b = f2bf(src[i]);
-        if (dst) dst[i] = b;
-        if (dst_t) dst_t[(size_t)(i % cols) * rows + i / cols] = b;
-    }
+__global__ void to_bf16_kernel(const float* __restrict__ src, long long n, __nv_bfloat16* dst) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = f2bf(src[i]);
 }
 
 }  // namespace
@@ -176,7 +231,7 @@ cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int 
 
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s) {
     if (p.nblocks <= 0) return cudaSuccess;
-    adam_kernel<<<p.nblocks, 256, 0, s>>>(p);
+    adam_kernel<<<p.nblocks, ADAM_THREADS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -186,13 +241,12 @@ cudaError_t launch_small(int op, float* scal, unsigned long long* iteration, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_bf16(const float* src, int rows, int cols, void* dst, void* dst_t, cudaStream_t s) {
+cudaError_t launch_to_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t s) {
     const long long n = (long long)rows * cols;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    to_bf16_kernel<<<blocks, 256, 0, s>>>(src, rows, cols, reinterpret_cast<__nv_bfloat16*>(dst),
-                                          reinterpret_cast<__nv_bfloat16*>(dst_t));
+    to_bf16_kernel<<<blocks, 256, 0, s>>>(src, n, reinterpret_cast<__nv_bfloat16*>(dst));
     return cudaGetLastError();
 }
 
