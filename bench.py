@@ -369,7 +369,7 @@ def run_reference(args):
 
 def select_tiles(api, L, args):
     """Autotune the update's GEMM sites (default) or apply the shapes of a saved report."""
-    site_id = {"forward": 0, "input_grad": 1, "weight_grad": 2}
+    site_id = {"forward": 0, "input_grad": 1, "weight_grad": 2, "act_forward": 3}
     if args.tiles:
         with open(args.tiles) as f:
             rep = json.load(f)

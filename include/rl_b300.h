@@ -285,8 +285,9 @@ rl_status rl_profile_enable(rl_ctx* ctx, int32_t kernel_class, int32_t on);
 rl_status rl_profile_read(rl_ctx* ctx, float* total_ms, int32_t* launches);
 rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_ms, int32_t* launches);
 
-/* Tile autotuner: times each GEMM site of the update (per hidden layer: forward, input gradient,
- * weight gradient; actor and critic in one launch; minibatch rows) over candidate tile widths
+/* Tile autotuner: times each GEMM site (per hidden layer: the update's forward, input gradient
+ * and weight gradient at minibatch rows, and the rollout's forward at num_envs rows; actor and
+ * critic in one launch) over candidate tile widths
  * (64, 128, 256 output columns), cluster sizes (1 or 2 CTAs sharing one weight/B tile through
  * TMA multicast) and, for weight gradients, split-K counts (half, default, double) on the
  * context's own buffers, keeps the fastest, and drops a captured iteration graph so the next
@@ -297,8 +298,10 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
 
 /* Pins the tile shape of one GEMM site of a BF16 context (no counterpart in the paper: a tuning
  * control of this implementation).  site: 0 forward, 1 input gradient (layer >= 1), 2 weight
- * gradient; layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the
- * site's output width; cluster: 1 or 2 (2 needs at least two 128-row tiles at the site);
+ * gradient (the update's sites, minibatch rows), 3 the rollout's forward (num_envs rows);
+ * layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the site's output
+ * width; cluster: 1 or 2 (2 needs at least two 128-row tiles at the site, and for sites 1 and
+ * 2 a tile width of at least 128);
  * splits: weight-gradient split-K count (1 .. twice the default, rounded so every slice is a
  * multiple of 64 rows), ignored for the other sites.  Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */

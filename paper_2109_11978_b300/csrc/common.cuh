@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/rl_b300.h"
 
 namespace rl {
@@ -63,6 +65,33 @@ __device__ __forceinline__ float box_muller(uint64_t w) {
     float u1 = __fmul_rn(__uint2float_rn((hi32(w) >> 8) + 1u), 5.9604644775390625e-08f);
     float u2 = uniform01(lo32(w));
     return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// ---------------------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of an iteration are launched with programmatic
+// stream serialization: a kernel's blocks may be scheduled while its predecessor drains, run
+// their set-up, and wait in pdl_wait() until the predecessor grid has completed and its memory
+// is visible; pdl_trigger() lets the successor be scheduled early.  Every kernel calls pdl_wait()
+// before it reads or writes global memory (so completion is transitive along the stream).
+// Without the launch attribute both are no-ops.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -106,6 +106,8 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
 
 template <int MODE, int ENVS>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
 __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float rec_raw[];
     float (*rec)[REC] = reinterpret_cast<float (*)[REC]>(rec_raw);       // [ENVS][REC]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -373,7 +375,8 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
 template <int MODE, int ENVS>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
     const size_t smem = (size_t)ENVS * REC * sizeof(float);
-    env_step_kernel<MODE, ENVS><<<(p.N + ENVS - 1) / ENVS, THREADS, smem, s>>>(p);
+    cudaError_t e = launch_pdl(env_step_kernel<MODE, ENVS>, dim3((p.N + ENVS - 1) / ENVS), dim3(THREADS), smem, s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

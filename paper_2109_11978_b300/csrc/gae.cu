@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(GAE_THREADS) gae_scan_kernel(int T, int N, flo
                                                                const uint8_t* __restrict__ done,
                                                                float* __restrict__ adv, float* __restrict__ ret,
                                                                double* __restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     const int n = blockIdx.x * GAE_THREADS + threadIdx.x;
     double s1 = 0.0, s2 = 0.0;
     if (n < N) {
@@ -94,6 +96,8 @@ __global__ void __launch_bounds__(GAE_THREADS) gae_scan_kernel(int T, int N, flo
 
 __global__ void gae_normalize_kernel(size_t total, int nparts, const double* __restrict__ partials,
                                      float* __restrict__ adv, int normalize, float* __restrict__ stats) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double red[2][32];
     __shared__ float ms[2];
     double a = 0.0, b = 0.0;
@@ -164,15 +168,18 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
     if (T <= 0 || N <= 0) return cudaSuccess;
     const bool need = normalize || adv_stats;
     double* part = need ? reinterpret_cast<double*>(partials) : nullptr;
-    gae_scan_kernel<<<gae_num_partials(T, N), GAE_THREADS, 0, s>>>(T, N, gamma, lam, rew, val, last_val, done,
-                                                                    adv, ret, part);
+    cudaError_t e0 = launch_pdl(gae_scan_kernel, dim3(gae_num_partials(T, N)), dim3(GAE_THREADS), 0, s, T, N, gamma, lam,
+                                rew, val, last_val, done, adv, ret, part);
+    if (e0 != cudaSuccess) return e0;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !need) return e;
     const size_t total = (size_t)T * N;
     int blocks = (int)((total / 4 + 255) / 256);
     if (blocks < 1) blocks = 1;
     if (blocks > 1184) blocks = 1184;   // 8 x 148 SMs
-    gae_normalize_kernel<<<blocks, 256, 0, s>>>(total, nparts, part, adv, normalize, adv_stats);
+    e = launch_pdl(gae_normalize_kernel, dim3(blocks), dim3(256), 0, s, total, nparts, (const double*)part, adv, normalize,
+                   adv_stats);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

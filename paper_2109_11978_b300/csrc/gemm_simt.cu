@@ -20,6 +20,8 @@ constexpr int BM = 128, BN = 64, BK = 16, NT = 256;
 template <int EPI, bool AT, bool BT>
 __global__ void __launch_bounds__(NT) gemm_f32_kernel(int M, int N, int K, int lda, int ldb, int ldc, int ldh,
                                                       int splits, int kchunk, GemmBatch g) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int bz = blockIdx.z, b = bz / splits, sp = bz % splits;
@@ -145,10 +147,10 @@ __global__ void __launch_bounds__(NT) gemm_f32_kernel(int M, int N, int K, int l
 template <int EPI>
 cudaError_t dispatch(bool a_t, bool b_t, dim3 grid, int M, int N, int K, int lda, int ldb, int ldc, int ldh,
                      int splits, int kchunk, const GemmBatch& g, cudaStream_t s) {
-    if (!a_t && !b_t) gemm_f32_kernel<EPI, false, false><<<grid, NT, 0, s>>>(M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g);
-    else if (!a_t && b_t) gemm_f32_kernel<EPI, false, true><<<grid, NT, 0, s>>>(M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g);
-    else if (a_t && !b_t) gemm_f32_kernel<EPI, true, false><<<grid, NT, 0, s>>>(M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g);
-    else gemm_f32_kernel<EPI, true, true><<<grid, NT, 0, s>>>(M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g);
+    if (!a_t && !b_t) { cudaError_t e = launch_pdl(gemm_f32_kernel<EPI, false, false>, grid, dim3(NT), 0, s, M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g); if (e != cudaSuccess) return e; }
+    else if (!a_t && b_t) { cudaError_t e = launch_pdl(gemm_f32_kernel<EPI, false, true>, grid, dim3(NT), 0, s, M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g); if (e != cudaSuccess) return e; }
+    else if (a_t && !b_t) { cudaError_t e = launch_pdl(gemm_f32_kernel<EPI, true, false>, grid, dim3(NT), 0, s, M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g); if (e != cudaSuccess) return e; }
+    else { cudaError_t e = launch_pdl(gemm_f32_kernel<EPI, true, true>, grid, dim3(NT), 0, s, M, N, K, lda, ldb, ldc, ldh, splits, kchunk, g); if (e != cudaSuccess) return e; }
     return cudaGetLastError();
 }
 

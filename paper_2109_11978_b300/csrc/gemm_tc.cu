@@ -243,8 +243,10 @@ struct TileCfg {
     // per epilogue warp one 32 x 32 block of the output
     static constexpr int STG_WARP = 32 * RP;
     static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
+    // the bias vectors of both batch entries (at most 1024 columns), loaded once per CTA
+    static constexpr int BIAS_BYTES = EPI == EPI_BIAS_ELU ? 2 * 1024 * 4 : 0;
     static constexpr int BAR_BYTES = 256;
-    static constexpr int FIXED = STG_BYTES + BAR_BYTES + 1024 /*align*/;
+    static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
     static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3;
     static constexpr int SMEM = STAGES * STAGE + FIXED;
 };
@@ -271,7 +273,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stage_t = smem + C::STAGES * C::STAGE;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
+    float* bias_s = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
     // barriers: full[S], empty[S], tfull[2], tempty[2], drain
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
     const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + 2);
@@ -318,6 +321,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     if (CM > 1) cluster_sync_all();    // every CTA's barriers exist before any multicast lands
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // set-up done: wait for the preceding kernel's results, let the next kernel's CTAs be placed
+    pdl_wait();
+    pdl_trigger();
+    if (EPI == EPI_BIAS_ELU) {
+        for (int i = threadIdx.x; i < p.batch * p.N; i += TC_THREADS) {
+            const int b = i / p.N;
+            bias_s[b * 1024 + (i - b * p.N)] = __ldg(p.bias[b] + (i - b * p.N));
+        }
+        __syncthreads();
+    }
 
     auto decode = [&](int t, int& mi, int& ni, int& sp, int& b) {
         mi = (t % mct) * CM + rank;
@@ -458,15 +471,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const int nkb = kblocks_of(sp, kb0);
             const int a = local & 1;
             const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            const int m0 = mi * BM, n0 = ni * BN;
+            const int row = m0 + 32 * q + lane;
+            const bool row_ok = row < p.M;
+            const bool tile_ok = mi < mt;
+            // ELU-gradient form: the activation row segment of the first chunk is fetched before the
+            // wait for the accumulator, the next chunk's while the current one is stored
+            const __nv_bfloat16* hrow = nullptr;
+            uint4 hcur[4];
+            if (EPI == EPI_ELU_GRAD) {
+                hrow = reinterpret_cast<const __nv_bfloat16*>(p.H[b]) + (size_t)row * p.ldh + n0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) hcur[g] = make_uint4(0u, 0u, 0u, 0u);
+                if (busy && row_ok) {
+                    const uint4* hp = reinterpret_cast<const uint4*>(hrow + slice * C::SLICE_COLS);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) hcur[g] = __ldg(hp + g);
+                }
+            }
             if (*abort_flag || !mbar_wait(tfull0 + 8 * a, aph, p.status)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const int m0 = mi * BM, n0 = ni * BN;
-            const int row = m0 + 32 * q + lane;
-            const bool row_ok = row < p.M;
-            const bool tile_ok = mi < mt;
 #pragma unroll 1
             for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
@@ -493,10 +520,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     __syncwarp();
                 } else {
                     if (EPI == EPI_BIAS_ELU) {
-                        const float4* bias4 = reinterpret_cast<const float4*>(p.bias[b] + col);
+                        const float4* bias4 = reinterpret_cast<const float4*>(bias_s + b * 1024 + col);
 #pragma unroll
                         for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 bb = __ldg(bias4 + j4);
+                            const float4 bb = bias4[j4];
                             v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
                             v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
                             v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
@@ -504,14 +531,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         }
                     } else {   // EPI_ELU_GRAD
                         if (row_ok) {
-                            const uint4* hp = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.H[b]) +
-                                                                             (size_t)row * p.ldh + col);
 #pragma unroll
                             for (int g = 0; g < 4; ++g) {
-                                const uint4 hv = __ldg(hp + g);
-                                const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hv);
+                                const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hcur[g]);
 #pragma unroll
                                 for (int j = 0; j < 8; ++j) v[8 * g + j] *= elu_grad_y(bf2f(h8[j]));
+                            }
+                            // the next chunk's activations, in flight while this chunk is stored
+                            if (c + 32 < (slice + 1) * C::SLICE_COLS) {
+                                const uint4* hp = reinterpret_cast<const uint4*>(hrow + c + 32);
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) hcur[g] = __ldg(hp + g);
                             }
                         } else {
 #pragma unroll
@@ -607,21 +637,22 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     const int total = mct * (p.N / BN) * p.splits * p.batch;
     const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
     if (CM == 1) {
-        tc_gemm_kernel<BN, EPI, 1, MJ><<<clusters, TC_THREADS, C::SMEM, s>>>(p);
-        return cudaGetLastError();
+        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ>, dim3(clusters), dim3(TC_THREADS), C::SMEM, s, p);
     }
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CM;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3((unsigned)(clusters * CM));
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ>, p);
 }
 

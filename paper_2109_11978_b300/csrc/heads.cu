@@ -30,6 +30,8 @@ __device__ __forceinline__ float ld_act(const void* base, size_t i) {
 
 template <bool BF16, int NK>
 __global__ void __launch_bounds__(HEAD_WARPS * 32) act_head_kernel(HeadParams p) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float sm[];
     float* Wa = sm;                 // [A][H]
     float* Wc = sm + p.A * p.H;     // [H]
@@ -126,6 +128,8 @@ struct LossShape {
 
 template <bool BF16, int H, int LR>
 __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p) {
+    pdl_wait();
+    pdl_trigger();
     using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
     using S = LossShape<H, LR>;
     constexpr int SP = H + Tile<T>::PAD;           // tile pitch (elements)
@@ -413,7 +417,8 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
 
 template <bool BF16, int NK>
 static cudaError_t act_dispatch(const HeadParams& p, int blocks, size_t smem, cudaStream_t s) {
-    act_head_kernel<BF16, NK><<<blocks, HEAD_WARPS * 32, smem, s>>>(p);
+    cudaError_t e = launch_pdl(act_head_kernel<BF16, NK>, dim3(blocks), dim3(HEAD_WARPS * 32), smem, s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -442,7 +447,8 @@ static size_t loss_head_smem_t() {
 
 template <bool BF16, int H, int LR>
 static cudaError_t loss_dispatch(const HeadParams& p, cudaStream_t s) {
-    loss_head_kernel<BF16, H, LR><<<p.nblocks, LR * LH_TPR, loss_head_smem_t<BF16, H, LR>(), s>>>(p);
+    cudaError_t e = launch_pdl(loss_head_kernel<BF16, H, LR>, dim3(p.nblocks), dim3(LR * LH_TPR), loss_head_smem_t<BF16, H, LR>(), s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -153,10 +153,10 @@ struct AdamParams {
     float* grad_out;       // optional: reduced gradient (flat internal) instead of a step
 };
 constexpr int ADAM_THREADS = 256;
-constexpr int ADAM_WIDE = 64;      // segments with more partials than this: 8 warps split the partials
-// parameters per block: one (scalar) or four (vec) per thread, per lane for wide segments
+constexpr int ADAM_WIDE = 64;      // segments with more partials than this: a warp per parameter group
+// parameters per block: one (scalar) or four (vec) per thread, or per warp for wide segments
 __host__ __device__ inline long long adam_per_block(int nsplit, int vec) {
-    return (long long)(nsplit > ADAM_WIDE ? 32 : ADAM_THREADS) * (vec ? 4 : 1);
+    return (long long)(nsplit > ADAM_WIDE ? ADAM_THREADS / 32 : ADAM_THREADS) * (vec ? 4 : 1);
 }
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 

@@ -102,6 +102,8 @@ struct Smem {
 
 template <int H>
 __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
+    pdl_wait();
+    pdl_trigger();
     using S = Smem<H>;
     constexpr int HP = S::HP;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -468,7 +470,8 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
 
 template <int H>
 cudaError_t mma_dispatch(const HeadParams& p, cudaStream_t s) {
-    loss_mma_kernel<H><<<p.nblocks, THREADS, Smem<H>::BYTES, s>>>(p);
+    cudaError_t e = launch_pdl(loss_mma_kernel<H>, dim3(p.nblocks), dim3(THREADS), Smem<H>::BYTES, s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

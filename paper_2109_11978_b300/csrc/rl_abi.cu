@@ -79,9 +79,10 @@ struct rl_ctx {
     AdamParams adam;
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
-    int bn_fwd[4], bn_dx[4], bn_dw[4];
-    int cm_fwd[4], cm_dx[4], cm_dw[4];     // cluster size along M (B tile multicast)
+    int bn_fwd[4], bn_dx[4], bn_dw[4], bn_act[4];
+    int cm_fwd[4], cm_dx[4], cm_dw[4], cm_act[4];   // cluster size along M (B tile multicast)
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
+    CUtensorMap tm_actB[2][4];                   // forward B maps of the rollout's policy inference
     CUtensorMap tm_x0;                           // gathered minibatch observations
     CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
     CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
@@ -193,6 +194,7 @@ bool encode_layer_maps(rl_ctx* c, int l) {
     for (int n = 0; n < 2; ++n) {
         const LayerInfo& Li = c->L[n][l];
         ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l] / c->cm_fwd[l]);
+        ok = ok && make_tmap_bf16(&c->tm_actB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_act[l] / c->cm_act[l]);
         if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
@@ -209,8 +211,9 @@ bool encode_layer_maps(rl_ctx* c, int l) {
 }
 
 // One hidden layer of the forward pass for `rows` rows (X = layer-0 input), batch = nnets
-// networks starting at net0: 2 (actor + critic) or 1 with net0 = 1 (critic only).
-rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets) {
+// networks starting at net0: 2 (actor + critic) or 1 with net0 = 1 (critic only).  act: the
+// rollout's policy inference (its own tile shapes, tuned for num_envs rows), else the update.
+rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets, bool act) {
     const LayerInfo& Li = c->L[0][l];
     if (c->bf16) {
         TcParams tp;
@@ -222,7 +225,7 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
             } else {
                 tp.tmA[j] = c->tm_fwdA[n][l];
             }
-            tp.tmB[j] = c->tm_fwdB[n][l];
+            tp.tmB[j] = act ? c->tm_actB[n][l] : c->tm_fwdB[n][l];
             tp.C[j] = c->H[n][l];
             tp.bias[j] = c->params + c->L[n][l].b;
         }
@@ -232,8 +235,8 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.kb_per_split = tp.kblocks;
         tp.splits = 1;
         tp.batch = nnets;
-        tp.bn = c->bn_fwd[l];
-        tp.cm = c->cm_fwd[l];
+        tp.bn = act ? c->bn_act[l] : c->bn_fwd[l];
+        tp.cm = act ? c->cm_act[l] : c->cm_fwd[l];
         tp.epi = EPI_BIAS_ELU;
         tp.ldc = Li.out;
         tp.status = c->status;
@@ -254,9 +257,9 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
 }
 
 // Forward through every hidden layer.
-rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets) {
+rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act) {
     for (int l = 0; l < c->NH; ++l) {
-        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets);
+        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, act);
         if (st != RL_OK) return st;
     }
     return RL_OK;
@@ -348,7 +351,7 @@ HeadParams head_common(rl_ctx* c, int rows) {
 rl_status act_impl(rl_ctx* c, Enq& q, int t, int n, const void* obs, float* actions, float* mu, float* logp,
                    float* values) {
     const bool critic_only = !actions && !mu && !logp;
-    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2);
+    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2, true);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, n);
     h.t = t;
@@ -387,7 +390,7 @@ EnvParams env_params(rl_ctx* c) {
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
                             const float* ret, bool step) {
-    rl_status st = forward_hidden(c, q, c->X0, M, 0, 2);
+    rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, false);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
     const int l = c->NH - 1;
@@ -616,13 +619,33 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                     c->cm_fwd[l] = cm;
                     if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
                     float ms = 0.f;
-                    st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2); }, ms);
+                    st = timed([&] { return fwd_layer(c, q, l, c->X0, c->Mb, 0, 2, false); }, ms);
                     if (st == RL_OK) trial("forward", l, bn, cm, 1, ms);
                     if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; }
                 }
             c->bn_fwd[l] = best_bn;
             c->cm_fwd[l] = best_cm;
             note("forward", l, best_bn, best_cm, 1, best);
+            // the rollout's policy inference: num_envs rows, both networks
+            {
+                const int act_tiles = (c->N + 127) / 128;
+                int abn = c->bn_act[l], acm = c->cm_act[l];
+                float abest = 1e30f;
+                for (int bn : bns)
+                    for (int cm : cms) {
+                        if (Li.out % bn || (cm > 1 && act_tiles < cm) || st != RL_OK) continue;
+                        c->bn_act[l] = bn;
+                        c->cm_act[l] = cm;
+                        if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
+                        float ms = 0.f;
+                        st = timed([&] { return fwd_layer(c, q, l, c->obs, c->N, 0, 2, true); }, ms);
+                        if (st == RL_OK) trial("act_forward", l, bn, cm, 1, ms);
+                        if (st == RL_OK && ms < abest) { abest = ms; abn = bn; acm = cm; }
+                    }
+                c->bn_act[l] = abn;
+                c->cm_act[l] = acm;
+                note("act_forward", l, abn, acm, 1, abest);
+            }
             // input gradient
             if (l > 0 && st == RL_OK) {
                 best_bn = c->bn_dx[l];
@@ -696,13 +719,13 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
 }
 
 rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
-    if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 2 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
+    if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
     if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 2)) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
-    const int width = site == 0 ? Li.out : Li.in;
-    const int row_tiles = site == 2 ? (Li.out + 127) / 128 : (c->Mb + 127) / 128;
+    const int width = (site == 0 || site == 3) ? Li.out : Li.in;
+    const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
     if (width % bn || row_tiles < cm) return RL_ERR_INVALID_ARG;
-    if (site >= 1 && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;     // whole 64-wide B boxes per CTA
+    if ((site == 1 || site == 2) && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
     if (site == 2) {
         if (splits < 1 || splits > c->S_cap[l]) return RL_ERR_INVALID_ARG;
@@ -710,12 +733,12 @@ rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits)
         kc = (kc + 63) / 64 * 64;
         Sr = (c->Mb + kc - 1) / kc;
     }
-    const int old_bn = site == 0 ? c->bn_fwd[l] : site == 1 ? c->bn_dx[l] : c->bn_dw[l];
-    const int old_cm = site == 0 ? c->cm_fwd[l] : site == 1 ? c->cm_dx[l] : c->cm_dw[l];
+    int* const bnp[4] = {c->bn_fwd, c->bn_dx, c->bn_dw, c->bn_act};
+    int* const cmp[4] = {c->cm_fwd, c->cm_dx, c->cm_dw, c->cm_act};
+    const int old_bn = bnp[site][l], old_cm = cmp[site][l];
     auto assign = [&](int b, int m) {
-        if (site == 0) { c->bn_fwd[l] = b; c->cm_fwd[l] = m; }
-        else if (site == 1) { c->bn_dx[l] = b; c->cm_dx[l] = m; }
-        else { c->bn_dw[l] = b; c->cm_dw[l] = m; }
+        bnp[site][l] = b;
+        cmp[site][l] = m;
     };
     assign(bn, cm);
     if (!encode_layer_maps(c, l)) {
@@ -946,6 +969,8 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         c->bn_dw[l] = bn;
         // B-tile multicast across pairs of row tiles wherever there are at least two row tiles
         c->cm_fwd[l] = (c->bf16 && c->Mb > 128) ? 2 : 1;
+        c->bn_act[l] = pick_bn(Li.out);
+        c->cm_act[l] = (c->bf16 && c->N > 128) ? 2 : 1;
         c->cm_dx[l] = (c->bf16 && c->Mb > 128 && c->bn_dx[l] >= 128) ? 2 : 1;
         c->cm_dw[l] = (c->bf16 && Li.out > 128 && bn >= 128) ? 2 : 1;
         for (int n = 0; n < 2; ++n) {

@@ -27,6 +27,8 @@ __device__ __forceinline__ uint64_t feistel(uint64_t x, uint64_t key, int half) 
 }
 
 __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigned long long* iteration, int* idx) {
+    pdl_wait();
+    pdl_trigger();
     const int e = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
@@ -45,6 +47,8 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
 template <bool BF16>
 __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
                                                      int Op, void* X) {
+    pdl_wait();
+    pdl_trigger();
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= M) return;
     constexpr int E = BF16 ? 2 : 4;
@@ -91,15 +95,18 @@ struct Vec<1> {
 
 template <int V>
 __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg& sg, int s, float step_size,
-                                             float inv_sqrt_bc2, float (*red)[32 * 4]) {
+                                             float inv_sqrt_bc2) {
     using O = Vec<V>;
     using T = typename O::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // narrow segments (few partials): one thread per V parameters, each summing every partial;
+    // wide segments (many partials): one warp per V parameters, lane l summing partials l, l + 32,
+    // ..., then a fixed xor tree across the lanes (every lane ends with the same bits)
     const bool wide = sg.nsplit > ADAM_WIDE;
     const long long base = (long long)(blockIdx.x - sg.block_start) * adam_per_block(sg.nsplit, V == 4);
-    const long long i = base + (long long)(wide ? lane : (int)threadIdx.x) * V;
+    const long long i = base + (long long)(wide ? warp : (int)threadIdx.x) * V;
     const bool in = i < sg.size;
-    const bool owner = in && (!wide || warp == 0);          // the thread that applies the step
+    const bool owner = in && (!wide || lane == 0);          // the thread that applies the step
     const long long gi = sg.offset + i;
     T m = O::zero(), v = O::zero(), w = O::zero();
     if (owner && !p.grad_out) {
@@ -110,8 +117,8 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
     // partial sums: eight independent accumulators, combined in a fixed order
     T g0 = O::zero(), g1 = g0, g2 = g0, g3 = g0, g4 = g0, g5 = g0, g6 = g0, g7 = g0;
     if (in) {
-        const int dq = wide ? 8 : 1;
-        int q = wide ? warp : 0;
+        const int dq = wide ? 32 : 1;
+        int q = wide ? lane : 0;
         const float* src = sg.partials + i;
         const size_t st = (size_t)dq * sg.stride;
         for (; q + 7 * dq < sg.nsplit; q += 8 * dq) {
@@ -127,15 +134,11 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
     T g = g0;
     if (wide) {
 #pragma unroll
-        for (int c = 0; c < V; ++c) red[warp][lane * V + c] = O::get(g, c);
-        __syncthreads();
-        if (warp != 0) return;
-#pragma unroll
         for (int c = 0; c < V; ++c) {
-            float acc = 0.f;
+            float x = O::get(g, c);
 #pragma unroll
-            for (int ww = 0; ww < 8; ++ww) acc += red[ww][lane * V + c];
-            O::set(g, c, acc);
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            O::set(g, c, x);
         }
     }
     if (!owner) return;
@@ -171,6 +174,8 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
 }
 
 __global__ void __launch_bounds__(ADAM_THREADS) adam_kernel(AdamParams p) {
+    pdl_wait();
+    pdl_trigger();
     int s = 0;
     while (s + 1 < p.nsegs && (int)blockIdx.x >= p.seg[s + 1].block_start) ++s;
     const AdamSeg sg = p.seg[s];
@@ -178,13 +183,14 @@ __global__ void __launch_bounds__(ADAM_THREADS) adam_kernel(AdamParams p) {
     // loss kernel together with Algorithm 1 and the step count
     const float step_size = p.scal ? p.scal[SC_STEPSIZE] : 0.f;
     const float inv_sqrt_bc2 = p.scal ? p.scal[SC_INVSQRT_BC2] : 1.f;
-    __shared__ float red[8][32 * 4];
-    if (sg.vec) adam_segment<4>(p, sg, s, step_size, inv_sqrt_bc2, red);
-    else adam_segment<1>(p, sg, s, step_size, inv_sqrt_bc2, red);
+    if (sg.vec) adam_segment<4>(p, sg, s, step_size, inv_sqrt_bc2);
+    else adam_segment<1>(p, sg, s, step_size, inv_sqrt_bc2);
 }
 
 __global__ void small_kernel(int op, float* scal, unsigned long long* iteration, const float* src, float* dst,
                              float nsamp) {
+    pdl_wait();
+    pdl_trigger();
     const int i = threadIdx.x;
     if (op == SMALL_ITER_INC) {
         if (i == 0) *iteration += 1ull;
@@ -205,6 +211,8 @@ __global__ void small_kernel(int op, float* scal, unsigned long long* iteration,
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, long long n, __nv_bfloat16* dst) {
+    pdl_wait();
+    pdl_trigger();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = f2bf(src[i]);
 }
@@ -216,7 +224,8 @@ cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned 
     int bits = 2;
     while ((1ll << bits) < B) bits += 2;
     dim3 grid((B + 255) / 256, epochs);
-    permutation_kernel<<<grid, 256, 0, s>>>(B, bits / 2, seed, iteration, idx);
+    cudaError_t e = launch_pdl(permutation_kernel, grid, dim3(256), 0, s, B, bits / 2, seed, iteration, idx);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -224,20 +233,23 @@ cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int 
     if (M <= 0) return cudaSuccess;
     if (Op % 64) return cudaErrorInvalidValue;
     const int grid = (M + 7) / 8;
-    if (bf16) gather_kernel<true><<<grid, 256, 0, s>>>(obs, idx, M, Op, X);
-    else gather_kernel<false><<<grid, 256, 0, s>>>(obs, idx, M, Op, X);
+    cudaError_t e = bf16 ? launch_pdl(gather_kernel<true>, dim3(grid), dim3(256), 0, s, obs, idx, M, Op, X)
+                         : launch_pdl(gather_kernel<false>, dim3(grid), dim3(256), 0, s, obs, idx, M, Op, X);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s) {
     if (p.nblocks <= 0) return cudaSuccess;
-    adam_kernel<<<p.nblocks, ADAM_THREADS, 0, s>>>(p);
+    cudaError_t e = launch_pdl(adam_kernel, dim3(p.nblocks), dim3(ADAM_THREADS), 0, s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_small(int op, float* scal, unsigned long long* iteration, const float* stats_src, float* stats_dst,
                          float nsamp, cudaStream_t s) {
-    small_kernel<<<1, 32, 0, s>>>(op, scal, iteration, stats_src, stats_dst, nsamp);
+    cudaError_t e = launch_pdl(small_kernel, dim3(1), dim3(32), 0, s, op, scal, iteration, stats_src, stats_dst, nsamp);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -246,7 +258,8 @@ cudaError_t launch_to_bf16(const float* src, int rows, int cols, void* dst, cuda
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    to_bf16_kernel<<<blocks, 256, 0, s>>>(src, n, reinterpret_cast<__nv_bfloat16*>(dst));
+    cudaError_t e = launch_pdl(to_bf16_kernel, dim3(blocks), dim3(256), 0, s, src, n, reinterpret_cast<__nv_bfloat16*>(dst));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -329,12 +329,12 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
     widths = {0: hidden, 1: [Op] + list(hidden[:-1])}     # output width of forward / input-gradient sites
     pinned = 0
     for layer in range(len(hidden)):
-        for site in (0, 1, 2):
+        for site in (0, 1, 2, 3):
             if site == 1 and layer == 0:
                 continue
-            width = hidden[layer] if site == 0 else widths[1][layer]
+            width = hidden[layer] if site in (0, 3) else widths[1][layer]
             out_tiles = -(-hidden[layer] // 128)
-            if width % bn or (site == 2 and out_tiles < cm):
+            if width % bn or (site == 2 and out_tiles < cm) or (site in (1, 2) and cm > 1 and bn < 128):
                 continue
             choices = [1] if splits == "one" else [64, 48, 32, 24, 16, 12, 8, 6, 4, 3, 2]
             for s_ in choices:
@@ -366,8 +366,8 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
 def test_set_gemm_tiles_rejects_invalid():
     w = workload("tiny", precision=1)
     L, _, _, _ = _setup(w)
-    for args in ((3, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 4, 1), (0, 9, 64, 1, 1),
-                 (2, 0, 64, 1, 0)):
+    for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 4, 1), (0, 9, 64, 1, 1),
+                 (2, 0, 64, 1, 0), (3, 0, 128, 1, 1)):
         with pytest.raises(api.RLError):
             api.rl_set_gemm_tiles(L.ctx, *args)
     L.close()
