@@ -240,12 +240,14 @@ struct TileCfg {
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
-    // per epilogue warp one 32 x 32 block of the output
-    static constexpr int STG_WARP = 32 * RP;
+    // per epilogue warp one 32 x 32 block of the output; the ELU-gradient form instead keeps two
+    // 32 x 32 bf16 activation blocks (TMA, 64-byte swizzle), each overwritten in place by its
+    // output block before the coalesced store
+    static constexpr int STG_WARP = EPI == EPI_ELU_GRAD ? 2 * 2048 : 32 * RP;
     static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
     // the bias vectors of both batch entries (at most 1024 columns), loaded once per CTA
     static constexpr int BIAS_BYTES = EPI == EPI_BIAS_ELU ? 2 * 1024 * 4 : 0;
-    static constexpr int BAR_BYTES = 256;
+    static constexpr int BAR_BYTES = 512;
     static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
     static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3;
     static constexpr int SMEM = STAGES * STAGE + FIXED;
@@ -274,12 +276,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stage_t = smem + C::STAGES * C::STAGE;
     float* bias_s = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
+    (void)bias_s;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
-    // barriers: full[S], empty[S], tfull[2], tempty[2], drain
+    // barriers: full[S], empty[S], tfull[2], tempty[2], drain, hbar[EPI_WARPS][2]
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
     const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + 2);
     const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 4);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5);
+    const uint32_t hbar0 = smem_u32(bars + 2 * C::STAGES + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5 + 2 * EPI_WARPS);
+    static_assert((2 * C::STAGES + 5 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     // a multicast instantiation launched without its cluster shape would address CTAs that do
@@ -306,6 +311,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             mbar_init(tempty0 + 8 * a, EPI_WARPS);
         }
         mbar_init(drain, 1);
+        if (EPI == EPI_ELU_GRAD)
+            for (int h = 0; h < 2 * EPI_WARPS; ++h) mbar_init(hbar0 + 8 * h, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -464,6 +471,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int slice = ew >> 2;              // column slice of the tile (slice >= SLICES: idle)
         const bool busy = slice < C::SLICES;
         uint8_t* stg_raw = stage_t + (size_t)ew * C::STG_WARP;
+        // ELU-gradient form: the warp's activation blocks (32 rows x 32 columns of H per chunk) are
+        // fetched by TMA into two buffers, one chunk ahead of the chunk being processed
+        constexpr int CPT = C::SLICE_COLS / 32;                 // chunks per tile of one warp
+        int hj = 0;                                              // chunks processed so far
+        bool h_pending = false;                                  // chunk hj issued, not yet waited
+        auto h_issue = [&](int j) {
+            // chunk j of this warp's sequence: tile cid + (j / CPT) ncl, column chunk j % CPT
+            const int t = cid + (j / CPT) * ncl;
+            if (t >= total) return false;
+            int mi, ni, sp, b;
+            decode(t, mi, ni, sp, b);
+            const int x = ni * BN + slice * C::SLICE_COLS + 32 * (j % CPT);
+            const int y = min(mi, mt - 1) * BM + 32 * q;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // prior reads/writes of the buffer
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t bar = hbar0 + 8 * (2 * ew + (j & 1));
+                mbar_expect_tx(bar, 2048u);
+                tma_load_2d(smem_u32(stg_raw + 2048 * (j & 1)), &p.tmH[b], bar, x, y);
+            }
+            return true;
+        };
+        if (EPI == EPI_ELU_GRAD && busy) h_pending = h_issue(0);
         int local = 0;
         for (int t = cid; t < total; t += ncl, ++local) {
             int mi, ni, sp, b, kb0;
@@ -475,25 +505,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const int row = m0 + 32 * q + lane;
             const bool row_ok = row < p.M;
             const bool tile_ok = mi < mt;
-            // ELU-gradient form: the activation row segment of the first chunk is fetched before the
-            // wait for the accumulator, the next chunk's while the current one is stored
-            const __nv_bfloat16* hrow = nullptr;
-            uint4 hcur[4];
-            if (EPI == EPI_ELU_GRAD) {
-                hrow = reinterpret_cast<const __nv_bfloat16*>(p.H[b]) + (size_t)row * p.ldh + n0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) hcur[g] = make_uint4(0u, 0u, 0u, 0u);
-                if (busy && row_ok) {
-                    const uint4* hp = reinterpret_cast<const uint4*>(hrow + slice * C::SLICE_COLS);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) hcur[g] = __ldg(hp + g);
-                }
-            }
             if (*abort_flag || !mbar_wait(tfull0 + 8 * a, aph, p.status)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
+            bool stop = false;
 #pragma unroll 1
             for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
@@ -518,56 +535,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         if (rr < p.M) *reinterpret_cast<float4*>(dst + (size_t)rr * p.ldc + 4 * g) = val;
                     }
                     __syncwarp();
-                } else {
-                    if (EPI == EPI_BIAS_ELU) {
-                        const float4* bias4 = reinterpret_cast<const float4*>(bias_s + b * 1024 + col);
+                } else if (EPI == EPI_BIAS_ELU) {
+                    const float4* bias4 = reinterpret_cast<const float4*>(bias_s + b * 1024 + col);
 #pragma unroll
-                        for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 bb = bias4[j4];
-                            v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
-                            v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
-                            v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
-                            v[4 * j4 + 3] = elu_fast(v[4 * j4 + 3] + bb.w);
-                        }
-                    } else {   // EPI_ELU_GRAD
-                        if (row_ok) {
-#pragma unroll
-                            for (int g = 0; g < 4; ++g) {
-                                const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hcur[g]);
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) v[8 * g + j] *= elu_grad_y(bf2f(h8[j]));
-                            }
-                            // the next chunk's activations, in flight while this chunk is stored
-                            if (c + 32 < (slice + 1) * C::SLICE_COLS) {
-                                const uint4* hp = reinterpret_cast<const uint4*>(hrow + c + 32);
-#pragma unroll
-                                for (int g = 0; g < 4; ++g) hcur[g] = __ldg(hp + g);
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = 0.f;
-                        }
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 bb = bias4[j4];
+                        v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
+                        v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
+                        v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
+                        v[4 * j4 + 3] = elu_fast(v[4 * j4 + 3] + bb.w);
                     }
                     __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
-                    {
-                        // row-major copy through shared memory: four lanes write one row's 64 bytes
+                    // row-major copy through shared memory: four lanes write one row's 64 bytes
 #pragma unroll
-                        for (int g = 0; g < 4; ++g)
-                            *reinterpret_cast<uint4*>(stg_raw + lane * C::RP + 16 * g) = reinterpret_cast<const uint4*>(o)[g];
-                        __syncwarp();
-                        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
+                    for (int g = 0; g < 4; ++g)
+                        *reinterpret_cast<uint4*>(stg_raw + lane * C::RP + 16 * g) = reinterpret_cast<const uint4*>(o)[g];
+                    __syncwarp();
+                    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
 #pragma unroll
-                        for (int idx = lane; idx < 128; idx += 32) {
-                            const int r = idx >> 2, g = idx & 3;
-                            const int rr = m0 + 32 * q + r;
-                            const uint4 val = *reinterpret_cast<const uint4*>(stg_raw + r * C::RP + 16 * g);
-                            if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
-                        }
-                        __syncwarp();
+                    for (int idx = lane; idx < 128; idx += 32) {
+                        const int r = idx >> 2, g = idx & 3;
+                        const int rr = m0 + 32 * q + r;
+                        const uint4 val = *reinterpret_cast<const uint4*>(stg_raw + r * C::RP + 16 * g);
+                        if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
                     }
-                    if (EPI == EPI_ELU_GRAD && p.colsum[b]) {
+                    __syncwarp();
+                } else {   // EPI_ELU_GRAD
+                    // the next chunk's activations go into the other buffer (free: its chunk is done)
+                    const bool next = h_issue(hj + 1);
+                    uint8_t* hb = stg_raw + 2048 * (hj & 1);
+                    if (!mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status)) {
+                        *abort_flag = 1;
+                        h_pending = next;
+                        ++hj;
+                        stop = true;
+                        break;
+                    }
+                    // 64-byte swizzle: 16-byte unit u of row r sits at unit u ^ ((r >> 1) & 3)
+                    const int sw = (lane >> 1) & 3;
+                    if (row_ok) {
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const uint4 hv = *reinterpret_cast<const uint4*>(hb + lane * 64 + 16 * (g ^ sw));
+                            const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hv);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) v[8 * g + j] *= elu_grad_y(bf2f(h8[j]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                    }
+                    __align__(16) __nv_bfloat16 o[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
+                    // the output block replaces the activation block in place (same swizzle), then
+                    // leaves with four lanes per row
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        *reinterpret_cast<uint4*>(hb + lane * 64 + 16 * (g ^ sw)) = reinterpret_cast<const uint4*>(o)[g];
+                    __syncwarp();
+                    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
+#pragma unroll
+                    for (int idx = lane; idx < 128; idx += 32) {
+                        const int r = idx >> 2, g = idx & 3;
+                        const int rr = m0 + 32 * q + r;
+                        const uint4 val = *reinterpret_cast<const uint4*>(hb + r * 64 + 16 * (g ^ ((r >> 1) & 3)));
+                        if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
+                    }
+                    __syncwarp();
+                    h_pending = next;
+                    ++hj;
+                    if (p.colsum[b]) {
                         const float s = colsum32(v, lane);    // column col + lane, over this warp's 32 rows
                         if (tile_ok) p.colsum[b][((size_t)mi * 4 + q) * p.N + col + lane] = s;
                     }
@@ -577,7 +617,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+            if (stop) break;
         }
+        // an activation block still in flight lands before the CTA leaves (bounded)
+        if (EPI == EPI_ELU_GRAD && h_pending)
+            mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status);
     }
     tc_fence_before();
     __syncthreads();
@@ -737,17 +781,25 @@ static EncodeTiledFn get_encode() {
 
 // 2D bf16 tensor [rows][cols] (cols contiguous, row stride ld elements), box 64 x box_rows,
 // 128-byte swizzle, zero fill outside.  cols and ld must make 16-byte strides.
-bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
+static bool make_tmap(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_cols,
+                      uint32_t box_rows, CUtensorMapSwizzle sw) {
     EncodeTiledFn enc = get_encode();
     if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16 || cols > ld) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
+    return make_tmap(map, base, rows, cols, ld, (uint32_t)BK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld) {
+    return make_tmap(map, base, rows, cols, ld, 32u, 32u, CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 

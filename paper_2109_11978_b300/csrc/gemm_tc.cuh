@@ -26,6 +26,7 @@ struct TcParams {
     int ldc;
     const float* bias[2];      // EPI_BIAS_ELU
     const void* H[2];          // EPI_ELU_GRAD: bf16 activation [M][ldh]
+    CUtensorMap tmH[2];        // EPI_ELU_GRAD: the same activation, 32 x 32 boxes, 64-byte swizzle
     int ldh;
     float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [M/128][N]
     long long split_stride;    // EPI_STORE: elements between split slices
@@ -34,6 +35,8 @@ struct TcParams {
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
+// epilogue operand map: bf16 [rows][cols] (row stride ld), 32 x 32 boxes, 64-byte swizzle
+bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld);
 int tc_smem_bytes(int bn, int epi);
 int tc_cluster_fit(int bn, int epi, int cm);   // clusters resident at once (after tc_prepare)
 cudaError_t tc_prepare();
