@@ -289,8 +289,9 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
  * and weight gradient at minibatch rows, and the rollout's forward at num_envs rows; actor and
  * critic in one launch) over candidate tile widths
  * (64, 128, 256 output columns), cluster sizes (1 or 2 CTAs sharing one weight/B tile through
- * TMA multicast) and, for weight gradients, split-K counts (half, default, double) on the
- * context's own buffers, keeps the fastest, and drops a captured iteration graph so the next
+ * TMA multicast) and, for weight gradients, split-K counts (a quarter, half, default, double;
+ * timed together with the summation of their partials, which Adam performs) on the context's
+ * own buffers, keeps the fastest, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
  * scratch (parameters, Adam state and env state are untouched).  report (host, may be NULL): a
  * JSON summary of the chosen shapes and their times, truncated to report_bytes. */

@@ -482,6 +482,36 @@ void build_adam(rl_ctx* c) {
     a.nblocks = blocks;
 }
 
+// Adam's partial-sum pass restricted to the weight matrices of hidden layer l (both networks),
+// writing the summed gradient to the scratch gradient instead of stepping: the autotuner times
+// it with the weight-gradient GEMM, since the split count trades GEMM parallelism for the
+// partial-sum traffic.
+AdamParams weight_reduce_params(rl_ctx* c, int l) {
+    AdamParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = c->params;
+    a.m = c->am;
+    a.v = c->av;
+    a.grad_out = c->grad_int;
+    int blocks = 0;
+    for (int n = 0; n < 2; ++n) {
+        const LayerInfo& Li = c->L[n][l];
+        AdamSeg& sg = a.seg[a.nsegs];
+        sg.offset = Li.w;
+        sg.size = (long long)Li.out * Li.in;
+        sg.partials = c->gw[n][l];
+        sg.stride = sg.size;
+        sg.nsplit = c->S[l];
+        sg.block_start = blocks;
+        sg.vec = (sg.offset % 4 == 0 && sg.size % 4 == 0) ? 1 : 0;
+        const long long per_block = adam_per_block(sg.nsplit, sg.vec);
+        blocks += (int)((sg.size + per_block - 1) / per_block);
+        ++a.nsegs;
+    }
+    a.nblocks = blocks;
+    return a;
+}
+
 rl_status refresh_bf16(rl_ctx* c, cudaStream_t s) {
     if (!c->bf16) return RL_OK;
     for (int n = 0; n < 2; ++n)
@@ -681,7 +711,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 if (Li.in % bn) continue;
                 for (int cm : cms) {
                     if (cm > 1 && (!c->bf16 || out_tiles < cm || bn < 128)) continue;   // whole 64-wide B boxes per CTA
-                    for (int S : {S0 / 2, S0, 2 * S0}) {
+                    for (int S : {S0 / 4, S0 / 2, S0, 2 * S0}) {
                         if (S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
                         int kc = (c->Mb + S - 1) / S;
                         kc = (kc + 63) / 64 * 64;
@@ -693,7 +723,17 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                         c->kchunk[l] = kc;
                         if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
                         float ms = 0.f;
-                        st = timed([&] { return dw_layer(c, q, l, c->Mb); }, ms);
+                        // the split-K partials are summed by Adam: time the GEMM together with that
+                        // reduction (Adam's partial-sum pass over this layer's weights, gradient out)
+                        st = timed(
+                            [&] {
+                                rl_status r = dw_layer(c, q, l, c->Mb);
+                                if (r != RL_OK) return r;
+                                AdamParams red = weight_reduce_params(c, l);
+                                CK(launch_adam(red, s));
+                                return RL_OK;
+                            },
+                            ms);
                         if (st == RL_OK) trial("weight_grad", l, bn, cm, Sr, ms);
                         if (st == RL_OK && ms < best) { best = ms; best_bn = bn; best_cm = cm; best_S = Sr; best_kc = kc; }
                     }

@@ -42,20 +42,44 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
 }
 
 // ---------------------------------------------------------------- gather
-// One warp per minibatch row: the sampled row of the rollout observations is copied with
-// 16-byte vector loads and stores (Op * element size is a multiple of 128 bytes).
+// One warp per four minibatch rows: the four sampled row indices are read first, then every
+// 16-byte vector of the four rollout observation rows is loaded before any is stored (up to
+// 16 loads in flight per lane); Op * element size is a multiple of 128 bytes.
+constexpr int GATHER_ROWS = 4;      // rows per warp
+constexpr int GATHER_VPL = 4;       // 16-byte vectors per lane and row held in registers at once
+
 template <bool BF16>
 __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
-                                                     int Op, void* X) {
+                                                     int Op, void* __restrict__ X) {
     pdl_wait();
     pdl_trigger();
-    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (row >= M) return;
+    const int lane = threadIdx.x & 31;
+    const int row0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * GATHER_ROWS;
+    if (row0 >= M) return;
     constexpr int E = BF16 ? 2 : 4;
-    const int nvec = Op * E / 16;
-    const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(obs) + (size_t)__ldg(idx + row) * Op * E);
-    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(X) + (size_t)row * Op * E);
-    for (int v = lane; v < nvec; v += 32) dst[v] = __ldg(src + v);
+    const int nvec = Op * E / 16;                         // vectors per row (a multiple of 8)
+    const uint8_t* src[GATHER_ROWS];
+#pragma unroll
+    for (int r = 0; r < GATHER_ROWS; ++r)
+        src[r] = reinterpret_cast<const uint8_t*>(obs) + (size_t)(row0 + r < M ? __ldg(idx + row0 + r) : 0) * Op * E;
+    for (int v0 = 0; v0 < nvec; v0 += 32 * GATHER_VPL) {
+        uint4 val[GATHER_ROWS][GATHER_VPL];
+#pragma unroll
+        for (int r = 0; r < GATHER_ROWS; ++r)
+#pragma unroll
+            for (int k = 0; k < GATHER_VPL; ++k) {
+                const int v = v0 + lane + 32 * k;
+                if (row0 + r < M && v < nvec) val[r][k] = __ldg(reinterpret_cast<const uint4*>(src[r]) + v);
+            }
+#pragma unroll
+        for (int r = 0; r < GATHER_ROWS; ++r)
+#pragma unroll
+            for (int k = 0; k < GATHER_VPL; ++k) {
+                const int v = v0 + lane + 32 * k;
+                if (row0 + r < M && v < nvec)
+                    reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(X) + (size_t)(row0 + r) * Op * E)[v] = val[r][k];
+            }
+    }
 }
 
 // ---------------------------------------------------------------- Adam
@@ -232,7 +256,7 @@ cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned 
 cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (Op % 64) return cudaErrorInvalidValue;
-    const int grid = (M + 7) / 8;
+    const int grid = (M + 8 * GATHER_ROWS - 1) / (8 * GATHER_ROWS);
     cudaError_t e = bf16 ? launch_pdl(gather_kernel<true>, dim3(grid), dim3(256), 0, s, obs, idx, M, Op, X)
                          : launch_pdl(gather_kernel<false>, dim3(grid), dim3(256), 0, s, obs, idx, M, Op, X);
     if (e != cudaSuccess) return e;
