@@ -4,12 +4,13 @@
 // observation with bilinear height samples and Table 4 noise.
 //
 // Layout: the env state is a structure of arrays in HBM ([57][N] fp32 + [3][N] int32), so
-// every state row is read and written with 128-byte coalesced accesses.  A block owns 32
-// robots.  Phase 1: warp 0, one robot per lane, runs the per-robot recurrence in registers
-// and leaves a 60-float record per robot in shared memory.  Phase 2: all 8 warps assemble the
-// observation rows (one robot per warp at a time, two adjacent columns per lane), so the row
-// of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height samples of a
-// robot are gathered by 32 lanes in parallel from the L2-resident heightfield.
+// every state row is read and written with coalesced accesses.  A block owns 16 robots (256 when
+// N is large).  Phase 1: one robot per thread (warp 0 for 16-robot blocks), the per-robot
+// recurrence in registers, leaving a 60-float record per robot in shared memory.  Phase 2: all 8
+// warps assemble the observation rows (one robot per warp at a time, two adjacent columns per
+// lane), so the row of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height
+// samples of a robot are gathered by 32 lanes in parallel from the L2-resident heightfield; the
+// rotated sample offsets of the grid come from a per-block table.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -41,6 +42,7 @@ constexpr int CONTACT_PERIOD = 40, CONTACT_DUTY = 20, CONTACT_ENV_STRIDE = 7;
 
 constexpr int THREADS = 256;    // 8 warps; a block owns ENVS = 32 (small N) or 256 robots
 constexpr int REC = 64;         // floats per robot record in shared memory
+constexpr int GTAB = 1024;      // height-grid offset table entries (larger grids compute in place)
 
 // Record fields (after the 48 proprioceptive observations).
 constexpr int R_PX = 48, R_PY = 49, R_HC = 50, R_HS = 51, R_Z = 52, R_BX = 53, R_BY = 54;
@@ -114,13 +116,20 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
     const int env0 = blockIdx.x * ENVS;
     const int N = p.N;
     const unsigned long long it = p.iteration ? *p.iteration : 0ull;
-    // Phase 1 runs one robot per thread: on warp 0 only for 32-robot blocks (small N, where
-    // spreading robots over many SMs matters more), on every thread for 256-robot blocks.
-    const int local = ENVS == 32 ? lane : (int)threadIdx.x;
-
-    if (ENVS == 256 || warp == 0) {
+    // Phase 1 runs one robot per thread: on lanes 0..ENVS-1 of warp 0 for small blocks (small N,
+    // where spreading robots over many SMs matters more), on every thread for 256-robot blocks.
+    const int local = ENVS < 32 ? lane : (int)threadIdx.x;
+    // grid sample offsets (before rotation) of the height columns, shared by the block's robots
+    float* gtab = rec_raw + ENVS * REC;                                  // [2][GTAB]
+    const int ng = p.GX * p.GY;
+    for (int k = threadIdx.x; k < ng && k < GTAB; k += THREADS) {
+        const int ix = k % p.GX, iy = k / p.GX;
+        gtab[k] = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
+        gtab[GTAB + k] = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+    }
+    float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (reward, reset, level)
+    if (ENVS == 256 || (warp == 0 && lane < ENVS)) {
         const int e = env0 + local;
-        float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (reward, reset, level)
         if (e < N) {
             float* sf = p.sf;
             int* si = p.si;
@@ -319,15 +328,16 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
             R[R_KEYLO] = __uint_as_float(lo32(key));
             R[R_KEYHI] = __uint_as_float(hi32(key));
         }
-        if (MODE == 0 && p.stats) {       // whole warp participates; lanes past N add zeros
+    }
+    // per-block statistics: every lane of the phase-1 warps takes part (idle lanes add zeros)
+    if (MODE == 0 && p.stats && (ENVS == 256 || warp == 0)) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                st_r += __shfl_xor_sync(0xffffffffu, st_r, o);
-                st_d += __shfl_xor_sync(0xffffffffu, st_d, o);
-                st_l += __shfl_xor_sync(0xffffffffu, st_l, o);
-            }
-            if (lane == 0) { atomicAdd(p.stats + 0, st_r); atomicAdd(p.stats + 1, st_d); atomicAdd(p.stats + 2, st_l); }
+        for (int o = 16; o > 0; o >>= 1) {
+            st_r += __shfl_xor_sync(0xffffffffu, st_r, o);
+            st_d += __shfl_xor_sync(0xffffffffu, st_d, o);
+            st_l += __shfl_xor_sync(0xffffffffu, st_l, o);
         }
+        if (lane == 0) { atomicAdd(p.stats + 0, st_r); atomicAdd(p.stats + 1, st_d); atomicAdd(p.stats + 2, st_l); }
     }
     __syncthreads();
 
@@ -350,9 +360,15 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
                     val = R[c];
                 } else if (c < p.O) {
                     const int k = c - 48;
-                    const int ix = k % p.GX, iy = k / p.GX;
-                    const float gxo = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
-                    const float gyo = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+                    float gxo, gyo;
+                    if (k < GTAB) {
+                        gxo = gtab[k];
+                        gyo = gtab[GTAB + k];
+                    } else {
+                        const int ix = k % p.GX, iy = k / p.GX;
+                        gxo = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
+                        gyo = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+                    }
                     const float fx = (px + (hc * gxo - hs * gyo)) * p.inv_res;
                     const float fy = (py + (hs * gxo + hc * gyo)) * p.inv_res;
                     val = z - terrain_height(p.hf, p.nx, p.ny, ibx, fx, iby, fy);
@@ -374,16 +390,16 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
 
 template <int MODE, int ENVS>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
-    const size_t smem = (size_t)ENVS * REC * sizeof(float);
+    const size_t smem = ((size_t)ENVS * REC + 2 * GTAB) * sizeof(float);
     cudaError_t e = launch_pdl(env_step_kernel<MODE, ENVS>, dim3((p.N + ENVS - 1) / ENVS), dim3(THREADS), smem, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// Dynamic shared-memory limit of the 256-robot blocks (64 KiB of robot records), set once
-// before any launch (and so before any stream capture).
+// Dynamic shared-memory limit of the 256-robot blocks (64 KiB of robot records + the 8 KiB grid
+// table), set once before any launch (and so before any stream capture).
 cudaError_t env_prepare() {
-    const int smem = 256 * REC * (int)sizeof(float);
+    const int smem = (256 * REC + 2 * GTAB) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(env_step_kernel<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(env_step_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
@@ -393,8 +409,8 @@ cudaError_t env_prepare() {
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
     const bool big = p.N >= 2 * 148 * 256;
-    if (mode == 0) return big ? launch_cfg<0, 256>(p, s) : launch_cfg<0, 32>(p, s);
-    return big ? launch_cfg<1, 256>(p, s) : launch_cfg<1, 32>(p, s);
+    if (mode == 0) return big ? launch_cfg<0, 256>(p, s) : launch_cfg<0, 16>(p, s);
+    return big ? launch_cfg<1, 256>(p, s) : launch_cfg<1, 16>(p, s);
 }
 
 }  // namespace rl
