@@ -40,7 +40,8 @@ constexpr int SLOT_CMD = 133, SLOT_HEADING = 136, SLOT_EPLEN = 138, SLOT_OBS = 2
 // Foot-contact schedule of the stand-in.
 constexpr int CONTACT_PERIOD = 40, CONTACT_DUTY = 20, CONTACT_ENV_STRIDE = 7;
 
-constexpr int THREADS = 256;    // 8 warps; a block owns ENVS = 32 (small N) or 256 robots
+// Block shapes: 256 threads owning 256 robots (large N, one robot per thread in phase 1), or
+// 256 threads owning 16 robots (small N: every SM gets a block or two).
 constexpr int REC = 64;         // floats per robot record in shared memory
 constexpr int GTAB = 1024;      // height-grid offset table entries (larger grids compute in place)
 
@@ -106,8 +107,8 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
     return (1.f - fu) * (1.f - fv) * h00 + fu * (1.f - fv) * h10 + (1.f - fu) * fv * h01 + fu * fv * h11;
 }
 
-template <int MODE, int ENVS>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
-__global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
+template <int MODE, int ENVS, int THREADS>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
+__global__ void __launch_bounds__(THREADS, 512 / THREADS) env_step_kernel(EnvParams p) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ float rec_raw[];
@@ -388,10 +389,10 @@ __global__ void __launch_bounds__(THREADS, 2) env_step_kernel(EnvParams p) {
 
 }  // namespace
 
-template <int MODE, int ENVS>
+template <int MODE, int ENVS, int THREADS>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
     const size_t smem = ((size_t)ENVS * REC + 2 * GTAB) * sizeof(float);
-    cudaError_t e = launch_pdl(env_step_kernel<MODE, ENVS>, dim3((p.N + ENVS - 1) / ENVS), dim3(THREADS), smem, s, p);
+    cudaError_t e = launch_pdl(env_step_kernel<MODE, ENVS, THREADS>, dim3((p.N + ENVS - 1) / ENVS), dim3(THREADS), smem, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -400,8 +401,9 @@ static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
 // table), set once before any launch (and so before any stream capture).
 cudaError_t env_prepare() {
     const int smem = (256 * REC + 2 * GTAB) * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(env_step_kernel<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(env_step_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(env_step_kernel<0, 256, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(env_step_kernel<1, 256, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -409,8 +411,8 @@ cudaError_t env_prepare() {
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
     const bool big = p.N >= 2 * 148 * 256;
-    if (mode == 0) return big ? launch_cfg<0, 256>(p, s) : launch_cfg<0, 16>(p, s);
-    return big ? launch_cfg<1, 256>(p, s) : launch_cfg<1, 16>(p, s);
+    if (mode == 0) return big ? launch_cfg<0, 256, 256>(p, s) : launch_cfg<0, 16, 256>(p, s);
+    return big ? launch_cfg<1, 256, 256>(p, s) : launch_cfg<1, 16, 256>(p, s);
 }
 
 }  // namespace rl
