@@ -288,8 +288,8 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
 /* Tile autotuner: times each GEMM site (per hidden layer: the update's forward, input gradient
  * and weight gradient at minibatch rows, and the rollout's forward at num_envs rows; actor and
  * critic in one launch) over candidate tile widths
- * (64, 128, 256 output columns), cluster sizes (1 or 2 CTAs sharing one weight/B tile through
- * TMA multicast) and, for weight gradients, split-K counts (a quarter, half, default, double;
+ * (64, 128, 256 output columns), cluster modes (one CTA per tile, two CTAs sharing one B tile
+ * through TMA multicast, or a CTA pair on the cta_group::2 MMA) and, for weight gradients, split-K counts (a quarter, half, default, double;
  * timed together with the summation of their partials, which Adam performs) on the context's
  * own buffers, keeps the fastest, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
@@ -301,8 +301,10 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * control of this implementation).  site: 0 forward, 1 input gradient (layer >= 1), 2 weight
  * gradient (the update's sites, minibatch rows), 3 the rollout's forward (num_envs rows);
  * layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the site's output
- * width; cluster: 1 or 2 (2 needs at least two 128-row tiles at the site, and for sites 1 and
- * 2 a tile width of at least 128);
+ * width; cluster: 1 (one CTA per 128-row tile), 2 (pairs of row tiles share the B tile by TMA
+ * multicast) or 3 (pairs of CTAs run one 256-row tile on the cta_group::2 MMA, each loading half
+ * of B); 2 and 3 need at least two 128-row tiles at the site, 3 a tile width of at least 128, and
+ * 2 at sites 1 and 2 a tile width of at least 128;
  * splits: weight-gradient split-K count (1 .. twice the default, rounded so every slice is a
  * multiple of 64 rows), ignored for the other sites.  Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
@@ -320,6 +322,16 @@ rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const voi
  * weight-gradient GEMM reads the row-major activations and gradients), C [M][N] fp32.
  * M % 8 == 0, N % 64 == 0, K >= 1, pointers 16-byte aligned.  No counterpart in the paper. */
 rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const void* Bt, float* C, void* stream);
+
+/* Diagnostic with an explicit tile shape: operands 0 computes C = A B^T (A [M][K], B [N][K]), 1
+ * computes C = At^T Bt (At [K][M], Bt [K][N]); bn: output tile width 64, 128 or 256 dividing N;
+ * cluster: 1 (one CTA per tile), 2 (pairs of row tiles share the B tile by TMA multicast), 3
+ * (pairs of CTAs run one 256-row tile on the cta_group::2 tensor-core MMA, each CTA loading half
+ * of the B tile; bn 128 or 256).  Requirements as for rl_gemm_bf16 (operands 0) or
+ * rl_gemm_bf16_tn (operands 1); cluster 2 with operands 1 and cluster 3 need bn >= 128.  No
+ * counterpart in the paper. */
+rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, int32_t operands,
+                             int32_t bn, int32_t cluster, void* stream);
 
 /* Number of kernel launches one rl_train_iteration enqueues (host-side count). */
 int32_t rl_launches_per_iteration(rl_ctx* ctx);

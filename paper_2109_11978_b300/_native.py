@@ -87,6 +87,7 @@ SIGNATURES = {
     "rl_set_gemm_tiles": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "rl_gemm_bf16": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rl_gemm_bf16_tn": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "rl_gemm_bf16_shape": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "rl_group_create": (_i32, [_i32, ctypes.POINTER(rl_config), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "rl_group_destroy": (None, [_vp]),
     "rl_group_learner": (_vp, [_vp, _i32]),

@@ -192,6 +192,19 @@ def rl_gemm_bf16_tn(At, Bt, C):
     check(lib().rl_gemm_bf16_tn(int(M), int(Nn), int(K), _ptr(At), _ptr(Bt), _ptr(C), _stream()), "rl_gemm_bf16_tn")
 
 
+def rl_gemm_bf16_shape(A, B, C, operands=0, bn=128, cluster=1):
+    """C = A B^T (operands 0: A [M][K], B [N][K]) or At^T Bt (operands 1: At [K][M], Bt [K][N]) with an
+    explicit tile width and cluster mode (1 single CTA, 2 B-tile multicast, 3 cta_group::2 pair)."""
+    if operands == 0:
+        M, K = A.shape
+        Nn = B.shape[0]
+    else:
+        K, M = A.shape
+        Nn = B.shape[1]
+    check(lib().rl_gemm_bf16_shape(int(M), int(Nn), int(K), _ptr(A), _ptr(B), _ptr(C), int(operands), int(bn), int(cluster),
+                                   _stream()), "rl_gemm_bf16_shape")
+
+
 def rl_launches_per_iteration(ctx):
     return int(lib().rl_launches_per_iteration(ctx))
 

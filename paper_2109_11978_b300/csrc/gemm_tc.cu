@@ -15,7 +15,7 @@
 // Persistent CTA per SM, 576 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
 // swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
 // lane 0 issues 4 tcgen05.mma (K = 16 each) per stage, releases the stage with tcgen05.commit and
-// signals a finished tile on one of two TMEM accumulators; sixteen epilogue warps read the tile
+// signals a finished tile on one of up to four TMEM accumulators; sixteen epilogue warps read the tile
 // back with tcgen05.ld while the next tile accumulates in the other buffer.  Every mbarrier wait
 // is bounded by the global timer; a wait that runs out records RL_ERR_TIMEOUT in the status
 // word, the CTA stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its
@@ -120,10 +120,10 @@ __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
 // A MN-major at bit 15, B MN-major at bit 16 (clear: K-major), N >> 3 at bits 17-22, M >> 4 at
 // bits 24-28.
-template <int N, bool A_MN, bool B_MN>
+template <int N, bool A_MN, bool B_MN, int M = BM>
 __device__ __forceinline__ uint32_t idesc_bf16() {
     return (1u << 4) | (1u << 7) | (1u << 10) | (A_MN ? (1u << 15) : 0u) | (B_MN ? (1u << 16) : 0u) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -156,6 +156,45 @@ __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
                  "h"(mask)
                  : "memory");
+}
+
+// Pair (cta_group::2) forms: the two CTAs of a cluster compute one 256-row tile; the MMA is
+// issued by the even CTA, reads A (128 rows) and half of B from each CTA's shared memory and
+// accumulates each CTA's 128 rows in that CTA's tensor memory.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t cbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(cbar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
+}
+// TMA load into this CTA's shared memory, completing bytes on the even CTA's mbarrier
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t cbar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(cbar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"(mask)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -229,10 +268,10 @@ __device__ __forceinline__ float colsum32(float (&v)[32], int lane) {
     return v[0];
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int BROWS = BN>
 struct TileCfg {
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int B_BYTES = BROWS * BK * 2;          // B rows staged per CTA (BN / 2 in pair mode)
     static constexpr int STAGE = A_BYTES + B_BYTES;
     // row-major staging pitch in bytes (a 32-column row of bf16 or fp32 plus 16 bytes: the
     // 16-byte writes of eight consecutive rows fall in distinct banks)
@@ -250,6 +289,9 @@ struct TileCfg {
     static constexpr int BAR_BYTES = 512;
     static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
     static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3;
+    // TMEM accumulator buffers (BN columns each, 512 columns in all): the MMA warp can run that many
+    // tiles ahead of the epilogue
+    static constexpr int NACC = 512 / BN < 4 ? 512 / BN : 4;
     static constexpr int SMEM = STAGES * STAGE + FIXED;
 };
 
@@ -260,17 +302,21 @@ struct TileCfg {
 // cluster, so the B operand is read from L2 once per cluster instead of once per CTA.  A stage
 // is refilled only after all CM CTAs' MMAs have released it (the MMA commit arrives on every
 // CTA's "empty" barrier).  The TMA warp streams K blocks through a STAGES-deep ring; the MMA warp
-// accumulates each tile into one of two TMEM buffers (2 x BN columns) while the sixteen epilogue
+// accumulates each tile into one of NACC TMEM buffers (NACC x BN = 512 columns, at most 4 buffers)
+// while the sixteen epilogue
 // warps drain the other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue
 // warp e reads TMEM lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
-template <int BN, int EPI, int CM, int MJ>
+template <int BN, int EPI, int CM, int MJ, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-    using C = TileCfg<BN, EPI>;
+    // PAIR: the cluster's two CTAs run one 256 x BN tile on the pair (cta_group::2) tensor core;
+    // each CTA stages its 128 rows of A and half of B, the even CTA issues the MMAs
+    static_assert(!PAIR || CM == 2, "pair mode runs on clusters of two");
+    using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN>;
     constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
     constexpr bool B_MN = MJ != MAJ_K;                      // B^T [K][N] in memory
-    constexpr int B_SLICE_ROWS = BN / CM;
-    constexpr int B_BOXES = B_MN ? BN / 64 / CM : 1;        // MN-major: 64-wide boxes per CTA
-    static_assert(!B_MN || (BN / 64) % CM == 0, "MN-major B tile must split into whole boxes");
+    constexpr int B_SLICE_ROWS = PAIR ? BN / 2 : BN / CM;   // B rows this CTA loads
+    constexpr int B_BOXES = B_MN ? B_SLICE_ROWS / 64 : 1;   // MN-major: 64-wide boxes per CTA
+    static_assert(!B_MN || B_SLICE_ROWS % 64 == 0, "MN-major B tile must split into whole boxes");
     constexpr uint16_t MC_MASK = (uint16_t)((1u << CM) - 1u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -280,11 +326,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
     // barriers: full[S], empty[S], tfull[2], tempty[2], drain, hbar[EPI_WARPS][2]
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
-    const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + 2);
-    const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 4);
-    const uint32_t hbar0 = smem_u32(bars + 2 * C::STAGES + 5);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5 + 2 * EPI_WARPS);
-    static_assert((2 * C::STAGES + 5 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
+    constexpr int NACC = C::NACC;
+    const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + NACC);
+    const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 2 * NACC);
+    const uint32_t hbar0 = smem_u32(bars + 2 * C::STAGES + 2 * NACC + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS);
+    static_assert((2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     // a multicast instantiation launched without its cluster shape would address CTAs that do
@@ -303,12 +350,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, CM);
+            mbar_init(full0 + 8 * s, PAIR ? 2 : 1);             // pair: one arrival per CTA (even CTA's)
+            mbar_init(empty0 + 8 * s, PAIR ? 1 : CM);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, EPI_WARPS);
+            mbar_init(tempty0 + 8 * a, PAIR ? 2 * EPI_WARPS : EPI_WARPS);
         }
         mbar_init(drain, 1);
         if (EPI == EPI_ELU_GRAD)
@@ -318,10 +365,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)(2 * BN))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                         "r"((uint32_t)(NACC * BN))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                         "r"((uint32_t)(NACC * BN))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -376,6 +430,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         break;
                     }
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    if constexpr (PAIR) {
+                        // both CTAs' copies complete on the even CTA's barrier, which the MMA waits on
+                        const uint32_t cfull = mapa_rank(full0 + 8 * s, 0);
+                        mbar_expect_tx_cluster(cfull, (uint32_t)C::STAGE);
+                        if (!A_MN) {
+                            tma_load_2d_pair(sa, ma, cfull, (kb0 + i) * BK, ay);
+                        } else {
+                            tma_load_2d_pair(sa, ma, cfull, ay, (kb0 + i) * BK);
+                            tma_load_2d_pair(sa + 8192, ma, cfull, ay + 64, (kb0 + i) * BK);
+                        }
+                        if (!B_MN) {
+                            tma_load_2d_pair(sa + C::A_BYTES, mb, cfull, (kb0 + i) * BK, ni * BN + rank * B_SLICE_ROWS);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < B_BOXES; ++j)
+                                tma_load_2d_pair(sa + C::A_BYTES + 8192 * j, mb, cfull, ni * BN + rank * B_SLICE_ROWS + 64 * j,
+                                                 (kb0 + i) * BK);
+                        }
+                        continue;
+                    }
                     mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
                     if (!A_MN) {
                         tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, ay);
@@ -404,13 +478,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                 }
             }
-            if (!ok) {
-                // let the copies already issued land before the CTA leaves (bounded)
+            if (!ok && !PAIR) {
+                // let the copies already issued land before the CTA leaves (bounded; in pair mode
+                // they complete on the even CTA's barriers and cannot be observed here)
                 for (int k = 1; k <= C::STAGES && it - k >= 0; ++k) {
                     const int j = it - k;
                     mbar_wait(full0 + 8 * (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, p.status);
                 }
-            } else if (CM > 1) {
+            } else if (ok && CM > 1) {
                 // every CTA of the cluster has released the last use of each stage: no copy or
                 // MMA-completion arrival of this cluster can still target this CTA's memory
                 for (int k = 1; k <= C::STAGES && it - k >= 0; ++k) {
@@ -421,16 +496,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer
-            const uint32_t idesc = idesc_bf16<BN, A_MN, B_MN>();
+            // ---------------- MMA issuer (pair mode: the even CTA only)
+            const uint32_t idesc = idesc_bf16<BN, A_MN, B_MN, PAIR ? 2 * BM : BM>();
             int it = 0, local = 0;
             bool ok = true;
-            for (int t = cid; t < total && ok; t += ncl, ++local) {
+            const bool issuer = !PAIR || rank == 0;
+            for (int t = cid; issuer && t < total && ok; t += ncl, ++local) {
                 int mi, ni, sp, b, kb0;
                 decode(t, mi, ni, sp, b);
                 const int nkb = kblocks_of(sp, kb0);
-                const int a = local & 1;
-                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                const int a = local % NACC;
+                const uint32_t aph = (uint32_t)(local / NACC) & 1u;
                 if (*abort_flag || !mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status)) {
                     *abort_flag = 1;
                     break;
@@ -452,17 +528,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     // K16 step: 32 bytes along the swizzled row (K-major), two 8-row atoms (MN-major)
                     constexpr uint64_t KSTEP_A = A_MN ? (2048 >> 4) : (32 >> 4);
                     constexpr uint64_t KSTEP_B = B_MN ? (2048 >> 4) : (32 >> 4);
+                    if constexpr (PAIR) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
-                        mma_bf16(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    if (CM == 1) mma_commit(empty0 + 8 * s);
-                    else mma_commit_mc(empty0 + 8 * s, MC_MASK);
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16_pair(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit_pair_mc(empty0 + 8 * s, MC_MASK);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        if (CM == 1) mma_commit(empty0 + 8 * s);
+                        else mma_commit_mc(empty0 + 8 * s, MC_MASK);
+                    }
                 }
-                mma_commit(tfull0 + 8 * a);   // arrives when every MMA issued so far has completed
+                // arrives when every MMA issued so far has completed (pair: in both CTAs)
+                if constexpr (PAIR) mma_commit_pair_mc(tfull0 + 8 * a, MC_MASK);
+                else mma_commit(tfull0 + 8 * a);
             }
-            // drain: every MMA this thread issued has finished before the TMEM is freed
-            mma_commit(drain);
-            mbar_wait(drain, 0u, p.status);
+            if (issuer) {
+                // drain: every MMA this thread issued has finished before the TMEM is freed
+                if constexpr (PAIR) mma_commit_pair(drain);
+                else mma_commit(drain);
+                mbar_wait(drain, 0u, p.status);
+                if (PAIR && ok && !*abort_flag) {
+                    // the odd CTA's epilogue arrives on this CTA's tempty barriers: wait for the last
+                    // release of each buffer so that no arrival is still on its way when this CTA leaves
+                    for (int k = 1; k <= NACC && local - k >= 0; ++k) {
+                        const int j = local - k;
+                        if (!mbar_wait(tempty0 + 8 * (j % NACC), (uint32_t)(j / NACC) & 1u, p.status)) break;
+                    }
+                }
+            }
         }
     } else {
         // ---------------- epilogue warps
@@ -499,8 +595,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             int mi, ni, sp, b, kb0;
             decode(t, mi, ni, sp, b);
             const int nkb = kblocks_of(sp, kb0);
-            const int a = local & 1;
-            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            const int a = local % NACC;
+            const uint32_t aph = (uint32_t)(local / NACC) & 1u;
             const int m0 = mi * BM, n0 = ni * BN;
             const int row = m0 + 32 * q + lane;
             const bool row_ok = row < p.M;
@@ -613,10 +709,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                 }
             }
-            // the TMEM buffer is free for the next tile's MMAs
+            // the TMEM buffer is free for the next tile's MMAs (pair: on the even CTA's barrier)
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+            if (lane == 0) {
+                if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * a, 0));
+                else mbar_arrive(tempty0 + 8 * a);
+            }
             if (stop) break;
         }
         // an activation block still in flight lands before the CTA leaves (bounded)
@@ -627,7 +726,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(NACC * BN)) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(NACC * BN)) : "memory");
     }
 }
 
@@ -641,10 +743,20 @@ static ClusterFit g_fit[64];
 static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 2 : -1; }
 static int cm_index(int cm) { return cm == 1 ? 0 : cm == 2 ? 1 : cm == 4 ? 2 : -1; }
 
-template <int BN, int EPI, int CM, int MJ>
+template <int BN, int EPI, int CM, int MJ, bool PAIR>
+constexpr int smem_of() {
+    return TileCfg<BN, EPI, PAIR ? BN / 2 : BN>::SMEM;
+}
+// slot of the cluster-fit table: 0 single CTA, 1 cluster of two (multicast), 2 pair
+template <int CM, bool PAIR>
+constexpr int fit_slot() {
+    return PAIR ? 2 : (CM == 1 ? 0 : 1);
+}
+
+template <int BN, int EPI, int CM, int MJ, bool PAIR>
 cudaError_t set_attr(int dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TileCfg<BN, EPI>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_of<BN, EPI, CM, MJ, PAIR>());
     if (e != cudaSuccess) return e;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -658,30 +770,30 @@ cudaError_t set_attr(int dev) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)(n * CM));
         cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = TileCfg<BN, EPI>::SMEM;
+        cfg.dynamicSmemBytes = smem_of<BN, EPI, CM, MJ, PAIR>();
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int fit = 0;
-        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MJ>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, &cfg);
         if (e != cudaSuccess) return e;
         if (fit > 0 && fit < n) n = fit;
     }
-    if (dev >= 0 && dev < 64) g_fit[dev].clusters[bn_index(BN)][EPI][cm_index(CM)] = n > 0 ? n : 1;
+    if (dev >= 0 && dev < 64) g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR>()] = n > 0 ? n : 1;
     return cudaSuccess;
 }
 
-template <int BN, int EPI, int CM, int MJ>
+template <int BN, int EPI, int CM, int MJ, bool PAIR>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
-    using C = TileCfg<BN, EPI>;
     int dev = 0;
     cudaGetDevice(&dev);
-    int fit = (dev >= 0 && dev < 64) ? g_fit[dev].clusters[bn_index(BN)][EPI][cm_index(CM)] : 0;
+    int fit = (dev >= 0 && dev < 64) ? g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR>()] : 0;
     if (fit <= 0) return cudaErrorNotReady;        // tc_prepare has not run on this device
     const int mct = ((p.M + BM - 1) / BM + CM - 1) / CM;
     const int total = mct * (p.N / BN) * p.splits * p.batch;
     const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
+    constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR>();
     if (CM == 1) {
-        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ>, dim3(clusters), dim3(TC_THREADS), C::SMEM, s, p);
+        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[2];
@@ -693,22 +805,27 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3((unsigned)(clusters * CM));
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.dynamicSmemBytes = SMEM;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ>, p);
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, p);
 }
 
 // Instantiated operand forms: forward (EPI_BIAS_ELU) both K-major; input gradient
 // (EPI_ELU_GRAD) A K-major, B = W read MN-major; split-K weight gradient and the diagnostic
 // GEMMs (EPI_STORE) both K-major or both MN-major.  A cluster of 2 with an MN-major B needs
-// whole 64-column boxes per CTA (BN >= 128).
+// whole 64-column boxes per CTA (BN >= 128); pair mode runs with BN = 128 or 256.
 
 template <int BN, int EPI, int MJ>
 cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
-    if (p.cm == 1) return launch_cfg<BN, EPI, 1, MJ>(p, s);
-    if (p.cm == 2 && (MJ == MAJ_K || BN >= 128)) return launch_cfg<BN, EPI, 2, (MJ == MAJ_K || BN >= 128) ? MJ : MAJ_K>(p, s);
+    if (p.cm == 1) return launch_cfg<BN, EPI, 1, MJ, false>(p, s);
+    if (p.cm == 2 && p.pair) {
+        if constexpr (BN >= 128) return launch_cfg<BN, EPI, 2, MJ, true>(p, s);
+        return cudaErrorInvalidValue;
+    }
+    if (p.cm == 2 && (MJ == MAJ_K || BN >= 128))
+        return launch_cfg<BN, EPI, 2, (MJ == MAJ_K || BN >= 128) ? MJ : MAJ_K, false>(p, s);
     return cudaErrorInvalidValue;
 }
 
@@ -738,12 +855,14 @@ cudaError_t launch_bn(const TcParams& p, cudaStream_t s) {
 template <int EPI, int MJ>
 cudaError_t prepare_form(int dev) {
     cudaError_t e = cudaSuccess;
-    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ>(dev);
-    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ>(dev);
-    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ>(dev);
-    e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ>(dev);
-    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ>(dev);
-    if (MJ == MAJ_K) e = e != cudaSuccess ? e : set_attr<64, EPI, 2, MAJ_K>(dev);
+    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ, true>(dev);
+    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, true>(dev);
+    if (MJ == MAJ_K) e = e != cudaSuccess ? e : set_attr<64, EPI, 2, MAJ_K, false>(dev);
     return e;
 }
 
@@ -754,6 +873,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.bn <= 0 || p.N % p.bn || p.kblocks <= 0 || p.splits <= 0 || p.batch < 1 || p.batch > 2) return cudaErrorInvalidValue;
     if (p.cm != 1 && p.cm != 2) return cudaErrorInvalidValue;
     if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
+    if (p.pair && (p.cm != 2 || p.bn < 128)) return cudaErrorInvalidValue;
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -826,7 +946,7 @@ cudaError_t tc_prepare() {
 int tc_cluster_fit(int bn, int epi, int cm) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    const int bi = bn_index(bn), ci = cm_index(cm);
+    const int bi = bn_index(bn), ci = cm_index(cm);   // cm 4: the pair slot
     if (bi < 0 || ci < 0 || epi < 0 || epi > 2) return 0;
     return g_fit[dev].clusters[bi][epi][ci];
 }

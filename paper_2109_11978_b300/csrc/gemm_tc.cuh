@@ -18,6 +18,8 @@ struct TcParams {
     int batch;                 // 1 or 2 (actor, critic share one launch)
     int bn;                    // 64, 128 or 256
     int cm;                    // CTAs per cluster along M sharing (multicasting) the B tile: 1 or 2
+    int pair;                  // with cm = 2: the pair runs one 256-row tile on the cta_group::2 MMA,
+                               // each CTA loading half of B (B maps: box rows bn / 2); bn 128 / 256
     int mn;                    // operand forms: MAJ_K (A [M][K], B [N][K]), MAJ_MN (A^T [K][M],
                                // B^T [K][N], EPI_STORE), MAJ_B_MN (A [M][K], B^T [K][N],
                                // EPI_ELU_GRAD); MN-major operands use 64 x 64 boxes

@@ -80,7 +80,9 @@ struct rl_ctx {
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
     int bn_fwd[4], bn_dx[4], bn_dw[4], bn_act[4];
-    int cm_fwd[4], cm_dx[4], cm_dw[4], cm_act[4];   // cluster size along M (B tile multicast)
+    // cluster mode per site: 1 single CTA, 2 pairs of row tiles sharing the B tile (multicast),
+    // 3 pairs of CTAs running one 256-row tile on the cta_group::2 MMA (half of B each)
+    int cm_fwd[4], cm_dx[4], cm_dw[4], cm_act[4];
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
     CUtensorMap tm_actB[2][4];                   // forward B maps of the rollout's policy inference
     CUtensorMap tm_x0;                           // gathered minibatch observations
@@ -183,6 +185,13 @@ struct Enq {
     }
 };
 
+// B rows one CTA loads per K step for a K-major B (tile width bn, cluster mode cm)
+uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 ? bn / 2 : bn / cm); }
+void set_cluster(TcParams& tp, int cm) {
+    tp.cm = cm == 1 ? 1 : 2;
+    tp.pair = cm == 3 ? 1 : 0;
+}
+
 int pick_bn(int n) {
     if (n % 128 == 0) return 128;
     return 64;
@@ -193,8 +202,8 @@ bool encode_layer_maps(rl_ctx* c, int l) {
     bool ok = true;
     for (int n = 0; n < 2; ++n) {
         const LayerInfo& Li = c->L[n][l];
-        ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_fwd[l] / c->cm_fwd[l]);
-        ok = ok && make_tmap_bf16(&c->tm_actB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, c->bn_act[l] / c->cm_act[l]);
+        ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_fwd[l], c->cm_fwd[l]));
+        ok = ok && make_tmap_bf16(&c->tm_actB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_act[l], c->cm_act[l]));
         if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
@@ -238,7 +247,7 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.splits = 1;
         tp.batch = nnets;
         tp.bn = act ? c->bn_act[l] : c->bn_fwd[l];
-        tp.cm = act ? c->cm_act[l] : c->cm_fwd[l];
+        set_cluster(tp, act ? c->cm_act[l] : c->cm_fwd[l]);
         tp.epi = EPI_BIAS_ELU;
         tp.ldc = Li.out;
         tp.status = c->status;
@@ -282,7 +291,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.colsum[n] = c->gb[n][k - 1];
         }
         tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
-        tp.batch = 2; tp.bn = c->bn_dx[k]; tp.cm = c->cm_dx[k]; tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
+        tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -312,7 +321,7 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.C[n] = c->gw[n][k];
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
-        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; tp.cm = c->cm_dw[k]; tp.mn = MAJ_MN; tp.epi = EPI_STORE;
+        tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; set_cluster(tp, c->cm_dw[k]); tp.mn = MAJ_MN; tp.epi = EPI_STORE;
         tp.ldc = Li.in;
         tp.split_stride = (long long)Li.out * Li.in;
         tp.status = c->status;
@@ -637,7 +646,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
         trials += buf;
     };
     const int bns[3] = {64, 128, 256};
-    const int cms[2] = {1, 2};
+    const int cms[3] = {1, 2, 3};
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
         const int row_tiles = (c->Mb + 127) / 128;
@@ -647,7 +656,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
             float best = 1e30f;
             for (int bn : bns)
                 for (int cm : cms) {
-                    if (Li.out % bn || (cm > 1 && row_tiles < cm) || st != RL_OK) continue;
+                    if (Li.out % bn || (cm > 1 && row_tiles < 2) || (cm == 3 && bn < 128) || st != RL_OK) continue;
                     c->bn_fwd[l] = bn;
                     c->cm_fwd[l] = cm;
                     if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -666,7 +675,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 float abest = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.out % bn || (cm > 1 && act_tiles < cm) || st != RL_OK) continue;
+                        if (Li.out % bn || (cm > 1 && act_tiles < 2) || (cm == 3 && bn < 128) || st != RL_OK) continue;
                         c->bn_act[l] = bn;
                         c->cm_act[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -686,7 +695,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 best = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.in % bn || (cm > 1 && (row_tiles < cm || bn < 128)) || st != RL_OK) continue;
+                        if (Li.in % bn || (cm > 1 && (row_tiles < 2 || bn < 128)) || st != RL_OK) continue;
                         c->bn_dx[l] = bn;
                         c->cm_dx[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -710,7 +719,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
                 for (int cm : cms) {
-                    if (cm > 1 && (!c->bf16 || out_tiles < cm || bn < 128)) continue;   // whole 64-wide B boxes per CTA
+                    if (cm > 1 && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
                     for (int S : {S0 / 4, S0 / 2, S0, 2 * S0}) {
                         if (S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
                         int kc = (c->Mb + S - 1) / S;
@@ -763,11 +772,11 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
 
 rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
     if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
-    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 2)) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || cm < 1 || cm > 3) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
     const int width = (site == 0 || site == 3) ? Li.out : Li.in;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
-    if (width % bn || row_tiles < cm) return RL_ERR_INVALID_ARG;
+    if (width % bn || (cm > 1 && row_tiles < 2) || (cm == 3 && bn < 128)) return RL_ERR_INVALID_ARG;
     if ((site == 1 || site == 2) && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
     if (site == 2) {
@@ -1401,6 +1410,36 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
     tp.bn = bn; tp.cm = cm; tp.mn = MAJ_MN; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    CK(launch_tc_gemm(tp, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, int32_t operands,
+                             int32_t bn, int32_t cluster, void* stream) {
+    if (M < 1 || N < 64 || N % 64 || K < 1 || !A || !B || !C) return RL_ERR_INVALID_ARG;
+    if (operands != 0 && operands != 1) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || N % bn || cluster < 1 || cluster > 3) return RL_ERR_INVALID_ARG;
+    if (operands == 0 && K % 8) return RL_ERR_INVALID_ARG;
+    if (operands == 1 && M % 8) return RL_ERR_INVALID_ARG;
+    if ((cluster == 3 || (cluster == 2 && operands == 1)) && bn < 128) return RL_ERR_INVALID_ARG;
+    if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
+    TcParams tp;
+    std::memset(&tp, 0, sizeof(tp));
+    const int cm = cluster == 1 ? 1 : 2;
+    const int pair = cluster == 3 ? 1 : 0;
+    const uint32_t brows = pair ? bn / 2 : bn / cm;
+    if (operands == 0) {
+        if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
+        if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, brows)) return RL_ERR_CUDA;
+        tp.mn = MAJ_K;
+    } else {
+        if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)) return RL_ERR_CUDA;
+        if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
+        tp.mn = MAJ_MN;
+    }
+    CK(tc_prepare());
+    tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
+    tp.bn = bn; tp.cm = cm; tp.pair = pair; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }

@@ -59,6 +59,32 @@ def test_tc_gemm_mn_major_matches_fp64(M, N, K):
     assert err < max(2e-6, 5e-7 * np.sqrt(K)), err
 
 
+@pytest.mark.parametrize("operands,bn,cluster", [(0, 64, 1), (0, 128, 2), (0, 256, 3), (0, 128, 3), (1, 128, 1),
+                                                 (1, 256, 2), (1, 256, 3), (1, 128, 3)])
+@pytest.mark.parametrize("M,N,K", [(300, 512, 200), (1024, 256, 1000)])
+def test_tc_gemm_tile_modes(operands, bn, cluster, M, N, K):
+    """Every cluster mode of the tensor-core GEMM on both operand forms, with a ragged row count
+    (the last cluster has a CTA past the rows) and a ragged K: cluster 2 multicasts the B tile,
+    cluster 3 runs 256-row tiles on the cta_group::2 MMA with half of B in each CTA."""
+    g = torch.Generator().manual_seed(M + 3 * N + K + bn + 11 * cluster + 97 * operands)
+    if operands == 0:
+        K8 = (K + 7) // 8 * 8
+        A = torch.randn(M, K8, generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K8, generator=g).to(torch.bfloat16)
+        ref = A.double().numpy() @ B.double().numpy().T
+    else:
+        M8 = (M + 7) // 8 * 8
+        A = torch.randn(K, M8, generator=g).to(torch.bfloat16)
+        B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+        ref = A.double().numpy().T @ B.double().numpy()
+    C = torch.full(ref.shape, float("nan"), device="cuda")
+    api.rl_gemm_bf16_shape(A.cuda(), B.cuda(), C, operands, bn, cluster)
+    torch.cuda.synchronize()
+    err = np.abs(C.cpu().double().numpy() - ref).max() / np.abs(ref).max()
+    k_len = A.shape[1] if operands == 0 else A.shape[0]
+    assert err < max(2e-6, 5e-7 * np.sqrt(k_len)), err     # FP32 accumulation, one rounding per 16 products
+
+
 def _learner(w, hf=None, params=None):
     cfg = lib_config(w)
     O, _ = obs_dims(w)
