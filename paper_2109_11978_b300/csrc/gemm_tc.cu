@@ -58,19 +58,26 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase.  Returns false (and records the timeout) after WAIT_NS.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
-    if (mbar_try(bar, parity)) return true;
+// Bounded wait on an mbarrier phase (slow path).  Returns false when the CTA's abort flag is
+// raised by another role, or (recording the timeout) after WAIT_NS.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int* status, volatile int* abort) {
     const unsigned long long t0 = global_ns();
     for (;;) {
 #pragma unroll 1
         for (int i = 0; i < 256; ++i)
             if (mbar_try(bar, parity)) return true;
+        if (abort && *abort) return false;
         if (global_ns() - t0 > WAIT_NS) {
             set_status(status, RL_ERR_TIMEOUT);
             return false;
         }
     }
+}
+
+// Bounded wait, fast path inline: one poll of the phase, the slow path only if it is not done.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, volatile int* abort = nullptr) {
+    if (mbar_try(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, status, abort);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -138,6 +145,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+// TMA store of a shared-memory box to the tensor (rows / columns past the tensor are clipped),
+// tracked by the thread's bulk async-group.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most n of this thread's store groups may still be reading shared memory
+template <int n>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(n) : "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Multicast form: the box lands at the same shared-memory offset in every CTA of the cluster
 // named by `mask`, and completes bytes on the mbarrier at the same offset in each of them.
@@ -273,16 +294,13 @@ struct TileCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BROWS * BK * 2;          // B rows staged per CTA (BN / 2 in pair mode)
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    // row-major staging pitch in bytes (a 32-column row of bf16 or fp32 plus 16 bytes: the
-    // 16-byte writes of eight consecutive rows fall in distinct banks)
-    static constexpr int RP = EPI == EPI_STORE ? 144 : 80;
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
-    // per epilogue warp one 32 x 32 block of the output; the ELU-gradient form instead keeps two
-    // 32 x 32 bf16 activation blocks (TMA, 64-byte swizzle), each overwritten in place by its
-    // output block before the coalesced store
-    static constexpr int STG_WARP = EPI == EPI_ELU_GRAD ? 2 * 2048 : 32 * RP;
+    // per epilogue warp, output blocks of 32 x 32 leave by TMA store from shared memory: bf16 forms
+    // two 2 KB blocks (64-byte swizzle; the ELU-gradient form first loads its activation block
+    // into the same buffer), the fp32 split-K form one 4 KB block (128-byte swizzle)
+    static constexpr int STG_WARP = 4096;
     static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
     // the bias vectors of both batch entries (at most 1024 columns), loaded once per CTA
     static constexpr int BIAS_BYTES = EPI == EPI_BIAS_ELU ? 2 * 1024 * 4 : 0;
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 for (int i = 0; i < nkb; ++i, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-                    if (*abort_flag || !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) {
+                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, abort_flag)) {
                         *abort_flag = 1;
                         ok = false;
                         break;
@@ -501,13 +519,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             int it = 0, local = 0;
             bool ok = true;
             const bool issuer = !PAIR || rank == 0;
+            const uint32_t sa0 = smem_u32(smem);
+            const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0) : sw128_desc(sa0);
+            const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + C::A_BYTES) : sw128_desc(sa0 + C::A_BYTES);
             for (int t = cid; issuer && t < total && ok; t += ncl, ++local) {
                 int mi, ni, sp, b, kb0;
                 decode(t, mi, ni, sp, b);
                 const int nkb = kblocks_of(sp, kb0);
                 const int a = local % NACC;
                 const uint32_t aph = (uint32_t)(local / NACC) & 1u;
-                if (*abort_flag || !mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status)) {
+                if (!mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status, abort_flag)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -516,15 +537,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 for (int i = 0; i < nkb; ++i, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-                    if (*abort_flag || !mbar_wait(full0 + 8 * s, ph, p.status)) {
+                    if (!mbar_wait(full0 + 8 * s, ph, p.status, abort_flag)) {
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    const uint64_t ad = A_MN ? sw128_desc_mn(sa) : sw128_desc(sa);
-                    const uint64_t bd = B_MN ? sw128_desc_mn(sa + C::A_BYTES) : sw128_desc(sa + C::A_BYTES);
+                    // stage s descriptors: stage 0's plus the stage offset in 16-byte units
+                    const uint64_t soff = (uint64_t)((s * C::STAGE) >> 4);
+                    const uint64_t ad = ad0 + soff, bd = bd0 + soff;
                     // K16 step: 32 bytes along the swizzled row (K-major), two 8-row atoms (MN-major)
                     constexpr uint64_t KSTEP_A = A_MN ? (2048 >> 4) : (32 >> 4);
                     constexpr uint64_t KSTEP_B = B_MN ? (2048 >> 4) : (32 >> 4);
@@ -581,6 +602,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const int x = ni * BN + slice * C::SLICE_COLS + 32 * (j % CPT);
             const int y = min(mi, mt - 1) * BM + 32 * q;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // prior reads/writes of the buffer
+            if (lane == 0) bulk_wait_read<0>();      // the output store from this buffer has read it
             __syncwarp();
             if (lane == 0) {
                 const uint32_t bar = hbar0 + 8 * (2 * ew + (j & 1));
@@ -590,6 +612,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             return true;
         };
         if (EPI == EPI_ELU_GRAD && busy) h_pending = h_issue(0);
+        int oj = 0;                                              // bf16 output blocks written (buffer index)
         int local = 0;
         for (int t = cid; t < total; t += ncl, ++local) {
             int mi, ni, sp, b, kb0;
@@ -601,7 +624,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const int row = m0 + 32 * q + lane;
             const bool row_ok = row < p.M;
             const bool tile_ok = mi < mt;
-            if (*abort_flag || !mbar_wait(tfull0 + 8 * a, aph, p.status)) {
+            if (!mbar_wait(tfull0 + 8 * a, aph, p.status, abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
@@ -617,20 +640,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 const int col = n0 + c;
                 if (EPI == EPI_STORE) {
-                    // through shared memory, so that eight lanes write one row's 128 bytes
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4*>(stg_raw + lane * C::RP + 4 * j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    // fp32 block, 128-byte swizzle (16-byte unit u of row r at unit u ^ (r & 7)),
+                    // out by TMA store once the previous store from the buffer has read it
+                    if (lane == 0) bulk_wait_read<0>();
                     __syncwarp();
-                    float* dst = reinterpret_cast<float*>(p.C[b]) + (size_t)sp * p.split_stride + col;
 #pragma unroll
-                    for (int idx = lane; idx < 256; idx += 32) {
-                        const int r = idx >> 3, g = idx & 7;
-                        const int rr = m0 + 32 * q + r;
-                        const float4 val = *reinterpret_cast<const float4*>(stg_raw + r * C::RP + 16 * g);
-                        if (rr < p.M) *reinterpret_cast<float4*>(dst + (size_t)rr * p.ldc + 4 * g) = val;
+                    for (int u = 0; u < 8; ++u)
+                        *reinterpret_cast<float4*>(stg_raw + lane * 128 + 16 * (u ^ (lane & 7))) =
+                            make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && tile_ok) {
+                        tma_store_3d(&p.tmC[b], smem_u32(stg_raw), col, m0 + 32 * q, sp);
+                        bulk_commit();
                     }
-                    __syncwarp();
                 } else if (EPI == EPI_BIAS_ELU) {
                     const float4* bias4 = reinterpret_cast<const float4*>(bias_s + b * 1024 + col);
 #pragma unroll
@@ -644,25 +667,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
-                    // row-major copy through shared memory: four lanes write one row's 64 bytes
+                    // bf16 block in one of two buffers (64-byte swizzle: 16-byte unit u of row r at
+                    // unit u ^ ((r >> 1) & 3)), out by TMA store; the store issued from this buffer
+                    // two blocks ago must have read it
+                    uint8_t* ob = stg_raw + 2048 * (oj & 1);
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+                    const int sw = (lane >> 1) & 3;
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
-                        *reinterpret_cast<uint4*>(stg_raw + lane * C::RP + 16 * g) = reinterpret_cast<const uint4*>(o)[g];
+                        *reinterpret_cast<uint4*>(ob + lane * 64 + 16 * (g ^ sw)) = reinterpret_cast<const uint4*>(o)[g];
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
-                    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
-#pragma unroll
-                    for (int idx = lane; idx < 128; idx += 32) {
-                        const int r = idx >> 2, g = idx & 3;
-                        const int rr = m0 + 32 * q + r;
-                        const uint4 val = *reinterpret_cast<const uint4*>(stg_raw + r * C::RP + 16 * g);
-                        if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
+                    if (lane == 0 && tile_ok) {
+                        tma_store_3d(&p.tmC[b], smem_u32(ob), col, m0 + 32 * q, 0);
+                        bulk_commit();
                     }
-                    __syncwarp();
+                    ++oj;
                 } else {   // EPI_ELU_GRAD
                     // the next chunk's activations go into the other buffer (free: its chunk is done)
                     const bool next = h_issue(hj + 1);
                     uint8_t* hb = stg_raw + 2048 * (hj & 1);
-                    if (!mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status)) {
+                    if (!mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status, abort_flag)) {
                         *abort_flag = 1;
                         h_pending = next;
                         ++hj;
@@ -686,21 +712,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
-                    // the output block replaces the activation block in place (same swizzle), then
-                    // leaves with four lanes per row
+                    // the output block replaces the activation block in place (same swizzle) and
+                    // leaves by TMA store
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
                         *reinterpret_cast<uint4*>(hb + lane * 64 + 16 * (g ^ sw)) = reinterpret_cast<const uint4*>(o)[g];
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
-                    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C[b]) + col;
-#pragma unroll
-                    for (int idx = lane; idx < 128; idx += 32) {
-                        const int r = idx >> 2, g = idx & 3;
-                        const int rr = m0 + 32 * q + r;
-                        const uint4 val = *reinterpret_cast<const uint4*>(hb + r * 64 + 16 * (g ^ ((r >> 1) & 3)));
-                        if (rr < p.M) *reinterpret_cast<uint4*>(dst + (size_t)rr * p.ldc + 8 * g) = val;
+                    if (lane == 0 && tile_ok) {
+                        tma_store_3d(&p.tmC[b], smem_u32(hb), col, m0 + 32 * q, 0);
+                        bulk_commit();
                     }
-                    __syncwarp();
                     h_pending = next;
                     ++hj;
                     if (p.colsum[b]) {
@@ -718,9 +740,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
             if (stop) break;
         }
-        // an activation block still in flight lands before the CTA leaves (bounded)
+        // an activation block still in flight lands before the CTA leaves (bounded); the output
+        // stores complete
         if (EPI == EPI_ELU_GRAD && h_pending)
             mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status);
+        if (lane == 0) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -920,6 +944,23 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
 
 bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld) {
     return make_tmap(map, base, rows, cols, ld, 32u, 32u, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
+bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,
+                   uint64_t split_ld) {
+    EncodeTiledFn enc = get_encode();
+    const uint64_t es = fp32 ? 4 : 2;
+    if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15u) || (ld * es) % 16 || cols > ld || splits < 1 ||
+        (splits > 1 && ((split_ld * es) % 16 || split_ld < rows * ld)))
+        return false;
+    cuuint64_t dims[3] = {cols, rows, splits};
+    cuuint64_t strides[2] = {ld * es, (splits > 1 ? split_ld : rows * ld) * es};
+    cuuint32_t box[3] = {32u, 32u, 1u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, fp32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 

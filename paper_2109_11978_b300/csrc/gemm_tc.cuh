@@ -24,14 +24,11 @@ struct TcParams {
                                // B^T [K][N], EPI_STORE), MAJ_B_MN (A [M][K], B^T [K][N],
                                // EPI_ELU_GRAD); MN-major operands use 64 x 64 boxes
     int epi;                   // EPI_STORE (fp32 split partials), EPI_BIAS_ELU, EPI_ELU_GRAD (bf16 out)
-    void* C[2];                // output per batch entry
-    int ldc;
+    CUtensorMap tmC[2];        // output per batch entry, [splits][M][N] (make_tmap_out): fp32 for
+                               // EPI_STORE (split z at z), bf16 otherwise (one split)
     const float* bias[2];      // EPI_BIAS_ELU
-    const void* H[2];          // EPI_ELU_GRAD: bf16 activation [M][ldh]
-    CUtensorMap tmH[2];        // EPI_ELU_GRAD: the same activation, 32 x 32 boxes, 64-byte swizzle
-    int ldh;
-    float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [M/128][N]
-    long long split_stride;    // EPI_STORE: elements between split slices
+    CUtensorMap tmH[2];        // EPI_ELU_GRAD: bf16 activation [M][N], 32 x 32 boxes, 64-byte swizzle
+    float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [4 M/128][N]
     int* status;               // device status word
 };
 
@@ -39,6 +36,10 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 // epilogue operand map: bf16 [rows][cols] (row stride ld), 32 x 32 boxes, 64-byte swizzle
 bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld);
+// output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), 32 x 32
+// x 1 boxes: fp32 with 128-byte swizzle, or bf16 with 64-byte swizzle
+bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,
+                   uint64_t split_ld);
 int tc_smem_bytes(int bn, int epi);
 int tc_cluster_fit(int bn, int epi, int cm);   // clusters resident at once (after tc_prepare)
 cudaError_t tc_prepare();

@@ -237,7 +237,8 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
                 tp.tmA[j] = c->tm_fwdA[n][l];
             }
             tp.tmB[j] = act ? c->tm_actB[n][l] : c->tm_fwdB[n][l];
-            tp.C[j] = c->H[n][l];
+            if (!make_tmap_out(&tp.tmC[j], c->H[n][l], false, 1, (uint64_t)rows, (uint64_t)Li.out, (uint64_t)Li.out, 0))
+                return RL_ERR_CUDA;
             tp.bias[j] = c->params + c->L[n][l].b;
         }
         tp.M = rows;
@@ -249,7 +250,6 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.bn = act ? c->bn_act[l] : c->bn_fwd[l];
         set_cluster(tp, act ? c->cm_act[l] : c->cm_fwd[l]);
         tp.epi = EPI_BIAS_ELU;
-        tp.ldc = Li.out;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -285,13 +285,13 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
         for (int n = 0; n < 2; ++n) {
             tp.tmA[n] = c->tm_dxA[n][k];
             tp.tmB[n] = c->tm_dxB[n][k];
-            tp.C[n] = c->dY[n][k - 1];
-            tp.H[n] = c->H[n][k - 1];
+            if (!make_tmap_out(&tp.tmC[n], c->dY[n][k - 1], false, 1, (uint64_t)M, (uint64_t)Li.in, (uint64_t)Li.in, 0))
+                return RL_ERR_CUDA;
             tp.tmH[n] = c->tm_dxH[n][k];
             tp.colsum[n] = c->gb[n][k - 1];
         }
         tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
-        tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD; tp.ldc = Li.in; tp.ldh = Li.in;
+        tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -318,12 +318,12 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
         for (int n = 0; n < 2; ++n) {
             tp.tmA[n] = c->tm_dwA[n][k];
             tp.tmB[n] = c->tm_dwB[n][k];
-            tp.C[n] = c->gw[n][k];
+            if (!make_tmap_out(&tp.tmC[n], c->gw[n][k], true, (uint64_t)c->S[k], (uint64_t)Li.out, (uint64_t)Li.in, (uint64_t)Li.in,
+                               (uint64_t)Li.out * Li.in))
+                return RL_ERR_CUDA;
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
         tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; set_cluster(tp, c->cm_dw[k]); tp.mn = MAJ_MN; tp.epi = EPI_STORE;
-        tp.ldc = Li.in;
-        tp.split_stride = (long long)Li.out * Li.in;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -1393,7 +1393,8 @@ rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const voi
     if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)(bn / cm))) return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.cm = cm; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    tp.bn = bn; tp.cm = cm; tp.epi = EPI_STORE;
+    if (!make_tmap_out(&tp.tmC[0], C, true, 1, (uint64_t)M, (uint64_t)N, (uint64_t)N, 0)) return RL_ERR_CUDA;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }
@@ -1409,7 +1410,8 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
     if (!make_tmap_bf16(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.cm = cm; tp.mn = MAJ_MN; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    tp.bn = bn; tp.cm = cm; tp.mn = MAJ_MN; tp.epi = EPI_STORE;
+    if (!make_tmap_out(&tp.tmC[0], C, true, 1, (uint64_t)M, (uint64_t)N, (uint64_t)N, 0)) return RL_ERR_CUDA;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }
@@ -1439,7 +1441,8 @@ rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, con
     }
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.cm = cm; tp.pair = pair; tp.epi = EPI_STORE; tp.C[0] = C; tp.ldc = N;
+    tp.bn = bn; tp.cm = cm; tp.pair = pair; tp.epi = EPI_STORE;
+    if (!make_tmap_out(&tp.tmC[0], C, true, 1, (uint64_t)M, (uint64_t)N, (uint64_t)N, 0)) return RL_ERR_CUDA;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;
 }
