@@ -276,6 +276,10 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
                 rc[4 + j] = (live && j < A) ? g_logp * (diff[j] * diff[j] * iv - 1.f) : 0.f;
             }
             if (j < 12) g_s[r * FP + j] = g;
+            // column 12 of G carries g_v: the critic's weight gradient comes out of the same
+            // transposed product (row 12 of G^T H_c); Wa has no row 12, so the actor backward
+            // is unaffected
+            if (j == 12) g = g_v;
             __nv_bfloat16 hi, lo;
             split_bf16(g, hi, lo);
             sb[S::G_HI + r * GP + j] = hi;
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
 #pragma unroll
         for (int np = 0; np < H / NW / 16; ++np) {
             const int n0 = (H / NW) * warp + 16 * np;
-            float acc[2][4] = {};
+            float acc[2][4] = {}, accc[2][4] = {};
 #pragma unroll
             for (int ks = 0; ks < ROWS / 16; ++ks) {
                 const int k0 = 16 * ks;                       // rows
@@ -315,6 +319,12 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
                 mma16816(acc[0], al, b[0], b[1]);
                 mma16816(acc[1], ah, b[2], b[3]);
                 mma16816(acc[1], al, b[2], b[3]);
+                // the same G^T against H_c: row 12 is the critic head's weight gradient
+                ldsm_x4_t(hc + br * HP + bc, b[0], b[1], b[2], b[3]);
+                mma16816(accc[0], ah, b[0], b[1]);
+                mma16816(accc[0], al, b[0], b[1]);
+                mma16816(accc[1], ah, b[2], b[3]);
+                mma16816(accc[1], al, b[2], b[3]);
             }
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
@@ -326,14 +336,12 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
                         out[O_WA + j * H + col] = acc[nt][2 * h2];
                         out[O_WA + j * H + col + 1] = acc[nt][2 * h2 + 1];
                     }
+                    if (j == 12) {
+                        out[O_WC + col] = accc[nt][2 * h2];
+                        out[O_WC + col + 1] = accc[nt][2 * h2 + 1];
+                    }
                 }
         }
-    }
-    // critic head weight gradient: column k = sum over rows of g_v h_c[row][k]
-    for (int k = tid; k < H; k += THREADS) {
-        float a = 0.f;
-        for (int r = 0; r < ROWS; ++r) a += g_s[r * FP + 12] * __bfloat162float(hc[r * HP + k]);
-        out[O_WC + k] = a;
     }
     __syncthreads();
 
@@ -380,18 +388,42 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
     }
     __syncthreads();
 
-    // ---- hidden bias gradients (column sums of the bf16 dY rows) and the block's statistics:
-    // items [0, H) actor columns, [H, 2H) critic columns, [2H, 2H + 29) record columns
-    for (int i = tid; i < 2 * H + 29; i += THREADS) {
-        if (i < 2 * H) {
-            const __nv_bfloat16* t = i < H ? ha : hc;
-            const int k = i < H ? i : i - H;
-            float sum = 0.f;
-            for (int r = 0; r < rows; ++r) sum += __bfloat162float(t[r * HP + k]);
-            out[(i < H ? O_DBA : O_DBC) + k] = sum;
-        } else {
-            // record column c: 0..3 loss terms, 4 g_v, 5..16 g_mu, 17..28 g_log_std
-            const int c = i - 2 * H;
+    // ---- hidden bias gradients: column sums of the bf16 dY rows as ones^T dY on the MMA (rows
+    // past M are zero); warp w: columns [H/NW w, H/NW (w + 1)) of both networks
+    {
+        const uint32_t one2 = 0x3F803F80u;                  // two bf16 ones
+        const uint32_t ones[4] = {one2, one2, one2, one2};
+#pragma unroll
+        for (int np = 0; np < H / NW / 16; ++np) {
+            const int n0 = (H / NW) * warp + 16 * np;
+            float sa[2][4] = {}, sc[2][4] = {};
+#pragma unroll
+            for (int ks = 0; ks < ROWS / 16; ++ks) {
+                const int br = 16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1), bc = n0 + 8 * (lane >> 4);
+                uint32_t b[4];
+                ldsm_x4_t(ha + br * HP + bc, b[0], b[1], b[2], b[3]);
+                mma16816(sa[0], ones, b[0], b[1]);
+                mma16816(sa[1], ones, b[2], b[3]);
+                ldsm_x4_t(hc + br * HP + bc, b[0], b[1], b[2], b[3]);
+                mma16816(sc[0], ones, b[0], b[1]);
+                mma16816(sc[1], ones, b[2], b[3]);
+            }
+            if (gq == 0) {                                   // row 0 of the (identical) rows
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int col = n0 + 8 * nt + 2 * tq;
+                    out[O_DBA + col] = sa[nt][0];
+                    out[O_DBA + col + 1] = sa[nt][1];
+                    out[O_DBC + col] = sc[nt][0];
+                    out[O_DBC + col + 1] = sc[nt][1];
+                }
+            }
+        }
+    }
+    // the block's statistics: record columns 0..3 loss terms, 4 g_v, 5..16 g_mu, 17..28 g_log_std
+    for (int i = tid; i < 29; i += THREADS) {
+        {
+            const int c = i;
             const float* col = c < 4 ? recs + c : c == 4 ? g_s + 12 : c < 17 ? g_s + (c - 5) : recs + 4 + (c - 17);
             const int pitch = (c >= 4 && c < 17) ? FP : RP;
             float sum = 0.f;
