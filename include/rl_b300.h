@@ -288,8 +288,9 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
 /* Tile autotuner: times each GEMM site (per hidden layer: the update's forward, input gradient
  * and weight gradient at minibatch rows, and the rollout's forward at num_envs rows; actor and
  * critic in one launch) over candidate tile widths
- * (64, 128, 256 output columns), cluster modes (one CTA per tile, two CTAs sharing one B tile
- * through TMA multicast, or a CTA pair on the cta_group::2 MMA) and, for weight gradients, split-K counts (a quarter, half, default, double;
+ * (64, 128, 256 output columns), tile modes (one CTA per tile, two CTAs sharing one B tile
+ * through TMA multicast, a CTA pair on the cta_group::2 MMA, or one CTA per tile with two K blocks
+ * per pipeline stage) and, for weight gradients, split-K counts (a quarter, half, default, double;
  * timed together with the summation of their partials, which Adam performs) on the context's
  * own buffers, keeps the fastest, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
@@ -302,9 +303,10 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * gradient (the update's sites, minibatch rows), 3 the rollout's forward (num_envs rows);
  * layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the site's output
  * width; cluster: 1 (one CTA per 128-row tile), 2 (pairs of row tiles share the B tile by TMA
- * multicast) or 3 (pairs of CTAs run one 256-row tile on the cta_group::2 MMA, each loading half
- * of B); 2 and 3 need at least two 128-row tiles at the site, 3 a tile width of at least 128, and
- * 2 at sites 1 and 2 a tile width of at least 128;
+ * multicast), 3 (pairs of CTAs run one 256-row tile on the cta_group::2 MMA, each loading half
+ * of B) or 4 (one CTA per tile, two K blocks per pipeline stage fetched by one 3D TMA copy per
+ * operand); 2 and 3 need at least two 128-row tiles at the site, 3 a tile width of at least 128,
+ * 2 at sites 1 and 2 a tile width of at least 128, and 4 a tile width of at most 128;
  * splits: weight-gradient split-K count (1 .. twice the default, rounded so every slice is a
  * multiple of 64 rows), ignored for the other sites.  Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
@@ -328,8 +330,10 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
  * cluster: 1 (one CTA per tile), 2 (pairs of row tiles share the B tile by TMA multicast), 3
  * (pairs of CTAs run one 256-row tile on the cta_group::2 tensor-core MMA, each CTA loading half
  * of the B tile; bn 128 or 256).  Requirements as for rl_gemm_bf16 (operands 0) or
- * rl_gemm_bf16_tn (operands 1); cluster 2 with operands 1 and cluster 3 need bn >= 128.  No
- * counterpart in the paper. */
+ * rl_gemm_bf16_tn (operands 1); cluster 2 with operands 1 and cluster 3 need bn >= 128.
+ * operands 2 / 3: the forms of 0 / 1 with two K blocks per pipeline stage (one 3D TMA copy per
+ * operand and stage), cluster 1 and bn <= 128 only; operands 2 needs K % 64 == 0, operands 3
+ * M % 64 == 0.  No counterpart in the paper. */
 rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, int32_t operands,
                              int32_t bn, int32_t cluster, void* stream);
 

@@ -194,8 +194,9 @@ def rl_gemm_bf16_tn(At, Bt, C):
 
 def rl_gemm_bf16_shape(A, B, C, operands=0, bn=128, cluster=1):
     """C = A B^T (operands 0: A [M][K], B [N][K]) or At^T Bt (operands 1: At [K][M], Bt [K][N]) with an
-    explicit tile width and cluster mode (1 single CTA, 2 B-tile multicast, 3 cta_group::2 pair)."""
-    if operands == 0:
+    explicit tile width and cluster mode (1 single CTA, 2 B-tile multicast, 3 cta_group::2 pair);
+    operands 2 / 3: the same forms with two K blocks per pipeline stage (cluster 1, bn <= 128)."""
+    if operands in (0, 2):
         M, K = A.shape
         Nn = B.shape[0]
     else:

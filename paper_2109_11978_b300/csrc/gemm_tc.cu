@@ -95,6 +95,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// 3D tile load: the tensor viewed as {64 elements, rows, 64-element chunks} (chunk stride 128
+// bytes), so one copy brings several 64-wide column chunks, each landing as its own 128-byte-
+// swizzled [rows][64] block.  Used to fetch two K blocks (K-major) or two M/N chunks (MN-major)
+// per instruction.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor, K-major operand with 128-byte swizzle: 8-row x 128-byte
 // atoms stacked every 1024 bytes (stride byte offset), leading byte offset unused, descriptor
 // version 1 (bits 46-48), layout code 2 = SWIZZLE_128B (bits 61-63).  The tile base is 1024-byte
@@ -112,12 +123,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 // Shared-memory matrix descriptor, MN-major operand with 128-byte swizzle: an atom is 64
 // consecutive M (or N) elements (one 128-byte row) x 8 K rows, 1024 bytes; atoms follow each
 // other every 1024 bytes along K (stride byte offset) and every 8192 bytes along M/N (leading
-// byte offset: one TMA box of 64 x 64 holds eight atoms stacked along K).  A K16 step is two
-// atoms further along K (2048 bytes).
-__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+// byte offset: 8192 when a TMA box of 64 x 64 holds eight atoms stacked along K, 16384 when a
+// stage holds 128 K rows per chunk).  A K16 step is two atoms further along K (2048 bytes).
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo = 8192u) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)(8192u >> 4) << 16;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1u << 46;
     d |= (uint64_t)2u << 61;
@@ -269,9 +280,25 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Fast ELU for the bf16 forms: the result is rounded to 8 mantissa bits, so exp(x) - 1 from the
-// fast exponential is accurate enough (absolute error ~1e-7).
-__device__ __forceinline__ float elu_fast(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
+// 2^x on the special-function unit (ex2.approx, results below 2^-126 flushed to zero).
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ELU for the bf16 forms, branch-free: exp(x) - 1 >= x for every x, so
+// ELU(x) = max(x, exp(min(x, 0)) - 1), with exp(m) = 2^(m log2 e) from the approximate
+// exponential (absolute error ~1e-7; the result is rounded to 8 mantissa bits).
+__device__ __forceinline__ float elu_fast(float x) {
+    return fmaxf(x, ex2_ftz(fminf(x, 0.f) * 1.4426950408889634f) - 1.f);
+}
+
+// Two floats to a bf16 pair (round to nearest even), the first in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
 
 // Column sums of a 32 x 32 block held one row per lane (v[j] = column j): recursive halving,
 // 31 shuffles; afterwards lane l holds the sum of column l.
@@ -289,11 +316,12 @@ __device__ __forceinline__ float colsum32(float (&v)[32], int lane) {
     return v[0];
 }
 
-template <int BN, int EPI, int BROWS = BN>
+template <int BN, int EPI, int BROWS = BN, int KS = 1>
 struct TileCfg {
-    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int A_BYTES = BM * BK * 2;             // one K block of A
     static constexpr int B_BYTES = BROWS * BK * 2;          // B rows staged per CTA (BN / 2 in pair mode)
-    static constexpr int STAGE = A_BYTES + B_BYTES;
+    // a stage holds KS K blocks: all of A's, then all of B's
+    static constexpr int STAGE = KS * (A_BYTES + B_BYTES);
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
@@ -306,7 +334,7 @@ struct TileCfg {
     static constexpr int BIAS_BYTES = EPI == EPI_BIAS_ELU ? 2 * 1024 * 4 : 0;
     static constexpr int BAR_BYTES = 512;
     static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
-    static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3;
+    static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3 * STAGE + FIXED <= 227 * 1024 ? 3 : 2;
     // TMEM accumulator buffers (BN columns each, 512 columns in all): the MMA warp can run that many
     // tiles ahead of the epilogue
     static constexpr int NACC = 512 / BN < 4 ? 512 / BN : 4;
@@ -324,12 +352,20 @@ struct TileCfg {
 // while the sixteen epilogue
 // warps drain the other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue
 // warp e reads TMEM lanes 32 (warp % 4) .. + 31 (its rows) and one slice of up to 4 of the columns.
-template <int BN, int EPI, int CM, int MJ, bool PAIR>
+//
+// KS = 2 (single CTA, BN <= 128): a stage carries two K blocks, fetched with one 3D copy per
+// operand, and the MMA warp issues eight MMAs per stage wait.  Each TMA copy and each stage
+// hand-off costs the issuing thread a fixed few hundred cycles whatever its size, so halving their
+// number per K block lifts the narrow tiles' mainloop, which is bound by that per-stage cost rather
+// than by the tensor core.  A split or tile with an odd number of K blocks loads a whole last
+// stage and multiplies only its first half.
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     // PAIR: the cluster's two CTAs run one 256 x BN tile on the pair (cta_group::2) tensor core;
     // each CTA stages its 128 rows of A and half of B, the even CTA issues the MMAs
     static_assert(!PAIR || CM == 2, "pair mode runs on clusters of two");
-    using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN>;
+    static_assert(KS == 1 || (KS == 2 && CM == 1 && !PAIR && BN <= 128), "two-block stages: single CTA, BN <= 128");
+    using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>;
     constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
     constexpr bool B_MN = MJ != MAJ_K;                      // B^T [K][N] in memory
     constexpr int B_SLICE_ROWS = PAIR ? BN / 2 : BN / CM;   // B rows this CTA loads
@@ -439,7 +475,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 // a row tile past M (the last cluster tile of a ragged M) reloads the last valid
                 // rows; its results are never stored
                 const int ay = min(mi, mt - 1) * BM;
-                for (int i = 0; i < nkb; ++i, ++it) {
+                const int nst = (nkb + KS - 1) / KS;     // stages of this tile
+                for (int i = 0; i < nst; ++i, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
                     if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, abort_flag)) {
@@ -448,6 +485,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         break;
                     }
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    if constexpr (KS == 2) {
+                        // K blocks kb, kb + 1: K-major operands as two 64-column chunks of their rows,
+                        // MN-major ones as 128 K rows of their 64-wide M / N chunks
+                        const int kb = kb0 + 2 * i;
+                        mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
+                        if (!A_MN) tma_load_3d(sa, ma, full0 + 8 * s, 0, ay, kb);
+                        else tma_load_3d(sa, ma, full0 + 8 * s, 0, kb * BK, ay / 64);
+                        if (!B_MN) tma_load_3d(sa + 2 * C::A_BYTES, mb, full0 + 8 * s, 0, ni * BN, kb);
+                        else tma_load_3d(sa + 2 * C::A_BYTES, mb, full0 + 8 * s, 0, kb * BK, ni * BN / 64);
+                        continue;
+                    }
                     if constexpr (PAIR) {
                         // both CTAs' copies complete on the even CTA's barrier, which the MMA waits on
                         const uint32_t cfull = mapa_rank(full0 + 8 * s, 0);
@@ -520,8 +568,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             bool ok = true;
             const bool issuer = !PAIR || rank == 0;
             const uint32_t sa0 = smem_u32(smem);
-            const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0) : sw128_desc(sa0);
-            const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + C::A_BYTES) : sw128_desc(sa0 + C::A_BYTES);
+            constexpr uint32_t LBO = KS == 2 ? 16384u : 8192u;   // MN-major: bytes between 64-wide chunks
+            const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0, LBO) : sw128_desc(sa0);
+            const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + KS * C::A_BYTES, LBO) : sw128_desc(sa0 + KS * C::A_BYTES);
             for (int t = cid; issuer && t < total && ok; t += ncl, ++local) {
                 int mi, ni, sp, b, kb0;
                 decode(t, mi, ni, sp, b);
@@ -534,7 +583,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * BN);
-                for (int i = 0; i < nkb; ++i, ++it) {
+                const int nst = (nkb + KS - 1) / KS;
+                for (int i = 0; i < nst; ++i, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
                     if (!mbar_wait(full0 + 8 * s, ph, p.status, abort_flag)) {
@@ -549,7 +599,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     // K16 step: 32 bytes along the swizzled row (K-major), two 8-row atoms (MN-major)
                     constexpr uint64_t KSTEP_A = A_MN ? (2048 >> 4) : (32 >> 4);
                     constexpr uint64_t KSTEP_B = B_MN ? (2048 >> 4) : (32 >> 4);
-                    if constexpr (PAIR) {
+                    if constexpr (KS == 2) {
+                        // second K block: 64 K rows further (MN-major), the next chunk (K-major)
+                        constexpr uint64_t SUB_A = A_MN ? (8192 >> 4) : (C::A_BYTES >> 4);
+                        constexpr uint64_t SUB_B = B_MN ? (8192 >> 4) : (C::B_BYTES >> 4);
+                        const int nsub = min(2, nkb - 2 * i);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            if (j >= nsub) break;
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk)
+                                mma_bf16(d, ad + SUB_A * j + KSTEP_A * kk, bd + SUB_B * j + KSTEP_B * kk, idesc,
+                                         (i > 0 || j > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(empty0 + 8 * s);
+                    } else if constexpr (PAIR) {
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
                             mma_bf16_pair(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
@@ -634,7 +698,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-                if (nkb == 0) {
+                if (EPI == EPI_STORE && nkb == 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 }
@@ -664,9 +728,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
                         v[4 * j4 + 3] = elu_fast(v[4 * j4 + 3] + bb.w);
                     }
-                    __align__(16) __nv_bfloat16 o[32];
+                    uint32_t o[16];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
+                    for (int j = 0; j < 16; ++j) o[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
                     // bf16 block in one of two buffers (64-byte swizzle: 16-byte unit u of row r at
                     // unit u ^ ((r >> 1) & 3)), out by TMA store; the store issued from this buffer
                     // two blocks ago must have read it
@@ -676,7 +740,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     const int sw = (lane >> 1) & 3;
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
-                        *reinterpret_cast<uint4*>(ob + lane * 64 + 16 * (g ^ sw)) = reinterpret_cast<const uint4*>(o)[g];
+                        *reinterpret_cast<uint4*>(ob + lane * 64 + 16 * (g ^ sw)) =
+                            make_uint4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0 && tile_ok) {
@@ -698,25 +763,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     // 64-byte swizzle: 16-byte unit u of row r sits at unit u ^ ((r >> 1) & 3)
                     const int sw = (lane >> 1) & 3;
                     if (row_ok) {
+                        // ELU'(x) from y = ELU(x): 1 for y > 0, y + 1 otherwise, i.e. min(y, 0) + 1,
+                        // so the product is fma(v, min(y, 0), v)
 #pragma unroll
                         for (int g = 0; g < 4; ++g) {
                             const uint4 hv = *reinterpret_cast<const uint4*>(hb + lane * 64 + 16 * (g ^ sw));
-                            const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&hv);
+                            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) v[8 * g + j] *= elu_grad_y(bf2f(h8[j]));
+                            for (int j = 0; j < 4; ++j) {
+                                const float y0 = __uint_as_float(hw[j] << 16), y1 = __uint_as_float(hw[j] & 0xFFFF0000u);
+                                v[8 * g + 2 * j] = fmaf(v[8 * g + 2 * j], fminf(y0, 0.f), v[8 * g + 2 * j]);
+                                v[8 * g + 2 * j + 1] = fmaf(v[8 * g + 2 * j + 1], fminf(y1, 0.f), v[8 * g + 2 * j + 1]);
+                            }
                         }
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = 0.f;
                     }
-                    __align__(16) __nv_bfloat16 o[32];
+                    uint32_t o[16];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) o[j] = f2bf(v[j]);
+                    for (int j = 0; j < 16; ++j) o[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
                     // the output block replaces the activation block in place (same swizzle) and
                     // leaves by TMA store
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
-                        *reinterpret_cast<uint4*>(hb + lane * 64 + 16 * (g ^ sw)) = reinterpret_cast<const uint4*>(o)[g];
+                        *reinterpret_cast<uint4*>(hb + lane * 64 + 16 * (g ^ sw)) =
+                            make_uint4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0 && tile_ok) {
@@ -767,9 +839,9 @@ static ClusterFit g_fit[64];
 static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 2 : -1; }
 static int cm_index(int cm) { return cm == 1 ? 0 : cm == 2 ? 1 : cm == 4 ? 2 : -1; }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
 constexpr int smem_of() {
-    return TileCfg<BN, EPI, PAIR ? BN / 2 : BN>::SMEM;
+    return TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>::SMEM;
 }
 // slot of the cluster-fit table: 0 single CTA, 1 cluster of two (multicast), 2 pair
 template <int CM, bool PAIR>
@@ -777,10 +849,10 @@ constexpr int fit_slot() {
     return PAIR ? 2 : (CM == 1 ? 0 : 1);
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1>
 cudaError_t set_attr(int dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_of<BN, EPI, CM, MJ, PAIR>());
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_of<BN, EPI, CM, MJ, PAIR, KS>());
     if (e != cudaSuccess) return e;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -794,11 +866,11 @@ cudaError_t set_attr(int dev) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)(n * CM));
         cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = smem_of<BN, EPI, CM, MJ, PAIR>();
+        cfg.dynamicSmemBytes = smem_of<BN, EPI, CM, MJ, PAIR, KS>();
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int fit = 0;
-        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&fit, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS>, &cfg);
         if (e != cudaSuccess) return e;
         if (fit > 0 && fit < n) n = fit;
     }
@@ -806,7 +878,7 @@ cudaError_t set_attr(int dev) {
     return cudaSuccess;
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -815,9 +887,9 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     const int mct = ((p.M + BM - 1) / BM + CM - 1) / CM;
     const int total = mct * (p.N / BN) * p.splits * p.batch;
     const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
-    constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR>();
-    if (CM == 1) {
-        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);
+    constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR, KS>();
+    if constexpr (CM == 1) {
+        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false, KS>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[2];
@@ -833,7 +905,7 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR>, p);
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS>, p);
 }
 
 // Instantiated operand forms: forward (EPI_BIAS_ELU) both K-major; input gradient
@@ -843,7 +915,13 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
 
 template <int BN, int EPI, int MJ>
 cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
-    if (p.cm == 1) return launch_cfg<BN, EPI, 1, MJ, false>(p, s);
+    if (p.cm == 1) {
+        if (p.ks == 2) {
+            if constexpr (BN <= 128) return launch_cfg<BN, EPI, 1, MJ, false, 2>(p, s);
+            return cudaErrorInvalidValue;
+        }
+        return launch_cfg<BN, EPI, 1, MJ, false>(p, s);
+    }
     if (p.cm == 2 && p.pair) {
         if constexpr (BN >= 128) return launch_cfg<BN, EPI, 2, MJ, true>(p, s);
         return cudaErrorInvalidValue;
@@ -887,6 +965,8 @@ cudaError_t prepare_form(int dev) {
     e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ, true>(dev);
     e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, true>(dev);
     if (MJ == MAJ_K) e = e != cudaSuccess ? e : set_attr<64, EPI, 2, MAJ_K, false>(dev);
+    e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 2>(dev);
+    e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 2>(dev);
     return e;
 }
 
@@ -898,6 +978,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.cm != 1 && p.cm != 2) return cudaErrorInvalidValue;
     if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
     if (p.pair && (p.cm != 2 || p.bn < 128)) return cudaErrorInvalidValue;
+    if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -941,6 +1022,35 @@ static bool make_tmap(CUtensorMap* map, const void* base, uint64_t rows, uint64_
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
     return make_tmap(map, base, rows, cols, ld, (uint32_t)BK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
 }
+
+// bf16 [rows][cols] viewed as {64, rows, cols / 64} (64-element chunks 128 bytes apart), box
+// {64, box_rows, box_chunks}, 128-byte swizzle.  cols must be a multiple of 64 so that no chunk
+// reaches past a row; chunks of a box past the last one read as zeros.
+static bool make_tmap_chunks(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows,
+                             uint32_t box_chunks) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16 || cols > ld || cols % 64 ||
+        box_rows < 1 || box_rows > 256 || box_chunks < 1 || box_chunks > 4)
+        return false;
+    cuuint64_t dims[3] = {64, rows, cols / 64};
+    cuuint64_t strides[2] = {ld * 2, 128};
+    cuuint32_t box[3] = {64, box_rows, box_chunks};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
+    return make_tmap_chunks(map, base, rows, cols, ld, box_rows, 2);
+}
+
+bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols) {
+    return tile_cols % 64 == 0 && make_tmap_chunks(map, base, krows, cols, ld, 2 * BK, tile_cols / 64);
+}
+
+int tc_stage_blocks(int bn, int cm, int pair) { return (cm == 1 && !pair && bn <= 128) ? 2 : 1; }
 
 bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld) {
     return make_tmap(map, base, rows, cols, ld, 32u, 32u, CU_TENSOR_MAP_SWIZZLE_64B);

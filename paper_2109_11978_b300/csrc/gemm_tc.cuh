@@ -30,10 +30,18 @@ struct TcParams {
     CUtensorMap tmH[2];        // EPI_ELU_GRAD: bf16 activation [M][N], 32 x 32 boxes, 64-byte swizzle
     float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [4 M/128][N]
     int* status;               // device status word
+    int ks;                    // K blocks per stage: 0 / 1, or 2 (cm 1, no pair, bn <= 128) with the
+                               // operand maps of make_tmap_bf16_k2 (K-major) / make_tmap_bf16_mn2
 };
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
+// two-K-block stage maps (cols a multiple of 64): K-major operand [rows][K], box 2 x (64 x box_rows);
+// MN-major operand [K rows][cols], box 128 K rows x tile_cols (tile_cols / 64 chunks of 64)
+bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
+bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols);
+// K blocks per stage for a tile shape: 2 for single-CTA tiles of width <= 128, else 1
+int tc_stage_blocks(int bn, int cm, int pair);
 // epilogue operand map: bf16 [rows][cols] (row stride ld), 32 x 32 boxes, 64-byte swizzle
 bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld);
 // output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), 32 x 32

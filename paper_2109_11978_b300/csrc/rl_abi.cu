@@ -88,6 +88,9 @@ struct rl_ctx {
     CUtensorMap tm_x0;                           // gathered minibatch observations
     CUtensorMap tm_dxA[2][4], tm_dxB[2][4], tm_dxH[2][4];
     CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
+    // the same operands for two-K-block stages (single-CTA tiles of width <= 128)
+    CUtensorMap tm_fwdB2[2][4], tm_actB2[2][4], tm_fwdA2[2][4];
+    CUtensorMap tm_dxA2[2][4], tm_dxB2[2][4], tm_dwA2[2][4], tm_dwB2[2][4];
     // graph / profiling
     cudaStream_t gstream = nullptr;              // capture / replay stream (never the legacy stream)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -185,12 +188,17 @@ struct Enq {
     }
 };
 
-// B rows one CTA loads per K step for a K-major B (tile width bn, cluster mode cm)
-uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 ? bn / 2 : bn / cm); }
+// Tile modes of a GEMM site: 1 one CTA per tile, 2 pairs of row tiles sharing the B tile (TMA
+// multicast), 3 pairs of CTAs on one 256-row tile (cta_group::2), 4 one CTA per tile with two K
+// blocks per pipeline stage (bn <= 128).
+// B rows one CTA loads per K step for a K-major B (tile width bn, mode cm)
+uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 || cm == 2 ? bn / 2 : bn); }
 void set_cluster(TcParams& tp, int cm) {
-    tp.cm = cm == 1 ? 1 : 2;
+    tp.cm = (cm == 2 || cm == 3) ? 2 : 1;
     tp.pair = cm == 3 ? 1 : 0;
+    tp.ks = cm == 4 ? 2 : 1;
 }
+bool two_block(int cm) { return cm == 4; }
 
 int pick_bn(int n) {
     if (n % 128 == 0) return 128;
@@ -202,6 +210,21 @@ bool encode_layer_maps(rl_ctx* c, int l) {
     bool ok = true;
     for (int n = 0; n < 2; ++n) {
         const LayerInfo& Li = c->L[n][l];
+        // two-K-block stage maps of the sites whose tile shape uses them
+        if (two_block(c->cm_fwd[l]))
+            ok = ok && make_tmap_bf16_k2(&c->tm_fwdB2[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_fwd[l]);
+        if (two_block(c->cm_act[l]))
+            ok = ok && make_tmap_bf16_k2(&c->tm_actB2[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_act[l]);
+        if (l > 0) ok = ok && make_tmap_bf16_k2(&c->tm_fwdA2[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
+        if (l > 0 && two_block(c->cm_dx[l])) {
+            ok = ok && make_tmap_bf16_k2(&c->tm_dxA2[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
+            ok = ok && make_tmap_bf16_mn2(&c->tm_dxB2[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_dx[l]);
+        }
+        if (two_block(c->cm_dw[l])) {
+            const void* xb2 = l == 0 ? c->X0 : c->H[n][l - 1];
+            ok = ok && make_tmap_bf16_mn2(&c->tm_dwA2[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
+            ok = ok && make_tmap_bf16_mn2(&c->tm_dwB2[n][l], xb2, c->Mb, Li.in, Li.in, (uint32_t)c->bn_dw[l]);
+        }
         ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_fwd[l], c->cm_fwd[l]));
         ok = ok && make_tmap_bf16(&c->tm_actB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_act[l], c->cm_act[l]));
         if (l > 0) ok = ok && make_tmap_bf16(&c->tm_fwdA[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
@@ -229,14 +252,19 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
     if (c->bf16) {
         TcParams tp;
         std::memset(&tp, 0, sizeof(tp));
+        const int bn = act ? c->bn_act[l] : c->bn_fwd[l], cm = act ? c->cm_act[l] : c->cm_fwd[l];
+        const bool k2 = two_block(cm);
         for (int j = 0; j < nnets; ++j) {
             const int n = net0 + j;
             if (l == 0) {
-                if (!make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)) return RL_ERR_CUDA;
+                const bool mk = k2 ? make_tmap_bf16_k2(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)
+                                   : make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128);
+                if (!mk) return RL_ERR_CUDA;
             } else {
-                tp.tmA[j] = c->tm_fwdA[n][l];
+                tp.tmA[j] = k2 ? c->tm_fwdA2[n][l] : c->tm_fwdA[n][l];
             }
-            tp.tmB[j] = act ? c->tm_actB[n][l] : c->tm_fwdB[n][l];
+            if (k2) tp.tmB[j] = act ? c->tm_actB2[n][l] : c->tm_fwdB2[n][l];
+            else tp.tmB[j] = act ? c->tm_actB[n][l] : c->tm_fwdB[n][l];
             if (!make_tmap_out(&tp.tmC[j], c->H[n][l], false, 1, (uint64_t)rows, (uint64_t)Li.out, (uint64_t)Li.out, 0))
                 return RL_ERR_CUDA;
             tp.bias[j] = c->params + c->L[n][l].b;
@@ -247,8 +275,8 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.kb_per_split = tp.kblocks;
         tp.splits = 1;
         tp.batch = nnets;
-        tp.bn = act ? c->bn_act[l] : c->bn_fwd[l];
-        set_cluster(tp, act ? c->cm_act[l] : c->cm_fwd[l]);
+        tp.bn = bn;
+        set_cluster(tp, cm);
         tp.epi = EPI_BIAS_ELU;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
@@ -282,9 +310,10 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
     if (c->bf16) {
         TcParams tp;
         std::memset(&tp, 0, sizeof(tp));
+        const bool k2 = two_block(c->cm_dx[k]);
         for (int n = 0; n < 2; ++n) {
-            tp.tmA[n] = c->tm_dxA[n][k];
-            tp.tmB[n] = c->tm_dxB[n][k];
+            tp.tmA[n] = k2 ? c->tm_dxA2[n][k] : c->tm_dxA[n][k];
+            tp.tmB[n] = k2 ? c->tm_dxB2[n][k] : c->tm_dxB[n][k];
             if (!make_tmap_out(&tp.tmC[n], c->dY[n][k - 1], false, 1, (uint64_t)M, (uint64_t)Li.in, (uint64_t)Li.in, 0))
                 return RL_ERR_CUDA;
             tp.tmH[n] = c->tm_dxH[n][k];
@@ -315,9 +344,10 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
     if (c->bf16) {
         TcParams tp;
         std::memset(&tp, 0, sizeof(tp));
+        const bool k2 = two_block(c->cm_dw[k]);
         for (int n = 0; n < 2; ++n) {
-            tp.tmA[n] = c->tm_dwA[n][k];
-            tp.tmB[n] = c->tm_dwB[n][k];
+            tp.tmA[n] = k2 ? c->tm_dwA2[n][k] : c->tm_dwA[n][k];
+            tp.tmB[n] = k2 ? c->tm_dwB2[n][k] : c->tm_dwB[n][k];
             if (!make_tmap_out(&tp.tmC[n], c->gw[n][k], true, (uint64_t)c->S[k], (uint64_t)Li.out, (uint64_t)Li.in, (uint64_t)Li.in,
                                (uint64_t)Li.out * Li.in))
                 return RL_ERR_CUDA;
@@ -646,7 +676,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
         trials += buf;
     };
     const int bns[3] = {64, 128, 256};
-    const int cms[3] = {1, 2, 3};
+    const int cms[4] = {1, 2, 3, 4};
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
         const int row_tiles = (c->Mb + 127) / 128;
@@ -656,7 +686,9 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
             float best = 1e30f;
             for (int bn : bns)
                 for (int cm : cms) {
-                    if (Li.out % bn || (cm > 1 && row_tiles < 2) || (cm == 3 && bn < 128) || st != RL_OK) continue;
+                    if (Li.out % bn || ((cm == 2 || cm == 3) && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128) ||
+                        st != RL_OK)
+                        continue;
                     c->bn_fwd[l] = bn;
                     c->cm_fwd[l] = cm;
                     if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -675,7 +707,9 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 float abest = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.out % bn || (cm > 1 && act_tiles < 2) || (cm == 3 && bn < 128) || st != RL_OK) continue;
+                        if (Li.out % bn || ((cm == 2 || cm == 3) && act_tiles < 2) || (cm == 3 && bn < 128) ||
+                            (cm == 4 && bn > 128) || st != RL_OK)
+                            continue;
                         c->bn_act[l] = bn;
                         c->cm_act[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -695,7 +729,9 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 best = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.in % bn || (cm > 1 && (row_tiles < 2 || bn < 128)) || st != RL_OK) continue;
+                        if (Li.in % bn || ((cm == 2 || cm == 3) && (row_tiles < 2 || bn < 128)) || (cm == 4 && bn > 128) ||
+                            st != RL_OK)
+                            continue;
                         c->bn_dx[l] = bn;
                         c->cm_dx[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
@@ -719,7 +755,8 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
                 for (int cm : cms) {
-                    if (cm > 1 && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
+                    if ((cm == 2 || cm == 3) && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
+                    if (cm == 4 && (!c->bf16 || bn > 128)) continue;
                     for (int S : {S0 / 4, S0 / 2, S0, 2 * S0}) {
                         if (S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
                         int kc = (c->Mb + S - 1) / S;
@@ -772,12 +809,13 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
 
 rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
     if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
-    if ((bn != 64 && bn != 128 && bn != 256) || cm < 1 || cm > 3) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || cm < 1 || cm > 4) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
     const int width = (site == 0 || site == 3) ? Li.out : Li.in;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
-    if (width % bn || (cm > 1 && row_tiles < 2) || (cm == 3 && bn < 128)) return RL_ERR_INVALID_ARG;
-    if ((site == 1 || site == 2) && cm > 1 && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
+    const bool paired = cm == 2 || cm == 3;
+    if (width % bn || (paired && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128)) return RL_ERR_INVALID_ARG;
+    if ((site == 1 || site == 2) && paired && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
     if (site == 2) {
         if (splits < 1 || splits > c->S_cap[l]) return RL_ERR_INVALID_ARG;
@@ -1419,29 +1457,38 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
 rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, int32_t operands,
                              int32_t bn, int32_t cluster, void* stream) {
     if (M < 1 || N < 64 || N % 64 || K < 1 || !A || !B || !C) return RL_ERR_INVALID_ARG;
-    if (operands != 0 && operands != 1) return RL_ERR_INVALID_ARG;
+    if (operands < 0 || operands > 3) return RL_ERR_INVALID_ARG;
+    const bool k2 = operands >= 2;             // two K blocks per stage
+    const bool mn = operands == 1 || operands == 3;
     if ((bn != 64 && bn != 128 && bn != 256) || N % bn || cluster < 1 || cluster > 3) return RL_ERR_INVALID_ARG;
-    if (operands == 0 && K % 8) return RL_ERR_INVALID_ARG;
-    if (operands == 1 && M % 8) return RL_ERR_INVALID_ARG;
-    if ((cluster == 3 || (cluster == 2 && operands == 1)) && bn < 128) return RL_ERR_INVALID_ARG;
+    if (!mn && K % 8) return RL_ERR_INVALID_ARG;
+    if (mn && M % 8) return RL_ERR_INVALID_ARG;
+    if ((cluster == 3 || (cluster == 2 && mn)) && bn < 128) return RL_ERR_INVALID_ARG;
+    if (k2 && (cluster != 1 || bn > 128 || (!mn && K % 64) || (mn && M % 64))) return RL_ERR_INVALID_ARG;
     if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
     const int cm = cluster == 1 ? 1 : 2;
     const int pair = cluster == 3 ? 1 : 0;
     const uint32_t brows = pair ? bn / 2 : bn / cm;
-    if (operands == 0) {
-        if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
-        if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, brows)) return RL_ERR_CUDA;
+    if (!mn) {
+        const bool ok = k2 ? make_tmap_bf16_k2(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128) &&
+                                 make_tmap_bf16_k2(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)
+                           : make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128) &&
+                                 make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, brows);
+        if (!ok) return RL_ERR_CUDA;
         tp.mn = MAJ_K;
     } else {
-        if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)) return RL_ERR_CUDA;
-        if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
+        const bool ok = k2 ? make_tmap_bf16_mn2(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 128) &&
+                                 make_tmap_bf16_mn2(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, (uint32_t)bn)
+                           : make_tmap_bf16(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64) &&
+                                 make_tmap_bf16(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64);
+        if (!ok) return RL_ERR_CUDA;
         tp.mn = MAJ_MN;
     }
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
-    tp.bn = bn; tp.cm = cm; tp.pair = pair; tp.epi = EPI_STORE;
+    tp.bn = bn; tp.cm = cm; tp.pair = pair; tp.epi = EPI_STORE; tp.ks = k2 ? 2 : 1;
     if (!make_tmap_out(&tp.tmC[0], C, true, 1, (uint64_t)M, (uint64_t)N, (uint64_t)N, 0)) return RL_ERR_CUDA;
     CK(launch_tc_gemm(tp, S_(stream)));
     return RL_OK;

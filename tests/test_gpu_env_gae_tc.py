@@ -85,6 +85,32 @@ def test_tc_gemm_tile_modes(operands, bn, cluster, M, N, K):
     assert err < max(2e-6, 5e-7 * np.sqrt(k_len)), err     # FP32 accumulation, one rounding per 16 products
 
 
+@pytest.mark.parametrize("operands,bn", [(2, 64), (2, 128), (3, 64), (3, 128)])
+@pytest.mark.parametrize("M,N,K", [(300, 512, 192), (64, 128, 64), (1024, 256, 1088), (320, 128, 200), (512, 256, 24576)])
+def test_tc_gemm_two_block_stages(operands, bn, M, N, K):
+    """Stages of two K blocks (one 3D copy per operand): an odd K-block count multiplies only the
+    first half of the last stage; K-major forms need whole 64-column K chunks, MN-major forms whole
+    64-wide M chunks, so the ragged dimension is M (K-major) or K (MN-major)."""
+    if operands == 3:
+        M = (M + 63) // 64 * 64
+    else:
+        K = (K + 63) // 64 * 64
+    g = torch.Generator().manual_seed(M + 5 * N + K + bn + 131 * operands)
+    if operands == 2:
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+        ref = A.double().numpy() @ B.double().numpy().T
+    else:
+        A = torch.randn(K, M, generator=g).to(torch.bfloat16)
+        B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+        ref = A.double().numpy().T @ B.double().numpy()
+    C = torch.full(ref.shape, float("nan"), device="cuda")
+    api.rl_gemm_bf16_shape(A.cuda(), B.cuda(), C, operands, bn, 1)
+    torch.cuda.synchronize()
+    err = np.abs(C.cpu().double().numpy() - ref).max() / np.abs(ref).max()
+    assert err < max(2e-6, 5e-7 * np.sqrt(K)), err
+
+
 def _learner(w, hf=None, params=None):
     cfg = lib_config(w)
     O, _ = obs_dims(w)

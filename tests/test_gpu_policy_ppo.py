@@ -315,11 +315,13 @@ def test_autotune_keeps_results(form):
 
 
 @pytest.mark.parametrize("bn,cm,splits", [(64, 1, "one"), (64, 2, "most"), (128, 1, "most"), (128, 2, "one"),
-                                          (256, 1, "one"), (256, 2, "most"), (128, 3, "one"), (256, 3, "most")])
+                                          (256, 1, "one"), (256, 2, "most"), (128, 3, "one"), (256, 3, "most"),
+                                          (64, 4, "most"), (128, 4, "one"), (128, 4, "most")])
 def test_gemm_tile_shapes_keep_results(bn, cm, splits):
-    """Every tile width and cluster mode of the tensor-core GEMM (cluster 2: pairs of row tiles
-    share the weight tile through TMA multicast; 3: CTA pairs on the cta_group::2 MMA), pinned at
-    every site where it is valid, gives
+    """Every tile width and tile mode of the tensor-core GEMM (2: pairs of row tiles share the
+    weight tile through TMA multicast; 3: CTA pairs on the cta_group::2 MMA; 4: two K blocks per
+    pipeline stage, so splits of an odd K-block count end on a half-used stage), pinned at every
+    site where it is valid, gives
     the oracle's gradient within the BF16 tolerance.  2880 minibatch rows = 23 row tiles: the last
     pair of a cluster has one tile past the rows, and the last row tile is ragged."""
     w = workload("rough", num_envs=480, precision=1)
@@ -335,7 +337,9 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
                 continue
             width = hidden[layer] if site in (0, 3) else widths[1][layer]
             out_tiles = -(-hidden[layer] // 128)
-            if width % bn or (site == 2 and cm > 1 and out_tiles < 2) or (cm > 1 and bn < 128 and (cm == 3 or site in (1, 2))):
+            paired = cm in (2, 3)
+            if (width % bn or (site == 2 and paired and out_tiles < 2) or (paired and bn < 128 and (cm == 3 or site in (1, 2)))
+                    or (cm == 4 and bn > 128)):
                 continue
             choices = [1] if splits == "one" else [64, 48, 32, 24, 16, 12, 8, 6, 4, 3, 2]
             for s_ in choices:
@@ -367,8 +371,8 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
 def test_set_gemm_tiles_rejects_invalid():
     w = workload("tiny", precision=1)
     L, _, _, _ = _setup(w)
-    for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 4, 1), (0, 9, 64, 1, 1),
-                 (2, 0, 64, 1, 0), (3, 0, 128, 1, 1), (0, 0, 64, 3, 1)):
+    for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 5, 1), (0, 9, 64, 1, 1),
+                 (2, 0, 64, 1, 0), (3, 0, 128, 1, 1), (0, 0, 64, 3, 1), (0, 0, 256, 4, 1)):
         with pytest.raises(api.RLError):
             api.rl_set_gemm_tiles(L.ctx, *args)
     L.close()
