@@ -294,6 +294,15 @@ __device__ __forceinline__ float elu_fast(float x) {
     return fmaxf(x, ex2_ftz(fminf(x, 0.f) * 1.4426950408889634f) - 1.f);
 }
 
+// 16-byte asynchronous copy global -> shared through the load/store unit (cp.async), which leaves
+// the TMA unit to the operand stream; src_bytes 0 fills the 16 bytes with zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Two floats to a bf16 pair (round to nearest even), the first in the low half.
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -378,12 +387,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     float* bias_s = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
     (void)bias_s;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
-    // barriers: full[S], empty[S], tfull[2], tempty[2], drain, hbar[EPI_WARPS][2]
+    // barriers: full[S], empty[S], tfull[NACC], tempty[NACC], drain (the area keeps room for
+    // 2 EPI_WARPS more)
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
     constexpr int NACC = C::NACC;
     const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + NACC);
     const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 2 * NACC);
-    const uint32_t hbar0 = smem_u32(bars + 2 * C::STAGES + 2 * NACC + 1);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS);
     static_assert((2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -412,8 +421,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             mbar_init(tempty0 + 8 * a, PAIR ? 2 * EPI_WARPS : EPI_WARPS);
         }
         mbar_init(drain, 1);
-        if (EPI == EPI_ELU_GRAD)
-            for (int h = 0; h < 2 * EPI_WARPS; ++h) mbar_init(hbar0 + 8 * h, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -653,29 +660,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const bool busy = slice < C::SLICES;
         uint8_t* stg_raw = stage_t + (size_t)ew * C::STG_WARP;
         // ELU-gradient form: the warp's activation blocks (32 rows x 32 columns of H per chunk) are
-        // fetched by TMA into two buffers, one chunk ahead of the chunk being processed
+        // fetched by cp.async (four lanes per 64-byte row, rows past M read as zeros) into two
+        // buffers with the output block's swizzle, one chunk ahead of the chunk being processed;
+        // the load/store unit carries them so that the TMA unit serves only the operand stream and
+        // the output stores
         constexpr int CPT = C::SLICE_COLS / 32;                 // chunks per tile of one warp
         int hj = 0;                                              // chunks processed so far
-        bool h_pending = false;                                  // chunk hj issued, not yet waited
         auto h_issue = [&](int j) {
             // chunk j of this warp's sequence: tile cid + (j / CPT) ncl, column chunk j % CPT
             const int t = cid + (j / CPT) * ncl;
-            if (t >= total) return false;
-            int mi, ni, sp, b;
-            decode(t, mi, ni, sp, b);
-            const int x = ni * BN + slice * C::SLICE_COLS + 32 * (j % CPT);
-            const int y = min(mi, mt - 1) * BM + 32 * q;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // prior reads/writes of the buffer
-            if (lane == 0) bulk_wait_read<0>();      // the output store from this buffer has read it
+            // the output store that last read the buffer (chunk j - 2) is done reading it
+            if (lane == 0) bulk_wait_read<0>();
             __syncwarp();
-            if (lane == 0) {
-                const uint32_t bar = hbar0 + 8 * (2 * ew + (j & 1));
-                mbar_expect_tx(bar, 2048u);
-                tma_load_2d(smem_u32(stg_raw + 2048 * (j & 1)), &p.tmH[b], bar, x, y);
+            if (t < total) {
+                int mi, ni, sp, b;
+                decode(t, mi, ni, sp, b);
+                const int x = ni * BN + slice * C::SLICE_COLS + 32 * (j % CPT);
+                const int y = mi * BM + 32 * q;
+                const uint32_t dst = smem_u32(stg_raw + 2048 * (j & 1));
+                const int u = lane & 3;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = 8 * i + (lane >> 2);
+                    const bool ok = y + r < p.M;
+                    const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(p.hsrc[b]) +
+                                               (size_t)(ok ? y + r : 0) * p.ldh + x + 8 * u;
+                    cp_async16(dst + r * 64 + 16 * (u ^ ((r >> 1) & 3)), src, ok ? 16u : 0u);
+                }
             }
-            return true;
+            cp_async_commit();     // an empty group past the last chunk keeps the wait counts uniform
         };
-        if (EPI == EPI_ELU_GRAD && busy) h_pending = h_issue(0);
+        if (EPI == EPI_ELU_GRAD && busy) h_issue(0);
         int oj = 0;                                              // bf16 output blocks written (buffer index)
         int local = 0;
         for (int t = cid; t < total; t += ncl, ++local) {
@@ -693,7 +708,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 break;
             }
             tc_fence_after();
-            bool stop = false;
 #pragma unroll 1
             for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
                 float v[32];
@@ -750,16 +764,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                     ++oj;
                 } else {   // EPI_ELU_GRAD
-                    // the next chunk's activations go into the other buffer (free: its chunk is done)
-                    const bool next = h_issue(hj + 1);
+                    // the next chunk's activations go into the other buffer, then this chunk's
+                    // copies (every lane's) are waited for
+                    h_issue(hj + 1);
                     uint8_t* hb = stg_raw + 2048 * (hj & 1);
-                    if (!mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status, abort_flag)) {
-                        *abort_flag = 1;
-                        h_pending = next;
-                        ++hj;
-                        stop = true;
-                        break;
-                    }
+                    cp_async_wait<1>();
+                    __syncwarp();
                     // 64-byte swizzle: 16-byte unit u of row r sits at unit u ^ ((r >> 1) & 3)
                     const int sw = (lane >> 1) & 3;
                     if (row_ok) {
@@ -795,7 +805,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         tma_store_3d(&p.tmC[b], smem_u32(hb), col, m0 + 32 * q, 0);
                         bulk_commit();
                     }
-                    h_pending = next;
                     ++hj;
                     if (p.colsum[b]) {
                         const float s = colsum32(v, lane);    // column col + lane, over this warp's 32 rows
@@ -810,12 +819,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * a, 0));
                 else mbar_arrive(tempty0 + 8 * a);
             }
-            if (stop) break;
         }
-        // an activation block still in flight lands before the CTA leaves (bounded); the output
-        // stores complete
-        if (EPI == EPI_ELU_GRAD && h_pending)
-            mbar_wait(hbar0 + 8 * (2 * ew + (hj & 1)), (uint32_t)(hj >> 1) & 1u, p.status);
+        // activation copies still in flight land and the output stores complete before the CTA
+        // leaves
+        if (EPI == EPI_ELU_GRAD) cp_async_wait<0>();
         if (lane == 0) bulk_wait_all();
     }
     tc_fence_before();
@@ -979,6 +986,12 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
     if (p.pair && (p.cm != 2 || p.bn < 128)) return cudaErrorInvalidValue;
     if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
+    if (p.epi == EPI_ELU_GRAD) {
+        // activation rows are read as 16-byte pieces
+        for (int b = 0; b < p.batch; ++b)
+            if (!p.hsrc[b] || (reinterpret_cast<uintptr_t>(p.hsrc[b]) & 15u)) return cudaErrorInvalidValue;
+        if (p.ldh < p.N || p.ldh % 8) return cudaErrorInvalidValue;
+    }
     switch (p.epi) {
         case EPI_STORE: return launch_bn<EPI_STORE>(p, s);
         case EPI_BIAS_ELU: return launch_bn<EPI_BIAS_ELU>(p, s);
@@ -1051,10 +1064,6 @@ bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint
 }
 
 int tc_stage_blocks(int bn, int cm, int pair) { return (cm == 1 && !pair && bn <= 128) ? 2 : 1; }
-
-bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld) {
-    return make_tmap(map, base, rows, cols, ld, 32u, 32u, CU_TENSOR_MAP_SWIZZLE_64B);
-}
 
 bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,
                    uint64_t split_ld) {

@@ -27,7 +27,8 @@ struct TcParams {
     CUtensorMap tmC[2];        // output per batch entry, [splits][M][N] (make_tmap_out): fp32 for
                                // EPI_STORE (split z at z), bf16 otherwise (one split)
     const float* bias[2];      // EPI_BIAS_ELU
-    CUtensorMap tmH[2];        // EPI_ELU_GRAD: bf16 activation [M][N], 32 x 32 boxes, 64-byte swizzle
+    const void* hsrc[2];       // EPI_ELU_GRAD: bf16 activation [M][ldh] whose ELU derivative scales
+    int ldh;                   // the product (row stride a multiple of 8)
     float* colsum[2];          // EPI_ELU_GRAD: per-row-tile column sums [4 M/128][N]
     int* status;               // device status word
     int ks;                    // K blocks per stage: 0 / 1, or 2 (cm 1, no pair, bn <= 128) with the
@@ -42,8 +43,6 @@ bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64
 bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols);
 // K blocks per stage for a tile shape: 2 for single-CTA tiles of width <= 128, else 1
 int tc_stage_blocks(int bn, int cm, int pair);
-// epilogue operand map: bf16 [rows][cols] (row stride ld), 32 x 32 boxes, 64-byte swizzle
-bool make_tmap_epi_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld);
 // output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), 32 x 32
 // x 1 boxes: fp32 with 128-byte swizzle, or bf16 with 64-byte swizzle
 bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,

@@ -86,7 +86,7 @@ struct rl_ctx {
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
     CUtensorMap tm_actB[2][4];                   // forward B maps of the rollout's policy inference
     CUtensorMap tm_x0;                           // gathered minibatch observations
-    CUtensorMap tm_dxA[2][4], tm_dxB[2][4], tm_dxH[2][4];
+    CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
     CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
     // the same operands for two-K-block stages (single-CTA tiles of width <= 128)
     CUtensorMap tm_fwdB2[2][4], tm_actB2[2][4], tm_fwdA2[2][4];
@@ -231,10 +231,8 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
             ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
-            // input gradient, B read MN-major: W_l [out][in] as it is stored, 64 x 64 boxes; the
-            // epilogue's ELU derivative reads H_{l-1} [rows][in] in 32 x 32 blocks
+            // input gradient, B read MN-major: W_l [out][in] as it is stored, 64 x 64 boxes
             ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, 64);
-            ok = ok && make_tmap_epi_bf16(&c->tm_dxH[n][l], c->H[n][l - 1], c->Mb, Li.in, Li.in);
         }
         // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in], 64 x 64 boxes
         ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 64);
@@ -316,10 +314,10 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
             tp.tmB[n] = k2 ? c->tm_dxB2[n][k] : c->tm_dxB[n][k];
             if (!make_tmap_out(&tp.tmC[n], c->dY[n][k - 1], false, 1, (uint64_t)M, (uint64_t)Li.in, (uint64_t)Li.in, 0))
                 return RL_ERR_CUDA;
-            tp.tmH[n] = c->tm_dxH[n][k];
+            tp.hsrc[n] = c->H[n][k - 1];
             tp.colsum[n] = c->gb[n][k - 1];
         }
-        tp.M = M; tp.N = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
+        tp.M = M; tp.N = Li.in; tp.ldh = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
         tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD;
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
