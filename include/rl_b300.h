@@ -290,7 +290,7 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
  * critic in one launch) over candidate tile widths
  * (64, 128, 256 output columns), tile modes (one CTA per tile, two CTAs sharing one B tile
  * through TMA multicast, a CTA pair on the cta_group::2 MMA, or one CTA per tile with two K blocks
- * per pipeline stage) and, for weight gradients, split-K counts (a quarter, half, default, double;
+ * per pipeline stage) and, for weight gradients, split-K counts (one and two waves of the width's tiles over the SMs, half and double the default;
  * timed together with the summation of their partials, which Adam performs) on the context's
  * own buffers, keeps the fastest, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
@@ -307,8 +307,9 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * of B) or 4 (one CTA per tile, two K blocks per pipeline stage fetched by one 3D TMA copy per
  * operand); 2 and 3 need at least two 128-row tiles at the site, 3 a tile width of at least 128,
  * 2 at sites 1 and 2 a tile width of at least 128, and 4 a tile width of at most 128;
- * splits: weight-gradient split-K count (1 .. twice the default, rounded so every slice is a
- * multiple of 64 rows), ignored for the other sites.  Drops a captured iteration graph.
+ * splits: weight-gradient split-K count (1 .. the larger of twice the default and two waves of
+ * 64-wide tiles over 148 SMs, rounded so every slice is a multiple of 64 rows), ignored for the
+ * other sites.  Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
 rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits);
 

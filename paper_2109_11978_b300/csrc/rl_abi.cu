@@ -755,8 +755,17 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 for (int cm : cms) {
                     if ((cm == 2 || cm == 3) && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
                     if (cm == 4 && (!c->bf16 || bn > 128)) continue;
-                    for (int S : {S0 / 4, S0 / 2, S0, 2 * S0}) {
-                        if (S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
+                    // split counts: one or two waves of this width's tiles over the SMs, and the
+                    // default's half and double
+                    const long long tl = (long long)out_tiles * (Li.in / bn) * 2;
+                    const int one_wave = (int)std::max(1ll, 148ll / tl), two_waves = (int)std::max(1ll, 296ll / tl);
+                    int cand[4] = {one_wave, two_waves, S0 / 2, 2 * S0};
+                    if (!c->bf16) { cand[0] = S0 / 4; cand[1] = S0; }
+                    for (int ci = 0; ci < 4; ++ci) {
+                        const int S = cand[ci];
+                        bool seen = false;
+                        for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == S;
+                        if (seen || S < 1 || S > c->S_cap[l] || st != RL_OK) continue;
                         int kc = (c->Mb + S - 1) / S;
                         kc = (kc + 63) / 64 * 64;
                         const int Sr = (c->Mb + kc - 1) / kc;
@@ -1042,7 +1051,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         const long long tiles = (long long)((Li.out + 127) / 128) * (Li.in / bn) * 2;
         int S;
         if (c->bf16)
-            S = (int)std::max(1ll, std::min((long long)std::max(1, c->Mb / 384), (148ll + tiles / 2) / tiles));
+            S = (int)std::max(1ll, std::min((long long)std::max(1, c->Mb / 384), 148ll / tiles));
         else
             S = (int)std::max(1ll, std::min(16ll, (2ll * 148 + tiles / 2) / tiles));
         const int unit = 64;
@@ -1051,7 +1060,9 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         S = (c->Mb + kc - 1) / kc;
         c->S[l] = S;
         c->kchunk[l] = kc;
-        c->S_cap[l] = std::min(2 * S, std::max(1, c->Mb / 64));   // room for the autotuner's larger splits
+        // room for the autotuner's larger splits: two waves of the narrowest (64-column) tiles
+        const long long tiles64 = (long long)((Li.out + 127) / 128) * (Li.in / 64) * 2;
+        c->S_cap[l] = (int)std::min((long long)std::max(1, c->Mb / 64), std::max(2ll * S, 296ll / tiles64 + 1));
         c->bn_fwd[l] = pick_bn(Li.out);
         c->bn_dx[l] = pick_bn(Li.in);
         c->bn_dw[l] = bn;
