@@ -79,6 +79,9 @@ struct HeadParams {
     float* values;
     // loss mode
     const int* idx;              // minibatch row -> sample index (null = identity)
+    const float* rec;            // packed per-sample loss inputs (launch_pack_records layout, indexed like
+                                 // the fields below), or null
+    int rec_ld;
     const float* a_old;          // [B][A]
     const float* logp_old;       // [B]
     const float* mu_old;         // [B][A]
@@ -162,6 +165,11 @@ cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
 cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, cudaStream_t s);
+// Per-sample loss inputs packed once per iteration into one 128-byte record per sample:
+// [a_old A][mu_old A][logp_old][adv][v_old][ret][zeros], REC_LD floats per record (A <= 12).
+constexpr int REC_LD = 32;
+cudaError_t launch_pack_records(int B, int A, const float* a_old, const float* mu_old, const float* logp_old,
+                                const float* adv, const float* v_old, const float* ret, float* rec, cudaStream_t s);
 // Minibatch indices: permutation of [0, B) by a cycle-walking Feistel network keyed by
 // (seed, iteration, epoch); idx [epochs][B].
 cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned long long* iteration,

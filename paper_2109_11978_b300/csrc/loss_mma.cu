@@ -128,7 +128,32 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
     float aold[MAX_A], muold[MAX_A], lpo = 0.f, adv = 0.f, vo = 0.f, R = 0.f;
 #pragma unroll
     for (int j = 0; j < MAX_A; ++j) aold[j] = muold[j] = 0.f;
-    if (live) {
+    if (live && p.rec) {
+        // the sample's packed 128-byte record: one line per row instead of one per field
+        const int m = m0 + tid;
+        const int s = p.idx ? __ldg(p.idx + m) : m;
+        const float4* r4 = reinterpret_cast<const float4*>(p.rec + (size_t)s * p.rec_ld);
+        float f[28];
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+            const float4 x = __ldg(r4 + v);
+            f[4 * v] = x.x; f[4 * v + 1] = x.y; f[4 * v + 2] = x.z; f[4 * v + 3] = x.w;
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_A; ++j)
+            if (j < A) {
+                aold[j] = f[j];
+                muold[j] = f[A + j];
+            }
+        // the four scalars follow the 2A action fields (A <= 12)
+#pragma unroll
+        for (int k = 0; k < 28; ++k) {
+            if (k == 2 * A) lpo = f[k];
+            if (k == 2 * A + 1) adv = f[k];
+            if (k == 2 * A + 2) vo = f[k];
+            if (k == 2 * A + 3) R = f[k];
+        }
+    } else if (live) {
         const int m = m0 + tid;
         const int s = p.idx ? __ldg(p.idx + m) : m;
 #pragma unroll

@@ -71,6 +71,7 @@ struct rl_ctx {
     void* dY[2][4] = {};
     float* gw[2][4] = {};
     int S[4] = {}, kchunk[4] = {}, S_cap[4] = {};
+    float* recs = nullptr;                       // packed per-sample loss inputs (BF16 update)
     float* gb[2][4] = {};
     int mtiles = 0;
     int gb_parts = 0;            // bias-gradient partials per row tile (4 TMEM lane quarters in bf16)
@@ -429,12 +430,14 @@ EnvParams env_params(rl_ctx* c) {
 // X0 must already hold the minibatch observations.
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
-                            const float* ret, bool step) {
+                            const float* ret, bool step, const float* rec = nullptr) {
     rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, false);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
     const int l = c->NH - 1;
     h.idx = idx;
+    h.rec = rec;
+    h.rec_ld = REC_LD;
     h.a_old = a_old;
     h.logp_old = logp_old;
     h.mu_old = mu_old;
@@ -566,11 +569,17 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
     cudaStream_t s = q.s;
     CK(cudaMemcpyAsync(c->logstd_old, c->params + c->logstd, sizeof(float) * c->A, cudaMemcpyDeviceToDevice, s));
     CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s); }));
+    // the BF16 loss head reads each row's loss inputs from one packed 128-byte record per sample
+    // (one line per row of a shuffled minibatch instead of one per field)
+    if (c->bf16)
+        CK(q.run(RL_PROF_OTHER, 1,
+                 [&] { return launch_pack_records(B, c->A, actions, mu_old, logp_old, adv, val_old, ret, c->recs, s); }));
     for (int e = 0; e < epochs; ++e) {
         for (int m = 0; m < minibatches; ++m) {
             const int* idx = c->perm + (size_t)e * B + (size_t)m * Mb;
             CK(q.run(RL_PROF_GATHER, 1, [&] { return launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, s); }));
-            rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true);
+            rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
+                                             c->bf16 ? c->recs : nullptr);
             if (st != RL_OK) return st;
             c->adam.grad_out = nullptr;
             CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
@@ -1079,6 +1088,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     }
     c->head_blocks = loss_head_blocks(c->Mb, c->HL, c->bf16 ? 1 : 0);
     CK(dalloc(c, &c->head_part, sizeof(float) * (size_t)c->head_blocks * head_part_floats(c->A, c->HL)));
+    if (c->bf16) CK(dalloc(c, &c->recs, sizeof(float) * (size_t)c->B * REC_LD));
     if (c->bf16) {
         for (int n = 0; n < 2; ++n)
             for (int l = 0; l < c->NH; ++l) {

@@ -263,6 +263,37 @@ cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int 
     return cudaGetLastError();
 }
 
+// One warp per sample: lane j writes field j of the sample's 128-byte record (lanes past the
+// 2A + 4 fields write zeros), so every record leaves as one full line.
+__global__ void __launch_bounds__(256) pack_records_kernel(int B, int A, const float* __restrict__ a_old,
+                                                           const float* __restrict__ mu_old, const float* __restrict__ logp_old,
+                                                           const float* __restrict__ adv, const float* __restrict__ v_old,
+                                                           const float* __restrict__ ret, float* __restrict__ rec) {
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const long long s = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= B) return;
+    float f = 0.f;
+    if (lane < A) f = a_old[s * A + lane];
+    else if (lane < 2 * A) f = mu_old[s * A + lane - A];
+    else if (lane == 2 * A) f = logp_old[s];
+    else if (lane == 2 * A + 1) f = adv[s];
+    else if (lane == 2 * A + 2) f = v_old[s];
+    else if (lane == 2 * A + 3) f = ret[s];
+    rec[s * REC_LD + lane] = f;
+}
+
+cudaError_t launch_pack_records(int B, int A, const float* a_old, const float* mu_old, const float* logp_old,
+                                const float* adv, const float* v_old, const float* ret, float* rec, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    if (A < 1 || 2 * A + 4 > REC_LD || !rec) return cudaErrorInvalidValue;
+    cudaError_t e = launch_pdl(pack_records_kernel, dim3((B + 7) / 8), dim3(256), 0, s, B, A, a_old, mu_old, logp_old, adv,
+                               v_old, ret, rec);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s) {
     if (p.nblocks <= 0) return cudaSuccess;
     cudaError_t e = launch_pdl(adam_kernel, dim3(p.nblocks), dim3(ADAM_THREADS), 0, s, p);
