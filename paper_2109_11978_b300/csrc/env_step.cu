@@ -3,10 +3,10 @@
 // reward, termination / time-out / bootstrap, the curriculum update and respawn, and the
 // observation with bilinear height samples and Table 4 noise.
 //
-// Layout: the env state is a structure of arrays in HBM ([57][N] fp32 + [3][N] int32), so
-// every state row is read and written with coalesced accesses.  A block owns 16 robots (256 when
-// N is large).  Phase 1: one robot per thread (warp 0 for 16-robot blocks), the per-robot
-// recurrence in registers, leaving a 60-float record per robot in shared memory.  Phase 2: all 8
+// Layout: the env state is a structure of arrays in HBM ([57][N] fp32 + [3][N] int32).  A block
+// owns 16 robots.  Phase 1: the stand-in's independent recurrences of a robot (its 12 joints and
+// three base chains) on separate threads, the feet on a sixteenth, meeting in shared memory for
+// the reward and the reset, leaving a 60-float record per robot in shared memory.  Phase 2: all 8
 // warps assemble the observation rows (one robot per warp at a time, two adjacent columns per
 // lane), so the row of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height
 // samples of a robot are gathered by 32 lanes in parallel from the L2-resident heightfield; the
@@ -107,231 +107,289 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
     return (1.f - fu) * (1.f - fv) * h00 + fu * (1.f - fv) * h10 + (1.f - fu) * fv * h01 + fu * fv * h11;
 }
 
-template <int MODE, int ENVS, int THREADS>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
-__global__ void __launch_bounds__(THREADS, 512 / THREADS) env_step_kernel(EnvParams p) {
+// Phase-1 roles of a block's 256 threads (16 robots): threads 0..191 one (robot, joint) pair
+// each; then 16 threads each for the three independent base chains of the stand-in (planar
+// velocity / yaw / heading / position; vertical and roll / pitch rates; gravity direction and
+// height) and 16 for the feet (from thread 192 on: 16 threads per role).  Each role is a whole
+// number of warps or half-warps.
+constexpr int T_PLANE = 192;
+
+template <int MODE>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
+__global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     pdl_wait();
     pdl_trigger();
+    constexpr int ENVS = 16, THREADS = 256;
     extern __shared__ float rec_raw[];
     float (*rec)[REC] = reinterpret_cast<float (*)[REC]>(rec_raw);       // [ENVS][REC]
+    // exchange of phase 1: the joints' reward terms, the rates, the feet, the reset decision
+    __shared__ float xj[4][ENVS][12];
+    __shared__ float xr[3][ENVS];
+    __shared__ float xf[ENVS];
+    __shared__ int xfi[ENVS], xd[ENVS], xl[ENVS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
     const int env0 = blockIdx.x * ENVS;
     const int N = p.N;
     const unsigned long long it = p.iteration ? *p.iteration : 0ull;
-    // Phase 1 runs one robot per thread: on lanes 0..ENVS-1 of warp 0 for small blocks (small N,
-    // where spreading robots over many SMs matters more), on every thread for 256-robot blocks.
-    const int local = ENVS < 32 ? lane : (int)threadIdx.x;
     // grid sample offsets (before rotation) of the height columns, shared by the block's robots
     float* gtab = rec_raw + ENVS * REC;                                  // [2][GTAB]
     const int ng = p.GX * p.GY;
-    for (int k = threadIdx.x; k < ng && k < GTAB; k += THREADS) {
+    for (int k = tid; k < ng && k < GTAB; k += THREADS) {
         const int ix = k % p.GX, iy = k / p.GX;
         gtab[k] = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
         gtab[GTAB + k] = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
     }
-    float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (reward, reset, level)
-    if (ENVS == 256 || (warp == 0 && lane < ENVS)) {
-        const int e = env0 + local;
-        if (e < N) {
-            float* sf = p.sf;
-            int* si = p.si;
-            auto F = [&](int r) -> float& { return sf[(size_t)r * N + e]; };
-            float px = F(RL_F_PX), py = F(RL_F_PY), z = F(RL_F_Z), hc = F(RL_F_HC), hs = F(RL_F_HS);
-            float vx = F(5), vy = F(6), vz = F(7), wx = F(8), wy = F(9), wz = F(10);
-            float gx = F(11), gy = F(12), gz = F(13), cx = F(14), cy = F(15), cw = F(16);
-            float tair[4], q[12], qd[12], ap[12];
+    // Phase 1: the stand-in's joints and base chains are independent recurrences, each on its own
+    // thread with the same fp32 operations as one robot per thread would use; the reward sums
+    // and the reset decision meet on the robot's planar thread through shared memory (the joint
+    // terms summed in joint order).
+    const bool joint = tid < T_PLANE;
+    const int lr = joint ? tid / 12 : (tid - T_PLANE) & 15;           // robot of the block
+    const int jl = joint ? tid % 12 : 0;
+    const int role = joint ? 0 : 1 + (tid - T_PLANE) / 16;             // 1 planar, 2 rates, 3 grav, 4 feet
+    const int e = env0 + lr;
+    const bool valid = e < N;
+    const int ec = valid ? e : N - 1;          // a readable robot for the threads of a missing one
+    float* sf = p.sf;
+    int* si = p.si;
+    auto F = [&](int r) -> float& { return sf[(size_t)r * N + ec]; };
+    float q = 0.f, qd = 0.f, ap = 0.f, a = 0.f;                          // joint
+    float px = 0.f, py = 0.f, hc = 0.f, hs = 0.f, vx = 0.f, vy = 0.f, wz = 0.f, cx = 0.f, cy = 0.f, cw = 0.f;   // planar
+    float vz = 0.f, wx = 0.f, wy = 0.f;                                  // rates
+    float gx = 0.f, gy = 0.f, gz = 0.f, z = 0.f;                         // grav
+    float tair[4] = {0.f, 0.f, 0.f, 0.f};                               // feet
+    if (joint) {
+        q = F(RL_F_Q + jl); qd = F(RL_F_QD + jl); ap = F(RL_F_AP + jl);
+    } else if (role == 1) {
+        px = F(RL_F_PX); py = F(RL_F_PY); hc = F(RL_F_HC); hs = F(RL_F_HS);
+        vx = F(5); vy = F(6); wz = F(10); cx = F(14); cy = F(15); cw = F(16);
+    } else if (role == 2) {
+        vz = F(7); wx = F(8); wy = F(9);
+    } else if (role == 3) {
+        gx = F(11); gy = F(12); gz = F(13); z = F(RL_F_Z);
+    } else {
 #pragma unroll
-            for (int f = 0; f < 4; ++f) tair[f] = F(RL_F_TAIR + f);
+        for (int f = 0; f < 4; ++f) tair[f] = F(RL_F_TAIR + f);
+    }
+    int eplen = si[(size_t)RL_I_EPLEN * N + ec];
+    int level = si[(size_t)RL_I_LEVEL * N + ec];
+    int contact = si[(size_t)RL_I_CONTACT * N + ec];
+    uint64_t key;
+    float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (planar threads)
+    if (MODE == 0) {
+        key = rng_key(p.seed, kStreamEnv, it, (uint64_t)p.t, (uint64_t)ec);
+        const float qd_old = qd;
+        if (joint) a = __ldg(p.actions + (size_t)ec * 12 + jl);
+        // Pushes (Sec. 3.3): every push_interval steps of the episode, +-push_vel in x, y.
+        if (role == 1 && p.push_on && eplen > 0 && (eplen % p.push_interval) == 0) {
+            vx = FADD(vx, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH)))));
+            vy = FADD(vy, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH + 1)))));
+        }
+        const float zn = znom(level);
+        float sq_tau = 0.f;     // tau^2 of the last substep (Table 2 torque term), joints
+        for (int k = 0; k < p.decimation; ++k) {
+            const uint32_t base = 32u * (uint32_t)k;
+            if (joint) {
+                // PD torque (Sec. 3.2) on the target q* = q_def + action_scale a, recomputed every
+                // substep (App. A.1.1), consumed by the physics stand-in (exact fp32 recurrence).
+                const float qs = FADD(p.q_def[jl], FMUL(p.ascale, a));
+                const float tau = FSUB(FMUL(p.kp, FSUB(qs, q)), FMUL(p.kd, qd));
+                if (k == p.decimation - 1) sq_tau = tau * tau;
+                const float xi = irwin_hall(rng_word(key, base + jl));
+                qd = FADD(FADD(FMUL(A_Q, qd), FMUL(p.sim_dt, FMUL(INV_I, tau))), FMUL(S_Q, xi));
+                q = FADD(q, FMUL(p.sim_dt, qd));
+            } else if (role == 1) {
+                vx = FADD(FADD(FMUL(RHO_V, vx), FMUL(ONE_M_RHO_V, cx)), FMUL(S_V, irwin_hall(rng_word(key, base + 12))));
+                vy = FADD(FADD(FMUL(RHO_V, vy), FMUL(ONE_M_RHO_V, cy)), FMUL(S_V, irwin_hall(rng_word(key, base + 13))));
+                wz = FADD(FADD(FMUL(RHO_W, wz), FMUL(ONE_M_RHO_W, cw)), FMUL(S_W, irwin_hall(rng_word(key, base + 17))));
+                const float w = FMUL(wz, p.sim_dt);
+                const float c1 = FSUB(hc, FMUL(hs, w)), s1 = FADD(hs, FMUL(hc, w));
+                const float nrm = __fsqrt_rn(FADD(FMUL(c1, c1), FMUL(s1, s1)));
+                hc = __fdiv_rn(c1, nrm);
+                hs = __fdiv_rn(s1, nrm);
+                const float dx = FSUB(FMUL(hc, vx), FMUL(hs, vy)), dy = FADD(FMUL(hs, vx), FMUL(hc, vy));
+                px = FADD(px, FMUL(p.sim_dt, dx));
+                py = FADD(py, FMUL(p.sim_dt, dy));
+            } else if (role == 2) {
+                vz = FADD(FMUL(RHO_V, vz), FMUL(S_V, irwin_hall(rng_word(key, base + 14))));
+                wx = FADD(FMUL(RHO_W, wx), FMUL(S_W, irwin_hall(rng_word(key, base + 15))));
+                wy = FADD(FMUL(RHO_W, wy), FMUL(S_W, irwin_hall(rng_word(key, base + 16))));
+            } else if (role == 3) {
+                gx = FADD(FMUL(RHO_G, gx), FMUL(S_G, irwin_hall(rng_word(key, base + 18))));
+                gy = FADD(FMUL(RHO_G, gy), FMUL(S_G, irwin_hall(rng_word(key, base + 19))));
+                gz = -__fsqrt_rn(fmaxf(0.0f, FSUB(1.0f, FADD(FMUL(gx, gx), FMUL(gy, gy)))));
+                z = FADD(FADD(FMUL(RHO_Z, z), FMUL(ONE_M_RHO_Z, zn)), FMUL(S_Z, irwin_hall(rng_word(key, base + 20))));
+            }
+        }
+        const int eplen_new = eplen + 1;
+        if (joint) {
+            const float inv_dt = 1.0f / p.dt;
+            const float qdd = (qd - qd_old) * inv_dt, da = a - ap;
+            xj[0][lr][jl] = qdd * qdd;
+            xj[1][lr][jl] = qd * qd;
+            xj[2][lr][jl] = da * da;
+            xj[3][lr][jl] = sq_tau;
+        } else if (role == 2) {
+            xr[0][lr] = vz; xr[1][lr] = wx; xr[2][lr] = wy;
+        } else if (role == 4) {
+            // Feet: contact schedule, air time (fp32, exact), first contacts.
+            const int off = (int)(((long long)ec * CONTACT_ENV_STRIDE) % CONTACT_PERIOD);
+            int cbits = 0;
+            float r_air = 0.f;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const int ph = (f == 1 || f == 2) ? 20 : 0;
+                const bool on = ((eplen_new + off + ph) % CONTACT_PERIOD) < CONTACT_DUTY;
+                cbits |= (int)on << f;
+                tair[f] = FADD(tair[f], p.dt);
+                const bool first = on && !((contact >> f) & 1);
+                if (first) r_air += tair[f] - AIR_TARGET;
+                if (on) tair[f] = 0.f;
+            }
+            xf[lr] = r_air;
+            xfi[lr] = cbits;
+        }
+        __syncthreads();
+        if (role == 1) {
+            const bool crash = hi32(rng_word(key, SLOT_CRASH)) < p.crash_thr;
+            const float n_coll = (float)mulhi_n(hi32(rng_word(key, SLOT_COLL)), 3u);
+            float sq_qdd = 0.f, sq_qd = 0.f, sq_rate = 0.f, sq_t = 0.f;
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
-                q[j] = F(RL_F_Q + j);
-                qd[j] = F(RL_F_QD + j);
-                ap[j] = F(RL_F_AP + j);
+                sq_qdd += xj[0][lr][j];
+                sq_qd += xj[1][lr][j];
+                sq_rate += xj[2][lr][j];
+                sq_t += xj[3][lr][j];
             }
-            int eplen = si[(size_t)RL_I_EPLEN * N + e];
-            int level = si[(size_t)RL_I_LEVEL * N + e];
-            int contact = si[(size_t)RL_I_CONTACT * N + e];
-            uint64_t key;
-            if (MODE == 0) {
-                key = rng_key(p.seed, kStreamEnv, it, (uint64_t)p.t, (uint64_t)e);
-                float a[12], qd_old[12];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) {
-                    a[j] = __ldg(p.actions + (size_t)e * 12 + j);
-                    qd_old[j] = qd[j];
+            const float vz_ = xr[0][lr], wx_ = xr[1][lr], wy_ = xr[2][lr], r_air = xf[lr];
+            // Reward: the nine Table 2 terms, each weight times dt.
+            float e2 = (cx - vx) * (cx - vx) + (cy - vy) * (cy - vy);
+            float ew = (cw - wz) * (cw - wz);
+            float r = W_LIN * expf(-e2 * PHI_INV) + W_ANG * expf(-ew * PHI_INV) - W_VZ * vz_ * vz_ -
+                      W_WXY * (wx_ * wx_ + wy_ * wy_) - W_JOINT * (sq_qdd + sq_qd) - W_TAU * sq_t - W_RATE * sq_rate -
+                      W_COLL * n_coll + W_AIR * r_air;
+            r *= p.dt;
+            // Termination (Sec. 3.2: base contact = crash; Sec. 2.2.1: 20 s time-out) and the
+            // time-out bootstrap r += gamma V(o_t) (Sec. 2.2.2).
+            const bool timeout = (eplen_new >= p.max_ep) && !crash;
+            const bool done = crash || timeout;
+            if (timeout) r += p.gamma * __ldg(p.values + ec);
+            int level_new = level;
+            if (done) {
+                // Curriculum (Sec. 3.1), decided in fp64 with one rounding per operation.
+                const double dpx = px, dpy = py, dcx = cx, dcy = cy;
+                const double d2 = __dadd_rn(__dmul_rn(dpx, dpx), __dmul_rn(dpy, dpy));
+                const double half = __dmul_rn(0.5, (double)p.tile);
+                const bool promote = d2 > __dmul_rn(half, half);
+                const double vv = __dadd_rn(__dmul_rn(dcx, dcx), __dmul_rn(dcy, dcy));
+                const double T = __dmul_rn((double)p.max_ep, (double)p.dt);
+                const double thr = __dmul_rn(__dmul_rn(vv, __dmul_rn(T, T)), 0.25);
+                const bool demote = d2 < thr;
+                if (promote) {
+                    level_new = level + 1 >= p.L ? (int)mulhi_n(hi32(rng_word(key, SLOT_LOOP)), (uint32_t)p.L) : level + 1;
+                } else if (demote) {
+                    level_new = level > 0 ? level - 1 : 0;
                 }
-                // Pushes (Sec. 3.3): every push_interval steps of the episode, +-push_vel in x, y.
-                if (p.push_on && eplen > 0 && (eplen % p.push_interval) == 0) {
-                    vx = FADD(vx, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH)))));
-                    vy = FADD(vy, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH + 1)))));
-                }
-                const float zn = znom(level);
-                float sq_tau = 0.f;     // |tau|^2 of the last substep (Table 2 torque term)
-                for (int k = 0; k < p.decimation; ++k) {
-                    const uint32_t base = 32u * (uint32_t)k;
-                    const bool last = k == p.decimation - 1;
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        // PD torque (Sec. 3.2) on the target q* = q_def + action_scale a, recomputed
-                        // every substep (App. A.1.1) ...
-                        const float qs = FADD(p.q_def[j], FMUL(p.ascale, a[j]));
-                        const float tau = FSUB(FMUL(p.kp, FSUB(qs, q[j])), FMUL(p.kd, qd[j]));
-                        if (last) sq_tau += tau * tau;
-                        // ... consumed by the physics stand-in (exact fp32 recurrence).
-                        const float xi = irwin_hall(rng_word(key, base + j));
-                        qd[j] = FADD(FADD(FMUL(A_Q, qd[j]), FMUL(p.sim_dt, FMUL(INV_I, tau))), FMUL(S_Q, xi));
-                        q[j] = FADD(q[j], FMUL(p.sim_dt, qd[j]));
-                    }
-                    vx = FADD(FADD(FMUL(RHO_V, vx), FMUL(ONE_M_RHO_V, cx)), FMUL(S_V, irwin_hall(rng_word(key, base + 12))));
-                    vy = FADD(FADD(FMUL(RHO_V, vy), FMUL(ONE_M_RHO_V, cy)), FMUL(S_V, irwin_hall(rng_word(key, base + 13))));
-                    vz = FADD(FMUL(RHO_V, vz), FMUL(S_V, irwin_hall(rng_word(key, base + 14))));
-                    wx = FADD(FMUL(RHO_W, wx), FMUL(S_W, irwin_hall(rng_word(key, base + 15))));
-                    wy = FADD(FMUL(RHO_W, wy), FMUL(S_W, irwin_hall(rng_word(key, base + 16))));
-                    wz = FADD(FADD(FMUL(RHO_W, wz), FMUL(ONE_M_RHO_W, cw)), FMUL(S_W, irwin_hall(rng_word(key, base + 17))));
-                    const float w = FMUL(wz, p.sim_dt);
-                    const float c1 = FSUB(hc, FMUL(hs, w)), s1 = FADD(hs, FMUL(hc, w));
-                    const float nrm = __fsqrt_rn(FADD(FMUL(c1, c1), FMUL(s1, s1)));
-                    hc = __fdiv_rn(c1, nrm);
-                    hs = __fdiv_rn(s1, nrm);
-                    const float dx = FSUB(FMUL(hc, vx), FMUL(hs, vy)), dy = FADD(FMUL(hs, vx), FMUL(hc, vy));
-                    px = FADD(px, FMUL(p.sim_dt, dx));
-                    py = FADD(py, FMUL(p.sim_dt, dy));
-                    gx = FADD(FMUL(RHO_G, gx), FMUL(S_G, irwin_hall(rng_word(key, base + 18))));
-                    gy = FADD(FMUL(RHO_G, gy), FMUL(S_G, irwin_hall(rng_word(key, base + 19))));
-                    gz = -__fsqrt_rn(fmaxf(0.0f, FSUB(1.0f, FADD(FMUL(gx, gx), FMUL(gy, gy)))));
-                    z = FADD(FADD(FMUL(RHO_Z, z), FMUL(ONE_M_RHO_Z, zn)), FMUL(S_Z, irwin_hall(rng_word(key, base + 20))));
-                }
-                // Feet: contact schedule, air time (fp32, exact), first contacts.
-                const int eplen_new = eplen + 1;
-                const int off = (int)(((long long)e * CONTACT_ENV_STRIDE) % CONTACT_PERIOD);
-                int cbits = 0;
-                float r_air = 0.f;
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    const int ph = (f == 1 || f == 2) ? 20 : 0;
-                    const bool on = ((eplen_new + off + ph) % CONTACT_PERIOD) < CONTACT_DUTY;
-                    cbits |= (int)on << f;
-                    tair[f] = FADD(tair[f], p.dt);
-                    const bool first = on && !((contact >> f) & 1);
-                    if (first) r_air += tair[f] - AIR_TARGET;
-                    if (on) tair[f] = 0.f;
-                }
-                const bool crash = hi32(rng_word(key, SLOT_CRASH)) < p.crash_thr;
-                const float n_coll = (float)mulhi_n(hi32(rng_word(key, SLOT_COLL)), 3u);
-
-                // Reward: the nine Table 2 terms, each weight times dt.
-                float e2 = (cx - vx) * (cx - vx) + (cy - vy) * (cy - vy);
-                float ew = (cw - wz) * (cw - wz);
-                float sq_qdd = 0.f, sq_qd = 0.f, sq_rate = 0.f;
-                const float inv_dt = 1.0f / p.dt;
-#pragma unroll
-                for (int j = 0; j < 12; ++j) {
-                    float qdd = (qd[j] - qd_old[j]) * inv_dt;
-                    sq_qdd += qdd * qdd;
-                    sq_qd += qd[j] * qd[j];
-                    float da = a[j] - ap[j];
-                    sq_rate += da * da;
-                }
-                float r = W_LIN * expf(-e2 * PHI_INV) + W_ANG * expf(-ew * PHI_INV) - W_VZ * vz * vz -
-                          W_WXY * (wx * wx + wy * wy) - W_JOINT * (sq_qdd + sq_qd) - W_TAU * sq_tau -
-                          W_RATE * sq_rate - W_COLL * n_coll + W_AIR * r_air;
-                r *= p.dt;
-                // Termination (Sec. 3.2: base contact = crash; Sec. 2.2.1: 20 s time-out) and the
-                // time-out bootstrap r += gamma V(o_t) (Sec. 2.2.2).
-                const bool timeout = (eplen_new >= p.max_ep) && !crash;
-                const bool done = crash || timeout;
-                if (timeout) r += p.gamma * __ldg(p.values + e);
-
-                int level_new = level;
-                if (done) {
-                    // Curriculum (Sec. 3.1), decided in fp64 with one rounding per operation.
-                    const double dpx = px, dpy = py, dcx = cx, dcy = cy;
-                    const double d2 = __dadd_rn(__dmul_rn(dpx, dpx), __dmul_rn(dpy, dpy));
-                    const double half = __dmul_rn(0.5, (double)p.tile);
-                    const bool promote = d2 > __dmul_rn(half, half);
-                    const double vv = __dadd_rn(__dmul_rn(dcx, dcx), __dmul_rn(dcy, dcy));
-                    const double T = __dmul_rn((double)p.max_ep, (double)p.dt);
-                    const double thr = __dmul_rn(__dmul_rn(vv, __dmul_rn(T, T)), 0.25);
-                    const bool demote = d2 < thr;
-                    if (promote) {
-                        level_new = level + 1 >= p.L ? (int)mulhi_n(hi32(rng_word(key, SLOT_LOOP)), (uint32_t)p.L)
-                                                     : level + 1;
-                    } else if (demote) {
-                        level_new = level > 0 ? level - 1 : 0;
-                    }
-                }
+            }
+            if (valid) {
                 if (p.rew) p.rew[e] = r;
                 if (p.done) p.done[e] = (uint8_t)done;
                 if (p.timeout) p.timeout[e] = (uint8_t)timeout;
-#pragma unroll
-                for (int j = 0; j < 12; ++j) ap[j] = a[j];
-                eplen = eplen_new;
-                contact = cbits;
-                if (done) {
-                    level = level_new;
-                    Respawn rs = respawn_draw(key, p);
-                    px = 0.f; py = 0.f; z = znom(level);
-                    hc = rs.hc; hs = rs.hs;
-                    vx = vy = vz = wx = wy = wz = gx = gy = 0.f; gz = -1.f;
-                    cx = rs.cx; cy = rs.cy; cw = rs.cw;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) tair[f] = 0.f;
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) { q[j] = p.q_def[j]; qd[j] = 0.f; ap[j] = 0.f; }
-                    eplen = 0;
-                    contact = 0;
-                }
                 st_r = r;
                 st_d = (float)done;
-                st_l = (float)level;
-            } else {
-                // Spawn (initial state): level 0, fresh heading and command, random episode length.
-                key = rng_key(p.seed, kStreamInit, 0ull, 0ull, (uint64_t)e);
-                level = 0;
+                st_l = (float)(done ? level_new : level);
+            }
+            xd[lr] = done;
+            xl[lr] = level_new;
+        }
+        __syncthreads();
+        const bool done = xd[lr] != 0;
+        ap = a;
+        eplen = eplen_new;
+        contact = xfi[lr];
+        if (done) {
+            level = xl[lr];
+            // respawn: every thread resets its share (the planar thread draws heading and command)
+            if (joint) {
+                q = p.q_def[jl]; qd = 0.f; ap = 0.f;
+            } else if (role == 1) {
                 Respawn rs = respawn_draw(key, p);
-                px = 0.f; py = 0.f; z = znom(0);
+                px = 0.f; py = 0.f;
                 hc = rs.hc; hs = rs.hs;
-                vx = vy = vz = wx = wy = wz = gx = gy = 0.f; gz = -1.f;
+                vx = vy = wz = 0.f;
                 cx = rs.cx; cy = rs.cy; cw = rs.cw;
+            } else if (role == 2) {
+                vz = wx = wy = 0.f;
+            } else if (role == 3) {
+                gx = gy = 0.f; gz = -1.f; z = znom(level);
+            } else {
 #pragma unroll
                 for (int f = 0; f < 4; ++f) tair[f] = 0.f;
-#pragma unroll
-                for (int j = 0; j < 12; ++j) { q[j] = p.q_def[j]; qd[j] = 0.f; ap[j] = 0.f; }
-                eplen = p.randomize_eplen ? (int)mulhi_n(hi32(rng_word(key, SLOT_EPLEN)), (uint32_t)p.max_ep) : 0;
-                contact = 0;
             }
-            // Store the state.
-            F(RL_F_PX) = px; F(RL_F_PY) = py; F(RL_F_Z) = z; F(RL_F_HC) = hc; F(RL_F_HS) = hs;
-            F(5) = vx; F(6) = vy; F(7) = vz; F(8) = wx; F(9) = wy; F(10) = wz;
-            F(11) = gx; F(12) = gy; F(13) = gz; F(14) = cx; F(15) = cy; F(16) = cw;
+            eplen = 0;
+            contact = 0;
+        }
+    } else {
+        // Spawn (initial state): level 0, fresh heading and command, random episode length.
+        key = rng_key(p.seed, kStreamInit, 0ull, 0ull, (uint64_t)ec);
+        level = 0;
+        if (joint) {
+            q = p.q_def[jl]; qd = 0.f; ap = 0.f;
+        } else if (role == 1) {
+            Respawn rs = respawn_draw(key, p);
+            px = 0.f; py = 0.f;
+            hc = rs.hc; hs = rs.hs;
+            vx = vy = wz = 0.f;
+            cx = rs.cx; cy = rs.cy; cw = rs.cw;
+        } else if (role == 2) {
+            vz = wx = wy = 0.f;
+        } else if (role == 3) {
+            gx = gy = 0.f; gz = -1.f; z = znom(0);
+        } else {
 #pragma unroll
-            for (int f = 0; f < 4; ++f) F(RL_F_TAIR + f) = tair[f];
-#pragma unroll
-            for (int j = 0; j < 12; ++j) { F(RL_F_Q + j) = q[j]; F(RL_F_QD + j) = qd[j]; F(RL_F_AP + j) = ap[j]; }
+            for (int f = 0; f < 4; ++f) tair[f] = 0.f;
+        }
+        eplen = p.randomize_eplen ? (int)mulhi_n(hi32(rng_word(key, SLOT_EPLEN)), (uint32_t)p.max_ep) : 0;
+        contact = 0;
+    }
+    // Store the state (each thread its share) and the record of the observation phase: the 48
+    // proprioceptive values (Sec. 3.2 order), then position / heading / height and the
+    // tile-centre cell.
+    float* R = rec[lr];
+    if (valid) {
+        if (joint) {
+            F(RL_F_Q + jl) = q; F(RL_F_QD + jl) = qd; F(RL_F_AP + jl) = ap;
+            R[12 + jl] = q - p.q_def[jl];
+            R[24 + jl] = qd;
+            R[36 + jl] = ap;
+        } else if (role == 1) {
+            F(RL_F_PX) = px; F(RL_F_PY) = py; F(RL_F_HC) = hc; F(RL_F_HS) = hs;
+            F(5) = vx; F(6) = vy; F(10) = wz; F(14) = cx; F(15) = cy; F(16) = cw;
             si[(size_t)RL_I_EPLEN * N + e] = eplen;
             si[(size_t)RL_I_LEVEL * N + e] = level;
             si[(size_t)RL_I_CONTACT * N + e] = contact;
             if (p.level_out) p.level_out[e] = level;
             if (p.tidx_out) p.tidx_out[e] = level * p.C + (e % p.C);
-            // Record for the observation phase: the 48 proprioceptive values (Sec. 3.2 order),
-            // then the position / heading / height and the tile-centre cell.
-            float* R = rec[local];
-            R[0] = vx; R[1] = vy; R[2] = vz; R[3] = wx; R[4] = wy; R[5] = wz;
-            R[6] = gx; R[7] = gy; R[8] = gz; R[9] = cx; R[10] = cy; R[11] = cw;
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                R[12 + j] = q[j] - p.q_def[j];
-                R[24 + j] = qd[j];
-                R[36 + j] = ap[j];
-            }
-            R[R_PX] = px; R[R_PY] = py; R[R_HC] = hc; R[R_HS] = hs; R[R_Z] = z;
+            R[0] = vx; R[1] = vy; R[5] = wz; R[9] = cx; R[10] = cy; R[11] = cw;
+            R[R_PX] = px; R[R_PY] = py; R[R_HC] = hc; R[R_HS] = hs;
             R[R_BX] = __int_as_float(level * p.cpt + p.cpt / 2);
             R[R_BY] = __int_as_float((e % p.C) * p.cpt + p.cpt / 2);
             R[R_KEYLO] = __uint_as_float(lo32(key));
             R[R_KEYHI] = __uint_as_float(hi32(key));
+        } else if (role == 2) {
+            F(7) = vz; F(8) = wx; F(9) = wy;
+            R[2] = vz; R[3] = wx; R[4] = wy;
+        } else if (role == 3) {
+            F(11) = gx; F(12) = gy; F(13) = gz; F(RL_F_Z) = z;
+            R[6] = gx; R[7] = gy; R[8] = gz;
+            R[R_Z] = z;
+        } else {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) F(RL_F_TAIR + f) = tair[f];
         }
     }
-    // per-block statistics: every lane of the phase-1 warps takes part (idle lanes add zeros)
-    if (MODE == 0 && p.stats && (ENVS == 256 || warp == 0)) {
+    // per-block statistics (the planar threads of warp 6 carry them; other lanes add zeros)
+    if (MODE == 0 && p.stats && warp == T_PLANE / 32) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             st_r += __shfl_xor_sync(0xffffffffu, st_r, o);
@@ -389,30 +447,20 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) env_step_kernel(EnvPar
 
 }  // namespace
 
-template <int MODE, int ENVS, int THREADS>
+template <int MODE>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
-    const size_t smem = ((size_t)ENVS * REC + 2 * GTAB) * sizeof(float);
-    cudaError_t e = launch_pdl(env_step_kernel<MODE, ENVS, THREADS>, dim3((p.N + ENVS - 1) / ENVS), dim3(THREADS), smem, s, p);
+    const size_t smem = ((size_t)16 * REC + 2 * GTAB) * sizeof(float);
+    cudaError_t e = launch_pdl(env_step_kernel<MODE>, dim3((p.N + 15) / 16), dim3(256), smem, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// Dynamic shared-memory limit of the 256-robot blocks (64 KiB of robot records + the 8 KiB grid
-// table), set once before any launch (and so before any stream capture).
-cudaError_t env_prepare() {
-    const int smem = (256 * REC + 2 * GTAB) * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(env_step_kernel<0, 256, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(env_step_kernel<1, 256, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return e;
-}
+// Shared memory is 12 KiB per block (16 robot records + the grid table): nothing to set.
+cudaError_t env_prepare() { return cudaSuccess; }
 
-// 256-robot blocks once there are enough robots to give every SM two of them.
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
-    const bool big = p.N >= 2 * 148 * 256;
-    if (mode == 0) return big ? launch_cfg<0, 256, 256>(p, s) : launch_cfg<0, 16, 256>(p, s);
-    return big ? launch_cfg<1, 256, 256>(p, s) : launch_cfg<1, 16, 256>(p, s);
+    return mode == 0 ? launch_cfg<0>(p, s) : launch_cfg<1>(p, s);
 }
 
 }  // namespace rl
