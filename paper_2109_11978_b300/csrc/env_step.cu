@@ -11,6 +11,7 @@
 // lane), so the row of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height
 // samples of a robot are gathered by 32 lanes in parallel from the L2-resident heightfield; the
 // rotated sample offsets of the grid come from a per-block table.
+#include "act_row.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -114,7 +115,8 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
 // number of warps or half-warps.
 constexpr int T_PLANE = 192;
 
-template <int MODE>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
+// FUSE: 0, or 16 * bf16 + H / 32 of a fused policy head (its per-row evaluation runs first).
+template <int MODE, int FUSE>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
 __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     pdl_wait();
     pdl_trigger();
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     __shared__ float xr[3][ENVS];
     __shared__ float xf[ENVS];
     __shared__ int xfi[ENVS], xd[ENVS], xl[ENVS];
+    __shared__ float act_s[ENVS][12], val_s[ENVS];            // fused head: actions and values
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tid = threadIdx.x;
     const int env0 = blockIdx.x * ENVS;
@@ -138,6 +141,19 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         const int ix = k % p.GX, iy = k / p.GX;
         gtab[k] = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
         gtab[GTAB + k] = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+    }
+    if constexpr (FUSE != 0) {
+        // Phase 0 (fused policy head): the head weights into shared memory, then one warp per
+        // robot evaluates mu, the sampled action, logp and V exactly as the action-head kernel
+        // does, writing the rollout's records and the block's actions / values for phase 1.
+        float* Wa = gtab + 2 * GTAB;
+        float* Wc = Wa + p.act.A * p.act.H;
+        for (int i = tid; i < p.act.A * p.act.H; i += THREADS) Wa[i] = p.act.Wa[i];
+        for (int i = tid; i < p.act.H; i += THREADS) Wc[i] = p.act.Wc[i];
+        __syncthreads();
+        for (int r = warp; r < ENVS; r += THREADS / 32)
+            if (env0 + r < N) act_row<(FUSE >> 4) != 0, (FUSE & 15)>(p.act, Wa, Wc, env0 + r, it, true, lane, act_s[r], &val_s[r]);
+        __syncthreads();
     }
     // Phase 1: the stand-in's joints and base chains are independent recurrences, each on its own
     // thread with the same fp32 operations as one robot per thread would use; the reward sums
@@ -179,7 +195,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     if (MODE == 0) {
         key = rng_key(p.seed, kStreamEnv, it, (uint64_t)p.t, (uint64_t)ec);
         const float qd_old = qd;
-        if (joint) a = __ldg(p.actions + (size_t)ec * 12 + jl);
+        if (joint) a = FUSE != 0 ? act_s[lr][jl] : __ldg(p.actions + (size_t)ec * 12 + jl);
         // Pushes (Sec. 3.3): every push_interval steps of the episode, +-push_vel in x, y.
         if (role == 1 && p.push_on && eplen > 0 && (eplen % p.push_interval) == 0) {
             vx = FADD(vx, FMUL(p.push_vel, uniform_pm1(hi32(rng_word(key, SLOT_PUSH)))));
@@ -273,7 +289,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             // time-out bootstrap r += gamma V(o_t) (Sec. 2.2.2).
             const bool timeout = (eplen_new >= p.max_ep) && !crash;
             const bool done = crash || timeout;
-            if (timeout) r += p.gamma * __ldg(p.values + ec);
+            if (timeout) r += p.gamma * (FUSE != 0 ? val_s[lr] : __ldg(p.values + ec));
             int level_new = level;
             if (done) {
                 // Curriculum (Sec. 3.1), decided in fp64 with one rounding per operation.
@@ -447,20 +463,37 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
 
 }  // namespace
 
-template <int MODE>
+template <int MODE, int FUSE>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
-    const size_t smem = ((size_t)16 * REC + 2 * GTAB) * sizeof(float);
-    cudaError_t e = launch_pdl(env_step_kernel<MODE>, dim3((p.N + 15) / 16), dim3(256), smem, s, p);
+    size_t smem = ((size_t)16 * REC + 2 * GTAB) * sizeof(float);
+    if (FUSE != 0) smem += (size_t)(p.act.A * p.act.H + p.act.H) * sizeof(float);
+    cudaError_t e = launch_pdl(env_step_kernel<MODE, FUSE>, dim3((p.N + 15) / 16), dim3(256), smem, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// Shared memory is 12 KiB per block (16 robot records + the grid table): nothing to set.
+// Shared memory: 12 KiB per block (16 robot records + the grid table), plus at most 13 KiB of
+// head weights when the policy head is fused: within the default limit, nothing to set.
 cudaError_t env_prepare() { return cudaSuccess; }
 
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
-    return mode == 0 ? launch_cfg<0>(p, s) : launch_cfg<1>(p, s);
+    if (mode != 0) return launch_cfg<1, 0>(p, s);
+    if (!p.act.ha) return launch_cfg<0, 0>(p, s);
+    // fused policy head: 12 actions (the stand-in's joints), last hidden width 64, 128 or 256
+    const HeadParams& h = p.act;
+    if (h.A != 12 || !(h.H == 64 || h.H == 128 || h.H == 256) || !h.hc || !h.Wa || !h.Wc || !h.ba || !h.bc || !h.log_std ||
+        !h.values || !h.actions || !h.mu || !h.logp)
+        return cudaErrorInvalidValue;
+    const int nk = h.H / 32;
+    if (h.bf16) {
+        if (nk == 2) return launch_cfg<0, 16 + 2>(p, s);
+        if (nk == 4) return launch_cfg<0, 16 + 4>(p, s);
+        return launch_cfg<0, 16 + 8>(p, s);
+    }
+    if (nk == 2) return launch_cfg<0, 2>(p, s);
+    if (nk == 4) return launch_cfg<0, 4>(p, s);
+    return launch_cfg<0, 8>(p, s);
 }
 
 }  // namespace rl

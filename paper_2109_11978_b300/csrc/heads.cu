@@ -11,6 +11,7 @@
 // applies Algorithm 1 to the device-side learning rate before Adam runs.
 #include <type_traits>
 
+#include "act_row.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,13 +21,6 @@ namespace {
 
 constexpr int HEAD_WARPS = 8;
 constexpr int MAX_A = 12;         // action dims (12 joint targets)
-constexpr float HALF_LOG_2PI = 0.91893853320467274f;
-
-template <bool BF16>
-__device__ __forceinline__ float ld_act(const void* base, size_t i) {
-    if (BF16) return bf2f(reinterpret_cast<const __nv_bfloat16*>(base)[i]);
-    return reinterpret_cast<const float*>(base)[i];
-}
 
 template <bool BF16, int NK>
 __global__ void __launch_bounds__(HEAD_WARPS * 32) act_head_kernel(HeadParams p) {
@@ -40,49 +34,9 @@ __global__ void __launch_bounds__(HEAD_WARPS * 32) act_head_kernel(HeadParams p)
     for (int i = threadIdx.x; i < p.H; i += blockDim.x) Wc[i] = p.Wc[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int nk = NK;
     const unsigned long long it = p.iteration ? *p.iteration : 0ull;
-    for (int m = blockIdx.x * HEAD_WARPS + warp; m < p.M; m += gridDim.x * HEAD_WARPS) {
-        float hc[NK];
-        float v = 0.f;
-#pragma unroll
-        for (int i = 0; i < NK; ++i)
-            if (i < nk) {
-                hc[i] = ld_act<BF16>(p.hc, (size_t)m * p.H + lane + 32 * i);
-                v += hc[i] * Wc[lane + 32 * i];
-            }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) p.values[m] = v + p.bc[0];
-        if (!actor) continue;
-        float ha[NK];
-#pragma unroll
-        for (int i = 0; i < NK; ++i)
-            if (i < nk) ha[i] = ld_act<BF16>(p.ha, (size_t)m * p.H + lane + 32 * i);
-        float mine = 0.f;   // mu of action dim == lane
-        for (int j = 0; j < p.A; ++j) {
-            float s = 0.f;
-#pragma unroll
-            for (int i = 0; i < NK; ++i)
-                if (i < nk) s += ha[i] * Wa[j * p.H + lane + 32 * i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == j) mine = s + p.ba[j];
-        }
-        float lp = 0.f;
-        if (lane < p.A) {
-            const float ls = p.log_std[lane];
-            const uint64_t key = rng_key(p.seed, kStreamAct, it, (uint64_t)p.t, (uint64_t)m);
-            const float eps = box_muller(rng_word(key, (uint32_t)lane));
-            const float a = mine + expf(ls) * eps;
-            lp = -0.5f * eps * eps - ls - HALF_LOG_2PI;
-            if (p.mu) p.mu[(size_t)m * p.A + lane] = mine;
-            if (p.actions) p.actions[(size_t)m * p.A + lane] = a;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
-        if (lane == 0 && p.logp) p.logp[m] = lp;
-    }
+    for (int m = blockIdx.x * HEAD_WARPS + warp; m < p.M; m += gridDim.x * HEAD_WARPS)
+        act_row<BF16, NK>(p, Wa, Wc, m, it, actor, lane, nullptr, nullptr);
 }
 
 // Loss head: four threads per minibatch row, LR rows per block.  The rows' last hidden

@@ -5,33 +5,6 @@
 
 namespace rl {
 
-// ------------------------------------------------------------------ env step
-struct EnvParams {
-    int N, O, Op, GX, GY, decimation, max_ep, L, C, cpt, nx, ny;
-    int push_interval, noise_on, push_on, randomize_eplen, t;
-    float kp, kd, ascale, dt, sim_dt, gamma, push_vel, grid_sp, inv_res, tile;
-    float cmd_range[3];
-    float q_def[12];
-    uint32_t crash_thr;
-    uint64_t seed;
-    const float* hf;
-    float* sf;
-    int* si;
-    const unsigned long long* iteration;
-    const float* actions;
-    const float* values;
-    void* obs;
-    int obs_bf16;
-    float* rew;
-    uint8_t* done;
-    uint8_t* timeout;
-    int* level_out;
-    int* tidx_out;
-    float* stats;   // optional: [0] += sum reward, [1] += resets, [2] += sum level
-};
-cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s);
-cudaError_t env_prepare();
-
 // ------------------------------------------------------------------ GAE
 cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, const float* val,
                        const float* last_val, const uint8_t* done, float* adv, float* ret,
@@ -120,6 +93,38 @@ __host__ __device__ inline HeadPart head_part(int A, int H) {
     return o;
 }
 __host__ __device__ inline int head_part_floats(int A, int H) { return head_part(A, H).PF; }
+// ------------------------------------------------------------------ env step
+struct EnvParams {
+    int N, O, Op, GX, GY, decimation, max_ep, L, C, cpt, nx, ny;
+    int push_interval, noise_on, push_on, randomize_eplen, t;
+    float kp, kd, ascale, dt, sim_dt, gamma, push_vel, grid_sp, inv_res, tile;
+    float cmd_range[3];
+    float q_def[12];
+    uint32_t crash_thr;
+    uint64_t seed;
+    const float* hf;
+    float* sf;
+    int* si;
+    const unsigned long long* iteration;
+    const float* actions;
+    const float* values;
+    void* obs;
+    int obs_bf16;
+    float* rew;
+    uint8_t* done;
+    uint8_t* timeout;
+    int* level_out;
+    int* tidx_out;
+    float* stats;   // optional: [0] += sum reward, [1] += resets, [2] += sum level
+    // fused policy head (act.ha non-null): the step first evaluates the action head on the
+    // rollout's last hidden rows (act.M = N), writes act.actions / mu / logp / values and steps
+    // with those actions and values instead of reading actions / values
+    HeadParams act;
+};
+cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s);
+cudaError_t env_prepare();
+
+
 cudaError_t launch_act_head(const HeadParams& p, cudaStream_t s);
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s);
 int loss_head_blocks(int M, int H, int bf16);   // blocks (= partial slots) of one loss-head launch

@@ -603,9 +603,15 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
     ep.stats = c->acc + ACC_ENV;
     for (int t = 0; t < c->T; ++t) {
         const size_t o = (size_t)t * c->N;
-        rl_status st = act_impl(c, q, t, c->N, obs + t * obs_step, c->actions + o * c->A, c->mu + o * c->A, c->logp + o,
-                                c->values + o);
+        // policy inference: the hidden layers here, the output heads fused into the env step
+        rl_status st = forward_hidden(c, q, obs + t * obs_step, c->N, 0, 2, true);
         if (st != RL_OK) return st;
+        ep.act = head_common(c, c->N);
+        ep.act.t = t;
+        ep.act.actions = c->actions + o * c->A;
+        ep.act.mu = c->mu + o * c->A;
+        ep.act.logp = c->logp + o;
+        ep.act.values = c->values + o;
         ep.t = t;
         ep.actions = c->actions + o * c->A;
         ep.values = c->values + o;

@@ -380,8 +380,9 @@ def test_set_gemm_tiles_rejects_invalid():
 
 def test_profile_classes_count_every_launch():
     """In-graph timing by kernel class: one event pair per launch, counted per class, with the
-    launch counts the iteration's structure fixes (T env steps, T + 1 action-head passes,
-    epochs x minibatches loss heads, gathers and Adam steps)."""
+    launch counts the iteration's structure fixes (T env steps, each with the rollout's policy head
+    fused in, one action-head pass for the bootstrap value, epochs x minibatches loss heads,
+    gathers and Adam steps)."""
     w = workload("tiny", precision=1)
     L, _, _, _ = _setup(w)
     api.rl_profile_enable(L.ctx, api.RL_PROF_ALL, True)
@@ -390,7 +391,7 @@ def test_profile_classes_count_every_launch():
     n_mb = w["epochs"] * w["minibatches"]
     counts = {name: api.rl_profile_read_class(L.ctx, i)[1] for i, name in enumerate(api.RL_PROF_NAMES)}
     assert counts["env_step"] == w["num_steps"]
-    assert counts["act_head"] == w["num_steps"] + 1
+    assert counts["act_head"] == 1
     assert counts["loss_head"] == n_mb and counts["adam"] == n_mb and counts["gather"] == n_mb
     nh = len(w["hidden"])
     assert counts["gemm"] == (w["num_steps"] + 1) * nh + n_mb * (3 * nh - 1)
