@@ -66,7 +66,11 @@ struct rl_ctx {
     int* perm = nullptr;
     int* iota = nullptr;
     float* logstd_old = nullptr;
-    void* X0 = nullptr;
+    void* X0 = nullptr;                          // the current minibatch's observations (= X0buf[xcur])
+    void* X0buf[2] = {nullptr, nullptr};         // two buffers: the next minibatch is gathered into the other
+    int xcur = 0;
+    cudaStream_t side = nullptr;                 // the next minibatch's gather runs here, beside the current one
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
     void* H[2][4] = {};
     void* dY[2][4] = {};
     float* gw[2][4] = {};
@@ -89,6 +93,9 @@ struct rl_ctx {
     CUtensorMap tm_x0;                           // gathered minibatch observations
     CUtensorMap tm_dxA[2][4], tm_dxB[2][4];
     CUtensorMap tm_dwA[2][4], tm_dwB[2][4];
+    // layer 0's weight-gradient B operand (the gathered observations) for each of the two
+    // observation buffers, one- and two-block stage forms: [buffer][net]
+    CUtensorMap tm_dwB_x0[2][2], tm_dwB2_x0[2][2];
     // the same operands for two-K-block stages (single-CTA tiles of width <= 128)
     CUtensorMap tm_fwdB2[2][4], tm_actB2[2][4], tm_fwdA2[2][4];
     CUtensorMap tm_dxA2[2][4], tm_dxB2[2][4], tm_dwA2[2][4], tm_dwB2[2][4];
@@ -225,6 +232,9 @@ bool encode_layer_maps(rl_ctx* c, int l) {
             const void* xb2 = l == 0 ? c->X0 : c->H[n][l - 1];
             ok = ok && make_tmap_bf16_mn2(&c->tm_dwA2[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
             ok = ok && make_tmap_bf16_mn2(&c->tm_dwB2[n][l], xb2, c->Mb, Li.in, Li.in, (uint32_t)c->bn_dw[l]);
+            if (l == 0)
+                for (int x = 0; x < 2; ++x)
+                    ok = ok && make_tmap_bf16_mn2(&c->tm_dwB2_x0[x][n], c->X0buf[x], c->Mb, Li.in, Li.in, (uint32_t)c->bn_dw[l]);
         }
         ok = ok && make_tmap_bf16(&c->tm_fwdB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_fwd[l], c->cm_fwd[l]));
         ok = ok && make_tmap_bf16(&c->tm_actB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, b_rows(c->bn_act[l], c->cm_act[l]));
@@ -239,6 +249,8 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 64);
         const void* xb = l == 0 ? c->X0 : c->H[n][l - 1];
         ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, c->Mb, Li.in, Li.in, 64);
+        if (l == 0)
+            for (int x = 0; x < 2; ++x) ok = ok && make_tmap_bf16(&c->tm_dwB_x0[x][n], c->X0buf[x], c->Mb, Li.in, Li.in, 64);
     }
     return ok;
 }
@@ -346,7 +358,8 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
         const bool k2 = two_block(c->cm_dw[k]);
         for (int n = 0; n < 2; ++n) {
             tp.tmA[n] = k2 ? c->tm_dwA2[n][k] : c->tm_dwA[n][k];
-            tp.tmB[n] = k2 ? c->tm_dwB2[n][k] : c->tm_dwB[n][k];
+            if (k == 0) tp.tmB[n] = k2 ? c->tm_dwB2_x0[c->xcur][n] : c->tm_dwB_x0[c->xcur][n];
+            else tp.tmB[n] = k2 ? c->tm_dwB2[n][k] : c->tm_dwB[n][k];
             if (!make_tmap_out(&tp.tmC[n], c->gw[n][k], true, (uint64_t)c->S[k], (uint64_t)Li.out, (uint64_t)Li.in, (uint64_t)Li.in,
                                (uint64_t)Li.out * Li.in))
                 return RL_ERR_CUDA;
@@ -574,17 +587,42 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
     if (c->bf16)
         CK(q.run(RL_PROF_OTHER, 1,
                  [&] { return launch_pack_records(B, c->A, actions, mu_old, logp_old, adv, val_old, ret, c->recs, s); }));
-    for (int e = 0; e < epochs; ++e) {
-        for (int m = 0; m < minibatches; ++m) {
-            const int* idx = c->perm + (size_t)e * B + (size_t)m * Mb;
-            CK(q.run(RL_PROF_GATHER, 1, [&] { return launch_gather(obs, c->bf16 ? 1 : 0, idx, Mb, c->Op, c->X0, s); }));
-            rl_status st = minibatch_fwd_bwd(c, q, Mb, idx, actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
-                                             c->bf16 ? c->recs : nullptr);
-            if (st != RL_OK) return st;
-            c->adam.grad_out = nullptr;
-            CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
+    // The next minibatch's observations are gathered on a side stream into the other buffer
+    // while the current minibatch trains (the gather is memory-bound, the GEMMs are not); the
+    // forward of the next minibatch waits for it.  With per-class profiling every launch stays on
+    // the main stream.
+    const bool overlap = !q.profile;
+    const int nmb = epochs * minibatches;
+    auto mb_idx = [&](int k) { return c->perm + (size_t)(k / minibatches) * B + (size_t)(k % minibatches) * Mb; };
+    c->xcur = 0;
+    c->X0 = c->X0buf[0];
+    CK(q.run(RL_PROF_GATHER, 1, [&] { return launch_gather(obs, c->bf16 ? 1 : 0, mb_idx(0), Mb, c->Op, c->X0buf[0], s); }));
+    for (int k = 0; k < nmb; ++k) {
+        const int cur = k & 1, nxt = cur ^ 1;
+        c->xcur = cur;
+        c->X0 = c->X0buf[cur];
+        if (k > 0 && overlap) CK(cudaStreamWaitEvent(s, c->ev_join[cur], 0));   // this minibatch's gather
+        if (k + 1 < nmb) {
+            // the other buffer was last read by minibatch k - 1, already ordered before this point
+            if (overlap) {
+                CK(cudaEventRecord(c->ev_fork[nxt], s));
+                CK(cudaStreamWaitEvent(c->side, c->ev_fork[nxt], 0));
+                CK(launch_gather(obs, c->bf16 ? 1 : 0, mb_idx(k + 1), Mb, c->Op, c->X0buf[nxt], c->side));
+                ++c->launches;
+                CK(cudaEventRecord(c->ev_join[nxt], c->side));
+            }
         }
+        rl_status st = minibatch_fwd_bwd(c, q, Mb, mb_idx(k), actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
+                                         c->bf16 ? c->recs : nullptr);
+        if (st != RL_OK) return st;
+        c->adam.grad_out = nullptr;
+        CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
+        if (k + 1 < nmb && !overlap)
+            CK(q.run(RL_PROF_GATHER, 1,
+                     [&] { return launch_gather(obs, c->bf16 ? 1 : 0, mb_idx(k + 1), Mb, c->Op, c->X0buf[nxt], s); }));
     }
+    c->xcur = 0;
+    c->X0 = c->X0buf[0];
     CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_small(SMALL_ITER_INC, c->scal, c->iter, nullptr, nullptr, 0.f, s); }));
     if (stats_out)
         CK(q.run(RL_PROF_OTHER, 1,
@@ -958,6 +996,11 @@ void rl_destroy(rl_ctx* c) {
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->side) cudaStreamDestroy(c->side);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_fork[i]) cudaEventDestroy(c->ev_fork[i]);
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    }
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -978,6 +1021,11 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaEventCreateWithFlags(&c->ev_fork[i], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
+    }
     CK(tc_prepare());
     CK(env_prepare());
     heads_prepare();
@@ -1049,7 +1097,8 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         CK(cudaMemcpy(c->iota, io.data(), sizeof(int) * c->Mb, cudaMemcpyHostToDevice));
     }
     CK(dalloc(c, &c->logstd_old, sizeof(float) * c->A));
-    CK(dalloc(c, &c->X0, (size_t)c->rows * c->Op * esize(c)));
+    for (int x = 0; x < 2; ++x) CK(dalloc(c, &c->X0buf[x], (size_t)c->rows * c->Op * esize(c)));
+    c->X0 = c->X0buf[0];
     for (int n = 0; n < 2; ++n)
         for (int l = 0; l < c->NH; ++l) {
             CK(dalloc(c, &c->H[n][l], (size_t)c->rows * c->hid[l] * esize(c)));
