@@ -23,8 +23,10 @@ namespace {
 constexpr int MAX_A = 12;
 constexpr float HALF_LOG_2PI = 0.91893853320467274f;
 constexpr int ROWS = 64;                  // rows per block (4 warps x 16)
-constexpr int THREADS = 128;
-constexpr int NW = THREADS / 32;
+// warps per block: eight for H >= 128 (the products split by output columns too), four for
+// H = 64; the 64 rows of a block are four 16-row MMA fragments
+template <int H>
+constexpr int warps_of() { return H >= 128 ? 8 : 4; }
 constexpr int GP = 24;                    // bf16 pitch of the [row][16] G tiles and [H][16] WaT tiles
 constexpr int FP = 17;                    // fp32 pitch of the [row][16] mu / G tiles
 constexpr int RP = 17;                    // per-row records: surr, vloss, kl, clip, g_ls[12]
@@ -101,7 +103,8 @@ struct Smem {
 };
 
 template <int H>
-__global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
+__global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams p) {
+    constexpr int NW = warps_of<H>(), THREADS = 32 * NW;
     pdl_wait();
     pdl_trigger();
     using S = Smem<H>;
@@ -216,42 +219,53 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
     __syncthreads();
 
     static_assert(FP == RP, "mu rows and records share their rows");
-    // ---- heads forward: warp w owns rows 16 w .. 16 w + 15
+    // ---- heads forward: rows 16 (w % 4) .. + 15; with eight warps the first four take the actor
+    // head and the other four the critic head, with four each warp both
     {
-        const int r0 = 16 * warp;
+        const int r0 = 16 * (warp & 3);
+        const bool do_a = NW == 4 || warp < 4, do_c = NW == 4 || warp >= 4;
         float acc[2][4] = {}, accv[4] = {};
 #pragma unroll
         for (int ks = 0; ks < H / 16; ++ks) {
             const int k0 = 16 * ks;
-            uint32_t a[4], c[4];
-            ldsm_x4(ha + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), a[0], a[1], a[2], a[3]);
-            ldsm_x4(hc + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), c[0], c[1], c[2], c[3]);
-            // B = Wa^T: fragment rows are Wa rows j (n), columns k
-            const int bn = (lane & 7) + 8 * (lane >> 4), bk = k0 + 8 * ((lane >> 3) & 1);
-            uint32_t bh[4], bl[4];
-            ldsm_x4(sb + S::WA_HI + bn * HP + bk, bh[0], bh[1], bh[2], bh[3]);
-            ldsm_x4(sb + S::WA_LO + bn * HP + bk, bl[0], bl[1], bl[2], bl[3]);
-            mma16816(acc[0], a, bh[0], bh[1]);
-            mma16816(acc[0], a, bl[0], bl[1]);
-            mma16816(acc[1], a, bh[2], bh[3]);
-            mma16816(acc[1], a, bl[2], bl[3]);
-            uint32_t ch0, ch1, cl0, cl1;
-            const int cn = lane & 7, ck = k0 + 8 * ((lane >> 3) & 1);
-            ldsm_x2(sb + S::WC_HI + cn * HP + ck, ch0, ch1);
-            ldsm_x2(sb + S::WC_LO + cn * HP + ck, cl0, cl1);
-            mma16816(accv, c, ch0, ch1);
-            mma16816(accv, c, cl0, cl1);
+            if (do_a) {
+                uint32_t a[4];
+                ldsm_x4(ha + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), a[0], a[1], a[2], a[3]);
+                // B = Wa^T: fragment rows are Wa rows j (n), columns k
+                const int bn = (lane & 7) + 8 * (lane >> 4), bk = k0 + 8 * ((lane >> 3) & 1);
+                uint32_t bh[4], bl[4];
+                ldsm_x4(sb + S::WA_HI + bn * HP + bk, bh[0], bh[1], bh[2], bh[3]);
+                ldsm_x4(sb + S::WA_LO + bn * HP + bk, bl[0], bl[1], bl[2], bl[3]);
+                mma16816(acc[0], a, bh[0], bh[1]);
+                mma16816(acc[0], a, bl[0], bl[1]);
+                mma16816(acc[1], a, bh[2], bh[3]);
+                mma16816(acc[1], a, bl[2], bl[3]);
+            }
+            if (do_c) {
+                uint32_t c[4];
+                ldsm_x4(hc + (r0 + (lane & 15)) * HP + k0 + 8 * (lane >> 4), c[0], c[1], c[2], c[3]);
+                uint32_t ch0, ch1, cl0, cl1;
+                const int cn = lane & 7, ck = k0 + 8 * ((lane >> 3) & 1);
+                ldsm_x2(sb + S::WC_HI + cn * HP + ck, ch0, ch1);
+                ldsm_x2(sb + S::WC_LO + cn * HP + ck, cl0, cl1);
+                mma16816(accv, c, ch0, ch1);
+                mma16816(accv, c, cl0, cl1);
+            }
         }
         // fragments -> [row][16] fp32 (mu columns 0..15, V from column 0 of the critic tile)
+        if (do_a) {
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
+            for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int r = r0 + gq + 8 * h2;
-                mu_s[r * FP + 8 * nt + 2 * tq] = acc[nt][2 * h2];
-                mu_s[r * FP + 8 * nt + 2 * tq + 1] = acc[nt][2 * h2 + 1];
-            }
-        if (tq == 0) {
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int r = r0 + gq + 8 * h2;
+                    mu_s[r * FP + 8 * nt + 2 * tq] = acc[nt][2 * h2];
+                    mu_s[r * FP + 8 * nt + 2 * tq + 1] = acc[nt][2 * h2 + 1];
+                }
+        }
+        // column 12 of the actor tile is zero (Wa rows >= A are zero): the critic writes it after
+        __syncthreads();
+        if (do_c && tq == 0) {
             mu_s[(r0 + gq) * FP + 12] = accv[0];
             mu_s[(r0 + gq + 8) * FP + 12] = accv[2];
         }
@@ -370,14 +384,17 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
     }
     __syncthreads();
 
-    // ---- backward into the last hidden layer, in place: dY_a = (G Wa) * ELU'(H_a)
+    // ---- backward into the last hidden layer, in place: dY_a = (G Wa) * ELU'(H_a); warp w: rows
+    // 16 (w % 4) .. + 15, with eight warps one half of the columns each
     {
-        const int r0 = 16 * warp;
+        const int r0 = 16 * (warp & 3);
+        constexpr int NPW = NW == 8 ? H / 32 : H / 16;          // 16-column tiles per warp
+        const int np0 = NW == 8 ? (warp >> 2) * NPW : 0;
         uint32_t gh[4], gl[4];
         ldsm_x4(sb + S::G_HI + (r0 + (lane & 15)) * GP + 8 * (lane >> 4), gh[0], gh[1], gh[2], gh[3]);
         ldsm_x4(sb + S::G_LO + (r0 + (lane & 15)) * GP + 8 * (lane >> 4), gl[0], gl[1], gl[2], gl[3]);
 #pragma unroll 2
-        for (int np = 0; np < H / 16; ++np) {
+        for (int np = np0; np < np0 + NPW; ++np) {
             const int n0 = 16 * np;
             // B = Wa [j][col]: column-major fragments over j, i.e. rows of Wa^T [col][j]
             const int bn = n0 + (lane & 7) + 8 * (lane >> 4), bk = 8 * ((lane >> 3) & 1);
@@ -527,7 +544,7 @@ __global__ void __launch_bounds__(THREADS) loss_mma_kernel(HeadParams p) {
 
 template <int H>
 cudaError_t mma_dispatch(const HeadParams& p, cudaStream_t s) {
-    cudaError_t e = launch_pdl(loss_mma_kernel<H>, dim3(p.nblocks), dim3(THREADS), Smem<H>::BYTES, s, p);
+    cudaError_t e = launch_pdl(loss_mma_kernel<H>, dim3(p.nblocks), dim3(32 * warps_of<H>()), Smem<H>::BYTES, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
