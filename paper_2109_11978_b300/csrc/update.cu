@@ -42,14 +42,15 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
 }
 
 // ---------------------------------------------------------------- gather
-// One warp per four minibatch rows: the four sampled row indices are read first, then every
-// 16-byte vector of the four rollout observation rows is loaded before any is stored (up to
-// 16 loads in flight per lane); Op * element size is a multiple of 128 bytes.
+// One warp per four minibatch rows: the four sampled row indices are read first, then one
+// 16-byte vector per lane of each of the four rollout observation rows is loaded before any is
+// stored (few registers, so gather blocks fit beside a GEMM CTA on an SM and many warps keep
+// loads in flight); Op * element size is a multiple of 128 bytes.
 constexpr int GATHER_ROWS = 4;      // rows per warp
-constexpr int GATHER_VPL = 4;       // 16-byte vectors per lane and row held in registers at once
+constexpr int GATHER_VPL = 1;       // 16-byte vectors per lane and row held in registers at once
 
 template <bool BF16>
-__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
+__global__ void __launch_bounds__(256, 6) gather_kernel(const void* __restrict__ obs, const int* __restrict__ idx, int M,
                                                      int Op, void* __restrict__ X) {
     pdl_wait();
     pdl_trigger();
