@@ -79,6 +79,12 @@ def read_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum summed over the GEMM launches of one iteration of
+# the rough-terrain workload (ncu, one pass per launch); reset to None whenever the GEMM kernel
+# changes until it is captured again.
+GEMM_DRAM_BYTES_PER_ITERATION = 8000.2e6 + 281.9e6
+
+
 def gemm_flops_per_iteration(w, O):
     """Algorithmic FLOPs of the MLP GEMM launches of one iteration (logical, unpadded sizes)."""
     N, T, E, MB = w["num_envs"], w["num_steps"], w["epochs"], w["minibatches"]
@@ -437,7 +443,9 @@ def main():
     peak = peaks.get("bf16_tflops_sustained", 1400.0)
     roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (all MLP GEMM launches of the iteration)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": GEMM_DRAM_BYTES_PER_ITERATION,
+            "traffic_note": "DRAM bytes (read + write) of the iteration's 235 GEMM launches from one ncu capture of this "
+                            "workload and GEMM build (profiles/gemm_rough4096_dram.md), per iteration like achieved",
             "peak_source": f"bf16_tflops_sustained ({peak_src})", "gemm_launches_per_iteration": gemm_n,
             "gemm_share_of_step": gemm_ms / (total_ms / args.steps) if total_ms else None,
             "algorithmic_flops_per_iteration": flops_iter}
