@@ -258,8 +258,9 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 32 columns of this warp's 32 TMEM lanes into r, without waiting: the registers are valid only
+// after tmem_ld_wait (which names them, so that no use is scheduled before it)
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -268,9 +269,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// waits for every tcgen05.ld this thread issued; r is tied to the wait
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// ties r to a wait issued just before (volatile statements keep their order)
+__device__ __forceinline__ void tmem_ld_after_wait(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -665,6 +677,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         // the load/store unit carries them so that the TMA unit serves only the operand stream and
         // the output stores
         constexpr int CPT = C::SLICE_COLS / 32;                 // chunks per tile of one warp
+        constexpr int PRE = EPI == EPI_ELU_GRAD ? 1 : CPT;      // chunks loaded from TMEM together
         int hj = 0;                                              // chunks processed so far
         auto h_issue = [&](int j) {
             // chunk j of this warp's sequence: tile cid + (j / CPT) ncl, column chunk j % CPT
@@ -708,10 +721,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 break;
             }
             tc_fence_after();
-#pragma unroll 1
-            for (int c = slice * C::SLICE_COLS; busy && c < (slice + 1) * C::SLICE_COLS; c += 32) {
+            // this warp's columns of the tile leave TMEM at once (the ELU-gradient form, short of
+            // registers, loads its chunks one by one) and the accumulator is released before the
+            // math and the stores, so the MMAs of a later tile can start in it
+            auto tmem_col = [&](int ch) {
+                return tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(slice * C::SLICE_COLS + 32 * ch);
+            };
+            auto release = [&]() {
+                // pair: on the even CTA's barrier
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * a, 0));
+                    else mbar_arrive(tempty0 + 8 * a);
+                }
+            };
+            uint32_t r[CPT][32];
+            if (busy) {
+#pragma unroll
+                for (int ch = 0; ch < PRE; ++ch) tmem_ld32_issue(tmem_col(ch), r[ch]);
+                tmem_ld_wait(r[0]);
+#pragma unroll
+                for (int ch = 1; ch < PRE; ++ch) tmem_ld_after_wait(r[ch]);
+            }
+            if (PRE == CPT || !busy) release();
+#pragma unroll
+            for (int ch = 0; ch < CPT; ++ch) {
+                if (!busy) break;
+                if (ch >= PRE) {
+                    tmem_ld32_issue(tmem_col(ch), r[ch]);
+                    tmem_ld_wait(r[ch]);
+                    if (ch == CPT - 1) release();
+                }
+                const int c = slice * C::SLICE_COLS + 32 * ch;
                 float v[32];
-                tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[ch][j]);
                 if (EPI == EPI_STORE && nkb == 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -811,13 +856,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         if (tile_ok) p.colsum[b][((size_t)mi * 4 + q) * p.N + col + lane] = s;
                     }
                 }
-            }
-            // the TMEM buffer is free for the next tile's MMAs (pair: on the even CTA's barrier)
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * a, 0));
-                else mbar_arrive(tempty0 + 8 * a);
             }
         }
         // activation copies still in flight land and the output stores complete before the CTA

@@ -71,6 +71,8 @@ struct rl_ctx {
     int xcur = 0;
     cudaStream_t side = nullptr;                 // the next minibatch's gather runs here, beside the current one
     cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+    cudaStream_t wside = nullptr;                // weight gradients, beside the next input gradient
+    cudaEvent_t ev_dw[4] = {}, ev_dw_join = nullptr;
     void* H[2][4] = {};
     void* dY[2][4] = {};
     float* gw[2][4] = {};
@@ -443,7 +445,7 @@ EnvParams env_params(rl_ctx* c) {
 // X0 must already hold the minibatch observations.
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
-                            const float* ret, bool step, const float* rec = nullptr) {
+                            const float* ret, bool step, const float* rec = nullptr, bool overlap_dw = false) {
     rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, false);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
@@ -472,15 +474,37 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.lr_min = c->cfg.lr_min;
     h.lr_max = c->cfg.lr_max;
     CK(q.run(RL_PROF_LOSS, 1, [&] { return launch_loss_head(h, q.s); }));
-    // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums
-    for (int k = c->NH - 1; k >= 1; --k) {
-        rl_status st = dx_layer(c, q, k, M);
+    // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums;
+    // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows.  dW_l needs only dY_l,
+    // so with overlap_dw it runs on a second stream as soon as dY_l exists, beside the next input
+    // gradient (the two persistent grids fill each other's ramp and tail), and the main stream
+    // joins it before returning.  The results are the same either way.
+    Enq qw{c, c->wside, q.profile};
+    auto fork_dw = [&](int k) -> rl_status {
+        CK(cudaEventRecord(c->ev_dw[k], q.s));
+        CK(cudaStreamWaitEvent(c->wside, c->ev_dw[k], 0));
+        return dw_layer(c, qw, k, M);
+    };
+    if (overlap_dw) {
+        st = fork_dw(c->NH - 1);
         if (st != RL_OK) return st;
     }
-    // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows
-    for (int k = 0; k < c->NH; ++k) {
-        rl_status st = dw_layer(c, q, k, M);
+    for (int k = c->NH - 1; k >= 1; --k) {
+        st = dx_layer(c, q, k, M);
         if (st != RL_OK) return st;
+        if (overlap_dw) {
+            st = fork_dw(k - 1);
+            if (st != RL_OK) return st;
+        }
+    }
+    if (overlap_dw) {
+        CK(cudaEventRecord(c->ev_dw_join, c->wside));
+        CK(cudaStreamWaitEvent(q.s, c->ev_dw_join, 0));
+    } else {
+        for (int k = 0; k < c->NH; ++k) {
+            st = dw_layer(c, q, k, M);
+            if (st != RL_OK) return st;
+        }
     }
     return RL_OK;
 }
@@ -613,7 +637,7 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
             }
         }
         rl_status st = minibatch_fwd_bwd(c, q, Mb, mb_idx(k), actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
-                                         c->bf16 ? c->recs : nullptr);
+                                         c->bf16 ? c->recs : nullptr, overlap);
         if (st != RL_OK) return st;
         c->adam.grad_out = nullptr;
         CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
@@ -997,6 +1021,10 @@ void rl_destroy(rl_ctx* c) {
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->wside) cudaStreamDestroy(c->wside);
+    for (cudaEvent_t e : c->ev_dw)
+        if (e) cudaEventDestroy(e);
+    if (c->ev_dw_join) cudaEventDestroy(c->ev_dw_join);
     for (int i = 0; i < 2; ++i) {
         if (c->ev_fork[i]) cudaEventDestroy(c->ev_fork[i]);
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
@@ -1022,6 +1050,9 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->wside, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->ev_dw) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_dw_join, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
         CK(cudaEventCreateWithFlags(&c->ev_fork[i], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
