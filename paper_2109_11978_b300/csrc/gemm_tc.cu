@@ -346,13 +346,14 @@ struct TileCfg {
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
-    // per epilogue warp, output blocks of 32 x 32 leave by TMA store from shared memory: bf16 forms
-    // two 2 KB blocks (64-byte swizzle; the ELU-gradient form first loads its activation block
-    // into the same buffer), the fp32 split-K form one 4 KB block (128-byte swizzle)
-    static constexpr int STG_WARP = 4096;
+    // per epilogue warp, output blocks of 32 x 32 leave by TMA store from shared memory: the
+    // forward form one 2 KB bf16 block (64-byte swizzle), the ELU-gradient form two (it first
+    // loads its activation block into the same buffer, one chunk ahead), the fp32 split-K form
+    // one 4 KB block (128-byte swizzle)
+    static constexpr int STG_WARP = EPI == EPI_BIAS_ELU ? 2048 : 4096;
     static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
-    // the bias vectors of both batch entries (at most 1024 columns), loaded once per CTA
-    static constexpr int BIAS_BYTES = EPI == EPI_BIAS_ELU ? 2 * 1024 * 4 : 0;
+    // the bias is read through L1 (broadcast loads), so that the ring keeps the room
+    static constexpr int BIAS_BYTES = 0;
     static constexpr int BAR_BYTES = 512;
     static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
     static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3 * STAGE + FIXED <= 227 * 1024 ? 3 : 2;
@@ -360,6 +361,44 @@ struct TileCfg {
     // tiles ahead of the epilogue
     static constexpr int NACC = 512 / BN < 4 ? 512 / BN : 4;
     static constexpr int SMEM = STAGES * STAGE + FIXED;
+};
+
+// The tile sequence of one persistent CTA, t = t0, t0 + step, ..., with each index decoded as
+// t = tm + mct (ni + nt (sp + splits b)) (cluster row tile, column tile, split, batch entry).  The
+// first index is divided out once; every step then adds the step's own decode with carries, so a
+// tile costs the producer and the MMA issuer (single threads, on the pipeline's critical path) a
+// few integer adds instead of a chain of divisions by runtime values.
+struct TileStep {
+    int step, mct, nt, splits, dm, dr;    // dm, dr: step % mct, step / mct
+};
+struct TileSeq {
+    int t, tm, ni, sp, b;
+    __device__ TileSeq(int t0, const TileStep& st) {
+        t = t0;
+        tm = t0 % st.mct;
+        int r = t0 / st.mct;
+        ni = r % st.nt;
+        r /= st.nt;
+        sp = r % st.splits;
+        b = r / st.splits;
+    }
+    __device__ void next(const TileStep& st) {
+        t += st.step;
+        tm += st.dm;
+        int c = st.dr;
+        if (tm >= st.mct) {
+            tm -= st.mct;
+            ++c;
+        }
+        ni += c;
+        while (ni >= st.nt) {
+            ni -= st.nt;
+            if (++sp == st.splits) {
+                sp = 0;
+                ++b;
+            }
+        }
+    }
 };
 
 // Persistent, warp-specialised GEMM.  Output tiles are grouped into cluster tiles of CM
@@ -422,6 +461,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int rank = CM > 1 ? (int)cluster_rank() : 0;
     const int cid = CM > 1 ? (int)cluster_id_x() : (int)blockIdx.x;
     const int ncl = CM > 1 ? (int)nclusters_x() : (int)gridDim.x;
+    const TileStep tstep{ncl, mct, nt, p.splits, ncl % mct, ncl / mct};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -458,22 +498,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     // set-up done: wait for the preceding kernel's results, let the next kernel's CTAs be placed
     pdl_wait();
     pdl_trigger();
-    if (EPI == EPI_BIAS_ELU) {
-        for (int i = threadIdx.x; i < p.batch * p.N; i += TC_THREADS) {
-            const int b = i / p.N;
-            bias_s[b * 1024 + (i - b * p.N)] = __ldg(p.bias[b] + (i - b * p.N));
-        }
-        __syncthreads();
-    }
 
-    auto decode = [&](int t, int& mi, int& ni, int& sp, int& b) {
-        mi = (t % mct) * CM + rank;
-        int r = t / mct;
-        ni = r % nt;
-        r /= nt;
-        sp = r % p.splits;
-        b = r / p.splits;
-    };
     auto kblocks_of = [&](int sp, int& kb0) {
         kb0 = sp * p.kb_per_split;
         const int kb1 = min(p.kblocks, kb0 + p.kb_per_split);
@@ -485,9 +510,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             // ---------------- TMA producer
             int it = 0;
             bool ok = true;
-            for (int t = cid; t < total && ok; t += ncl) {
-                int mi, ni, sp, b, kb0;
-                decode(t, mi, ni, sp, b);
+            for (TileSeq ts(cid, tstep); ts.t < total && ok; ts.next(tstep)) {
+                const int mi = ts.tm * CM + rank, ni = ts.ni, sp = ts.sp, b = ts.b;
+                int kb0;
                 const int nkb = kblocks_of(sp, kb0);
                 const CUtensorMap* ma = &p.tmA[b];
                 const CUtensorMap* mb = &p.tmB[b];
@@ -590,10 +615,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             constexpr uint32_t LBO = KS == 2 ? 16384u : 8192u;   // MN-major: bytes between 64-wide chunks
             const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0, LBO) : sw128_desc(sa0);
             const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + KS * C::A_BYTES, LBO) : sw128_desc(sa0 + KS * C::A_BYTES);
-            for (int t = cid; issuer && t < total && ok; t += ncl, ++local) {
-                int mi, ni, sp, b, kb0;
-                decode(t, mi, ni, sp, b);
-                const int nkb = kblocks_of(sp, kb0);
+            for (TileSeq ts(cid, tstep); issuer && ts.t < total && ok; ts.next(tstep), ++local) {
+                int kb0;
+                const int nkb = kblocks_of(ts.sp, kb0);
                 const int a = local % NACC;
                 const uint32_t aph = (uint32_t)(local / NACC) & 1u;
                 if (!mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status, abort_flag)) {
@@ -679,6 +703,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         constexpr int CPT = C::SLICE_COLS / 32;                 // chunks per tile of one warp
         constexpr int PRE = EPI == EPI_ELU_GRAD ? 1 : CPT;      // chunks loaded from TMEM together
         int hj = 0;                                              // chunks processed so far
+        // the epilogue warps decode each tile by division: the latency is theirs alone and other
+        // warps cover it, and the incremental form's extra live registers would spill here
+        auto decode = [&](int t, int& mi, int& ni, int& sp, int& b) {
+            mi = (t % mct) * CM + rank;
+            int r = t / mct;
+            ni = r % nt;
+            r /= nt;
+            sp = r % p.splits;
+            b = r / p.splits;
+        };
         auto h_issue = [&](int j) {
             // chunk j of this warp's sequence: tile cid + (j / CPT) ncl, column chunk j % CPT
             const int t = cid + (j / CPT) * ncl;
@@ -778,10 +812,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         bulk_commit();
                     }
                 } else if (EPI == EPI_BIAS_ELU) {
-                    const float4* bias4 = reinterpret_cast<const float4*>(bias_s + b * 1024 + col);
+                    const float4* bias4 = reinterpret_cast<const float4*>(p.bias[b] + col);
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 bb = bias4[j4];
+                        const float4 bb = __ldg(bias4 + j4);
                         v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
                         v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
                         v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
@@ -793,8 +827,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     // bf16 block in one of two buffers (64-byte swizzle: 16-byte unit u of row r at
                     // unit u ^ ((r >> 1) & 3)), out by TMA store; the store issued from this buffer
                     // two blocks ago must have read it
-                    uint8_t* ob = stg_raw + 2048 * (oj & 1);
-                    if (lane == 0) bulk_wait_read<1>();
+                    uint8_t* ob = stg_raw;
+                    if (lane == 0) bulk_wait_read<0>();
                     __syncwarp();
                     const int sw = (lane >> 1) & 3;
 #pragma unroll

@@ -133,12 +133,6 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
     const bool in = i < sg.size;
     const bool owner = in && (!wide || lane == 0);          // the thread that applies the step
     const long long gi = sg.offset + i;
-    T m = O::zero(), v = O::zero(), w = O::zero();
-    if (owner && !p.grad_out) {
-        m = O::ld_rw(p.m + gi);
-        v = O::ld_rw(p.v + gi);
-        w = O::ld_rw(p.p + gi);
-    }
     // partial sums: eight independent accumulators, combined in a fixed order
     T g0 = O::zero(), g1 = g0, g2 = g0, g3 = g0, g4 = g0, g5 = g0, g6 = g0, g7 = g0;
     if (in) {
@@ -171,6 +165,9 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
         O::st(p.grad_out + gi, g);
         return;
     }
+    // the moments and weights are read after the partial sums, so that the sums' eight
+    // accumulators and the moments are not live together
+    T m = O::ld_rw(p.m + gi), v = O::ld_rw(p.v + gi), w = O::ld_rw(p.p + gi);
 #pragma unroll
     for (int c = 0; c < V; ++c) {
         const float gc = O::get(g, c);
@@ -198,7 +195,7 @@ __device__ __forceinline__ void adam_segment(const AdamParams& p, const AdamSeg&
     }
 }
 
-__global__ void __launch_bounds__(ADAM_THREADS) adam_kernel(AdamParams p) {
+__global__ void __launch_bounds__(ADAM_THREADS, 4) adam_kernel(AdamParams p) {
     pdl_wait();
     pdl_trigger();
     int s = 0;
