@@ -356,7 +356,10 @@ struct TileCfg {
     static constexpr int BIAS_BYTES = 0;
     static constexpr int BAR_BYTES = 512;
     static constexpr int FIXED = STG_BYTES + BIAS_BYTES + BAR_BYTES + 1024 /*align*/;
-    static constexpr int STAGES = 4 * STAGE + FIXED <= 227 * 1024 ? 4 : 3 * STAGE + FIXED <= 227 * 1024 ? 3 : 2;
+    // as many ring stages as fit (at most 8): the ring is bound by the copy-to-release turnaround of
+    // a stage, so the bytes in flight set its rate
+    static constexpr int FIT = (227 * 1024 - FIXED) / STAGE;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT < 2 ? 2 : FIT;
     // TMEM accumulator buffers (BN columns each, 512 columns in all): the MMA warp can run that many
     // tiles ahead of the epilogue
     static constexpr int NACC = 512 / BN < 4 ? 512 / BN : 4;
