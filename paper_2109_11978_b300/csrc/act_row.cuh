@@ -1,6 +1,6 @@
 // Output heads of one rollout row (Sec. 2.2), shared by the action-head kernel and the env step
 // that fuses it: a warp per row, the lanes split the last hidden layer (coalesced row loads) and
-// finish the 12 actor outputs and the value with xor-shuffle reductions; the Gaussian policy
+// finish the actor outputs with one reduce-scatter and the value with an xor-shuffle reduction; the Gaussian policy
 // samples a = mu + exp(log_std) eps with eps from the counter-based generator keyed by
 // (seed, iteration, t, row), and logp is the sum of the per-dimension log densities.
 #pragma once
@@ -40,15 +40,34 @@ __device__ __forceinline__ void act_row(const HeadParams& p, const float* Wa, co
     float ha[NK];
 #pragma unroll
     for (int i = 0; i < NK; ++i) ha[i] = ld_act<BF16>(p.ha, (size_t)m * p.H + lane + 32 * i);
-    float mine = 0.f;   // mu of action dim == lane
-    for (int j = 0; j < p.A; ++j) {
-        float s = 0.f;
+    // the A (<= 16) per-lane partial dot products, summed over the warp by a reduce-scatter:
+    // each xor step (16, 8, 4, 2) hands half of the lane's values to its partner and keeps the
+    // other half, so that after four steps lane l holds the 16-lane sum of output (l >> 1) and the
+    // xor-1 step completes it (16 shuffles for all outputs instead of 5 per output)
+    float s[16];
 #pragma unroll
-        for (int i = 0; i < NK; ++i) s += ha[i] * Wa[j * p.H + lane + 32 * i];
+    for (int j = 0; j < 16; ++j) {
+        s[j] = 0.f;
+        if (j < p.A) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == j) mine = s + p.ba[j];
+            for (int i = 0; i < NK; ++i) s[j] += ha[i] * Wa[j * p.H + lane + 32 * i];
+        }
     }
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const int o = 16 >> st, n = 8 >> st;          // partner offset, values kept after the step
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            const float send = up ? s[k] : s[k + n];
+            const float keep = up ? s[k + n] : s[k];
+            s[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    s[0] += __shfl_xor_sync(0xffffffffu, s[0], 1);
+    // output j sits on lanes 2j and 2j + 1
+    const float tot = __shfl_sync(0xffffffffu, s[0], (2 * lane) & 31);
+    const float mine = lane < p.A ? tot + p.ba[lane] : 0.f;   // mu of action dim == lane
     float lp = 0.f;
     if (lane < p.A) {
         const float ls = p.log_std[lane];

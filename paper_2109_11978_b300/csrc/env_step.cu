@@ -424,6 +424,9 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         const uint64_t key = ((uint64_t)__float_as_uint(R[R_KEYHI]) << 32) | __float_as_uint(R[R_KEYLO]);
         const float px = R[R_PX], py = R[R_PY], hc = R[R_HC], hs = R[R_HS], z = R[R_Z];
         const int ibx = __float_as_int(R[R_BX]), iby = __float_as_int(R[R_BY]);
+        // unrolled over the row's column pairs, so that the height samples' loads of all of them
+        // are in flight together
+#pragma unroll 4
         for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
             float v[2];
             uint64_t w = (p.noise_on && c0 < p.O) ? rng_word(key, SLOT_OBS + (c0 >> 1)) : 0ull;
