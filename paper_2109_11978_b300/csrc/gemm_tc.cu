@@ -346,11 +346,11 @@ struct TileCfg {
     // column slices per TMEM lane quarter (4 warps each; fewer slices leave warps idle)
     static constexpr int SLICES = BN / 32 < 4 ? BN / 32 : 4;
     static constexpr int SLICE_COLS = BN / SLICES;
-    // per epilogue warp, output blocks of 32 x 32 leave by TMA store from shared memory: the
-    // forward form one 2 KB bf16 block (64-byte swizzle), the ELU-gradient form two (it first
-    // loads its activation block into the same buffer, one chunk ahead), the fp32 split-K form
-    // one 4 KB block (128-byte swizzle)
-    static constexpr int STG_WARP = EPI == EPI_BIAS_ELU ? 2048 : 4096;
+    // per epilogue warp, output blocks leave by TMA store from shared memory: the forward form
+    // one 2 KB bf16 block of 32 x 32 (64-byte swizzle), the ELU-gradient form two (it first loads
+    // its activation block into the same buffer, one chunk ahead), the fp32 split-K form one 2 KB
+    // half block of 32 x 16 at a time (64-byte swizzle)
+    static constexpr int STG_WARP = EPI == EPI_ELU_GRAD ? 4096 : 2048;
     static constexpr int STG_BYTES = EPI_WARPS * STG_WARP;
     // the bias is read through L1 (broadcast loads), so that the ring keeps the room
     static constexpr int BIAS_BYTES = 0;
@@ -800,19 +800,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 const int col = n0 + c;
                 if (EPI == EPI_STORE) {
-                    // fp32 block, 128-byte swizzle (16-byte unit u of row r at unit u ^ (r & 7)),
-                    // out by TMA store once the previous store from the buffer has read it
-                    if (lane == 0) bulk_wait_read<0>();
-                    __syncwarp();
+                    // two fp32 half blocks of 32 rows x 16 columns through the 2 KB buffer (64-byte
+                    // swizzle: 16-byte unit u of row r at unit u ^ ((r >> 1) & 3)), each out by TMA
+                    // store once the previous store from the buffer has read it
+                    const int sw = (lane >> 1) & 3;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        *reinterpret_cast<float4*>(stg_raw + lane * 128 + 16 * (u ^ (lane & 7))) =
-                            make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0 && tile_ok) {
-                        tma_store_3d(&p.tmC[b], smem_u32(stg_raw), col, m0 + 32 * q, sp);
-                        bulk_commit();
+                    for (int hh = 0; hh < 2; ++hh) {
+                        if (lane == 0) bulk_wait_read<0>();
+                        __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            *reinterpret_cast<float4*>(stg_raw + lane * 64 + 16 * (u ^ sw)) =
+                                make_float4(v[16 * hh + 4 * u], v[16 * hh + 4 * u + 1], v[16 * hh + 4 * u + 2],
+                                            v[16 * hh + 4 * u + 3]);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0 && tile_ok) {
+                            tma_store_3d(&p.tmC[b], smem_u32(stg_raw), col + 16 * hh, m0 + 32 * q, sp);
+                            bulk_commit();
+                        }
                     }
                 } else if (EPI == EPI_BIAS_ELU) {
                     const float4* bias4 = reinterpret_cast<const float4*>(p.bias[b] + col);
@@ -1149,10 +1155,10 @@ bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uin
         return false;
     cuuint64_t dims[3] = {cols, rows, splits};
     cuuint64_t strides[2] = {ld * es, (splits > 1 ? split_ld : rows * ld) * es};
-    cuuint32_t box[3] = {32u, 32u, 1u};
+    cuuint32_t box[3] = {fp32 ? 16u : 32u, 32u, 1u};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, fp32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

@@ -43,8 +43,8 @@ bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64
 bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols);
 // K blocks per stage for a tile shape: 2 for single-CTA tiles of width <= 128, else 1
 int tc_stage_blocks(int bn, int cm, int pair);
-// output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), 32 x 32
-// x 1 boxes: fp32 with 128-byte swizzle, or bf16 with 64-byte swizzle
+// output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), boxes
+// of 32 rows x 64 bytes (fp32: 16 columns, bf16: 32) x 1, 64-byte swizzle
 bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,
                    uint64_t split_ld);
 int tc_smem_bytes(int bn, int epi);

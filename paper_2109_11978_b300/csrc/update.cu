@@ -89,8 +89,9 @@ __global__ void __launch_bounds__(256, 6) gather_kernel(const void* __restrict__
 // scalars (Algorithm 1 has already updated alpha for this minibatch).  The gradient of each
 // parameter is the sum of its partials (split-K slices or per-block head partials), read
 // coalesced, four parameters per thread (float4) wherever the segment allows it, with eight
-// loads in flight and the parameter's own state (p, m, v) fetched before the partial sums; bf16
-// copies of the GEMM weights are refreshed in the same pass.
+// loads in flight, and the parameter's own state (p, m, v) fetched after the partial sums (so
+// that both are not live at once: four blocks fit per SM); bf16 copies of the GEMM weights are
+// refreshed in the same pass.
 template <int V>
 struct Vec;
 template <>
