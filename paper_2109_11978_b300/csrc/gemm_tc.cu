@@ -564,8 +564,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         continue;
                     }
                     mbar_expect_tx(full0 + 8 * s, (uint32_t)C::STAGE);
+                    // single CTA with 3D maps of the MN-major operands: one copy per operand
+                    const bool mn3 = CM == 1 && p.mn3;
                     if (!A_MN) {
                         tma_load_2d(sa, ma, full0 + 8 * s, (kb0 + i) * BK, ay);
+                    } else if (mn3) {
+                        tma_load_3d(sa, ma, full0 + 8 * s, 0, (kb0 + i) * BK, ay / 64);
                     } else {
                         // [K][M] source: two boxes of 64 M columns x 64 K rows
                         tma_load_2d(sa, ma, full0 + 8 * s, ay, (kb0 + i) * BK);
@@ -577,6 +581,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         else
                             tma_load_2d_mc(sa + C::A_BYTES + rank * B_SLICE_ROWS * BK * 2, mb, full0 + 8 * s,
                                            (kb0 + i) * BK, ni * BN + rank * B_SLICE_ROWS, MC_MASK);
+                    } else if (mn3) {
+                        tma_load_3d(sa + C::A_BYTES, mb, full0 + 8 * s, 0, (kb0 + i) * BK, ni * BN / 64);
                     } else {
                         // [K][N] source: boxes of 64 N columns x 64 K rows, this CTA's share
 #pragma unroll
@@ -1067,6 +1073,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
     if (p.pair && (p.cm != 2 || p.bn < 128)) return cudaErrorInvalidValue;
     if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
+    if (p.mn3 && (p.cm != 1 || p.pair || p.ks == 2 || p.mn == MAJ_K)) return cudaErrorInvalidValue;
     if (p.epi == EPI_ELU_GRAD) {
         // activation rows are read as 16-byte pieces
         for (int b = 0; b < p.batch; ++b)
@@ -1142,6 +1149,10 @@ bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64
 
 bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols) {
     return tile_cols % 64 == 0 && make_tmap_chunks(map, base, krows, cols, ld, 2 * BK, tile_cols / 64);
+}
+
+bool make_tmap_bf16_mn1(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols) {
+    return tile_cols % 64 == 0 && make_tmap_chunks(map, base, krows, cols, ld, BK, tile_cols / 64);
 }
 
 int tc_stage_blocks(int bn, int cm, int pair) { return (cm == 1 && !pair && bn <= 128) ? 2 : 1; }

@@ -33,6 +33,9 @@ struct TcParams {
     int* status;               // device status word
     int ks;                    // K blocks per stage: 0 / 1, or 2 (cm 1, no pair, bn <= 128) with the
                                // operand maps of make_tmap_bf16_k2 (K-major) / make_tmap_bf16_mn2
+    int mn3;                   // 1 (cm 1, no pair, ks 0 / 1): the MN-major operands are the 3D maps of
+                               // make_tmap_bf16_mn1 (one copy per operand and stage instead of one
+                               // per 64-wide box); 0: 64 x 64 box maps
 };
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
@@ -41,6 +44,9 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
 // MN-major operand [K rows][cols], box 128 K rows x tile_cols (tile_cols / 64 chunks of 64)
 bool make_tmap_bf16_k2(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 bool make_tmap_bf16_mn2(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols);
+// one-K-block stage map of an MN-major operand [K rows][cols] (cols a multiple of 64): box 64 K rows
+// x tile_cols (tile_cols / 64 chunks of 64, at most 4)
+bool make_tmap_bf16_mn1(CUtensorMap* map, const void* base, uint64_t krows, uint64_t cols, uint64_t ld, uint32_t tile_cols);
 // K blocks per stage for a tile shape: 2 for single-CTA tiles of width <= 128, else 1
 int tc_stage_blocks(int bn, int cm, int pair);
 // output map [splits][rows][cols] (row stride ld elements, split stride split_ld elements), boxes

@@ -244,15 +244,23 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         else c->tm_fwdA[n][l] = c->tm_x0;
         if (l > 0) {
             ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
-            // input gradient, B read MN-major: W_l [out][in] as it is stored, 64 x 64 boxes
-            ok = ok && make_tmap_bf16(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, 64);
+            // input gradient, B read MN-major: W_l [out][in] as it is stored; one 3D copy per stage
+            // in single-CTA mode, 64 x 64 boxes otherwise
+            ok = ok && (c->cm_dx[l] == 1 ? make_tmap_bf16_mn1(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in,
+                                                               (uint32_t)c->bn_dx[l])
+                                         : make_tmap_bf16(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, 64));
         }
-        // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in], 64 x 64 boxes
-        ok = ok && make_tmap_bf16(&c->tm_dwA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 64);
+        // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in]; one 3D copy per
+        // operand and stage in single-CTA mode, 64 x 64 boxes otherwise
+        const bool dw3 = c->cm_dw[l] == 1;
+        auto dw_map = [&](CUtensorMap* m, const void* base, int cols, int tile) {
+            return dw3 ? make_tmap_bf16_mn1(m, base, c->Mb, cols, cols, (uint32_t)tile) : make_tmap_bf16(m, base, c->Mb, cols, cols, 64);
+        };
+        ok = ok && dw_map(&c->tm_dwA[n][l], c->dY[n][l], Li.out, 128);
         const void* xb = l == 0 ? c->X0 : c->H[n][l - 1];
-        ok = ok && make_tmap_bf16(&c->tm_dwB[n][l], xb, c->Mb, Li.in, Li.in, 64);
+        ok = ok && dw_map(&c->tm_dwB[n][l], xb, Li.in, c->bn_dw[l]);
         if (l == 0)
-            for (int x = 0; x < 2; ++x) ok = ok && make_tmap_bf16(&c->tm_dwB_x0[x][n], c->X0buf[x], c->Mb, Li.in, Li.in, 64);
+            for (int x = 0; x < 2; ++x) ok = ok && dw_map(&c->tm_dwB_x0[x][n], c->X0buf[x], Li.in, c->bn_dw[l]);
     }
     return ok;
 }
@@ -334,6 +342,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
         }
         tp.M = M; tp.N = Li.in; tp.ldh = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
         tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD;
+        tp.mn3 = c->cm_dx[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -368,6 +377,7 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
         tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; set_cluster(tp, c->cm_dw[k]); tp.mn = MAJ_MN; tp.epi = EPI_STORE;
+        tp.mn3 = c->cm_dw[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
         tp.status = c->status;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
@@ -1549,8 +1559,14 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
     std::memset(&tp, 0, sizeof(tp));
     const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
     const int cm = (M > 128 && bn >= 128) ? 2 : 1;
-    if (!make_tmap_bf16(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)) return RL_ERR_CUDA;
-    if (!make_tmap_bf16(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)) return RL_ERR_CUDA;
+    // single CTA per tile with M a multiple of 64: one 3D copy per operand and stage
+    tp.mn3 = (cm == 1 && M % 64 == 0) ? 1 : 0;
+    if (!(tp.mn3 ? make_tmap_bf16_mn1(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 128)
+                 : make_tmap_bf16(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)))
+        return RL_ERR_CUDA;
+    if (!(tp.mn3 ? make_tmap_bf16_mn1(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, (uint32_t)bn)
+                 : make_tmap_bf16(&tp.tmB[0], Bt, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64)))
+        return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
     tp.bn = bn; tp.cm = cm; tp.mn = MAJ_MN; tp.epi = EPI_STORE;
@@ -1584,10 +1600,14 @@ rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, con
         if (!ok) return RL_ERR_CUDA;
         tp.mn = MAJ_K;
     } else {
+        // single CTA, one K block per stage, M a multiple of 64: 3D maps, one copy per operand
+        tp.mn3 = (!k2 && cluster == 1 && M % 64 == 0) ? 1 : 0;
         const bool ok = k2 ? make_tmap_bf16_mn2(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 128) &&
                                  make_tmap_bf16_mn2(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, (uint32_t)bn)
-                           : make_tmap_bf16(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64) &&
-                                 make_tmap_bf16(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64);
+                           : tp.mn3 ? make_tmap_bf16_mn1(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 128) &&
+                                          make_tmap_bf16_mn1(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, (uint32_t)bn)
+                                    : make_tmap_bf16(&tp.tmA[0], A, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64) &&
+                                          make_tmap_bf16(&tp.tmB[0], B, (uint64_t)K, (uint64_t)N, (uint64_t)N, 64);
         if (!ok) return RL_ERR_CUDA;
         tp.mn = MAJ_MN;
     }
