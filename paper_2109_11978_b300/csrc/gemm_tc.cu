@@ -13,10 +13,11 @@
 // every operand is used as it is stored and no transposed copy of any matrix is kept.
 //
 // Persistent CTA per SM, 576 threads, 128 x BN output tiles, K in steps of 64 (one 128-byte
-// swizzle row).  warp 0 lane 0 issues TMA loads into a 4-deep ring (full/empty mbarriers); warp 1
-// lane 0 issues 4 tcgen05.mma (K = 16 each) per stage, releases the stage with tcgen05.commit and
-// signals a finished tile on one of up to four TMEM accumulators; sixteen epilogue warps read the tile
-// back with tcgen05.ld while the next tile accumulates in the other buffer.  Every mbarrier wait
+// swizzle row).  warp 0 lane 0 issues TMA loads into a ring of as many stages as fit (full/empty
+// mbarriers); warp 1 lane 0 issues 4 tcgen05.mma (K = 16 each) per stage, releases the stage with
+// tcgen05.commit and signals a finished tile on one of up to four TMEM accumulators; sixteen
+// epilogue warps read the tile back with tcgen05.ld and release the accumulator at once, while the
+// next tile accumulates in another.  Every mbarrier wait
 // is bounded by the global timer; a wait that runs out records RL_ERR_TIMEOUT in the status
 // word, the CTA stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its
 // tensor memory and returns.
