@@ -145,6 +145,26 @@ rl_status rl_get_scalars(rl_ctx* ctx, double out[4]);
 /* Sets alpha, the iteration counter and the Adam step count (enqueued on stream). */
 rl_status rl_set_scalars(rl_ctx* ctx, double alpha, int64_t iteration, int64_t adam_step, void* stream);
 
+/* Checkpoint and resume of the whole learner (the paper has no counterpart; training of
+ * Sec. 2.2 / Algorithm 1 carries alpha and the Adam moments from iteration to iteration).  The
+ * image holds a header (magic "RLB300CK", version 1, the config, the segment sizes and the GEMM
+ * tile shapes of every site) followed by the parameters, Adam m and v, the device scalar block
+ * (alpha, Adam step, ...), the iteration counter, the env state (fp32 and int32 parts), the
+ * curriculum levels and the first observation of the next rollout.  Everything else is derived
+ * from these (bf16 weight copies) or drawn afresh from the seed and the iteration counter
+ * (shuffles, noise, actions), so a run resumed from an image continues bit for bit as the saved
+ * run would have.
+ * rl_checkpoint_bytes: size of the image in bytes (-1 for a NULL context).
+ * rl_checkpoint_save: writes the image to host memory dst (bytes >= rl_checkpoint_bytes); copies
+ *   on stream and synchronises it before returning.
+ * rl_checkpoint_load: restores an image into a context created with the same config and
+ *   heightfield: RL_ERR_INVALID_ARG for a wrong magic, version, config or size (the context is
+ *   then unchanged).  Re-applies the saved tile shapes, copies on stream, refreshes the bf16
+ *   weights and synchronises the stream before returning (src may be freed afterwards). */
+int64_t rl_checkpoint_bytes(rl_ctx* ctx);
+rl_status rl_checkpoint_save(rl_ctx* ctx, void* dst, size_t bytes, void* stream);
+rl_status rl_checkpoint_load(rl_ctx* ctx, const void* src, size_t bytes, void* stream);
+
 /* Env state access (layout above).  state_f: [RL_NF][num_envs] fp32, state_i: [RL_NI][num_envs]. */
 rl_status rl_env_get_state(rl_ctx* ctx, float* state_f, int32_t* state_i, void* stream);
 rl_status rl_env_set_state(rl_ctx* ctx, const float* state_f, const int32_t* state_i, void* stream);

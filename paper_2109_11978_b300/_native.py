@@ -66,6 +66,9 @@ SIGNATURES = {
     "rl_set_params": (_i32, [_vp, _vp, _vp]),
     "rl_get_scalars": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "rl_set_scalars": (_i32, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp]),
+    "rl_checkpoint_bytes": (ctypes.c_int64, [_vp]),
+    "rl_checkpoint_save": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "rl_checkpoint_load": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),
     "rl_env_get_state": (_i32, [_vp, _vp, _vp, _vp]),
     "rl_env_set_state": (_i32, [_vp, _vp, _vp, _vp]),
     "rl_env_reset_all": (_i32, [_vp, _vp, _vp]),

@@ -70,6 +70,24 @@ def rl_set_scalars(ctx, alpha, iteration, adam_step):
     check(lib().rl_set_scalars(ctx, float(alpha), int(iteration), int(adam_step), _stream()), "rl_set_scalars")
 
 
+def rl_checkpoint_bytes(ctx):
+    return int(lib().rl_checkpoint_bytes(ctx))
+
+
+def rl_checkpoint_save(ctx):
+    """The learner's checkpoint image as a host uint8 tensor."""
+    buf = torch.empty(rl_checkpoint_bytes(ctx), dtype=torch.uint8)
+    check(lib().rl_checkpoint_save(ctx, buf.data_ptr(), buf.numel(), _stream()), "rl_checkpoint_save")
+    return buf
+
+
+def rl_checkpoint_load(ctx, image):
+    buf = image.contiguous()
+    if buf.dtype != torch.uint8 or buf.is_cuda:
+        raise RLError("rl_checkpoint_load: the image is a host uint8 tensor")
+    check(lib().rl_checkpoint_load(ctx, buf.data_ptr(), buf.numel(), _stream()), "rl_checkpoint_load")
+
+
 def rl_env_get_state(ctx, sf, si):
     check(lib().rl_env_get_state(ctx, _ptr(sf), _ptr(si), _stream()), "rl_env_get_state")
 

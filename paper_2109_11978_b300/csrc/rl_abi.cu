@@ -1254,6 +1254,108 @@ rl_status rl_set_params(rl_ctx* c, const float* in, void* stream) {
     return refresh_bf16(c, S_(stream));
 }
 
+// ---- checkpoint image: header, then the state segments in a fixed order
+namespace {
+constexpr char CKPT_MAGIC[8] = {'R', 'L', 'B', '3', '0', '0', 'C', 'K'};
+constexpr uint32_t CKPT_VERSION = 1;
+constexpr int CKPT_SEGS = 9;
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, nseg;
+    uint64_t seg_bytes[CKPT_SEGS];
+    int32_t tiles[4][4][3];       // [hidden layer][site fwd / dx / dw / act][bn, cluster mode, splits]
+    rl_config cfg;
+};
+struct CkptSeg {
+    void* dev;
+    size_t bytes;
+};
+// params, Adam m, Adam v, scalar block, iteration counter, env fp32 state, env int state, curriculum
+// levels, the next rollout's first observation
+void ckpt_segments(rl_ctx* c, CkptSeg (&sg)[CKPT_SEGS]) {
+    sg[0] = {c->params, sizeof(float) * (size_t)c->P};
+    sg[1] = {c->am, sizeof(float) * (size_t)c->P};
+    sg[2] = {c->av, sizeof(float) * (size_t)c->P};
+    sg[3] = {c->scal, sizeof(float) * (size_t)SC_NSCAL};
+    sg[4] = {c->iter, sizeof(unsigned long long)};
+    sg[5] = {c->sf, sizeof(float) * (size_t)RL_NF * c->N};
+    sg[6] = {c->si, sizeof(int) * (size_t)RL_NI * c->N};
+    sg[7] = {c->level, sizeof(int) * (size_t)c->N};
+    sg[8] = {c->obs, (size_t)c->N * c->Op * esize(c)};
+}
+size_t ckpt_bytes(rl_ctx* c) {
+    CkptSeg sg[CKPT_SEGS];
+    ckpt_segments(c, sg);
+    size_t n = sizeof(CkptHeader);
+    for (const CkptSeg& x : sg) n += x.bytes;
+    return n;
+}
+}  // namespace
+
+int64_t rl_checkpoint_bytes(rl_ctx* c) { return c ? (int64_t)ckpt_bytes(c) : -1; }
+
+rl_status rl_checkpoint_save(rl_ctx* c, void* dst, size_t bytes, void* stream) {
+    if (!c || !dst || bytes < ckpt_bytes(c)) return RL_ERR_INVALID_ARG;
+    CkptSeg sg[CKPT_SEGS];
+    ckpt_segments(c, sg);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, CKPT_MAGIC, sizeof(h.magic));
+    h.version = CKPT_VERSION;
+    h.nseg = CKPT_SEGS;
+    for (int i = 0; i < CKPT_SEGS; ++i) h.seg_bytes[i] = sg[i].bytes;
+    for (int l = 0; l < c->NH && l < 4; ++l) {
+        const int bn[4] = {c->bn_fwd[l], c->bn_dx[l], c->bn_dw[l], c->bn_act[l]};
+        const int cm[4] = {c->cm_fwd[l], c->cm_dx[l], c->cm_dw[l], c->cm_act[l]};
+        for (int site = 0; site < 4; ++site) {
+            h.tiles[l][site][0] = bn[site];
+            h.tiles[l][site][1] = cm[site];
+            h.tiles[l][site][2] = site == 2 ? c->S[l] : 1;
+        }
+    }
+    h.cfg = c->cfg;
+    std::memcpy(dst, &h, sizeof(h));
+    uint8_t* out = reinterpret_cast<uint8_t*>(dst) + sizeof(h);
+    for (const CkptSeg& x : sg) {
+        CK(cudaMemcpyAsync(out, x.dev, x.bytes, cudaMemcpyDeviceToHost, S_(stream)));
+        out += x.bytes;
+    }
+    CK(cudaStreamSynchronize(S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_checkpoint_load(rl_ctx* c, const void* src, size_t bytes, void* stream) {
+    if (!c || !src || bytes < sizeof(CkptHeader)) return RL_ERR_INVALID_ARG;
+    CkptHeader h;
+    std::memcpy(&h, src, sizeof(h));
+    CkptSeg sg[CKPT_SEGS];
+    ckpt_segments(c, sg);
+    if (std::memcmp(h.magic, CKPT_MAGIC, sizeof(h.magic)) || h.version != CKPT_VERSION || h.nseg != CKPT_SEGS ||
+        bytes < ckpt_bytes(c) || std::memcmp(&h.cfg, &c->cfg, sizeof(rl_config)))
+        return RL_ERR_INVALID_ARG;
+    for (int i = 0; i < CKPT_SEGS; ++i)
+        if (h.seg_bytes[i] != sg[i].bytes) return RL_ERR_INVALID_ARG;
+    // the GEMM shapes of the saved run: split counts fix the order of the weight-gradient sums,
+    // so the resumed run repeats the saved one bit for bit
+    if (c->bf16)
+        for (int l = 0; l < c->NH && l < 4; ++l)
+            for (int site = 0; site < 4; ++site) {
+                if (site == 1 && l == 0) continue;
+                const int32_t* t = h.tiles[l][site];
+                const rl_status st = set_tiles_impl(c, site, l, t[0], t[1], t[2]);
+                if (st != RL_OK) return st;
+            }
+    const uint8_t* in = reinterpret_cast<const uint8_t*>(src) + sizeof(h);
+    for (const CkptSeg& x : sg) {
+        CK(cudaMemcpyAsync(x.dev, in, x.bytes, cudaMemcpyHostToDevice, S_(stream)));
+        in += x.bytes;
+    }
+    rl_status st = refresh_bf16(c, S_(stream));
+    if (st != RL_OK) return st;
+    CK(cudaStreamSynchronize(S_(stream)));
+    return RL_OK;
+}
+
 rl_status rl_get_scalars(rl_ctx* c, double out[4]) {
     if (!c || !out) return RL_ERR_INVALID_ARG;
     float sc[SC_NSCAL];

@@ -1,0 +1,100 @@
+"""Checkpoint and resume of the whole learner (rl_checkpoint_*): a run resumed from an image
+continues bit for bit, so after more iterations its parameters, env state, scalars, curriculum
+levels and per-iteration statistics equal those of the saved run that kept going; images of
+another config, with a damaged header or cut short are refused and leave the context as it was."""
+import pytest
+import torch
+
+from paper_2109_11978_b300 import api, synth
+from tests.helpers import lib_config, obs_dims, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _learner(w, tiles=None):
+    cfg = lib_config(w)
+    O, _ = obs_dims(w)
+    params = synth.xavier_params(w["seed"] + 1, O, w["hidden"], 12, log_std=-0.3, bias_scale=0.1)
+    hf = synth.heightfield(w["seed"] + 2) if w["grid"][0] else None
+    L = api.Learner(cfg, hf, params)
+    for t in tiles or ():
+        api.rl_set_gemm_tiles(L.ctx, *t)
+    return L
+
+
+def _snapshot(L):
+    torch.cuda.synchronize()
+    sf, si = L.get_state()
+    return {"params": L.params().cpu(), "sf": sf.cpu(), "si": si.cpu(), "levels": L.storage(11).clone().cpu(),
+            "obs0": L.storage(0)[0].float().cpu(), "scalars": api.rl_get_scalars(L.ctx)}
+
+
+def _run(L, n):
+    stats = []
+    for _ in range(n):
+        s = torch.zeros(api.RL_NSTATS, dtype=torch.float32).pin_memory()
+        api.rl_train_iteration(L.ctx, True, s)
+        torch.cuda.synchronize()
+        stats.append(s.clone())
+    return stats
+
+
+def _equal(a, b):
+    for k in a:
+        if k == "scalars":
+            assert a[k] == b[k], k
+        else:
+            assert torch.equal(a[k], b[k]), k
+
+
+# the second case pins split-K counts away from the defaults: the image carries them, and the
+# resumed context (created with the defaults) must take them over to repeat the sums' order
+@pytest.mark.parametrize("precision,tiles", [(0, None), (1, None), (1, [(2, 0, 64, 1, 5), (2, 1, 64, 1, 2)])])
+def test_resume_is_bit_exact(precision, tiles):
+    w = workload("small_rough", precision=precision, epochs=2, minibatches=2)
+    A = _learner(w, tiles)
+    _run(A, 2)
+    image = api.rl_checkpoint_save(A.ctx)
+    assert image.numel() == api.rl_checkpoint_bytes(A.ctx)
+    stats_a = _run(A, 3)
+    snap_a = _snapshot(A)
+    B = _learner(w)                      # fresh context, default tile shapes, initial weights
+    api.rl_checkpoint_load(B.ctx, image)
+    stats_b = _run(B, 3)
+    snap_b = _snapshot(B)
+    _equal(snap_a, snap_b)
+    # the statistics of the update are reduced in a fixed order and match exactly; the mean reward
+    # (index 7) sums per-block partials with float atomics, whose order varies from run to run
+    for x, y in zip(stats_a, stats_b):
+        keep = torch.ones_like(x, dtype=torch.bool)
+        keep[7] = False
+        assert torch.equal(x[keep], y[keep])
+        assert abs(float(x[7]) - float(y[7])) <= 1e-6 * max(1.0, abs(float(x[7])))
+    assert snap_a["scalars"]["iteration"] == 5
+    assert api.rl_last_device_status(A.ctx) == 0 and api.rl_last_device_status(B.ctx) == 0
+    A.close()
+    B.close()
+
+
+def test_refuses_foreign_or_damaged_images():
+    w = workload("small_rough", precision=1)
+    A = _learner(w)
+    _run(A, 1)
+    image = api.rl_checkpoint_save(A.ctx)
+    B = _learner(w)
+    before = _snapshot(B)
+    bad_magic = image.clone()
+    bad_magic[0] ^= 0xFF
+    bad_version = image.clone()
+    bad_version[8] ^= 0x01
+    for bad in (bad_magic, bad_version, image[: image.numel() - 1].clone(), image[:16].clone()):
+        with pytest.raises(api.RLError):
+            api.rl_checkpoint_load(B.ctx, bad)
+    other = _learner(workload("small_rough", precision=1, seed=7))     # another seed: another config
+    with pytest.raises(api.RLError):
+        api.rl_checkpoint_load(other.ctx, image)
+    with pytest.raises(api.RLError):
+        api.rl_checkpoint_load(B.ctx, image.cuda())
+    _equal(before, _snapshot(B))
+    for L in (A, B, other):
+        L.close()
