@@ -145,6 +145,17 @@ rl_status rl_get_scalars(rl_ctx* ctx, double out[4]);
 /* Sets alpha, the iteration counter and the Adam step count (enqueued on stream). */
 rl_status rl_set_scalars(rl_ctx* ctx, double alpha, int64_t iteration, int64_t adam_step, void* stream);
 
+/* Procedural terrain family of Sec. 3.1 (Fig. 2) as the heightfield rl_create takes: tile rows
+ * are curriculum levels (difficulty d = level / (num_levels - 1)), tile column k is terrain kind
+ * k % 7: flat, slope pyramid, slope pit, randomly rough, discrete obstacles, stairs pyramid,
+ * stairs pit.  Slopes rise at 25 deg x d, stair and obstacle steps are 0.05 + 0.15 d m, stairs
+ * 0.3 m wide, rough terrain varies by 0.1 m, obstacles stand on 1 m blocks; every tile keeps a
+ * flat 2 m x 2 m platform at its centre.  hf: device, fp32 [num_levels c][num_cols c] with
+ * c = tile_size / hf_res, written on stream.  Random heights come from the seed's counter-based
+ * generator, so equal configs give equal fields.  RL_ERR_INVALID_ARG unless the tile, 1 m and
+ * 0.3 m are whole numbers of cells (c even, a multiple of the 1 m block). */
+rl_status rl_terrain_generate(const rl_config* cfg, float* hf, void* stream);
+
 /* Checkpoint and resume of the whole learner (the paper has no counterpart; training of
  * Sec. 2.2 / Algorithm 1 carries alpha and the Adam moments from iteration to iteration).  The
  * image holds a header (magic "RLB300CK", version 1, the config, the segment sizes and the GEMM

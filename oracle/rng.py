@@ -37,6 +37,7 @@ STREAM_ENV = 1
 STREAM_ACT = 2
 STREAM_PERM = 3
 STREAM_INIT = 4
+STREAM_TERRAIN = 5
 
 # fp32 scale of the Irwin-Hall(4) normal: 1/sqrt((2^32-1)/3), stored as an exact fp32 value.
 IH_SCALE = np.float32(float.fromhex("0x1.bb67aep-16"))

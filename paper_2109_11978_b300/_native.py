@@ -66,6 +66,7 @@ SIGNATURES = {
     "rl_set_params": (_i32, [_vp, _vp, _vp]),
     "rl_get_scalars": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "rl_set_scalars": (_i32, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp]),
+    "rl_terrain_generate": (_i32, [ctypes.POINTER(rl_config), _vp, _vp]),
     "rl_checkpoint_bytes": (ctypes.c_int64, [_vp]),
     "rl_checkpoint_save": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),
     "rl_checkpoint_load": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),

@@ -70,6 +70,14 @@ def rl_set_scalars(ctx, alpha, iteration, adam_step):
     check(lib().rl_set_scalars(ctx, float(alpha), int(iteration), int(adam_step), _stream()), "rl_set_scalars")
 
 
+def rl_terrain_generate(cfg):
+    """The procedural terrain family for cfg as a CUDA fp32 tensor [num_levels c][num_cols c]."""
+    c = int(round(cfg.tile_size / cfg.hf_res))
+    out = torch.empty((cfg.num_levels * c, cfg.num_cols * c), dtype=torch.float32, device="cuda")
+    check(lib().rl_terrain_generate(ctypes.byref(cfg), _ptr(out), _stream()), "rl_terrain_generate")
+    return out
+
+
 def rl_checkpoint_bytes(ctx):
     return int(lib().rl_checkpoint_bytes(ctx))
 

@@ -18,7 +18,7 @@ namespace rl {
 // SplitMix64's slot-th output mix64(key + (slot + 1) * GAMMA).
 // ---------------------------------------------------------------------------------------
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-constexpr int kStreamEnv = 1, kStreamAct = 2, kStreamPerm = 3, kStreamInit = 4;
+constexpr int kStreamEnv = 1, kStreamAct = 2, kStreamPerm = 3, kStreamInit = 4, kStreamTerrain = 5;
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -169,6 +169,15 @@ __host__ __device__ inline long long adam_per_block(int nsplit, int vec) {
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
+// Procedural terrain family (terrain.cu): grid of levels (rows) x terrain kinds (columns) of c x c
+// cells; P, W, B: the spawn platform's half width, the stair width and the obstacle block in cells.
+struct TerrainParams {
+    int levels, cols, c, P, W, B;
+    float res;
+    uint64_t seed;
+};
+cudaError_t launch_terrain(const TerrainParams& p, float* hf, cudaStream_t s);
+
 cudaError_t launch_gather(const void* obs, int bf16, const int* idx, int M, int Op, void* X, cudaStream_t s);
 // Per-sample loss inputs packed once per iteration into one 128-byte record per sample:
 // [a_old A][mu_old A][logp_old][adv][v_old][ret][zeros], REC_LD floats per record (A <= 12).

@@ -1254,6 +1254,28 @@ rl_status rl_set_params(rl_ctx* c, const float* in, void* stream) {
     return refresh_bf16(c, S_(stream));
 }
 
+rl_status rl_terrain_generate(const rl_config* cfg, float* hf, void* stream) {
+    if (!cfg || !hf || cfg->num_levels < 1 || cfg->num_cols < 1 || !(cfg->hf_res > 0.f)) return RL_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(hf) & 3u) return RL_ERR_ALIGNMENT;
+    // lengths in whole cells: the tile, the platform half width (1 m), the stair width (0.3 m) and
+    // the obstacle block (1 m)
+    auto cells = [&](double len, int& n) {
+        const double r = (double)cfg->hf_res;
+        n = (int)std::llround(len / r);
+        return n > 0 && std::fabs(n * r - len) <= 1e-6 * std::max(1.0, len);
+    };
+    TerrainParams t;
+    if (!cells((double)cfg->tile_size, t.c) || !cells(1.0, t.P) || !cells(0.3, t.W) || !cells(1.0, t.B)) return RL_ERR_INVALID_ARG;
+    if (t.c % 2 || t.c % t.B || t.c / 2 < t.P) return RL_ERR_INVALID_ARG;
+    if ((long long)cfg->num_levels * t.c * cfg->num_cols * t.c > (1ll << 31)) return RL_ERR_INVALID_ARG;
+    t.levels = cfg->num_levels;
+    t.cols = cfg->num_cols;
+    t.res = cfg->hf_res;
+    t.seed = cfg->seed;
+    CK(launch_terrain(t, hf, S_(stream)));
+    return RL_OK;
+}
+
 // ---- checkpoint image: header, then the state segments in a fixed order
 namespace {
 constexpr char CKPT_MAGIC[8] = {'R', 'L', 'B', '3', '0', '0', 'C', 'K'};
