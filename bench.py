@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the grouped-learner and 16384-robot lines")
     ap.add_argument("--sweep", action="store_true", help="HBM size sweep of the env-step and GAE kernels (one JSON line per size)")
+    ap.add_argument("--robots-sweep", action="store_true",
+                    help="throughput against the number of parallel robots at three batch sizes (one JSON line per point)")
     ap.add_argument("--tiles-out", default=None, help="write the full autotune report (every trial) to this JSON file")
     ap.add_argument("--tiles", default=None,
                     help="apply the GEMM tile shapes of a saved autotune report instead of autotuning (for profiler runs, "
@@ -247,6 +249,33 @@ def large_config(torch, api, synth, steps=3, warmup=2):
             "env_steps_per_s": 16384 * 24 * len(times) / (sum(times) / 1000.0), "device_status": status}
 
 
+def robots_sweep(torch, api, synth, steps=3, warmup=2):
+    """Throughput against the number of parallel robots (Sec. 4.1, Fig. 3): batch sizes B = 49152,
+    98304 and 196608 samples per iteration with N = 128 ... 16384 robots (T = B / N steps), and the
+    20000 robots x 50 steps = 1 M configuration; the full iteration (rollout, GAE, 5 x 4 PPO update
+    with minibatch B / 4; 5 minibatches of 200000 for the 1 M point, whose quarter is not a whole
+    number of 64-row blocks) on the rough-terrain network, BF16, default tile shapes, one CUDA
+    graph per configuration."""
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    points = [(n, b // n, 4) for b in (49152, 98304, 196608) for n in (128, 256, 512, 1024, 2048, 4096, 8192, 16384)]
+    points.append((20000, 50, 5))
+    rows = []
+    for n, t, mbs in points:
+        w = dict(WORKLOAD)
+        w["num_envs"], w["num_steps"], w["minibatches"] = n, t, mbs
+        L, _ = make_learner(api, synth, api.RL_BF16, seed=50, w=w)
+        L.train_iteration(use_graph=True)
+        times = time_iterations(torch, L, steps, warmup, flush)
+        status = api.rl_last_device_status(L.ctx)
+        L.close()
+        ms = sum(times) / len(times)
+        row = {"num_envs": n, "num_steps": t, "batch": n * t, "minibatch": n * t // mbs, "ms_per_iteration": round(ms, 4),
+               "env_steps_per_s": n * t / (ms / 1000.0), "device_status": status}
+        print(json.dumps({"robots_sweep": row}), flush=True)
+        rows.append(row)
+    return rows
+
+
 # Algorithmic bytes per robot-step of rl_env_step: fp32 state 57 x 4 + int state 3 x 4 read and
 # written, actions 48 + value 4 read, observation row (256 x 2 bf16 or x 4 fp32), reward 4,
 # done 1, time-out 1, level 4 written.
@@ -400,6 +429,11 @@ def main():
         from paper_2109_11978_b300 import api, synth
         for line in sweep(torch, api, synth):
             print(json.dumps(line), flush=True)
+        return 0
+    if args.robots_sweep:
+        import torch
+        from paper_2109_11978_b300 import api, synth
+        robots_sweep(torch, api, synth)
         return 0
     rank, world, local = dist_info()
     import torch
