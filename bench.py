@@ -249,6 +249,32 @@ def large_config(torch, api, synth, steps=3, warmup=2):
             "env_steps_per_s": 16384 * 24 * len(times) / (sum(times) / 1000.0), "device_status": status}
 
 
+def actuator_lstm(torch, api, reps=5):
+    """Throughput of the batched LSTM actuator cell (Sec. 3.3) at the workload's 4096 robots x 12
+    joints: 96 chained substeps (24 policy steps x 4) per replay, random weights, CUDA events.
+    Bytes per joint-substep: h and c read and written (4 x 128 B), inputs 8 B, torque 4 B."""
+    n = WORKLOAD["num_envs"] * 12
+    g = torch.Generator(device="cuda").manual_seed(3)
+    w = (torch.rand(api.N.RL_ACT_WEIGHTS, device="cuda", generator=g) - 0.5) * 0.6
+    x = torch.randn((n, 2), device="cuda", generator=g)
+    h = torch.zeros((n, 32), device="cuda")
+    c = torch.zeros((n, 32), device="cuda")
+    tau = torch.empty(n, device="cuda")
+    steps = WORKLOAD["num_steps"] * 4
+    for _ in range(steps):
+        api.rl_actuator_lstm_step(w, x, h, c, tau)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps * steps):
+        api.rl_actuator_lstm_step(w, x, h, c, tau)
+    e1.record(s)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1000.0 / (reps * steps)
+    return {"joints": n, "us_per_substep": round(us, 3), "ms_per_iteration_96_substeps": round(us * steps / 1000.0, 4),
+            "joint_substeps_per_s": n / (us * 1e-6), "hbm_gbs": n * 524 / (us * 1e-6) / 1e9}
+
+
 def robots_sweep(torch, api, synth, steps=3, warmup=2):
     """Throughput against the number of parallel robots (Sec. 4.1, Fig. 3): batch sizes B = 49152,
     98304 and 196608 samples per iteration with N = 128 ... 16384 robots (T = B / N steps), and the
@@ -517,6 +543,7 @@ def main():
     if not args.no_extra:
         extra["grouped_learners"] = grouped_learners(torch, api, synth)
         extra["robots_16384"] = large_config(torch, api, synth)
+        extra["actuator_lstm"] = actuator_lstm(torch, api)
     if rank != 0:
         return 0
     out = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,

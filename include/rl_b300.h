@@ -145,6 +145,22 @@ rl_status rl_get_scalars(rl_ctx* ctx, double out[4]);
 /* Sets alpha, the iteration counter and the Adam step count (enqueued on stream). */
 rl_status rl_set_scalars(rl_ctx* ctx, double alpha, int64_t iteration, int64_t adam_step, void* stream);
 
+/* Batched LSTM actuator network (Sec. 3.3): one cell step for n joints, run once per simulation
+ * substep.  The paper feeds only the current measurements to an LSTM that outputs the joint
+ * torque; read here as inputs x = (q* - q, qd) [n][RL_ACT_INPUTS], one layer of RL_ACT_HIDDEN
+ * units, the standard cell with a forget gate (gate order input, forget, cell, output):
+ *   a = W_ih x + W_hh h + b;  c' = sigmoid(a_f) c + sigmoid(a_i) tanh(a_g);
+ *   h' = sigmoid(a_o) tanh(c');  tau = w_out . h' + b_out.
+ * weights: device fp32 [W_ih (4H x 2) | W_hh (4H x H) | b (4H) | w_out (H) | b_out], row-major,
+ * RL_ACT_WEIGHTS values (trained weights are not part of this library; any values run).
+ * h, c: device fp32 [n][RL_ACT_HIDDEN], updated in place; tau: device fp32 [n].  All device
+ * pointers 4-byte aligned (RL_ERR_ALIGNMENT); enqueued on stream; n = 0 is a no-op. */
+#define RL_ACT_INPUTS 2
+#define RL_ACT_HIDDEN 32
+#define RL_ACT_WEIGHTS (4 * RL_ACT_HIDDEN * RL_ACT_INPUTS + 4 * RL_ACT_HIDDEN * RL_ACT_HIDDEN + 4 * RL_ACT_HIDDEN + RL_ACT_HIDDEN + 1)
+rl_status rl_actuator_lstm_step(int32_t n, const float* weights, const float* x, float* h, float* c, float* tau,
+                                void* stream);
+
 /* Procedural terrain family of Sec. 3.1 (Fig. 2) as the heightfield rl_create takes: tile rows
  * are curriculum levels (difficulty d = level / (num_levels - 1)), tile column k is terrain kind
  * k % 7: flat, slope pyramid, slope pit, randomly rough, discrete obstacles, stairs pyramid,

@@ -22,6 +22,8 @@ RL_BF16 = 1
 RL_PROF_GEMM, RL_PROF_LOSS, RL_PROF_ADAM, RL_PROF_ENV, RL_PROF_ACT, RL_PROF_GATHER, RL_PROF_OTHER, RL_PROF_ALL = range(8)
 RL_PROF_NAMES = ("gemm", "loss_head", "adam", "env_step", "act_head", "gather", "other")
 RL_NF = 57
+RL_ACT_INPUTS, RL_ACT_HIDDEN = 2, 32
+RL_ACT_WEIGHTS = 4 * 32 * 2 + 4 * 32 * 32 + 4 * 32 + 32 + 1
 RL_NI = 3
 RL_NSTATS = 16
 
@@ -66,6 +68,7 @@ SIGNATURES = {
     "rl_set_params": (_i32, [_vp, _vp, _vp]),
     "rl_get_scalars": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "rl_set_scalars": (_i32, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp]),
+    "rl_actuator_lstm_step": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rl_terrain_generate": (_i32, [ctypes.POINTER(rl_config), _vp, _vp]),
     "rl_checkpoint_bytes": (ctypes.c_int64, [_vp]),
     "rl_checkpoint_save": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),

@@ -70,6 +70,19 @@ def rl_set_scalars(ctx, alpha, iteration, adam_step):
     check(lib().rl_set_scalars(ctx, float(alpha), int(iteration), int(adam_step), _stream()), "rl_set_scalars")
 
 
+def rl_actuator_lstm_step(weights, x, h, c, tau):
+    """One LSTM actuator step for x.shape[0] joints (CUDA fp32 tensors; h, c updated in place)."""
+    n = x.shape[0]
+    if weights.numel() != N.RL_ACT_WEIGHTS or tuple(x.shape) != (n, N.RL_ACT_INPUTS) or \
+            tuple(h.shape) != (n, N.RL_ACT_HIDDEN) or tuple(c.shape) != (n, N.RL_ACT_HIDDEN) or tau.numel() != n:
+        raise RLError("rl_actuator_lstm_step: shapes")
+    for t in (weights, x, h, c, tau):
+        if t.dtype != torch.float32:
+            raise RLError("rl_actuator_lstm_step: float32 tensors")
+    check(lib().rl_actuator_lstm_step(int(n), _ptr(weights), _ptr(x), _ptr(h), _ptr(c), _ptr(tau), _stream()),
+          "rl_actuator_lstm_step")
+
+
 def rl_terrain_generate(cfg):
     """The procedural terrain family for cfg as a CUDA fp32 tensor [num_levels c][num_cols c]."""
     c = int(round(cfg.tile_size / cfg.hf_res))

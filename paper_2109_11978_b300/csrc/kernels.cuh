@@ -169,6 +169,11 @@ __host__ __device__ inline long long adam_per_block(int nsplit, int vec) {
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
+// Batched LSTM actuator cell (actuator.cu): n joints, inputs [n][2], state h, c [n][32] updated in
+// place, torques [n]; weights as rl_actuator_lstm_step documents.
+constexpr int ACT_INPUTS = 2, ACT_HIDDEN = 32;
+cudaError_t launch_actuator_lstm(int n, const float* w, const float* x, float* h, float* c, float* tau, cudaStream_t s);
+
 // Procedural terrain family (terrain.cu): grid of levels (rows) x terrain kinds (columns) of c x c
 // cells; P, W, B: the spawn platform's half width, the stair width and the obstacle block in cells.
 struct TerrainParams {

@@ -1254,6 +1254,16 @@ rl_status rl_set_params(rl_ctx* c, const float* in, void* stream) {
     return refresh_bf16(c, S_(stream));
 }
 
+rl_status rl_actuator_lstm_step(int32_t n, const float* weights, const float* x, float* h, float* c, float* tau,
+                                void* stream) {
+    static_assert(ACT_INPUTS == RL_ACT_INPUTS && ACT_HIDDEN == RL_ACT_HIDDEN, "actuator cell sizes");
+    if (n < 0 || (n > 0 && (!weights || !x || !h || !c || !tau))) return RL_ERR_INVALID_ARG;
+    for (const void* p : {(const void*)weights, (const void*)x, (const void*)h, (const void*)c, (const void*)tau})
+        if (reinterpret_cast<uintptr_t>(p) & 3u) return RL_ERR_ALIGNMENT;
+    CK(launch_actuator_lstm(n, weights, x, h, c, tau, S_(stream)));
+    return RL_OK;
+}
+
 rl_status rl_terrain_generate(const rl_config* cfg, float* hf, void* stream) {
     if (!cfg || !hf || cfg->num_levels < 1 || cfg->num_cols < 1 || !(cfg->hf_res > 0.f)) return RL_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(hf) & 3u) return RL_ERR_ALIGNMENT;
