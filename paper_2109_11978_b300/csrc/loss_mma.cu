@@ -498,16 +498,56 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
     if (!last) return;
     __threadfence();
     if (warp != 0) return;
-    double st[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-        const float* q = p.part + (size_t)b * PF + O_ST;
+    // the scalars this block updates, read up front so that their latency overlaps the partials'
+    float* sc = p.scal;
+    float alpha = 0.f, step = 0.f, acc[8] = {};
+    if (lane == 0) {
+        alpha = __ldcg(sc + SC_ALPHA);
+        step = __ldcg(sc + SC_STEP);
+        if (p.stats) {
+            acc[0] = p.stats[0]; acc[1] = p.stats[1]; acc[2] = p.stats[2]; acc[3] = p.stats[4];
+            acc[4] = p.stats[6]; acc[5] = p.stats[12];
+        }
+    }
+    // per lane, blocks lane, lane + 32, ... summed in that order, then a fixed xor tree across the
+    // lanes; compensated fp32 sums (Neumaier's two-sum: the rounding error of every addition is
+    // carried in a second float) instead of fp64, whose arithmetic is slow on this part.  Eight
+    // blocks' partials are loaded before any is added, so that the loads overlap.
+    float st[4] = {0.f, 0.f, 0.f, 0.f}, ce[4] = {0.f, 0.f, 0.f, 0.f};
+    auto two_sum = [](float& sum, float& err, float x) {
+        const float t = sum + x;
+        err += fabsf(sum) >= fabsf(x) ? (sum - t) + x : (x - t) + sum;
+        sum = t;
+    };
+    for (int b0 = lane; b0 < (int)gridDim.x; b0 += 32 * 8) {
+        float v[8][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) st[i] += (double)__ldcg(q + i);
+        for (int k = 0; k < 8; ++k) {
+            const int b = b0 + 32 * k;
+            const float* q = p.part + (size_t)(b < (int)gridDim.x ? b : 0) * PF + O_ST;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[k][i] = __ldcg(q + i);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (b0 + 32 * k < (int)gridDim.x)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) two_sum(st[i], ce[i], v[k][i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) st[i] += __shfl_xor_sync(0xffffffffu, st[i], o);
+        for (int i = 0; i < 4; ++i) {
+            const float os = __shfl_xor_sync(0xffffffffu, st[i], o), oc = __shfl_xor_sync(0xffffffffu, ce[i], o);
+            // the lower lane's value first, so that both partners form the same sum
+            const bool lo = (lane & o) == 0;
+            float a = lo ? st[i] : os, ca = lo ? ce[i] : oc;
+            two_sum(a, ca, lo ? os : st[i]);
+            st[i] = a;
+            ce[i] = ca + (lo ? oc : ce[i]);
+        }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) st[i] += ce[i];
     if (lane == 0) {
         const float inv_M = 1.0f / (float)p.M;
         float ent = 0.f;
@@ -515,28 +555,27 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
         const float kl = (float)st[2] * inv_M;
         const float surr = -(float)st[0] * inv_M, vloss = (float)st[1] * inv_M;
         const float loss = surr + p.value_coef * vloss - p.entropy_coef * ent;
-        float* sc = p.scal;
         sc[SC_KL] = kl;
         sc[SC_LOSS] = loss;
         sc[SC_SURR] = surr;
         sc[SC_VLOSS] = vloss;
         sc[SC_ENT] = ent;
         sc[SC_CLIPFRAC] = (float)st[3] * inv_M;
-        float alpha = sc[SC_ALPHA];
         if (p.kl_target > 0.f) {
             if (kl > 2.f * p.kl_target) alpha = fmaxf(p.lr_min, alpha / 1.5f);
             else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
             sc[SC_ALPHA] = alpha;
         }
-        const float t = sc[SC_STEP] + 1.f;
+        const float t = step + 1.f;
         sc[SC_STEP] = t;
         const float bc1 = -expm1f(t * log1pf(-0.1f));
         const float bc2 = -expm1f(t * log1pf(-0.001f));
         sc[SC_STEPSIZE] = alpha / bc1;
         sc[SC_INVSQRT_BC2] = 1.0f / sqrtf(bc2);
         if (p.stats) {
-            p.stats[0] += loss; p.stats[1] += surr; p.stats[2] += vloss; p.stats[3] = ent;
-            p.stats[4] += kl; p.stats[5] = sc[SC_ALPHA]; p.stats[6] += sc[SC_CLIPFRAC]; p.stats[12] += 1.f;
+            p.stats[0] = acc[0] + loss; p.stats[1] = acc[1] + surr; p.stats[2] = acc[2] + vloss; p.stats[3] = ent;
+            p.stats[4] = acc[3] + kl; p.stats[5] = alpha; p.stats[6] = acc[4] + (float)st[3] * inv_M;
+            p.stats[12] = acc[5] + 1.f;
         }
         *p.counter = 0u;
     }
