@@ -531,8 +531,13 @@ void build_adam(rl_ctx* c) {
     const int PF = hp.PF, O_WA = hp.WA, O_BA = hp.BA, O_LS = hp.LS, O_WC = hp.WC, O_BC = hp.BC, O_DBA = hp.DBA,
               O_DBC = hp.DBC;
     int ns = 0, blocks = 0;
+    // two passes: the segments with many partials (a warp per parameter group, the slowest blocks)
+    // first, so that their blocks start in the first wave and the quick ones fill in behind them;
+    // the order of the blocks changes no sum
+    int pass = 0;
     auto add = [&](long long off, long long size, const float* part, long long stride, int nsplit, void* wbf, int rows,
                    int cols) {
+        if ((nsplit > ADAM_WIDE) != (pass == 0)) return;
         AdamSeg& s = a.seg[ns];
         s.offset = off;
         s.size = size;
@@ -551,19 +556,21 @@ void build_adam(rl_ctx* c) {
         blocks += (int)((size + per_block - 1) / per_block);
         ++ns;
     };
-    for (int n = 0; n < 2; ++n) {
-        for (int l = 0; l < c->NH; ++l) {
-            const LayerInfo& Li = c->L[n][l];
-            add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], Li.out, Li.in);
-            if (l < c->NH - 1)
-                add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, 0, 0);
-            else
-                add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, 0, 0);
+    for (pass = 0; pass < 2; ++pass) {
+        for (int n = 0; n < 2; ++n) {
+            for (int l = 0; l < c->NH; ++l) {
+                const LayerInfo& Li = c->L[n][l];
+                add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], Li.out, Li.in);
+                if (l < c->NH - 1)
+                    add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, 0, 0);
+                else
+                    add(Li.b, Li.out, c->head_part + (n == 0 ? O_DBA : O_DBC), PF, c->head_blocks, nullptr, 0, 0);
+            }
+            const LayerInfo& Lh = c->L[n][c->NH];
+            add(Lh.w, (long long)Lh.out * Lh.in, c->head_part + (n == 0 ? O_WA : O_WC), PF, c->head_blocks, nullptr, 0, 0);
+            add(Lh.b, Lh.out, c->head_part + (n == 0 ? O_BA : O_BC), PF, c->head_blocks, nullptr, 0, 0);
+            if (n == 0) add(c->logstd, c->A, c->head_part + O_LS, PF, c->head_blocks, nullptr, 0, 0);
         }
-        const LayerInfo& Lh = c->L[n][c->NH];
-        add(Lh.w, (long long)Lh.out * Lh.in, c->head_part + (n == 0 ? O_WA : O_WC), PF, c->head_blocks, nullptr, 0, 0);
-        add(Lh.b, Lh.out, c->head_part + (n == 0 ? O_BA : O_BC), PF, c->head_blocks, nullptr, 0, 0);
-        if (n == 0) add(c->logstd, c->A, c->head_part + O_LS, PF, c->head_blocks, nullptr, 0, 0);
     }
     a.nsegs = ns;
     a.nblocks = blocks;
