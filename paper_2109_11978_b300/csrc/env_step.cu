@@ -151,8 +151,16 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         for (int i = tid; i < p.act.A * p.act.H; i += THREADS) Wa[i] = p.act.Wa[i];
         for (int i = tid; i < p.act.H; i += THREADS) Wc[i] = p.act.Wc[i];
         __syncthreads();
-        for (int r = warp; r < ENVS; r += THREADS / 32)
-            if (env0 + r < N) act_row<(FUSE >> 4) != 0, (FUSE & 15)>(p.act, Wa, Wc, env0 + r, it, true, lane, act_s[r], &val_s[r]);
+        // the warp's two robots together (ENVS = 2 x the warps of the block)
+        static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
+        {
+            const int r0 = warp, r1 = warp + THREADS / 32;
+            const int mm[2] = {env0 + r0, env0 + r1};
+            const bool ok[2] = {env0 + r0 < N, env0 + r1 < N};
+            float* const as[2] = {act_s[r0], act_s[r1]};
+            float* const vs[2] = {&val_s[r0], &val_s[r1]};
+            if (ok[0]) act_rows<(FUSE >> 4) != 0, (FUSE & 15), 2>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs);
+        }
         __syncthreads();
     }
     // Phase 1: the stand-in's joints and base chains are independent recurrences, each on its own
