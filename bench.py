@@ -84,7 +84,7 @@ def read_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum summed over the GEMM launches of one iteration of
 # the rough-terrain workload (ncu, one pass per launch); reset to None whenever the GEMM kernel
 # changes until it is captured again.
-GEMM_DRAM_BYTES_PER_ITERATION = 7993.5e6 + 257.2e6
+GEMM_DRAM_BYTES_PER_ITERATION = 8001.3e6 + 256.2e6
 
 
 def gemm_flops_per_iteration(w, O):
