@@ -73,6 +73,8 @@ struct rl_ctx {
     cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
     cudaStream_t wside = nullptr;                // weight gradients, beside the next input gradient
     cudaEvent_t ev_dw[4] = {}, ev_dw_join = nullptr;
+    cudaEvent_t ev_perm_fork = nullptr, ev_perm_join = nullptr;   // the shuffle, beside GAE
+    cudaEvent_t ev_pack_fork = nullptr, ev_pack_join = nullptr;   // the records, beside minibatch 0
     void* H[2][4] = {};
     void* dY[2][4] = {};
     float* gw[2][4] = {};
@@ -455,7 +457,8 @@ EnvParams env_params(rl_ctx* c) {
 // X0 must already hold the minibatch observations.
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
-                            const float* ret, bool step, const float* rec = nullptr, bool overlap_dw = false) {
+                            const float* ret, bool step, const float* rec = nullptr, bool overlap_dw = false,
+                            cudaEvent_t before_loss = nullptr) {
     rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, false);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
@@ -483,6 +486,7 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.kl_target = step ? c->cfg.kl_target : 0.f;
     h.lr_min = c->cfg.lr_min;
     h.lr_max = c->cfg.lr_max;
+    if (before_loss) CK(cudaStreamWaitEvent(q.s, before_loss, 0));
     CK(q.run(RL_PROF_LOSS, 1, [&] { return launch_loss_head(h, q.s); }));
     // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums;
     // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows.  dW_l needs only dY_l,
@@ -617,17 +621,28 @@ rl_status refresh_bf16(rl_ctx* c, cudaStream_t s) {
 }
 
 rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
-                      const float* val_old, const float* adv, const float* ret, int epochs, int minibatches, float* stats_out) {
+                      const float* val_old, const float* adv, const float* ret, int epochs, int minibatches, float* stats_out,
+                      bool perm_on_side) {
     const int B = c->B, Mb = B / minibatches;
     if (Mb != c->Mb || epochs > c->cfg.epochs) return RL_ERR_INVALID_ARG;
     cudaStream_t s = q.s;
     CK(cudaMemcpyAsync(c->logstd_old, c->params + c->logstd, sizeof(float) * c->A, cudaMemcpyDeviceToDevice, s));
-    CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s); }));
+    if (!perm_on_side)
+        CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s); }));
     // the BF16 loss head reads each row's loss inputs from one packed 128-byte record per sample
-    // (one line per row of a shuffled minibatch instead of one per field)
-    if (c->bf16)
+    // (one line per row of a shuffled minibatch instead of one per field); the records are packed
+    // on the side stream, beside the first minibatch's gather and forward, when the shuffle ran there
+    const bool pack_on_side = perm_on_side && c->bf16;
+    if (pack_on_side) {
+        CK(cudaEventRecord(c->ev_pack_fork, s));
+        CK(cudaStreamWaitEvent(c->side, c->ev_pack_fork, 0));
+        CK(launch_pack_records(B, c->A, actions, mu_old, logp_old, adv, val_old, ret, c->recs, c->side));
+        ++c->launches;
+        CK(cudaEventRecord(c->ev_pack_join, c->side));
+    } else if (c->bf16) {
         CK(q.run(RL_PROF_OTHER, 1,
                  [&] { return launch_pack_records(B, c->A, actions, mu_old, logp_old, adv, val_old, ret, c->recs, s); }));
+    }
     // The next minibatch's observations are gathered on a side stream into the other buffer
     // while the current minibatch trains (the gather is memory-bound, the GEMMs are not); the
     // forward of the next minibatch waits for it.  With per-class profiling every launch stays on
@@ -637,6 +652,7 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
     auto mb_idx = [&](int k) { return c->perm + (size_t)(k / minibatches) * B + (size_t)(k % minibatches) * Mb; };
     c->xcur = 0;
     c->X0 = c->X0buf[0];
+    if (perm_on_side) CK(cudaStreamWaitEvent(s, c->ev_perm_join, 0));
     CK(q.run(RL_PROF_GATHER, 1, [&] { return launch_gather(obs, c->bf16 ? 1 : 0, mb_idx(0), Mb, c->Op, c->X0buf[0], s); }));
     for (int k = 0; k < nmb; ++k) {
         const int cur = k & 1, nxt = cur ^ 1;
@@ -654,7 +670,7 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
             }
         }
         rl_status st = minibatch_fwd_bwd(c, q, Mb, mb_idx(k), actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
-                                         c->bf16 ? c->recs : nullptr, overlap);
+                                         c->bf16 ? c->recs : nullptr, overlap, k == 0 && pack_on_side ? c->ev_pack_join : nullptr);
         if (st != RL_OK) return st;
         c->adam.grad_out = nullptr;
         CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
@@ -702,6 +718,17 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
         ep.tidx_out = nullptr;
         CK(q.run(RL_PROF_ENV, 1, [&] { return launch_env_step(ep, 0, s); }));
     }
+    // The shuffle depends only on the seed and the iteration counter (advanced at the end of the
+    // update): it runs on the side stream beside the last value, GAE and the record packing, which
+    // occupy few SMs.  With per-class profiling it stays on the main stream.
+    const bool perm_on_side = !q.profile;
+    if (perm_on_side) {
+        CK(cudaEventRecord(c->ev_perm_fork, s));
+        CK(cudaStreamWaitEvent(c->side, c->ev_perm_fork, 0));
+        CK(launch_permutation(c->B, c->cfg.epochs, c->cfg.seed, c->iter, c->perm, c->side));
+        ++c->launches;
+        CK(cudaEventRecord(c->ev_perm_join, c->side));
+    }
     rl_status st = act_impl(c, q, c->T, c->N, obs + c->T * obs_step, nullptr, nullptr, nullptr, c->last_val);
     if (st != RL_OK) return st;
     CK(q.run(RL_PROF_OTHER, 2, [&] {
@@ -709,7 +736,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
                           c->scal + SC_ADV_MEAN, c->gae_ws, c->gae_nparts, s);
     }));
     st = update_impl(c, q, c->obs, c->actions, c->logp, c->mu, c->values, c->adv, c->ret, c->cfg.epochs, c->cfg.minibatches,
-                     c->stats);
+                     c->stats, perm_on_side);
     if (st != RL_OK) return st;
     CK(cudaMemcpyAsync(obs, obs + c->T * obs_step, obs_step, cudaMemcpyDeviceToDevice, s));
     return RL_OK;
@@ -1042,6 +1069,10 @@ void rl_destroy(rl_ctx* c) {
     for (cudaEvent_t e : c->ev_dw)
         if (e) cudaEventDestroy(e);
     if (c->ev_dw_join) cudaEventDestroy(c->ev_dw_join);
+    if (c->ev_perm_fork) cudaEventDestroy(c->ev_perm_fork);
+    if (c->ev_perm_join) cudaEventDestroy(c->ev_perm_join);
+    if (c->ev_pack_fork) cudaEventDestroy(c->ev_pack_fork);
+    if (c->ev_pack_join) cudaEventDestroy(c->ev_pack_join);
     for (int i = 0; i < 2; ++i) {
         if (c->ev_fork[i]) cudaEventDestroy(c->ev_fork[i]);
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
@@ -1070,6 +1101,10 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(cudaStreamCreateWithFlags(&c->wside, cudaStreamNonBlocking));
     for (cudaEvent_t& e : c->ev_dw) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_dw_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_perm_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_perm_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_pack_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_pack_join, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
         CK(cudaEventCreateWithFlags(&c->ev_fork[i], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
@@ -1515,7 +1550,7 @@ rl_status rl_ppo_update(rl_ctx* c, const void* obs, const float* actions, const 
     cudaStream_t s = S_(stream);
     CK(launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s));
     Enq q{c, s, false};
-    return update_impl(c, q, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out);
+    return update_impl(c, q, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out, false);
 }
 
 rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* actions, const float* logp_old,
