@@ -274,6 +274,28 @@ def test_graph_replay_equals_eager():
     Lb.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_side_streams_equal_serial_order(prec):
+    """With per-class profiling every launch of the iteration stays on the main stream; without it
+    the shuffle, the record packing, the next minibatch's gather and the weight gradients run on
+    side streams.  Both orders give the same bits."""
+    w = workload("tiny", precision=prec, epochs=2, minibatches=2)
+    La, _, _, _ = _setup(w)
+    Lb, _, _, _ = _setup(w)
+    api.rl_profile_enable(Lb.ctx, api.RL_PROF_ALL, True)
+    for _ in range(2):
+        La.train_iteration(use_graph=True)
+        Lb.train_iteration(use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(La.params(), Lb.params())
+    for i in (0, 1, 5, 6, 9):
+        assert torch.equal(La.storage(i), Lb.storage(i)), i
+    assert api.rl_get_scalars(La.ctx) == api.rl_get_scalars(Lb.ctx)
+    assert api.rl_last_device_status(La.ctx) == 0 and api.rl_last_device_status(Lb.ctx) == 0
+    La.close()
+    Lb.close()
+
+
 @pytest.mark.parametrize("form", ["fp32", "bf16"])
 def test_autotune_keeps_results(form):
     """The autotuner only changes tile widths and split counts: the gradient stays within the
