@@ -555,7 +555,7 @@ def main():
                       "per_step_ms": [round(t, 4) for t in times]},
            "roofline": roof, "kernel_breakdown_in_graph": breakdown,
            "gpu_launches": launches * args.steps, "launches_per_step": launches,
-           "autotune": {k: tuned[k] for k in ("sites", "clusters_of_2_resident", "source") if k in tuned},
+           "autotune": {k: tuned[k] for k in ("sites", "pairs_resident", "source") if k in tuned},
            "e2e": e2e, "clocks": clk, "device_status": status}
     if compare:
         out["compare"] = compare

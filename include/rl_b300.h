@@ -139,6 +139,11 @@ void rl_destroy(rl_ctx* ctx);
 rl_status rl_get_params(rl_ctx* ctx, float* params_out, void* stream);
 rl_status rl_set_params(rl_ctx* ctx, const float* params, void* stream);
 
+/* Adam's first and second moments (Adam with bias correction; the paper only names the
+ * optimiser's learning rate, Algorithm 1) in the flat layout of rl_get_params: m_out, v_out device
+ * fp32, rl_param_count values each, written on stream. */
+rl_status rl_get_adam_moments(rl_ctx* ctx, float* m_out, float* v_out, void* stream);
+
 /* Host-visible learner scalars (synchronises): out[0] = alpha, out[1] = iteration counter,
  * out[2] = Adam step count, out[3] = last minibatch KL. */
 rl_status rl_get_scalars(rl_ctx* ctx, double out[4]);
@@ -247,8 +252,11 @@ rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew,
  * 4096 partials), held by every GPU that loads the library until the process exits.
  *   - N <= 262144 (4096 blocks of 64 robots); larger N returns RL_ERR_INVALID_ARG and
  *     launches nothing.  T is unrestricted.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *   - Each call made outside stream capture looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and remembers it; a call on a capturing
+ *     stream uses the remembered address.  So make the first call on a device before any stream
+ *     capture (a first call inside a capture returns RL_ERR_CUDA), and after a cudaDeviceReset
+ *     make one call outside capture before capturing again.
  *   - Every call on a device shares the one array and leaves its partial sums there.  Each call
  *     overwrites every slot it reads before reading it, so nothing has to start at zero, but
  *     calls that overlap on the GPU (other streams, other host threads) race on the array and
@@ -264,12 +272,16 @@ rl_status rl_gae_noalloc(int32_t T, int32_t N, float gamma, float lam, const flo
  * clipped value loss, entropy bonus, KL(pi_old || pi_new), alpha updated by Algorithm 1,
  * hand-written backward, Adam step with the new alpha.  Increments the iteration counter.
  *   obs [B][obs_pad] (fp32 / bf16 by precision); actions, mu_old [B][act_dim] fp32;
- *   logp_old, val_old, adv (normalised), ret [B] fp32; stats_out: device [RL_NSTATS] or NULL.
- * B must be divisible by minibatches. */
+ *   logp_old, val_old, adv (normalised), ret [B] fp32; clip: the clip range c of the surrogate
+ *   ratio (clip(ratio, 1 - c, 1 + c), Table 3: 0.2) and of the value loss (V_old +
+ *   clip(V - V_old, -c, c)), 0 < c < 1; stats_out: device [RL_NSTATS] or NULL.
+ * minibatches must give the config's minibatch size (B / minibatches) and epochs <= the config's
+ * epochs (RL_ERR_INVALID_ARG otherwise).  The permutations and, per minibatch, the KL and the
+ * alpha Algorithm 1 chose are left in rl_get_storage slots 13 and 14. */
 rl_status rl_ppo_update(rl_ctx* ctx, const void* obs, const float* actions, const float* logp_old,
                         const float* mu_old, const float* val_old, const float* adv,
-                        const float* ret, int32_t epochs, int32_t minibatches, float* stats_out,
-                        void* stream);
+                        const float* ret, int32_t epochs, int32_t minibatches, float clip,
+                        float* stats_out, void* stream);
 
 /* Loss and gradient of one minibatch without a parameter step (the hand-written backward of
  * rl_ppo_update, exposed for gradient checks).  Inputs are M contiguous rows (same layouts
@@ -304,7 +316,11 @@ rl_status rl_group_train_iteration(rl_group* g, int32_t use_graph, void* stream)
 /* Context-owned rollout storage (device pointers, valid until rl_destroy):
  * 0 obs [T+1][N][obs_pad], 1 actions [T][N][A], 2 mu [T][N][A], 3 logp [T][N], 4 values [T][N],
  * 5 rewards [T][N], 6 dones [T][N] u8, 7 timeouts [T][N] u8, 8 last values [N],
- * 9 advantages [T][N], 10 returns [T][N], 11 levels [N] int32, 12 stats [RL_NSTATS]. */
+ * 9 advantages [T][N], 10 returns [T][N], 11 levels [N] int32, 12 stats [RL_NSTATS],
+ * 13 the last update's minibatch permutations [epochs][B] int32 (minibatch m of epoch e is
+ * rows m B / minibatches ... (m + 1) B / minibatches - 1 of row e), 14 the last update's
+ * per-minibatch trace [epochs * minibatches][2] fp32 = (KL(pi_old || pi_new), alpha after
+ * Algorithm 1), in the order the minibatches ran. */
 rl_status rl_get_storage(rl_ctx* ctx, int32_t which, void** ptr, size_t* bytes);
 
 /* Device status word: RL_OK, or the first device-side failure recorded (RL_ERR_TIMEOUT for a
@@ -335,9 +351,8 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
 /* Tile autotuner: times each GEMM site (per hidden layer: the update's forward, input gradient
  * and weight gradient at minibatch rows, and the rollout's forward at num_envs rows; actor and
  * critic in one launch) over candidate tile widths
- * (64, 128, 256 output columns), tile modes (one CTA per tile, two CTAs sharing one B tile
- * through TMA multicast, a CTA pair on the cta_group::2 MMA, or one CTA per tile with two K blocks
- * per pipeline stage) and, for weight gradients, split-K counts (one and two waves of the width's tiles over the SMs, half and double the default;
+ * (64, 128, 256 output columns), tile modes (one CTA per tile, a CTA pair on the cta_group::2
+ * MMA, or one CTA per tile with two K blocks per pipeline stage) and, for weight gradients, split-K counts (one and two waves of the width's tiles over the SMs, half and double the default;
  * timed together with the summation of their partials, which Adam performs) on the context's
  * own buffers, keeps the fastest, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
@@ -349,11 +364,11 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * control of this implementation).  site: 0 forward, 1 input gradient (layer >= 1), 2 weight
  * gradient (the update's sites, minibatch rows), 3 the rollout's forward (num_envs rows);
  * layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the site's output
- * width; cluster: 1 (one CTA per 128-row tile), 2 (pairs of row tiles share the B tile by TMA
- * multicast), 3 (pairs of CTAs run one 256-row tile on the cta_group::2 MMA, each loading half
- * of B) or 4 (one CTA per tile, two K blocks per pipeline stage fetched by one 3D TMA copy per
- * operand); 2 and 3 need at least two 128-row tiles at the site, 3 a tile width of at least 128,
- * 2 at sites 1 and 2 a tile width of at least 128, and 4 a tile width of at most 128;
+ * width; cluster: 1 (one CTA per 128-row tile), 3 (pairs of CTAs run one 256-row tile on the
+ * cta_group::2 MMA, each loading half of B) or 4 (one CTA per tile, two K blocks per pipeline
+ * stage fetched by one 3D TMA copy per operand); 3 needs at least two 128-row tiles at the site
+ * and a tile width of at least 128, 4 a tile width of at most 128 (2, a B tile shared by TMA
+ * multicast, is not offered and returns RL_ERR_INVALID_ARG);
  * splits: weight-gradient split-K count (1 .. the larger of twice the default and two waves of
  * 64-wide tiles over 148 SMs, rounded so every slice is a multiple of 64 rows), ignored for the
  * other sites.  Drops a captured iteration graph.
@@ -375,10 +390,9 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
 
 /* Diagnostic with an explicit tile shape: operands 0 computes C = A B^T (A [M][K], B [N][K]), 1
  * computes C = At^T Bt (At [K][M], Bt [K][N]); bn: output tile width 64, 128 or 256 dividing N;
- * cluster: 1 (one CTA per tile), 2 (pairs of row tiles share the B tile by TMA multicast), 3
- * (pairs of CTAs run one 256-row tile on the cta_group::2 tensor-core MMA, each CTA loading half
- * of the B tile; bn 128 or 256).  Requirements as for rl_gemm_bf16 (operands 0) or
- * rl_gemm_bf16_tn (operands 1); cluster 2 with operands 1 and cluster 3 need bn >= 128.
+ * cluster: 1 (one CTA per tile) or 3 (pairs of CTAs run one 256-row tile on the cta_group::2
+ * tensor-core MMA, each CTA loading half of the B tile; bn 128 or 256).  Requirements as for
+ * rl_gemm_bf16 (operands 0) or rl_gemm_bf16_tn (operands 1).
  * operands 2 / 3: the forms of 0 / 1 with two K blocks per pipeline stage (one 3D TMA copy per
  * operand and stage), cluster 1 and bn <= 128 only; operands 2 needs K % 64 == 0, operands 3
  * M % 64 == 0.  No counterpart in the paper. */

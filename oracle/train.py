@@ -29,11 +29,15 @@ class Learner:
     def params(self):
         return mlp.unflatten(self.flat, self.ecfg.obs_dim, self.hidden, self.ecfg.act_dim)
 
-    def rollout(self, T, actions_override=None):
+    def rollout(self, T, actions_override=None, values_override=None):
         """T policy steps.  actions_override[t] (if given) replaces the sampled actions, so
-        the env math can be driven by another implementation's actions (teacher forcing)."""
+        the env math can be driven by another implementation's actions (teacher forcing);
+        values_override[t] likewise replaces V(o_t) where the env step uses it (the time-out
+        bootstrap of Sec. 2.2.2 adds gamma V(o_t), the value stored at act time).  The oracle's
+        own sampled actions and values are kept under "sampled_actions" and "values"."""
         N, O, A = self.ecfg.num_envs, self.ecfg.obs_dim, self.ecfg.act_dim
         st = {"obs": np.zeros((T, N, O)), "actions": np.zeros((T, N, A)), "mu": np.zeros((T, N, A)),
+              "sampled_actions": np.zeros((T, N, A)),
               "logp": np.zeros((T, N)), "values": np.zeros((T, N)), "reward": np.zeros((T, N)),
               "done": np.zeros((T, N), np.uint8), "timeout": np.zeros((T, N), np.uint8),
               "level": np.zeros((T, N), np.int32)}
@@ -41,12 +45,14 @@ class Learner:
         for t in range(T):
             out = mlp.act(p, self.obs, self.ecfg.seed, self.iteration, t)
             a = out["actions"] if actions_override is None else np.asarray(actions_override[t], np.float64)
+            v = out["values"] if values_override is None else np.asarray(values_override[t], np.float64)
             st["obs"][t] = self.obs
             st["actions"][t], st["mu"][t] = a, out["mu"]
+            st["sampled_actions"][t] = out["actions"]
             st["logp"][t] = mlp.log_prob(a, out["mu"], p["log_std"])
             st["values"][t] = out["values"]
             r = envmod.step(self.ecfg, self.hf, self.sf, self.si, a.astype(np.float32),
-                            out["values"], self.iteration, t)
+                            v, self.iteration, t)
             self.sf, self.si, self.obs = r["sf"], r["si"], r["obs"]
             st["reward"][t], st["done"][t], st["timeout"][t] = r["reward"], r["done"], r["timeout"]
             st["level"][t] = r["level"]

@@ -66,6 +66,7 @@ SIGNATURES = {
     "rl_destroy": (None, [_vp]),
     "rl_get_params": (_i32, [_vp, _vp, _vp]),
     "rl_set_params": (_i32, [_vp, _vp, _vp]),
+    "rl_get_adam_moments": (_i32, [_vp, _vp, _vp, _vp]),
     "rl_get_scalars": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "rl_set_scalars": (_i32, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp]),
     "rl_actuator_lstm_step": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -81,7 +82,7 @@ SIGNATURES = {
     "rl_gae_workspace_bytes": (ctypes.c_size_t, [_i32, _i32]),
     "rl_gae": (_i32, [_i32, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, ctypes.c_size_t, _vp]),
     "rl_gae_noalloc": (_i32, [_i32, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
-    "rl_ppo_update": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "rl_ppo_update": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _f32, _vp, _vp]),
     "rl_ppo_loss_grad": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rl_train_iteration": (_i32, [_vp, _i32, _vp, _vp]),
     "rl_get_storage": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)]),

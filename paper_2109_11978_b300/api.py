@@ -60,6 +60,10 @@ def rl_set_params(ctx, params):
     check(lib().rl_set_params(ctx, _ptr(params), _stream()), "rl_set_params")
 
 
+def rl_get_adam_moments(ctx, m_out, v_out):
+    check(lib().rl_get_adam_moments(ctx, _ptr(m_out), _ptr(v_out), _stream()), "rl_get_adam_moments")
+
+
 def rl_get_scalars(ctx):
     arr = (ctypes.c_double * 4)()
     check(lib().rl_get_scalars(ctx, arr), "rl_get_scalars")
@@ -155,9 +159,10 @@ def rl_gae_noalloc(gamma, lam, rew, val, last_val, done, adv_out, ret_out, norma
           "rl_gae_noalloc")
 
 
-def rl_ppo_update(ctx, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out=None):
+def rl_ppo_update(ctx, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, clip, stats_out=None):
     check(lib().rl_ppo_update(ctx, _ptr(obs), _ptr(actions), _ptr(logp_old), _ptr(mu_old), _ptr(val_old), _ptr(adv),
-                              _ptr(ret), int(epochs), int(minibatches), _ptr(stats_out), _stream()), "rl_ppo_update")
+                              _ptr(ret), int(epochs), int(minibatches), float(clip), _ptr(stats_out), _stream()),
+          "rl_ppo_update")
 
 
 def rl_ppo_loss_grad(ctx, obs, actions, logp_old, mu_old, log_std_old, val_old, adv, ret, grad_out, stats_out=None):
@@ -233,7 +238,7 @@ def rl_gemm_bf16_tn(At, Bt, C):
 
 def rl_gemm_bf16_shape(A, B, C, operands=0, bn=128, cluster=1):
     """C = A B^T (operands 0: A [M][K], B [N][K]) or At^T Bt (operands 1: At [K][M], Bt [K][N]) with an
-    explicit tile width and cluster mode (1 single CTA, 2 B-tile multicast, 3 cta_group::2 pair);
+    explicit tile width and cluster mode (1 single CTA, 3 cta_group::2 pair);
     operands 2 / 3: the same forms with two K blocks per pipeline stage (cluster 1, bn <= 128)."""
     if operands in (0, 2):
         M, K = A.shape
@@ -283,7 +288,8 @@ class Learner:
     """One learner (context) with torch views of its rollout storage.  Marshalling only."""
 
     STORAGE = {0: "obs", 1: "actions", 2: "mu", 3: "logp", 4: "values", 5: "rewards", 6: "dones", 7: "timeouts",
-               8: "last_values", 9: "advantages", 10: "returns", 11: "levels", 12: "stats"}
+               8: "last_values", 9: "advantages", 10: "returns", 11: "levels", 12: "stats", 13: "permutations",
+               14: "update_trace"}
 
     def __init__(self, cfg, heightfield, init_params):
         if not torch.cuda.is_available():
@@ -313,7 +319,8 @@ class Learner:
                   3: ((T, Nn), torch.float32), 4: ((T, Nn), torch.float32), 5: ((T, Nn), torch.float32),
                   6: ((T, Nn), torch.uint8), 7: ((T, Nn), torch.uint8), 8: ((Nn,), torch.float32),
                   9: ((T, Nn), torch.float32), 10: ((T, Nn), torch.float32), 11: ((Nn,), torch.int32),
-                  12: ((RL_NSTATS,), torch.float32)}
+                  12: ((RL_NSTATS,), torch.float32), 13: ((c.epochs, T * Nn), torch.int32),
+                  14: ((c.epochs * c.minibatches, 2), torch.float32)}
         shape, dt = shapes[which]
         return _alias(ptr, shape, dt)
 
@@ -321,6 +328,12 @@ class Learner:
         out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
         rl_get_params(self.ctx, out)
         return out
+
+    def adam_moments(self):
+        m = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        v = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        rl_get_adam_moments(self.ctx, m, v)
+        return m, v
 
     def set_params(self, p):
         rl_set_params(self.ctx, p.contiguous())

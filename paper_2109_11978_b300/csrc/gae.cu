@@ -142,21 +142,28 @@ int gae_num_partials(int T, int N) { return (N + GAE_THREADS - 1) / GAE_THREADS;
 int gae_noalloc_max_envs() { return NOALLOC_MAX_PARTS * GAE_THREADS; }
 
 // Device address of the scratch array on the current device.  In host code the array's name is
-// only a host-side stand-in, so the address is looked up once per device (with that device
-// current) and cached.
-cudaError_t gae_noalloc_scratch(void** out) {
+// only a host-side stand-in, so the address is looked up with the device current.  Outside stream
+// capture it is looked up on every call (so it stays right after a cudaDeviceReset, which loads
+// the module afresh) and remembered per device; during capture the remembered address is used,
+// since the lookup may load the module, which a capturing stream does not allow.
+cudaError_t gae_noalloc_scratch(cudaStream_t s, void** out) {
     static std::mutex mu;
     static void* addr[128] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_gae_noalloc_scratch);
         if (e != cudaSuccess) return e;
         addr[dev] = p;
+    } else if (!addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;   // first call on this device inside a capture
     }
     *out = addr[dev];
     return cudaSuccess;

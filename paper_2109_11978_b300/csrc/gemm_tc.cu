@@ -172,25 +172,6 @@ template <int n>
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(n) : "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Multicast form: the box lands at the same shared-memory offset in every CTA of the cluster
-// named by `mask`, and completes bytes on the mbarrier at the same offset in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-
-// Arrives on the mbarrier at the same offset in every CTA of `mask` once this thread's MMAs
-// issued so far have completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"(mask)
-                 : "memory");
-}
-
 // Pair (cta_group::2) forms: the two CTAs of a cluster compute one 256-row tile; the MMA is
 // issued by the even CTA, reads A (128 rows) and half of B from each CTA's shared memory and
 // accumulates each CTA's 128 rows in that CTA's tensor memory.
@@ -405,13 +386,12 @@ struct TileSeq {
     }
 };
 
-// Persistent, warp-specialised GEMM.  Output tiles are grouped into cluster tiles of CM
-// vertically adjacent 128 x BN tiles (same columns, same B tile); cluster tiles are dealt
-// round-robin to the clusters, and CTA r of a cluster computes row tile CM * i + r.  In every K
-// step each CTA loads its own A tile and 1/CM of the shared B tile, multicast to the whole
-// cluster, so the B operand is read from L2 once per cluster instead of once per CTA.  A stage
-// is refilled only after all CM CTAs' MMAs have released it (the MMA commit arrives on every
-// CTA's "empty" barrier).  The TMA warp streams K blocks through a STAGES-deep ring; the MMA warp
+// Persistent, warp-specialised GEMM.  Output tiles are dealt round-robin to the persistent CTAs
+// (one per SM).  In pair mode (PAIR, clusters of CM = 2) two vertically adjacent 128 x BN tiles
+// form one 256-row tile on the cta_group::2 tensor core: CTA r of the pair computes row tile
+// 2 i + r, loads its own A rows and half of the B tile into its own shared memory, and the even
+// CTA issues the MMAs, whose completion arrives on both CTAs' barriers.  No TMA copy is
+// multicast.  The TMA warp streams K blocks through a STAGES-deep ring; the MMA warp
 // accumulates each tile into one of NACC TMEM buffers (NACC x BN = 512 columns, at most 4 buffers)
 // while the sixteen epilogue
 // warps drain the other, so the epilogue of tile i overlaps the MMAs of tile i + 1.  Epilogue
@@ -427,7 +407,7 @@ template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     // PAIR: the cluster's two CTAs run one 256 x BN tile on the pair (cta_group::2) tensor core;
     // each CTA stages its 128 rows of A and half of B, the even CTA issues the MMAs
-    static_assert(!PAIR || CM == 2, "pair mode runs on clusters of two");
+    static_assert(PAIR ? CM == 2 : CM == 1, "clusters of two run the pair MMA only; every other tile is one CTA's");
     static_assert(KS == 1 || (KS == 2 && CM == 1 && !PAIR && BN <= 128), "two-block stages: single CTA, BN <= 128");
     using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>;
     constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
@@ -452,8 +432,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     static_assert((2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    // a multicast instantiation launched without its cluster shape would address CTAs that do
-    // not exist: refuse before touching any barrier
+    // a pair instantiation launched without its cluster shape would address a CTA that does not
+    // exist: refuse before touching any barrier
     if (CM > 1 && cluster_size() != (uint32_t)CM) {
         if (threadIdx.x == 0) set_status(p.status, RL_ERR_STATE);
         return;
@@ -496,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     tc_fence_before();
     __syncthreads();
-    if (CM > 1) cluster_sync_all();    // every CTA's barriers exist before any multicast lands
+    if (CM > 1) cluster_sync_all();    // both CTAs' barriers exist before the pair's copies and commits land
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // set-up done: wait for the preceding kernel's results, let the next kernel's CTAs be placed
@@ -577,24 +557,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         tma_load_2d(sa + 8192, ma, full0 + 8 * s, ay + 64, (kb0 + i) * BK);
                     }
                     if (!B_MN) {
-                        if (CM == 1)
-                            tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
-                        else
-                            tma_load_2d_mc(sa + C::A_BYTES + rank * B_SLICE_ROWS * BK * 2, mb, full0 + 8 * s,
-                                           (kb0 + i) * BK, ni * BN + rank * B_SLICE_ROWS, MC_MASK);
+                        tma_load_2d(sa + C::A_BYTES, mb, full0 + 8 * s, (kb0 + i) * BK, ni * BN);
                     } else if (mn3) {
                         tma_load_3d(sa + C::A_BYTES, mb, full0 + 8 * s, 0, (kb0 + i) * BK, ni * BN / 64);
                     } else {
-                        // [K][N] source: boxes of 64 N columns x 64 K rows, this CTA's share
+                        // [K][N] source: boxes of 64 N columns x 64 K rows
 #pragma unroll
-                        for (int j = 0; j < B_BOXES; ++j) {
-                            const int box = rank * B_BOXES + j;
-                            if (CM == 1)
-                                tma_load_2d(sa + C::A_BYTES + 8192 * box, mb, full0 + 8 * s, ni * BN + 64 * box, (kb0 + i) * BK);
-                            else
-                                tma_load_2d_mc(sa + C::A_BYTES + 8192 * box, mb, full0 + 8 * s, ni * BN + 64 * box,
-                                               (kb0 + i) * BK, MC_MASK);
-                        }
+                        for (int j = 0; j < B_BOXES; ++j)
+                            tma_load_2d(sa + C::A_BYTES + 8192 * j, mb, full0 + 8 * s, ni * BN + 64 * j, (kb0 + i) * BK);
                     }
                 }
             }
@@ -675,8 +645,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
                             mma_bf16(d, ad + KSTEP_A * kk, bd + KSTEP_B * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                        if (CM == 1) mma_commit(empty0 + 8 * s);
-                        else mma_commit_mc(empty0 + 8 * s, MC_MASK);
+                        mma_commit(empty0 + 8 * s);
                     }
                 }
                 // arrives when every MMA issued so far has completed (pair: in both CTAs)
@@ -932,13 +901,14 @@ struct ClusterFit {
 static ClusterFit g_fit[64];
 
 static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 2 : -1; }
-static int cm_index(int cm) { return cm == 1 ? 0 : cm == 2 ? 1 : cm == 4 ? 2 : -1; }
+// cluster modes of the ABI: 1 single CTA (and 4, its two-K-block form), 3 the cta_group::2 pair
+static int cm_index(int cm) { return cm == 1 || cm == 4 ? 0 : cm == 3 ? 2 : -1; }
 
 template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
 constexpr int smem_of() {
     return TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>::SMEM;
 }
-// slot of the cluster-fit table: 0 single CTA, 1 cluster of two (multicast), 2 pair
+// slot of the cluster-fit table: 0 single CTA, 2 pair (slot 1 unused)
 template <int CM, bool PAIR>
 constexpr int fit_slot() {
     return PAIR ? 2 : (CM == 1 ? 0 : 1);
@@ -1019,10 +989,7 @@ cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
     }
     if (p.cm == 2 && p.pair) {
         if constexpr (BN >= 128) return launch_cfg<BN, EPI, 2, MJ, true>(p, s);
-        return cudaErrorInvalidValue;
     }
-    if (p.cm == 2 && (MJ == MAJ_K || BN >= 128))
-        return launch_cfg<BN, EPI, 2, (MJ == MAJ_K || BN >= 128) ? MJ : MAJ_K, false>(p, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1054,12 +1021,9 @@ cudaError_t prepare_form(int dev) {
     cudaError_t e = cudaSuccess;
     e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false>(dev);
     e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ, false>(dev);
     e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ, false>(dev);
-    e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, false>(dev);
     e = e != cudaSuccess ? e : set_attr<128, EPI, 2, MJ, true>(dev);
     e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, true>(dev);
-    if (MJ == MAJ_K) e = e != cudaSuccess ? e : set_attr<64, EPI, 2, MAJ_K, false>(dev);
     e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 2>(dev);
     e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 2>(dev);
     return e;
@@ -1073,6 +1037,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.cm != 1 && p.cm != 2) return cudaErrorInvalidValue;
     if (p.mn != MAJ_K && p.mn != MAJ_MN && p.mn != MAJ_B_MN) return cudaErrorInvalidValue;
     if (p.pair && (p.cm != 2 || p.bn < 128)) return cudaErrorInvalidValue;
+    if (p.cm == 2 && !p.pair) return cudaErrorInvalidValue;     // clusters of two run the pair MMA only
     if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
     if (p.mn3 && (p.cm != 1 || p.pair || p.ks == 2 || p.mn == MAJ_K)) return cudaErrorInvalidValue;
     if (p.epi == EPI_ELU_GRAD) {
@@ -1199,7 +1164,7 @@ cudaError_t tc_prepare() {
 int tc_cluster_fit(int bn, int epi, int cm) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    const int bi = bn_index(bn), ci = cm_index(cm);   // cm 4: the pair slot
+    const int bi = bn_index(bn), ci = cm_index(cm);
     if (bi < 0 || ci < 0 || epi < 0 || epi > 2) return 0;
     return g_fit[dev].clusters[bi][epi][ci];
 }

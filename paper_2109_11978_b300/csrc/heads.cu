@@ -351,6 +351,10 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
             else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
             sc[SC_ALPHA] = alpha;
         }
+        if (p.trace) {
+            p.trace[0] = kl;
+            p.trace[1] = alpha;
+        }
         // Adam step count and bias corrections for the step that follows, once per minibatch:
         // 1 - beta^t = -expm1(t log1p(-(1 - beta))), accurate to a few ulp for every t
         const float t = sc[SC_STEP] + 1.f;

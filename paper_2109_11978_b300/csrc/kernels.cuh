@@ -11,7 +11,7 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
                        int normalize, float* adv_stats, float* partials, int nparts, cudaStream_t s);
 int gae_num_partials(int T, int N);
 int gae_noalloc_max_envs();
-cudaError_t gae_noalloc_scratch(void** out);
+cudaError_t gae_noalloc_scratch(cudaStream_t s, void** out);
 
 // ------------------------------------------------------------------ SIMT FP32 GEMM
 // C[m][n] = sum_k A(m,k) B(n,k);  A(m,k) = a_t ? A[k*lda+m] : A[m*lda+k];
@@ -71,6 +71,7 @@ struct HeadParams {
     float* scal;                 // device scalars (alpha, KL, ...)
     float* stats;                // [RL_NSTATS] accumulators (optional)
     float kl_target, lr_min, lr_max;
+    float* trace;                // optional: [2] = this minibatch's KL and alpha after Algorithm 1
 };
 // Per-block partial layout of the loss head (floats): Wa grad [A*H], ba [A], log_std [A], Wc grad
 // [H], bc [1], db_a [H], db_c [H], stats [8]; every field starts on a 16-byte boundary so Adam
@@ -190,9 +191,10 @@ constexpr int REC_LD = 32;
 cudaError_t launch_pack_records(int B, int A, const float* a_old, const float* mu_old, const float* logp_old,
                                 const float* adv, const float* v_old, const float* ret, float* rec, cudaStream_t s);
 // Minibatch indices: permutation of [0, B) by a cycle-walking Feistel network keyed by
-// (seed, iteration, epoch); idx [epochs][B].
+// (seed, iteration, epoch); idx [epochs][B]; a walk that runs out of its bound records
+// RL_ERR_STATE in *status.
 cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned long long* iteration,
-                               int* idx, cudaStream_t s);
+                               int* idx, int* status, cudaStream_t s);
 cudaError_t launch_small(int op, float* scal, unsigned long long* iteration, const float* stats_src,
                          float* stats_dst, float nsamp, cudaStream_t s);
 // Statistics accumulator layout (floats): [0] loss, [1] surrogate, [2] value loss, [3] entropy,

@@ -566,6 +566,10 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
             else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
             sc[SC_ALPHA] = alpha;
         }
+        if (p.trace) {
+            p.trace[0] = kl;
+            p.trace[1] = alpha;
+        }
         const float t = step + 1.f;
         sc[SC_STEP] = t;
         const float bc1 = -expm1f(t * log1pf(-0.1f));

@@ -64,6 +64,7 @@ struct rl_ctx {
     int gae_nparts = 0;
     // update workspaces
     int* perm = nullptr;
+    float* trace = nullptr;                      // per minibatch of the last update: KL, alpha after Algorithm 1
     int* iota = nullptr;
     float* logstd_old = nullptr;
     void* X0 = nullptr;                          // the current minibatch's observations (= X0buf[xcur])
@@ -89,8 +90,8 @@ struct rl_ctx {
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
     int bn_fwd[4], bn_dx[4], bn_dw[4], bn_act[4];
-    // cluster mode per site: 1 single CTA, 2 pairs of row tiles sharing the B tile (multicast),
-    // 3 pairs of CTAs running one 256-row tile on the cta_group::2 MMA (half of B each)
+    // cluster mode per site: 1 single CTA, 3 pairs of CTAs running one 256-row tile on the
+    // cta_group::2 MMA (half of B each), 4 single CTA with two K blocks per pipeline stage
     int cm_fwd[4], cm_dx[4], cm_dw[4], cm_act[4];
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
     CUtensorMap tm_actB[2][4];                   // forward B maps of the rollout's policy inference
@@ -200,13 +201,13 @@ struct Enq {
     }
 };
 
-// Tile modes of a GEMM site: 1 one CTA per tile, 2 pairs of row tiles sharing the B tile (TMA
-// multicast), 3 pairs of CTAs on one 256-row tile (cta_group::2), 4 one CTA per tile with two K
-// blocks per pipeline stage (bn <= 128).
+// Tile modes of a GEMM site: 1 one CTA per tile, 3 pairs of CTAs on one 256-row tile
+// (cta_group::2), 4 one CTA per tile with two K blocks per pipeline stage (bn <= 128).  (Mode 2,
+// pairs of row tiles sharing the B tile by TMA multicast, is not offered.)
 // B rows one CTA loads per K step for a K-major B (tile width bn, mode cm)
-uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 || cm == 2 ? bn / 2 : bn); }
+uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 ? bn / 2 : bn); }
 void set_cluster(TcParams& tp, int cm) {
-    tp.cm = (cm == 2 || cm == 3) ? 2 : 1;
+    tp.cm = cm == 3 ? 2 : 1;
     tp.pair = cm == 3 ? 1 : 0;
     tp.ks = cm == 4 ? 2 : 1;
 }
@@ -457,8 +458,8 @@ EnvParams env_params(rl_ctx* c) {
 // X0 must already hold the minibatch observations.
 rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const float* a_old, const float* logp_old,
                             const float* mu_old, const float* log_std_old, const float* v_old, const float* adv,
-                            const float* ret, bool step, const float* rec = nullptr, bool overlap_dw = false,
-                            cudaEvent_t before_loss = nullptr) {
+                            const float* ret, float clip, bool step, const float* rec = nullptr, bool overlap_dw = false,
+                            cudaEvent_t before_loss = nullptr, float* trace = nullptr) {
     rl_status st = forward_hidden(c, q, c->X0, M, 0, 2, false);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, M);
@@ -473,7 +474,8 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.v_old = v_old;
     h.adv = adv;
     h.ret = ret;
-    h.clip = c->cfg.clip;
+    h.clip = clip;
+    h.trace = trace;
     h.value_coef = c->cfg.value_coef;
     h.entropy_coef = c->cfg.entropy_coef;
     h.dya = c->dY[0][l];
@@ -621,14 +623,14 @@ rl_status refresh_bf16(rl_ctx* c, cudaStream_t s) {
 }
 
 rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
-                      const float* val_old, const float* adv, const float* ret, int epochs, int minibatches, float* stats_out,
-                      bool perm_on_side) {
+                      const float* val_old, const float* adv, const float* ret, int epochs, int minibatches, float clip,
+                      float* stats_out, bool perm_on_side) {
     const int B = c->B, Mb = B / minibatches;
     if (Mb != c->Mb || epochs > c->cfg.epochs) return RL_ERR_INVALID_ARG;
     cudaStream_t s = q.s;
     CK(cudaMemcpyAsync(c->logstd_old, c->params + c->logstd, sizeof(float) * c->A, cudaMemcpyDeviceToDevice, s));
     if (!perm_on_side)
-        CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, s); }));
+        CK(q.run(RL_PROF_OTHER, 1, [&] { return launch_permutation(B, epochs, c->cfg.seed, c->iter, c->perm, c->status, s); }));
     // the BF16 loss head reads each row's loss inputs from one packed 128-byte record per sample
     // (one line per row of a shuffled minibatch instead of one per field); the records are packed
     // on the side stream, beside the first minibatch's gather and forward, when the shuffle ran there
@@ -669,8 +671,9 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
                 CK(cudaEventRecord(c->ev_join[nxt], c->side));
             }
         }
-        rl_status st = minibatch_fwd_bwd(c, q, Mb, mb_idx(k), actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, true,
-                                         c->bf16 ? c->recs : nullptr, overlap, k == 0 && pack_on_side ? c->ev_pack_join : nullptr);
+        rl_status st = minibatch_fwd_bwd(c, q, Mb, mb_idx(k), actions, logp_old, mu_old, c->logstd_old, val_old, adv, ret, clip,
+                                         true, c->bf16 ? c->recs : nullptr, overlap,
+                                         k == 0 && pack_on_side ? c->ev_pack_join : nullptr, c->trace + 2 * k);
         if (st != RL_OK) return st;
         c->adam.grad_out = nullptr;
         CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
@@ -725,7 +728,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
     if (perm_on_side) {
         CK(cudaEventRecord(c->ev_perm_fork, s));
         CK(cudaStreamWaitEvent(c->side, c->ev_perm_fork, 0));
-        CK(launch_permutation(c->B, c->cfg.epochs, c->cfg.seed, c->iter, c->perm, c->side));
+        CK(launch_permutation(c->B, c->cfg.epochs, c->cfg.seed, c->iter, c->perm, c->status, c->side));
         ++c->launches;
         CK(cudaEventRecord(c->ev_perm_join, c->side));
     }
@@ -736,7 +739,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
                           c->scal + SC_ADV_MEAN, c->gae_ws, c->gae_nparts, s);
     }));
     st = update_impl(c, q, c->obs, c->actions, c->logp, c->mu, c->values, c->adv, c->ret, c->cfg.epochs, c->cfg.minibatches,
-                     c->stats, perm_on_side);
+                     c->cfg.clip, c->stats, perm_on_side);
     if (st != RL_OK) return st;
     CK(cudaMemcpyAsync(obs, obs + c->T * obs_step, obs_step, cudaMemcpyDeviceToDevice, s));
     return RL_OK;
@@ -795,7 +798,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
         trials += buf;
     };
     const int bns[3] = {64, 128, 256};
-    const int cms[4] = {1, 2, 3, 4};
+    const int cms[3] = {1, 3, 4};
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
         const int row_tiles = (c->Mb + 127) / 128;
@@ -805,7 +808,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
             float best = 1e30f;
             for (int bn : bns)
                 for (int cm : cms) {
-                    if (Li.out % bn || ((cm == 2 || cm == 3) && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128) ||
+                    if (Li.out % bn || (cm == 3 && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128) ||
                         st != RL_OK)
                         continue;
                     c->bn_fwd[l] = bn;
@@ -826,7 +829,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 float abest = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.out % bn || ((cm == 2 || cm == 3) && act_tiles < 2) || (cm == 3 && bn < 128) ||
+                        if (Li.out % bn || (cm == 3 && act_tiles < 2) || (cm == 3 && bn < 128) ||
                             (cm == 4 && bn > 128) || st != RL_OK)
                             continue;
                         c->bn_act[l] = bn;
@@ -848,7 +851,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 best = 1e30f;
                 for (int bn : bns)
                     for (int cm : cms) {
-                        if (Li.in % bn || ((cm == 2 || cm == 3) && (row_tiles < 2 || bn < 128)) || (cm == 4 && bn > 128) ||
+                        if (Li.in % bn || (cm == 3 && (row_tiles < 2 || bn < 128)) || (cm == 4 && bn > 128) ||
                             st != RL_OK)
                             continue;
                         c->bn_dx[l] = bn;
@@ -874,7 +877,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
                 for (int cm : cms) {
-                    if ((cm == 2 || cm == 3) && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
+                    if (cm == 3 && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
                     if (cm == 4 && (!c->bf16 || bn > 128)) continue;
                     // split counts: one or two waves of this width's tiles over the SMs, and the
                     // default's half and double
@@ -925,7 +928,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     cudaEventDestroy(e1);
     report += "], \"trials_site_layer_bn_cluster_splits_us\": [" + trials + "]";
     if (c->bf16) {
-        std::snprintf(buf, sizeof(buf), ", \"clusters_of_2_resident\": %d", tc_cluster_fit(256, EPI_BIAS_ELU, 2));
+        std::snprintf(buf, sizeof(buf), ", \"pairs_resident\": %d", tc_cluster_fit(256, EPI_BIAS_ELU, 3));
         report += buf;
     }
     report += "}";
@@ -935,13 +938,15 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     return RL_OK;
 }
 
-rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
+// Checks a tile shape for one GEMM site without applying it; on success *kc_out / *S_out hold the
+// weight-gradient K chunk and split count it implies (the current ones for the other sites).
+rl_status check_tiles(const rl_ctx* c, int site, int l, int bn, int cm, int splits, int* kc_out, int* S_out) {
     if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
-    if ((bn != 64 && bn != 128 && bn != 256) || cm < 1 || cm > 4) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 3 && cm != 4)) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
     const int width = (site == 0 || site == 3) ? Li.out : Li.in;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
-    const bool paired = cm == 2 || cm == 3;
+    const bool paired = cm == 3;
     if (width % bn || (paired && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128)) return RL_ERR_INVALID_ARG;
     if ((site == 1 || site == 2) && paired && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
@@ -951,6 +956,15 @@ rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits)
         kc = (kc + 63) / 64 * 64;
         Sr = (c->Mb + kc - 1) / kc;
     }
+    *kc_out = kc;
+    *S_out = Sr;
+    return RL_OK;
+}
+
+rl_status set_tiles_impl(rl_ctx* c, int site, int l, int bn, int cm, int splits) {
+    int kc = 0, Sr = 0;
+    const rl_status chk = check_tiles(c, site, l, bn, cm, splits, &kc, &Sr);
+    if (chk != RL_OK) return chk;
     int* const bnp[4] = {c->bn_fwd, c->bn_dx, c->bn_dw, c->bn_act};
     int* const cmp[4] = {c->cm_fwd, c->cm_dx, c->cm_dw, c->cm_act};
     const int old_bn = bnp[site][l], old_cm = cmp[site][l];
@@ -1173,6 +1187,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(dalloc(c, &c->gae_ws, rl_gae_workspace_bytes(c->T, c->N)));
     // update workspaces
     CK(dalloc(c, &c->perm, sizeof(int) * (size_t)g.epochs * c->B));
+    CK(dalloc(c, &c->trace, sizeof(float) * 2 * (size_t)g.epochs * g.minibatches));
     CK(dalloc(c, &c->iota, sizeof(int) * (size_t)c->Mb));
     {
         std::vector<int> io(c->Mb);
@@ -1213,12 +1228,12 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         c->bn_fwd[l] = pick_bn(Li.out);
         c->bn_dx[l] = pick_bn(Li.in);
         c->bn_dw[l] = bn;
-        // B-tile multicast across pairs of row tiles wherever there are at least two row tiles
-        c->cm_fwd[l] = (c->bf16 && c->Mb > 128) ? 2 : 1;
+        // one CTA per tile until the autotuner or rl_set_gemm_tiles picks another mode
+        c->cm_fwd[l] = 1;
         c->bn_act[l] = pick_bn(Li.out);
-        c->cm_act[l] = (c->bf16 && c->N > 128) ? 2 : 1;
-        c->cm_dx[l] = (c->bf16 && c->Mb > 128 && c->bn_dx[l] >= 128) ? 2 : 1;
-        c->cm_dw[l] = (c->bf16 && Li.out > 128 && bn >= 128) ? 2 : 1;
+        c->cm_act[l] = 1;
+        c->cm_dx[l] = 1;
+        c->cm_dw[l] = 1;
         for (int n = 0; n < 2; ++n) {
             CK(dalloc(c, &c->gw[n][l], sizeof(float) * (size_t)std::max(S, c->S_cap[l]) * Li.out * Li.in));
             if (l < c->NH - 1) CK(dalloc(c, &c->gb[n][l], sizeof(float) * (size_t)c->gb_parts * Li.out));
@@ -1285,6 +1300,17 @@ rl_status rl_get_params(rl_ctx* c, float* out, void* stream) {
     for (const Seg& sg : c->segs)
         CK(cudaMemcpy2DAsync(out + sg.loff, sizeof(float) * sg.cols_log, c->params + sg.ioff, sizeof(float) * sg.cols_int,
                              sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_get_adam_moments(rl_ctx* c, float* m_out, float* v_out, void* stream) {
+    if (!c || !m_out || !v_out) return RL_ERR_INVALID_ARG;
+    for (const Seg& sg : c->segs) {
+        CK(cudaMemcpy2DAsync(m_out + sg.loff, sizeof(float) * sg.cols_log, c->am + sg.ioff, sizeof(float) * sg.cols_int,
+                             sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, S_(stream)));
+        CK(cudaMemcpy2DAsync(v_out + sg.loff, sizeof(float) * sg.cols_log, c->av + sg.ioff, sizeof(float) * sg.cols_int,
+                             sizeof(float) * sg.cols_log, sg.rows, cudaMemcpyDeviceToDevice, S_(stream)));
+    }
     return RL_OK;
 }
 
@@ -1410,15 +1436,20 @@ rl_status rl_checkpoint_load(rl_ctx* c, const void* src, size_t bytes, void* str
     for (int i = 0; i < CKPT_SEGS; ++i)
         if (h.seg_bytes[i] != sg[i].bytes) return RL_ERR_INVALID_ARG;
     // the GEMM shapes of the saved run: split counts fix the order of the weight-gradient sums,
-    // so the resumed run repeats the saved one bit for bit
-    if (c->bf16)
-        for (int l = 0; l < c->NH && l < 4; ++l)
-            for (int site = 0; site < 4; ++site) {
-                if (site == 1 && l == 0) continue;
-                const int32_t* t = h.tiles[l][site];
-                const rl_status st = set_tiles_impl(c, site, l, t[0], t[1], t[2]);
-                if (st != RL_OK) return st;
-            }
+    // so the resumed run repeats the saved one bit for bit.  Every record is checked before any
+    // is applied, so a damaged image leaves the context as it was.
+    if (c->bf16) {
+        for (int pass = 0; pass < 2; ++pass)
+            for (int l = 0; l < c->NH && l < 4; ++l)
+                for (int site = 0; site < 4; ++site) {
+                    if (site == 1 && l == 0) continue;
+                    const int32_t* t = h.tiles[l][site];
+                    int kc = 0, S = 0;
+                    const rl_status st = pass == 0 ? check_tiles(c, site, l, t[0], t[1], t[2], &kc, &S)
+                                                   : set_tiles_impl(c, site, l, t[0], t[1], t[2]);
+                    if (st != RL_OK) return st;
+                }
+    }
     const uint8_t* in = reinterpret_cast<const uint8_t*>(src) + sizeof(h);
     for (const CkptSeg& x : sg) {
         CK(cudaMemcpyAsync(x.dev, in, x.bytes, cudaMemcpyHostToDevice, S_(stream)));
@@ -1535,7 +1566,7 @@ rl_status rl_gae_noalloc(int32_t T, int32_t N, float gamma, float lam, const flo
     if (N > gae_noalloc_max_envs()) return RL_ERR_INVALID_ARG;
     if (!aligned16(adv_out)) return RL_ERR_ALIGNMENT;
     void* scratch = nullptr;
-    CK(gae_noalloc_scratch(&scratch));
+    CK(gae_noalloc_scratch(S_(stream), &scratch));
     CK(launch_gae(T, N, gamma, lam, rew, val, last_val, done, adv_out, ret_out, normalize, adv_stats_out,
                   reinterpret_cast<float*>(scratch), gae_num_partials(T, N), S_(stream)));
     return RL_OK;
@@ -1543,14 +1574,15 @@ rl_status rl_gae_noalloc(int32_t T, int32_t N, float gamma, float lam, const flo
 
 rl_status rl_ppo_update(rl_ctx* c, const void* obs, const float* actions, const float* logp_old, const float* mu_old,
                         const float* val_old, const float* adv, const float* ret, int32_t epochs, int32_t minibatches,
-                        float* stats_out, void* stream) {
+                        float clip, float* stats_out, void* stream) {
     if (!c || !obs || !actions || !logp_old || !mu_old || !val_old || !adv || !ret) return RL_ERR_INVALID_ARG;
     if (epochs < 1 || minibatches < 1 || c->B % minibatches || c->B / minibatches != c->Mb || epochs > c->cfg.epochs)
         return RL_ERR_INVALID_ARG;
+    if (!(clip > 0.f && clip < 1.f)) return RL_ERR_INVALID_ARG;
     cudaStream_t s = S_(stream);
     CK(launch_small(SMALL_ZERO_STATS, c->scal, c->iter, nullptr, c->acc, 0.f, s));
     Enq q{c, s, false};
-    return update_impl(c, q, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, stats_out, false);
+    return update_impl(c, q, obs, actions, logp_old, mu_old, val_old, adv, ret, epochs, minibatches, clip, stats_out, false);
 }
 
 rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* actions, const float* logp_old,
@@ -1565,7 +1597,8 @@ rl_status rl_ppo_loss_grad(rl_ctx* c, int32_t M, const void* obs, const float* a
     for (int n = 0; n < 2; ++n)          // row tiles past M leave no bias-gradient partial
         for (int l = 0; l + 1 < c->NH; ++l)
             CK(cudaMemsetAsync(c->gb[n][l], 0, sizeof(float) * (size_t)c->gb_parts * c->hid[l], s));
-    rl_status st = minibatch_fwd_bwd(c, q, M, nullptr, actions, logp_old, mu_old, log_std_old, val_old, adv, ret, false);
+    rl_status st = minibatch_fwd_bwd(c, q, M, nullptr, actions, logp_old, mu_old, log_std_old, val_old, adv, ret, c->cfg.clip,
+                                     false);
     if (st != RL_OK) return st;
     AdamParams a = c->adam;
     a.grad_out = c->grad_int;
@@ -1638,6 +1671,8 @@ rl_status rl_get_storage(rl_ctx* c, int32_t which, void** ptr, size_t* bytes) {
         case 10: p = c->ret; b = NT * 4; break;
         case 11: p = c->level; b = (size_t)c->N * 4; break;
         case 12: p = c->stats; b = RL_NSTATS * 4; break;
+        case 13: p = c->perm; b = sizeof(int) * (size_t)c->cfg.epochs * c->B; break;
+        case 14: p = c->trace; b = sizeof(float) * 2 * (size_t)c->cfg.epochs * c->cfg.minibatches; break;
         default: return RL_ERR_INVALID_ARG;
     }
     *ptr = p;
@@ -1717,9 +1752,9 @@ rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const voi
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
     const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
-    const int cm = M > 128 ? 2 : 1;    // pairs of row tiles share the B tile (multicast)
+    const int cm = 1;
     if (!make_tmap_bf16(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128)) return RL_ERR_CUDA;
-    if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)(bn / cm))) return RL_ERR_CUDA;
+    if (!make_tmap_bf16(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)) return RL_ERR_CUDA;
     CK(tc_prepare());
     tp.M = M; tp.N = N; tp.kblocks = (K + 63) / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1; tp.batch = 1;
     tp.bn = bn; tp.cm = cm; tp.epi = EPI_STORE;
@@ -1734,8 +1769,8 @@ rl_status rl_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* At, const
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
     const int bn = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64);
-    const int cm = (M > 128 && bn >= 128) ? 2 : 1;
-    // single CTA per tile with M a multiple of 64: one 3D copy per operand and stage
+    const int cm = 1;
+    // M a multiple of 64: one 3D copy per operand and stage
     tp.mn3 = (cm == 1 && M % 64 == 0) ? 1 : 0;
     if (!(tp.mn3 ? make_tmap_bf16_mn1(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 128)
                  : make_tmap_bf16(&tp.tmA[0], At, (uint64_t)K, (uint64_t)M, (uint64_t)M, 64)))
@@ -1757,17 +1792,17 @@ rl_status rl_gemm_bf16_shape(int32_t M, int32_t N, int32_t K, const void* A, con
     if (operands < 0 || operands > 3) return RL_ERR_INVALID_ARG;
     const bool k2 = operands >= 2;             // two K blocks per stage
     const bool mn = operands == 1 || operands == 3;
-    if ((bn != 64 && bn != 128 && bn != 256) || N % bn || cluster < 1 || cluster > 3) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || N % bn || (cluster != 1 && cluster != 3)) return RL_ERR_INVALID_ARG;
     if (!mn && K % 8) return RL_ERR_INVALID_ARG;
     if (mn && M % 8) return RL_ERR_INVALID_ARG;
-    if ((cluster == 3 || (cluster == 2 && mn)) && bn < 128) return RL_ERR_INVALID_ARG;
+    if (cluster == 3 && bn < 128) return RL_ERR_INVALID_ARG;
     if (k2 && (cluster != 1 || bn > 128 || (!mn && K % 64) || (mn && M % 64))) return RL_ERR_INVALID_ARG;
     if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return RL_ERR_ALIGNMENT;
     TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
     const int cm = cluster == 1 ? 1 : 2;
     const int pair = cluster == 3 ? 1 : 0;
-    const uint32_t brows = pair ? bn / 2 : bn / cm;
+    const uint32_t brows = pair ? bn / 2 : bn;
     if (!mn) {
         const bool ok = k2 ? make_tmap_bf16_k2(&tp.tmA[0], A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128) &&
                                  make_tmap_bf16_k2(&tp.tmB[0], B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)bn)

@@ -26,7 +26,8 @@ __device__ __forceinline__ uint64_t feistel(uint64_t x, uint64_t key, int half) 
     return (L << half) | R;
 }
 
-__global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigned long long* iteration, int* idx) {
+__global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigned long long* iteration, int* idx,
+                                   int* status) {
     pdl_wait();
     pdl_trigger();
     const int e = blockIdx.y;
@@ -35,10 +36,16 @@ __global__ void permutation_kernel(int B, int half, uint64_t seed, const unsigne
     const uint64_t key = rng_key(seed, kStreamPerm, *iteration, (uint64_t)e, 0ull);
     uint64_t y = feistel((uint64_t)i, key, half);
     // A cycle of the permutation of [0, 2^(2h)) that starts in [0, B) returns to [0, B) in at
-    // most 2^(2h) - B + 1 steps; the bound only guards against a corrupted key.
+    // most 2^(2h) - B + 1 steps, so the walk always ends inside the bound; running out of it
+    // would mean a broken network, which is recorded as RL_ERR_STATE (the slot then holds i, an
+    // in-range index, so no later kernel reads outside the batch).
     const uint64_t limit = (1ull << (2 * half)) - (uint64_t)B + 2ull;
     for (uint64_t k = 0; y >= (uint64_t)B && k < limit; ++k) y = feistel(y, key, half);
-    idx[(size_t)e * B + i] = (int)(y < (uint64_t)B ? y : (uint64_t)i);
+    if (y >= (uint64_t)B) {
+        set_status(status, RL_ERR_STATE);
+        y = (uint64_t)i;
+    }
+    idx[(size_t)e * B + i] = (int)y;
 }
 
 // ---------------------------------------------------------------- gather
@@ -243,11 +250,11 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, long long n, __nv_
 }  // namespace
 
 cudaError_t launch_permutation(int B, int epochs, uint64_t seed, const unsigned long long* iteration, int* idx,
-                               cudaStream_t s) {
+                               int* status, cudaStream_t s) {
     int bits = 2;
     while ((1ll << bits) < B) bits += 2;
     dim3 grid((B + 255) / 256, epochs);
-    cudaError_t e = launch_pdl(permutation_kernel, grid, dim3(256), 0, s, B, bits / 2, seed, iteration, idx);
+    cudaError_t e = launch_pdl(permutation_kernel, grid, dim3(256), 0, s, B, bits / 2, seed, iteration, idx, status);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -98,3 +98,28 @@ def test_refuses_foreign_or_damaged_images():
     _equal(before, _snapshot(B))
     for L in (A, B, other):
         L.close()
+
+
+def test_damaged_tile_record_leaves_the_context_as_it_was():
+    """The image's GEMM tile records are all checked before any is applied: an image whose first
+    record asks for another valid shape and whose last record is invalid is refused, and the
+    context keeps its own shapes (its image is unchanged byte for byte)."""
+    w = workload("small_rough", precision=1)
+    A = _learner(w)
+    _run(A, 1)
+    image = api.rl_checkpoint_save(A.ctx)
+    B = _learner(w)
+    before = api.rl_checkpoint_save(B.ctx)
+    tiles = 8 + 4 + 4 + 9 * 8                   # magic, version, segment count, segment sizes
+    rec = lambda layer, site, k: tiles + ((layer * 4 + site) * 3 + k) * 4
+    bad = image.clone()
+    first = bad[rec(0, 0, 0):rec(0, 0, 0) + 4].view(torch.int32)
+    assert int(first[0]) in (64, 128)
+    first[0] = 64 if int(first[0]) == 128 else 128               # another valid width of layer 0's forward
+    last = bad[rec(1, 3, 1):rec(1, 3, 1) + 4].view(torch.int32)
+    last[0] = 2                                                   # cluster mode 2 is not offered
+    with pytest.raises(api.RLError):
+        api.rl_checkpoint_load(B.ctx, bad)
+    assert torch.equal(api.rl_checkpoint_save(B.ctx), before)
+    A.close()
+    B.close()

@@ -243,3 +243,33 @@ def test_minibatches_partition_batch():
     assert np.array_equal(np.sort(np.concatenate(mbs)), np.arange(96))
     other = ppo.minibatch_indices(96, 4, 3, 1, 3)
     assert not np.array_equal(np.concatenate(mbs), np.concatenate(other))
+
+
+def test_loss_and_grad_hand_worked_example():
+    """oracle.ppo.loss_and_grad on the three-sample example worked by hand in
+    tests/golden/ppo_loss_hand.txt: each branch of the clipped surrogate and of the clipped value
+    loss, the entropy bonus with its sign and weight, and the composed loss and head gradients."""
+    t = _read_kv("ppo_loss_hand.txt")
+    O, hidden, A = 2, (4,), 12
+    p = mlp.unflatten(np.zeros(mlp.param_count(O, hidden, A)), O, hidden, A)
+    p["critic"][-1] = (p["critic"][-1][0], np.array([0.5]))
+    obs = np.array([[0.3, -1.0], [2.0, 0.5], [-0.7, 0.1]])
+    actions = np.full((3, A), 0.5)
+    logp = mlp.log_prob(actions, np.zeros((3, A)), p["log_std"])
+    assert np.allclose(logp, t["logp"], rtol=0, atol=1e-12)
+    logp_old = logp - np.array([0.0, 0.5, -0.5])
+    adv = np.array([1.0, 2.0, 1.0])
+    v_old = np.array([0.5, 0.0, 0.0])
+    ret = np.array([1.5, 1.0, 0.0])
+    loss, g, st = ppo.loss_and_grad(p, obs, actions, logp_old, np.zeros((3, A)), np.zeros(A), v_old, adv, ret)
+    for k in ("surrogate", "value_loss", "entropy", "loss", "clip_frac", "kl"):
+        assert abs(st[k] - t[k]) <= 1e-12 * max(1.0, abs(t[k])), (k, st[k], t[k])
+    assert abs(loss - t["loss"]) <= 1e-12
+    assert np.allclose(g["actor"][-1][1], t["grad_actor_bias"], rtol=0, atol=1e-12)
+    assert np.allclose(g["log_std"], t["grad_log_std"], rtol=0, atol=1e-12)
+    assert np.allclose(g["critic"][-1][1], t["grad_critic_bias"], rtol=0, atol=1e-12)
+    for net in ("actor", "critic"):
+        for l, (gw, gb) in enumerate(g[net]):
+            assert not np.any(gw), (net, l)
+            if l < len(g[net]) - 1:
+                assert not np.any(gb), (net, l)
