@@ -114,8 +114,11 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
         const float ls = p.log_std[tid], lso = p.log_std_old[tid];
         cst[tid] = ls;
         cst[16 + tid] = expf(-2.f * ls);
-        cst[32 + tid] = expf(2.f * lso);
-        cst[48 + tid] = lso;
+        // KL(pi_old || pi) per dimension = (ls - lso) + (sigma_old^2 / sigma^2 - 1) / 2 + dm^2 / (2 sigma^2);
+        // its sample-independent part, with d = lso - ls, is expm1(2 d) / 2 - d: written this way it
+        // has no cancellation between terms near 1/2 (the KL of a small policy change is small)
+        const float dls = lso - ls;
+        cst[32 + tid] = 0.5f * expm1f(2.f * dls) - dls;
     }
     // stage the rows (coalesced 4-byte words)
     {
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
                 diff[j] = __ldg(p.a_old + (size_t)s * A + j) - mu[j];
                 logp += -0.5f * diff[j] * diff[j] * iv - ls - HALF_LOG_2PI;
                 const float dm = __ldg(p.mu_old + (size_t)s * A + j) - mu[j];
-                kl += ls - cst[48 + j] + 0.5f * (cst[32 + j] + dm * dm) * iv - 0.5f;
+                kl += cst[32 + j] + 0.5f * dm * dm * iv;
             }
         }
         const float lpo = live ? __ldg(p.logp_old + s) : 0.f;

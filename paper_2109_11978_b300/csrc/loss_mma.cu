@@ -189,8 +189,11 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
         const float ls = p.log_std[tid], lso = p.log_std_old[tid];
         cst[tid] = ls;
         cst[16 + tid] = expf(-2.f * ls);
-        cst[32 + tid] = expf(2.f * lso);
-        cst[48 + tid] = lso;
+        // KL(pi_old || pi) per dimension = (ls - lso) + (sigma_old^2 / sigma^2 - 1) / 2 + dm^2 / (2 sigma^2);
+        // its sample-independent part, with d = lso - ls, is expm1(2 d) / 2 - d: written this way it
+        // has no cancellation between terms near 1/2 (the KL of a small policy change is small)
+        const float dls = lso - ls;
+        cst[32 + tid] = 0.5f * expm1f(2.f * dls) - dls;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
                 diff[j] = aold[j] - mu[j];
                 logp += -0.5f * diff[j] * diff[j] * iv - ls - HALF_LOG_2PI;
                 const float dm = muold[j] - mu[j];
-                kl += ls - cst[48 + j] + 0.5f * (cst[32 + j] + dm * dm) * iv - 0.5f;
+                kl += cst[32 + j] + 0.5f * dm * dm * iv;
             }
         }
         const float inv_M = 1.0f / (float)p.M;

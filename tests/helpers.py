@@ -9,13 +9,6 @@ TOL_FP32 = 1e-5
 TOL_BF16 = 2e-2
 
 
-def rel_err2(x, ref):
-    """Norm-wise relative error in the 2-norm: |x - ref|_2 / |ref|_2."""
-    x = np.asarray(x, np.float64)
-    ref = np.asarray(ref, np.float64)
-    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-30)) if ref.size else 0.0
-
-
 def rel_err(x, ref):
     x = np.asarray(x, np.float64)
     ref = np.asarray(ref, np.float64)

@@ -55,7 +55,7 @@ def test_autograd_function_returns_the_library_gradient():
                          d["adv"], d["ret"], g_lib, stats)
     torch.cuda.synchronize()
     assert torch.equal(g_auto, g_lib)
-    assert float(loss) == float(stats[0])
+    assert float(loss.detach()) == float(stats[0])
     pr = OM.unflatten(params, O, w["hidden"], 12)
     lref, g, _ = OP.loss_and_grad(pr, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
                                   b["v_old"], b["adv"], b["ret"])

@@ -2,9 +2,9 @@
 whole training iteration against the FP64 oracle.
 
 FP32 form: 1e-5 relative (|x - ref|_inf / |ref|_inf per tensor) for mu, V, log pi, actions, loss
-terms and every gradient tensor.  BF16 form (bf16 GEMM operands, FP32 accumulation): 2e-2, in the
-same max-norm for the forward outputs and in the 2-norm (|g - ref|_2 / |ref|_2 per tensor) for
-the gradients; the max-norm error of the bf16 gradients is bounded at 5e-2 as well.
+terms and every gradient tensor.  BF16 form (bf16 GEMM operands, FP32 accumulation): 2e-2 in the
+same max-norm, for the forward outputs and for every gradient tensor (on a minibatch kept away from
+the clip kinks, where only rounding separates the two paths).
 Adam after one step is -alpha g / (|g| + eps), i.e. alpha times the sign of g for all but the
 smallest gradients: elements whose oracle gradient exceeds 1e-3 of the tensor's largest must
 match to 1e-5 alpha, every other element must stay within the step bound alpha.
@@ -18,8 +18,8 @@ from oracle import mlp as OM
 from oracle import ppo as OP
 from oracle.train import Learner as OLearner
 from paper_2109_11978_b300 import api
-from tests.gpu_helpers import _batch, _own_old_policy, _per_tensor_err, _segments, _setup
-from tests.helpers import TOL_BF16, TOL_FP32, oracle_env_config, oracle_ppo_config, rel_err, rel_err2, workload
+from tests.gpu_helpers import _batch, _obs, _own_old_policy, _per_tensor_err, _segments, _setup
+from tests.helpers import TOL_BF16, TOL_FP32, oracle_env_config, oracle_ppo_config, rel_err, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -71,12 +71,9 @@ def test_ppo_loss_grad(name, form):
                                 b["v_old"], b["adv"], b["ret"])
     gref = OP.flat_grad(g)
     tol = TOL_FP32 if prec == 0 else TOL_BF16
-    errs = _per_tensor_err(grad.cpu().numpy(), gref, (O, w["hidden"], 12), rel_err if prec == 0 else rel_err2)
+    errs = _per_tensor_err(grad.cpu().numpy(), gref, (O, w["hidden"], 12), rel_err)
     bad = {k: e for k, e in errs.items() if e >= tol}
     assert not bad, (bad, errs)
-    if prec == 1:
-        emax = _per_tensor_err(grad.cpu().numpy(), gref, (O, w["hidden"], 12), rel_err)
-        assert max(emax.values()) < 5e-2, emax
     s = stats.cpu().numpy()
     for i, k in ((0, "loss"), (1, "surrogate"), (2, "value_loss"), (3, "entropy")):
         assert abs(s[i] - st[k]) <= tol * max(1.0, abs(st[k])), (k, s[i], st[k])
@@ -218,9 +215,9 @@ def test_autotune_keeps_results(form):
     _, g, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
                                b["v_old"], b["adv"], b["ret"])
     gref = OP.flat_grad(g)
-    measure, tol = (rel_err, TOL_FP32) if prec == 0 else (rel_err2, TOL_BF16)
+    tol = TOL_FP32 if prec == 0 else TOL_BF16
     for gg in (g0, g1):
-        errs = _per_tensor_err(gg, gref, (O, w["hidden"], 12), measure)
+        errs = _per_tensor_err(gg, gref, (O, w["hidden"], 12), rel_err)
         assert max(errs.values()) < tol, errs
     L.train_iteration(use_graph=True)          # the graph is re-captured with the tuned shapes
     torch.cuda.synchronize()
@@ -273,7 +270,7 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
     p = OM.unflatten(params, O, hidden, 12)
     _, gr, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
                                 b["v_old"], b["adv"], b["ret"])
-    errs = _per_tensor_err(g.cpu().numpy(), OP.flat_grad(gr), (O, hidden, 12), rel_err2)
+    errs = _per_tensor_err(g.cpu().numpy(), OP.flat_grad(gr), (O, hidden, 12), rel_err)
     assert max(errs.values()) < TOL_BF16, errs
     L.train_iteration(use_graph=True)
     torch.cuda.synchronize()
