@@ -6,9 +6,9 @@
 // the whole per-sample state (mu, V, ratio, gradients) and the backward into the hidden layer
 // is written back coalesced.  Reductions over the minibatch (head weight / bias gradients,
 // log-std gradient, bias gradient of the last hidden layer, loss terms, KL) accumulate per
-// warp in registers, then per block in shared memory, then as one partial per block; the
-// last block to finish (a counter, no spin-wait) reduces the statistics, takes the KL mean and
-// applies Algorithm 1 to the device-side learning rate before Adam runs.
+// warp in registers, then per block in shared memory, then as one partial per block;
+// loss_stats_kernel then reduces the statistics, takes the KL mean and applies Algorithm 1 to the
+// device-side learning rate before Adam runs.
 #include <type_traits>
 
 #include "act_row.cuh"
@@ -73,8 +73,7 @@ struct LossShape {
     static constexpr int QW = NT / H;              // threads per hidden unit in the weight gradient
     static constexpr int FWD = (LH_TPR - 1) * LR * LH_GP;   // forward partials of quarters 1..3
     static constexpr int WG = (QW - 1) * H * LH_GP;          // weight-gradient partials of ranges 1..
-    static constexpr int LAST = 4 * NT;                      // last block's statistics
-    static constexpr int SCR = FWD > WG ? (FWD > LAST ? FWD : LAST) : (WG > LAST ? WG : LAST);
+    static constexpr int SCR = FWD > WG ? FWD : WG;
     // floats: WaT, Wc, constants, g rows, records, scratch
     static constexpr int FLOATS = H * MAX_A + H + 64 + LR * LH_GP + LR * LH_RP + SCR;
     static_assert(NT % H == 0 && QW >= 1 && LR % QW == 0, "loss head shape");
@@ -312,66 +311,7 @@ __global__ void __launch_bounds__(LR * LH_TPR, 2) loss_head_kernel(HeadParams p)
             }
     }
 
-    // Last block: statistics, KL mean and Algorithm 1 on the device learning rate.
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // One warp: each lane sums every 32nd block's statistics, then a fixed xor tree (float64
-    // adds are slow on this part, so the chain is kept short: ceil(blocks / 32) + 5 adds).
-    if (warp != 0) return;
-    double st[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-        const float* q = p.part + (size_t)b * PF + O_ST;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) st[i] += (double)__ldcg(q + i);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) st[i] += __shfl_xor_sync(0xffffffffu, st[i], o);
-    if (lane == 0) {
-        const float inv_M = 1.0f / (float)p.M;
-        float ent = 0.f;
-        for (int j = 0; j < A; ++j) ent += cst[j] + HALF_LOG_2PI + 0.5f;
-        const float kl = (float)st[2] * inv_M;
-        const float surr = -(float)st[0] * inv_M, vloss = (float)st[1] * inv_M;
-        const float loss = surr + p.value_coef * vloss - p.entropy_coef * ent;
-        float* sc = p.scal;
-        sc[SC_KL] = kl;
-        sc[SC_LOSS] = loss;
-        sc[SC_SURR] = surr;
-        sc[SC_VLOSS] = vloss;
-        sc[SC_ENT] = ent;
-        sc[SC_CLIPFRAC] = (float)st[3] * inv_M;
-        float alpha = sc[SC_ALPHA];
-        if (p.kl_target > 0.f) {
-            // Algorithm 1 (App. A.4)
-            if (kl > 2.f * p.kl_target) alpha = fmaxf(p.lr_min, alpha / 1.5f);
-            else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
-            sc[SC_ALPHA] = alpha;
-        }
-        if (p.trace) {
-            p.trace[0] = kl;
-            p.trace[1] = alpha;
-        }
-        // Adam step count and bias corrections for the step that follows, once per minibatch:
-        // 1 - beta^t = -expm1(t log1p(-(1 - beta))), accurate to a few ulp for every t
-        const float t = sc[SC_STEP] + 1.f;
-        sc[SC_STEP] = t;
-        const float bc1 = -expm1f(t * log1pf(-0.1f));      // beta1 = 0.9
-        const float bc2 = -expm1f(t * log1pf(-0.001f));    // beta2 = 0.999
-        sc[SC_STEPSIZE] = alpha / bc1;
-        sc[SC_INVSQRT_BC2] = 1.0f / sqrtf(bc2);
-        if (p.stats) {
-            p.stats[0] += loss; p.stats[1] += surr; p.stats[2] += vloss; p.stats[3] = ent;
-            p.stats[4] += kl; p.stats[5] = sc[SC_ALPHA]; p.stats[6] += sc[SC_CLIPFRAC]; p.stats[12] += 1.f;
-        }
-        *p.counter = 0u;
-    }
+    // the minibatch statistics and Algorithm 1 follow in loss_stats_kernel
 }
 
 }  // namespace
@@ -439,7 +379,9 @@ int loss_head_blocks(int M, int H, int bf16) {
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s) {
     if (p.M <= 0) return cudaSuccess;
     if (p.A > MAX_A || !(p.H == 64 || p.H == 128 || p.H == 256)) return cudaErrorInvalidValue;
-    if (p.nblocks != loss_head_blocks(p.M, p.H, p.bf16)) return cudaErrorInvalidValue;
+    // blocks past the rows leave zero partials, so a launch may have more blocks than its rows
+    // need (the context sizes them for the full minibatch)
+    if (p.nblocks < loss_head_blocks(p.M, p.H, p.bf16)) return cudaErrorInvalidValue;
     if (p.bf16) return launch_loss_mma(p, s);    // tensor-core form (loss_mma.cu)
     if (p.H == 64) return loss_dispatch<false, 64, 128>(p, s);
     if (p.H == 128) return loss_dispatch<false, 128, 128>(p, s);

@@ -67,7 +67,6 @@ struct HeadParams {
     void* dyc;                   // critic
     float* part;                 // per-block partials, layout HEAD_PART_* below
     int nblocks;
-    unsigned int* counter;       // last-block counter (zero at rest)
     float* scal;                 // device scalars (alpha, KL, ...)
     float* stats;                // [RL_NSTATS] accumulators (optional)
     float kl_target, lr_min, lr_max;
@@ -128,6 +127,9 @@ cudaError_t env_prepare();
 
 cudaError_t launch_act_head(const HeadParams& p, cudaStream_t s);
 cudaError_t launch_loss_head(const HeadParams& p, cudaStream_t s);
+// The minibatch statistics of a loss-head launch (its partials), Algorithm 1 and Adam's step size
+// and bias corrections (loss_stats.cu); one block, run after the loss head.
+cudaError_t launch_loss_stats(const HeadParams& p, cudaStream_t s);
 int loss_head_blocks(int M, int H, int bf16);   // blocks (= partial slots) of one loss-head launch
 // BF16 loss head on warp-level tensor-core MMAs (loss_mma.cu)
 int loss_mma_rows();

@@ -11,8 +11,8 @@
 // into a bf16 high part and a bf16 remainder, and the products hi*hi + hi*lo + lo*hi (weights:
 // hi + lo against exact bf16 activations) carry about 16 bits of each operand, which keeps the
 // result at fp32 level.  Per-row work (log pi, ratio, clipping, KL) runs one thread per row in
-// fp32.  The per-block partials and the last block's statistics / Algorithm 1 step follow the
-// same layout and order as the FP32 kernel.
+// fp32.  The per-block partials follow the same layout as the FP32 kernel's; the minibatch
+// statistics and Algorithm 1 run afterwards in loss_stats_kernel.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -92,18 +92,14 @@ struct Smem {
     static constexpr int MU = F0;                             // [ROWS][FP]: mu (12) and V at 12
     static constexpr int REC = MU;                            // [ROWS][RP]
     static constexpr int G = MU + ROWS * FP;                  // [ROWS][FP]: g_mu (12) and g_v at 12
-    // fp32 copies of Wa [A][H] and Wc [H] as loaded, split into the bf16 tiles before the mu /
-    // G rows are first written (they share the area)
-    static constexpr int WST = MU;
-    static constexpr int WST_END = WST + (2 * ROWS * FP > 13 * H ? 2 * ROWS * FP : 13 * H);
-    static constexpr int WCF = WST_END;                       // [H] Wc fp32
+    static constexpr int WCF = G + ROWS * FP;                 // [H] Wc fp32
     static constexpr int CST = WCF + H;                       // [64] log-std constants
     static constexpr int FLOATS = CST + 64;
     static constexpr int BYTES = FLOATS * 4;
 };
 
 template <int H>
-__global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams p) {
+__global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma_kernel(HeadParams p) {
     constexpr int NW = warps_of<H>(), THREADS = 32 * NW;
     pdl_wait();
     pdl_trigger();
@@ -125,52 +121,50 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
     const int m0 = blockIdx.x * ROWS;
     const int rows = max(0, min(ROWS, p.M - m0));
 
-    // ---- per-row inputs of the loss, issued first (their latency overlaps the staging)
-    const bool row_thread = tid < ROWS;
-    const bool live = row_thread && tid < rows;
-    float aold[MAX_A], muold[MAX_A], lpo = 0.f, adv = 0.f, vo = 0.f, R = 0.f;
+    // ---- per-row inputs of the loss, issued first (their latency overlaps the staging): TPR
+    // consecutive threads per row, thread q of a row holding dimensions q, q + TPR, ...
+    constexpr int TPR = THREADS / ROWS;                       // 4 (2 with four warps)
+    constexpr int DPT = MAX_A / TPR;                          // dimensions per thread
+    static_assert(TPR * ROWS == THREADS && DPT * TPR == MAX_A && 32 % TPR == 0, "row threads");
+    const int rr_ = tid / TPR, qq = tid % TPR;                // the thread's row and quarter
+    const bool live = rr_ < rows;
+    float aold[DPT], muold[DPT], lpo = 0.f, adv = 0.f, vo = 0.f, R = 0.f;
 #pragma unroll
-    for (int j = 0; j < MAX_A; ++j) aold[j] = muold[j] = 0.f;
-    if (live && p.rec) {
-        // the sample's packed 128-byte record: one line per row instead of one per field
-        const int m = m0 + tid;
+    for (int u = 0; u < DPT; ++u) aold[u] = muold[u] = 0.f;
+    if (live) {
+        const int m = m0 + rr_;
         const int s = p.idx ? __ldg(p.idx + m) : m;
-        const float4* r4 = reinterpret_cast<const float4*>(p.rec + (size_t)s * p.rec_ld);
-        float f[28];
+        if (p.rec) {
+            // the sample's packed 128-byte record [a_old A][mu_old A][logp_old][adv][V_old][R]
+            const float* rc = p.rec + (size_t)s * p.rec_ld;
 #pragma unroll
-        for (int v = 0; v < 7; ++v) {
-            const float4 x = __ldg(r4 + v);
-            f[4 * v] = x.x; f[4 * v + 1] = x.y; f[4 * v + 2] = x.z; f[4 * v + 3] = x.w;
-        }
-#pragma unroll
-        for (int j = 0; j < MAX_A; ++j)
-            if (j < A) {
-                aold[j] = f[j];
-                muold[j] = f[A + j];
+            for (int u = 0; u < DPT; ++u) {
+                const int jj = qq + TPR * u;
+                if (jj < A) {
+                    aold[u] = __ldg(rc + jj);
+                    muold[u] = __ldg(rc + A + jj);
+                }
             }
-        // the four scalars follow the 2A action fields (A <= 12)
+            lpo = __ldg(rc + 2 * A);
+            adv = __ldg(rc + 2 * A + 1);
+            vo = __ldg(rc + 2 * A + 2);
+            R = __ldg(rc + 2 * A + 3);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 28; ++k) {
-            if (k == 2 * A) lpo = f[k];
-            if (k == 2 * A + 1) adv = f[k];
-            if (k == 2 * A + 2) vo = f[k];
-            if (k == 2 * A + 3) R = f[k];
-        }
-    } else if (live) {
-        const int m = m0 + tid;
-        const int s = p.idx ? __ldg(p.idx + m) : m;
-#pragma unroll
-        for (int j = 0; j < MAX_A; ++j)
-            if (j < A) {
-                aold[j] = __ldg(p.a_old + (size_t)s * A + j);
-                muold[j] = __ldg(p.mu_old + (size_t)s * A + j);
+            for (int u = 0; u < DPT; ++u) {
+                const int jj = qq + TPR * u;
+                if (jj < A) {
+                    aold[u] = __ldg(p.a_old + (size_t)s * A + jj);
+                    muold[u] = __ldg(p.mu_old + (size_t)s * A + jj);
+                }
             }
-        lpo = __ldg(p.logp_old + s);
-        adv = __ldg(p.adv + s);
-        vo = __ldg(p.v_old + s);
-        R = __ldg(p.ret + s);
+            lpo = __ldg(p.logp_old + s);
+            adv = __ldg(p.adv + s);
+            vo = __ldg(p.v_old + s);
+            R = __ldg(p.ret + s);
+        }
     }
-    // ---- stage (asynchronous 16-byte copies): h tiles (zeros past M), fp32 head weights
+    // ---- stage (asynchronous 16-byte copies): h tiles (zeros past M), the critic head's fp32 weights
     {
         const __nv_bfloat16* ga = reinterpret_cast<const __nv_bfloat16*>(p.ha) + (size_t)m0 * H;
         const __nv_bfloat16* gc = reinterpret_cast<const __nv_bfloat16*>(p.hc) + (size_t)m0 * H;
@@ -181,9 +175,32 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
             cp_async16(ha + r * HP + c, ga + (size_t)rr * H + c, r < rows ? 16 : 0);
             cp_async16(hc + r * HP + c, gc + (size_t)rr * H + c, r < rows ? 16 : 0);
         }
-        float* wst = sf + S::WST;
-        for (int v = tid; v < A * H / 4; v += THREADS) cp_async16(wst + 4 * v, p.Wa + 4 * v, 16);
         for (int v = tid; v < H / 4; v += THREADS) cp_async16(wcf + 4 * v, p.Wc + 4 * v, 16);
+    }
+    // head weights -> bf16 hi / lo tiles (Wa rows j >= A and Wc rows 1..7 zero), read straight from
+    // global memory while the row copies are in flight
+    {
+        constexpr int NWA = 16 * H / THREADS;
+#pragma unroll
+        for (int u = 0; u < NWA; ++u) {
+            const int i = tid + u * THREADS;
+            const int j = i / H, k = i % H;
+            const float w = j < A ? __ldg(p.Wa + j * H + k) : 0.f;
+            __nv_bfloat16 hi, lo;
+            split_bf16(w, hi, lo);
+            sb[S::WA_HI + j * HP + k] = hi;
+            sb[S::WA_LO + j * HP + k] = lo;
+            sb[S::WAT_HI + k * GP + j] = hi;
+            sb[S::WAT_LO + k * GP + j] = lo;
+        }
+        for (int i = tid; i < 8 * H; i += THREADS) {
+            const int j = i / H, k = i % H;
+            const float w = j == 0 ? __ldg(p.Wc + k) : 0.f;
+            __nv_bfloat16 hi, lo;
+            split_bf16(w, hi, lo);
+            sb[S::WC_HI + j * HP + k] = hi;
+            sb[S::WC_LO + j * HP + k] = lo;
+        }
     }
     if (tid < A) {
         const float ls = p.log_std[tid], lso = p.log_std_old[tid];
@@ -196,29 +213,6 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
         cst[32 + tid] = 0.5f * expm1f(2.f * dls) - dls;
     }
     cp_async_wait_all();
-    __syncthreads();
-    // weights -> bf16 hi / lo tiles (Wa rows j >= A and Wc rows 1..7 zero)
-    {
-        const float* wst = sf + S::WST;
-        for (int i = tid; i < 16 * H; i += THREADS) {
-            const int j = i / H, k = i % H;
-            const float w = j < A ? wst[j * H + k] : 0.f;
-            __nv_bfloat16 hi, lo;
-            split_bf16(w, hi, lo);
-            sb[S::WA_HI + j * HP + k] = hi;
-            sb[S::WA_LO + j * HP + k] = lo;
-            sb[S::WAT_HI + k * GP + j] = hi;
-            sb[S::WAT_LO + k * GP + j] = lo;
-        }
-        for (int i = tid; i < 8 * H; i += THREADS) {
-            const int j = i / H, k = i % H;
-            const float w = j == 0 ? wcf[k] : 0.f;
-            __nv_bfloat16 hi, lo;
-            split_bf16(w, hi, lo);
-            sb[S::WC_HI + j * HP + k] = hi;
-            sb[S::WC_LO + j * HP + k] = lo;
-        }
-    }
     __syncthreads();
 
     static_assert(FP == RP, "mu rows and records share their rows");
@@ -275,25 +269,31 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
     }
     __syncthreads();
 
-    // ---- per row: loss terms, d loss / d mu and d loss / d V
-    if (row_thread) {
-        const int r = tid;
-        float mu[MAX_A];
+    // ---- per row: loss terms, d loss / d mu and d loss / d V; the row's TPR threads split the
+    // dimensions and combine their sums by xor shuffles inside their group of lanes
+    {
+        const int r = rr_;
+        float logp = 0.f, kl = 0.f, diff[DPT];
 #pragma unroll
-        for (int j = 0; j < MAX_A; ++j) mu[j] = mu_s[r * FP + j] + (j < A ? p.ba[j] : 0.f);
-        const float v = mu_s[r * FP + 12] + p.bc[0];
-        float logp = 0.f, kl = 0.f, diff[MAX_A];
-#pragma unroll
-        for (int j = 0; j < MAX_A; ++j) {
-            diff[j] = 0.f;
-            if (j < A && live) {
-                const float ls = cst[j], iv = cst[16 + j];
-                diff[j] = aold[j] - mu[j];
-                logp += -0.5f * diff[j] * diff[j] * iv - ls - HALF_LOG_2PI;
-                const float dm = muold[j] - mu[j];
-                kl += cst[32 + j] + 0.5f * dm * dm * iv;
+        for (int u = 0; u < DPT; ++u) {
+            const int jj = qq + TPR * u;
+            diff[u] = 0.f;
+            if (jj < A && live) {
+                const float mu = mu_s[r * FP + jj] + p.ba[jj];
+                const float ls = cst[jj], iv = cst[16 + jj];
+                diff[u] = aold[u] - mu;
+                logp += -0.5f * diff[u] * diff[u] * iv - ls - HALF_LOG_2PI;
+                const float dm = muold[u] - mu;
+                kl += cst[32 + jj] + 0.5f * dm * dm * iv;
             }
         }
+#pragma unroll
+        for (int o = 1; o < TPR; o <<= 1) {
+            logp += __shfl_xor_sync(0xffffffffu, logp, o);
+            kl += __shfl_xor_sync(0xffffffffu, kl, o);
+        }
+        const float v = mu_s[r * FP + 12] + p.bc[0];
+        __syncwarp();                   // the row's mu / V are read before its record overwrites them
         const float inv_M = 1.0f / (float)p.M;
         const float ratio = expf(logp - lpo);
         const float s1 = ratio * adv;
@@ -301,33 +301,39 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
         const float g_logp = -(s1 <= s2 ? adv : 0.f) * inv_M * ratio;
         const float dv = v - vo;
         const float vclip = vo + fminf(fmaxf(dv, -p.clip), p.clip);
-        const float u = (v - R) * (v - R), w = (vclip - R) * (vclip - R);
-        float g_v = p.value_coef * inv_M * (u >= w ? 2.f * (v - R) : ((dv > -p.clip && dv < p.clip) ? 2.f * (vclip - R) : 0.f));
+        const float uu = (v - R) * (v - R), w = (vclip - R) * (vclip - R);
+        float g_v = p.value_coef * inv_M * (uu >= w ? 2.f * (v - R) : ((dv > -p.clip && dv < p.clip) ? 2.f * (vclip - R) : 0.f));
         if (!live) g_v = 0.f;
         float* rc = recs + r * RP;
-        rc[0] = live ? fminf(s1, s2) : 0.f;
-        rc[1] = live ? fmaxf(u, w) : 0.f;
-        rc[2] = live ? kl : 0.f;
-        rc[3] = (live && fabsf(ratio - 1.f) > p.clip) ? 1.f : 0.f;
+        if (qq == 0) {
+            rc[0] = live ? fminf(s1, s2) : 0.f;
+            rc[1] = live ? fmaxf(uu, w) : 0.f;
+            rc[2] = live ? kl : 0.f;
+            rc[3] = (live && fabsf(ratio - 1.f) > p.clip) ? 1.f : 0.f;
+        }
+        // G columns c = qq + TPR u: 0..11 d loss / d mu, 12 d loss / d V (the critic's weight
+        // gradient comes out of the same transposed product as row 12 of G^T H_c; Wa has no row 12,
+        // so the actor backward is unaffected), 13..15 zero
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int u = 0; u < 16 / TPR; ++u) {
+            const int c = qq + TPR * u;
             float g = 0.f;
-            if (j < MAX_A) {
-                const float iv = j < A ? cst[16 + j] : 0.f;
-                g = (live && j < A) ? g_logp * diff[j] * iv : 0.f;
-                rc[4 + j] = (live && j < A) ? g_logp * (diff[j] * diff[j] * iv - 1.f) : 0.f;
+            if (u < DPT) {
+                const bool on = live && c < A;
+                const float iv = on ? cst[16 + c] : 0.f;
+                g = on ? g_logp * diff[u] * iv : 0.f;
+                rc[4 + c] = on ? g_logp * (diff[u] * diff[u] * iv - 1.f) : 0.f;
+                g_s[r * FP + c] = g;
             }
-            if (j < 12) g_s[r * FP + j] = g;
-            // column 12 of G carries g_v: the critic's weight gradient comes out of the same
-            // transposed product (row 12 of G^T H_c); Wa has no row 12, so the actor backward
-            // is unaffected
-            if (j == 12) g = g_v;
+            if (c == 12) {
+                g = g_v;
+                g_s[r * FP + 12] = g_v;
+            }
             __nv_bfloat16 hi, lo;
             split_bf16(g, hi, lo);
-            sb[S::G_HI + r * GP + j] = hi;
-            sb[S::G_LO + r * GP + j] = lo;
+            sb[S::G_HI + r * GP + c] = hi;
+            sb[S::G_LO + r * GP + c] = lo;
         }
-        g_s[r * FP + 12] = g_v;
     }
     __syncthreads();
 
@@ -423,13 +429,25 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
                 }
         }
     }
-    // critic: dY_c = g_v Wc * ELU'(H_c), two columns per thread step
-    for (int e2 = tid; e2 < ROWS * H / 2; e2 += THREADS) {
-        const int r = e2 / (H / 2), k = (e2 % (H / 2)) * 2;
+    // critic: dY_c = g_v Wc * ELU'(H_c), eight columns (one 16-byte vector) per thread step
+    static_assert((HP * 2) % 16 == 0 && (S::WCF % 4) == 0, "16-byte rows and weights");
+#pragma unroll 2
+    for (int e8 = tid; e8 < ROWS * H / 8; e8 += THREADS) {
+        const int r = e8 / (H / 8), k = (e8 % (H / 8)) * 8;
         const float gv = g_s[r * FP + 12];
-        __nv_bfloat162* e = reinterpret_cast<__nv_bfloat162*>(hc + r * HP + k);
-        const float2 hv = __bfloat1622float2(*e);
-        *e = __floats2bfloat162_rn(gv * wcf[k] * elu_grad_y(hv.x), gv * wcf[k + 1] * elu_grad_y(hv.y));
+        uint4* e = reinterpret_cast<uint4*>(hc + r * HP + k);
+        const uint4 hv = *e;
+        const float4 w0 = *reinterpret_cast<const float4*>(wcf + k), w1 = *reinterpret_cast<const float4*>(wcf + k + 4);
+        const float wk[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float y0 = __uint_as_float(hw[i] << 16), y1 = __uint_as_float(hw[i] & 0xFFFF0000u);
+            const __nv_bfloat162 d = __floats2bfloat162_rn(gv * wk[2 * i] * elu_grad_y(y0), gv * wk[2 * i + 1] * elu_grad_y(y1));
+            o[i] = *reinterpret_cast<const uint32_t*>(&d);
+        }
+        *e = make_uint4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
 
@@ -492,100 +510,7 @@ __global__ void __launch_bounds__(32 * warps_of<H>()) loss_mma_kernel(HeadParams
         }
     }
 
-    // ---- last block: statistics, KL mean, Algorithm 1, Adam step count and bias corrections
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (warp != 0) return;
-    // the scalars this block updates, read up front so that their latency overlaps the partials'
-    float* sc = p.scal;
-    float alpha = 0.f, step = 0.f, acc[8] = {};
-    if (lane == 0) {
-        alpha = __ldcg(sc + SC_ALPHA);
-        step = __ldcg(sc + SC_STEP);
-        if (p.stats) {
-            acc[0] = p.stats[0]; acc[1] = p.stats[1]; acc[2] = p.stats[2]; acc[3] = p.stats[4];
-            acc[4] = p.stats[6]; acc[5] = p.stats[12];
-        }
-    }
-    // per lane, blocks lane, lane + 32, ... summed in that order, then a fixed xor tree across the
-    // lanes; compensated fp32 sums (Neumaier's two-sum: the rounding error of every addition is
-    // carried in a second float) instead of fp64, whose arithmetic is slow on this part.  Eight
-    // blocks' partials are loaded before any is added, so that the loads overlap.
-    float st[4] = {0.f, 0.f, 0.f, 0.f}, ce[4] = {0.f, 0.f, 0.f, 0.f};
-    auto two_sum = [](float& sum, float& err, float x) {
-        const float t = sum + x;
-        err += fabsf(sum) >= fabsf(x) ? (sum - t) + x : (x - t) + sum;
-        sum = t;
-    };
-    for (int b0 = lane; b0 < (int)gridDim.x; b0 += 32 * 8) {
-        float v[8][4];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int b = b0 + 32 * k;
-            const float* q = p.part + (size_t)(b < (int)gridDim.x ? b : 0) * PF + O_ST;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) v[k][i] = __ldcg(q + i);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (b0 + 32 * k < (int)gridDim.x)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) two_sum(st[i], ce[i], v[k][i]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float os = __shfl_xor_sync(0xffffffffu, st[i], o), oc = __shfl_xor_sync(0xffffffffu, ce[i], o);
-            // the lower lane's value first, so that both partners form the same sum
-            const bool lo = (lane & o) == 0;
-            float a = lo ? st[i] : os, ca = lo ? ce[i] : oc;
-            two_sum(a, ca, lo ? os : st[i]);
-            st[i] = a;
-            ce[i] = ca + (lo ? oc : ce[i]);
-        }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) st[i] += ce[i];
-    if (lane == 0) {
-        const float inv_M = 1.0f / (float)p.M;
-        float ent = 0.f;
-        for (int j = 0; j < A; ++j) ent += cst[j] + HALF_LOG_2PI + 0.5f;
-        const float kl = (float)st[2] * inv_M;
-        const float surr = -(float)st[0] * inv_M, vloss = (float)st[1] * inv_M;
-        const float loss = surr + p.value_coef * vloss - p.entropy_coef * ent;
-        sc[SC_KL] = kl;
-        sc[SC_LOSS] = loss;
-        sc[SC_SURR] = surr;
-        sc[SC_VLOSS] = vloss;
-        sc[SC_ENT] = ent;
-        sc[SC_CLIPFRAC] = (float)st[3] * inv_M;
-        if (p.kl_target > 0.f) {
-            if (kl > 2.f * p.kl_target) alpha = fmaxf(p.lr_min, alpha / 1.5f);
-            else if (kl < 0.5f * p.kl_target) alpha = fminf(p.lr_max, alpha * 1.5f);
-            sc[SC_ALPHA] = alpha;
-        }
-        if (p.trace) {
-            p.trace[0] = kl;
-            p.trace[1] = alpha;
-        }
-        const float t = step + 1.f;
-        sc[SC_STEP] = t;
-        const float bc1 = -expm1f(t * log1pf(-0.1f));
-        const float bc2 = -expm1f(t * log1pf(-0.001f));
-        sc[SC_STEPSIZE] = alpha / bc1;
-        sc[SC_INVSQRT_BC2] = 1.0f / sqrtf(bc2);
-        if (p.stats) {
-            p.stats[0] = acc[0] + loss; p.stats[1] = acc[1] + surr; p.stats[2] = acc[2] + vloss; p.stats[3] = ent;
-            p.stats[4] = acc[3] + kl; p.stats[5] = alpha; p.stats[6] = acc[4] + (float)st[3] * inv_M;
-            p.stats[12] = acc[5] + 1.f;
-        }
-        *p.counter = 0u;
-    }
+    // the minibatch statistics and Algorithm 1 follow in loss_stats_kernel
 }
 
 template <int H>
@@ -599,12 +524,20 @@ cudaError_t mma_dispatch(const HeadParams& p, cudaStream_t s) {
 
 int loss_mma_rows() { return ROWS; }
 
+// Dynamic shared-memory limits, and the whole of the SM's unified L1 / shared memory offered as
+// shared memory, so that three 74 KB blocks of the 128-wide form are resident per SM (one wave
+// for a 24576-row minibatch instead of two).
+template <int H>
+cudaError_t mma_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(loss_mma_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<H>::BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(loss_mma_kernel<H>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
 cudaError_t loss_mma_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(loss_mma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<64>::BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(loss_mma_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(loss_mma_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::BYTES);
+    cudaError_t e = mma_attrs<64>();
+    if (e == cudaSuccess) e = mma_attrs<128>();
+    if (e == cudaSuccess) e = mma_attrs<256>();
     return e;
 }
 

@@ -46,7 +46,6 @@ struct rl_ctx {
     float *params = nullptr, *am = nullptr, *av = nullptr, *grad_int = nullptr;
     float* scal = nullptr;
     unsigned long long* iter = nullptr;
-    unsigned int* counter = nullptr;
     int* status = nullptr;
     float *acc = nullptr, *stats = nullptr;
     // env
@@ -482,7 +481,6 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.dyc = c->dY[1][l];
     h.part = c->head_part;
     h.nblocks = c->head_blocks;
-    h.counter = c->counter;
     h.scal = c->scal;
     h.stats = step ? c->acc : nullptr;
     h.kl_target = step ? c->cfg.kl_target : 0.f;
@@ -490,6 +488,9 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     h.lr_max = c->cfg.lr_max;
     if (before_loss) CK(cudaStreamWaitEvent(q.s, before_loss, 0));
     CK(q.run(RL_PROF_LOSS, 1, [&] { return launch_loss_head(h, q.s); }));
+    // the minibatch statistics and Algorithm 1 (read only by Adam): on the weight-gradient stream
+    // beside the first input gradient when the streams overlap, else right here
+    if (!overlap_dw) CK(q.run(RL_PROF_LOSS, 1, [&] { return launch_loss_stats(h, q.s); }));
     // input gradients: dY_{l-1} = (dY_l W_l) * ELU'(H_{l-1}), plus the bias-gradient column sums;
     // weight gradients: dW_l = dY_l^T H_{l-1}, split over the minibatch rows.  dW_l needs only dY_l,
     // so with overlap_dw it runs on a second stream as soon as dY_l exists, beside the next input
@@ -499,6 +500,10 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     auto fork_dw = [&](int k) -> rl_status {
         CK(cudaEventRecord(c->ev_dw[k], q.s));
         CK(cudaStreamWaitEvent(c->wside, c->ev_dw[k], 0));
+        if (k == c->NH - 1) {
+            CK(launch_loss_stats(h, c->wside));
+            ++c->launches;
+        }
         return dw_layer(c, qw, k, M);
     };
     if (overlap_dw) {
@@ -1158,7 +1163,6 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(dalloc(c, &c->grad_int, sizeof(float) * c->P));
     CK(dalloc(c, &c->scal, sizeof(float) * SC_NSCAL));
     CK(dalloc(c, &c->iter, sizeof(unsigned long long)));
-    CK(dalloc(c, &c->counter, sizeof(unsigned int)));
     CK(dalloc(c, &c->status, sizeof(int)));
     CK(dalloc(c, &c->acc, sizeof(float) * RL_NSTATS));
     CK(dalloc(c, &c->stats, sizeof(float) * RL_NSTATS));

@@ -48,14 +48,17 @@ def test_policy_act(name, form, rows):
     L.close()
 
 
-@pytest.mark.parametrize("name,form", [("tiny", "fp32"), ("rough", "fp32"), ("tiny", "bf16"), ("rough", "bf16")])
-def test_ppo_loss_grad(name, form):
+@pytest.mark.parametrize("name,form,hidden", [("tiny", "fp32", None), ("rough", "fp32", None), ("tiny", "bf16", None),
+                                              ("rough", "bf16", None), ("tiny", "bf16", (128, 256)),
+                                              ("tiny", "fp32", (128, 256))])
+def test_ppo_loss_grad(name, form, hidden):
     """FP32: the oracle and the GPU get identical inputs.  BF16: as in training, log pi_old, V_old
     and mu_old come from each path's own inference at the same parameters (plus identical offsets),
     so the bf16 forward error cancels inside the ratio exactly as it does in the loop; the batch is
-    kept away from the clip kinks."""
+    kept away from the clip kinks.  A last hidden layer of 256 runs the loss head's tensor-core
+    form, 64 and 128 its warp-per-row form."""
     prec = 1 if form == "bf16" else 0
-    w = workload(name, precision=prec)
+    w = workload(name, precision=prec, **({"hidden": hidden} if hidden else {}))
     L, params, O, Op = _setup(w)
     M = w["num_envs"] * w["num_steps"] // w["minibatches"]
     b, d = _batch(M, O, Op, 12, params, w["hidden"], 21, prec == 1, kink_margin=prec == 1)
@@ -303,7 +306,8 @@ def test_profile_classes_count_every_launch():
     counts = {name: api.rl_profile_read_class(L.ctx, i)[1] for i, name in enumerate(api.RL_PROF_NAMES)}
     assert counts["env_step"] == w["num_steps"]
     assert counts["act_head"] == 1
-    assert counts["loss_head"] == n_mb and counts["adam"] == n_mb and counts["gather"] == n_mb
+    # the loss head and its statistics / Algorithm 1 kernel per minibatch
+    assert counts["loss_head"] == 2 * n_mb and counts["adam"] == n_mb and counts["gather"] == n_mb
     nh = len(w["hidden"])
     assert counts["gemm"] == (w["num_steps"] + 1) * nh + n_mb * (3 * nh - 1)
     total_ms, total_n = api.rl_profile_read(L.ctx)
