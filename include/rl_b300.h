@@ -235,8 +235,9 @@ rl_status rl_policy_act(rl_ctx* ctx, int32_t t, int32_t n, const void* obs, floa
  * rew, val [T][N] fp32; last_val [N]; done [T][N] uint8; adv_out, ret_out [T][N] fp32.
  * normalize != 0 replaces A by (A - mean) / (std + 1e-8) over all T*N samples (population std;
  * R keeps the unnormalised A).  adv_stats_out (may be NULL): [2] = mean, std of A.
- * workspace: device scratch of rl_gae_workspace_bytes(T, N) bytes, 16-byte aligned (may be
- * NULL when normalize == 0 and adv_stats_out == NULL). */
+ * workspace: device scratch of rl_gae_workspace_bytes(T, N) bytes (16 bytes per block of 256
+ * robots, plus 16), 16-byte aligned (may be NULL when normalize == 0 and adv_stats_out == NULL);
+ * nothing in it has to start at zero. */
 size_t rl_gae_workspace_bytes(int32_t T, int32_t N);
 rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val,
                  const float* last_val, const uint8_t* done, float* adv_out, float* ret_out,
@@ -248,9 +249,10 @@ rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew,
  * plugin that is not allowed to call the CUDA allocator, or a latency-critical loop that must
  * not pay for cudaMalloc and its implicit synchronisation.  The paper has no counterpart; this is
  * a deployment convenience.  Same arguments, results and layouts as rl_gae, minus the workspace:
- * the normalisation partial sums live in a file-scope device array of the library (64 KiB,
- * 4096 partials), held by every GPU that loads the library until the process exits.
- *   - N <= 262144 (4096 blocks of 64 robots); larger N returns RL_ERR_INVALID_ARG and
+ * the normalisation partial sums live in a file-scope device array of the library (64 KiB:
+ * 4096 slots of 16 bytes, one per block of 256 robots plus one for the mean and standard
+ * deviation), held by every GPU that loads the library until the process exits.
+ *   - N <= 1048320 (4095 blocks of 256 robots); larger N returns RL_ERR_INVALID_ARG and
  *     launches nothing.  T is unrestricted.
  *   - Each call made outside stream capture looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and remembers it; a call on a capturing

@@ -22,21 +22,31 @@ __device__ __forceinline__ float ld_act(const void* base, size_t i) {
 // ok[r] false are computed on row m[0] and write nothing.  Wa [A][H] and Wc [H] in shared memory
 // (fp32).  Writes p.values[m] and, with actor, p.mu / p.actions / p.logp where non-null;
 // a_sm[r] [A] / v_sm[r] (shared memory, optional) receive the sampled action and the value too.
+// The rows' last hidden activations (lane l: units l, l + 32, ...), loaded by act_rows or ahead
+// of it (the fused env step issues them before it stages the head weights).
 template <bool BF16, int NK, int R>
-__device__ __forceinline__ void act_rows(const HeadParams& p, const float* Wa, const float* Wc, const int (&m_in)[R],
-                                         const bool (&ok)[R], unsigned long long it, bool actor, int lane,
-                                         float* const (&a_sm)[R], float* const (&v_sm)[R]) {
+__device__ __forceinline__ void act_rows_load(const HeadParams& p, const int (&m_in)[R], const bool (&ok)[R], bool actor,
+                                              int lane, float (&hc)[R][NK], float (&ha)[R][NK]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int m = ok[r] ? m_in[r] : m_in[0];
+#pragma unroll
+        for (int i = 0; i < NK; ++i) {
+            hc[r][i] = ld_act<BF16>(p.hc, (size_t)m * p.H + lane + 32 * i);
+            if (actor) ha[r][i] = ld_act<BF16>(p.ha, (size_t)m * p.H + lane + 32 * i);
+        }
+    }
+}
+
+// act_rows on rows already loaded by act_rows_load.
+template <bool BF16, int NK, int R>
+__device__ __forceinline__ void act_rows_loaded(const HeadParams& p, const float* Wa, const float* Wc, const int (&m_in)[R],
+                                                const bool (&ok)[R], unsigned long long it, bool actor, int lane,
+                                                float* const (&a_sm)[R], float* const (&v_sm)[R], const float (&hc)[R][NK],
+                                                const float (&ha)[R][NK]) {
     int m[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) m[r] = ok[r] ? m_in[r] : m_in[0];
-    float hc[R][NK], ha[R][NK];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int i = 0; i < NK; ++i) {
-            hc[r][i] = ld_act<BF16>(p.hc, (size_t)m[r] * p.H + lane + 32 * i);
-            if (actor) ha[r][i] = ld_act<BF16>(p.ha, (size_t)m[r] * p.H + lane + 32 * i);
-        }
     float v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -113,6 +123,15 @@ __device__ __forceinline__ void act_rows(const HeadParams& p, const float* Wa, c
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (ok[r]) p.logp[m[r]] = lp[r];
+}
+
+template <bool BF16, int NK, int R>
+__device__ __forceinline__ void act_rows(const HeadParams& p, const float* Wa, const float* Wc, const int (&m_in)[R],
+                                         const bool (&ok)[R], unsigned long long it, bool actor, int lane,
+                                         float* const (&a_sm)[R], float* const (&v_sm)[R]) {
+    float hc[R][NK], ha[R][NK];
+    act_rows_load<BF16, NK, R>(p, m_in, ok, actor, lane, hc, ha);
+    act_rows_loaded<BF16, NK, R>(p, Wa, Wc, m_in, ok, it, actor, lane, a_sm, v_sm, hc, ha);
 }
 
 // One row m by the calling warp (act_rows with R = 1).

@@ -146,20 +146,25 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         // Phase 0 (fused policy head): the head weights into shared memory, then one warp per
         // robot evaluates mu, the sampled action, logp and V exactly as the action-head kernel
         // does, writing the rollout's records and the block's actions / values for phase 1.
+        // the warp's two robots together (ENVS = 2 x the warps of the block); their hidden rows
+        // are loaded first, so that the loads overlap the staging of the head weights
+        static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
+        constexpr bool HB = (FUSE >> 4) != 0;
+        constexpr int NK = FUSE & 15;
+        const int r0 = warp, r1 = warp + THREADS / 32;
+        const int mm[2] = {env0 + r0, env0 + r1};
+        const bool ok[2] = {env0 + r0 < N, env0 + r1 < N};
+        float hc[2][NK], ha[2][NK];
+        if (ok[0]) act_rows_load<HB, NK, 2>(p.act, mm, ok, true, lane, hc, ha);
         float* Wa = gtab + 2 * GTAB;
         float* Wc = Wa + p.act.A * p.act.H;
         for (int i = tid; i < p.act.A * p.act.H; i += THREADS) Wa[i] = p.act.Wa[i];
         for (int i = tid; i < p.act.H; i += THREADS) Wc[i] = p.act.Wc[i];
         __syncthreads();
-        // the warp's two robots together (ENVS = 2 x the warps of the block)
-        static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
         {
-            const int r0 = warp, r1 = warp + THREADS / 32;
-            const int mm[2] = {env0 + r0, env0 + r1};
-            const bool ok[2] = {env0 + r0 < N, env0 + r1 < N};
             float* const as[2] = {act_s[r0], act_s[r1]};
             float* const vs[2] = {&val_s[r0], &val_s[r1]};
-            if (ok[0]) act_rows<(FUSE >> 4) != 0, (FUSE & 15), 2>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs);
+            if (ok[0]) act_rows_loaded<HB, NK, 2>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs, hc, ha);
         }
         __syncthreads();
     }
@@ -424,49 +429,67 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     }
     __syncthreads();
 
-    // Phase 2: observation rows, one robot per warp at a time, two columns per lane.
-    for (int le = warp; le < ENVS; le += THREADS / 32) {
-        const int e = env0 + le;
-        if (e >= N) break;
-        const float* R = rec[le];
-        const uint64_t key = ((uint64_t)__float_as_uint(R[R_KEYHI]) << 32) | __float_as_uint(R[R_KEYLO]);
-        const float px = R[R_PX], py = R[R_PY], hc = R[R_HC], hs = R[R_HS], z = R[R_Z];
-        const int ibx = __float_as_int(R[R_BX]), iby = __float_as_int(R[R_BY]);
-        // unrolled over the row's column pairs, so that the height samples' loads of all of them
-        // are in flight together
-#pragma unroll 4
-        for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
-            float v[2];
-            uint64_t w = (p.noise_on && c0 < p.O) ? rng_word(key, SLOT_OBS + (c0 >> 1)) : 0ull;
+    // Phase 2: observation rows, two columns per lane; a warp's two robots (warp, warp + 8) go
+    // through the column loop together, so that the height samples' loads of both rows (and of
+    // several column pairs, unrolled) are in flight at once.
+    static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
+    {
+        int ev[2];
+        bool okr[2];
+        const float* Rr[2];
+        uint64_t keyr[2];
+        float pxr[2], pyr[2], hcr[2], hsr[2], zr[2];
+        int ibxr[2], ibyr[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + h;
-                float val = 0.f;
-                if (c < 48) {
-                    val = R[c];
-                } else if (c < p.O) {
-                    const int k = c - 48;
-                    float gxo, gyo;
-                    if (k < GTAB) {
-                        gxo = gtab[k];
-                        gyo = gtab[GTAB + k];
-                    } else {
-                        const int ix = k % p.GX, iy = k / p.GX;
-                        gxo = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
-                        gyo = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+        for (int q = 0; q < 2; ++q) {
+            const int le = warp + q * (THREADS / 32);
+            ev[q] = env0 + le;
+            okr[q] = ev[q] < N;
+            const float* R = rec[le];
+            Rr[q] = R;
+            keyr[q] = ((uint64_t)__float_as_uint(R[R_KEYHI]) << 32) | __float_as_uint(R[R_KEYLO]);
+            pxr[q] = R[R_PX]; pyr[q] = R[R_PY]; hcr[q] = R[R_HC]; hsr[q] = R[R_HS]; zr[q] = R[R_Z];
+            ibxr[q] = __float_as_int(R[R_BX]); ibyr[q] = __float_as_int(R[R_BY]);
+        }
+#pragma unroll 2
+        for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!okr[q]) continue;
+                const float* R = Rr[q];
+                float v[2];
+                uint64_t w = (p.noise_on && c0 < p.O) ? rng_word(keyr[q], SLOT_OBS + (c0 >> 1)) : 0ull;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + h;
+                    float val = 0.f;
+                    if (c < 48) {
+                        val = R[c];
+                    } else if (c < p.O) {
+                        const int k = c - 48;
+                        float gxo, gyo;
+                        if (k < GTAB) {
+                            gxo = gtab[k];
+                            gyo = gtab[GTAB + k];
+                        } else {
+                            const int ix = k % p.GX, iy = k / p.GX;
+                            gxo = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
+                            gyo = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
+                        }
+                        const float fx = (pxr[q] + (hcr[q] * gxo - hsr[q] * gyo)) * p.inv_res;
+                        const float fy = (pyr[q] + (hsr[q] * gxo + hcr[q] * gyo)) * p.inv_res;
+                        val = zr[q] - terrain_height(p.hf, p.nx, p.ny, ibxr[q], fx, ibyr[q], fy);
                     }
-                    const float fx = (px + (hc * gxo - hs * gyo)) * p.inv_res;
-                    const float fy = (py + (hs * gxo + hc * gyo)) * p.inv_res;
-                    val = z - terrain_height(p.hf, p.nx, p.ny, ibx, fx, iby, fy);
+                    if (p.noise_on && c < p.O) val += noise_scale(c) * uniform_pm1(h == 0 ? hi32(w) : lo32(w));
+                    v[h] = val;
                 }
-                if (p.noise_on && c < p.O) val += noise_scale(c) * uniform_pm1(h == 0 ? hi32(w) : lo32(w));
-                v[h] = val;
-            }
-            if (p.obs_bf16) {
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
-                *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(p.obs) + (size_t)e * p.Op + c0) = b2;
-            } else {
-                *reinterpret_cast<float2*>(reinterpret_cast<float*>(p.obs) + (size_t)e * p.Op + c0) = make_float2(v[0], v[1]);
+                const int e = ev[q];
+                if (p.obs_bf16) {
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(p.obs) + (size_t)e * p.Op + c0) = b2;
+                } else {
+                    *reinterpret_cast<float2*>(reinterpret_cast<float*>(p.obs) + (size_t)e * p.Op + c0) = make_float2(v[0], v[1]);
+                }
             }
         }
     }

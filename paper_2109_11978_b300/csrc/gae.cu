@@ -5,9 +5,13 @@
 // contiguous), so at every step t a warp touches 32 consecutive robots: 128-byte coalesced
 // loads and stores.  One thread owns one robot and keeps its running A_{t+1}, V_{t+1} in
 // registers; the T steps are processed newest first in chunks of 8 whose loads are issued
-// together.  Each block also leaves the fp64 sum and sum of squares of its advantages in a
-// scratch slot; the normalising kernel reduces those few hundred partials (every block
-// redundantly, which avoids a third launch) and rescales the advantages in place.
+// together.  Each 256-thread block also leaves the sum and the sum of squares of its advantages
+// in a 16-byte scratch slot as compensated fp32 pairs (value, rounding error: Neumaier's
+// two-sum at every addition, a fixed xor tree across the lanes, the warps in order), so that no
+// fp64 arithmetic runs per element (fp64 is slow on this part).  One block then reduces the
+// slots in a fixed order and writes (mean, std) to the slot after them (the last additions and
+// the variance in fp64, a handful of operations); the normalising kernel reads those two
+// numbers and rescales the advantages in place with 16-byte vectors.
 #include <mutex>
 
 #include "common.cuh"
@@ -15,35 +19,51 @@
 
 namespace rl {
 
-// Scratch of rl_gae_noalloc: the per-block fp64 (sum, sum of squares) pairs of the advantage
-// statistics, in a file-scope device array instead of caller- or library-allocated memory.
-// 4096 blocks of 64 robots = at most 262,144 robots; 64 KiB held by every device that loads
-// the library, until the process exits.
-constexpr int NOALLOC_MAX_PARTS = 4096;
-static __device__ __align__(256) double g_gae_noalloc_scratch[2 * NOALLOC_MAX_PARTS];
+// Scratch of rl_gae_noalloc: the per-block (sum, error, sum of squares, error) slots of the
+// advantage statistics plus the (mean, std) slot, in a file-scope device array instead of caller-
+// or library-allocated memory.  4096 slots of 16 bytes = 4095 blocks of 256 robots, so at most
+// 1,048,320 robots; 64 KiB held by every device that loads the library, until the process exits.
+constexpr int NOALLOC_MAX_SLOTS = 4096;
+static __device__ __align__(256) float4 g_gae_noalloc_scratch[NOALLOC_MAX_SLOTS];
 
 namespace {
 
-constexpr int GAE_THREADS = 64;
+constexpr int GAE_THREADS = 256;
 constexpr int CHUNK = 8;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+__device__ __forceinline__ void two_sum(float& sum, float& err, float x) {
+    const float t = sum + x;
+    err += fabsf(sum) >= fabsf(x) ? (sum - t) + x : (x - t) + sum;
+    sum = t;
 }
 
-__global__ void __launch_bounds__(GAE_THREADS) gae_scan_kernel(int T, int N, float gamma, float lam,
-                                                               const float* __restrict__ rew,
-                                                               const float* __restrict__ val,
-                                                               const float* __restrict__ last_val,
-                                                               const uint8_t* __restrict__ done,
-                                                               float* __restrict__ adv, float* __restrict__ ret,
-                                                               double* __restrict__ partials) {
+// (value, error) pairs of two quantities combined across the lanes by a fixed xor tree (the
+// lower lane's value first, so both partners form the same sum)
+__device__ __forceinline__ void warp_pairs(float (&v)[4], int lane) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float os = __shfl_xor_sync(0xffffffffu, v[2 * q], o), oe = __shfl_xor_sync(0xffffffffu, v[2 * q + 1], o);
+            const bool lo = (lane & o) == 0;
+            float a = lo ? v[2 * q] : os, e = lo ? v[2 * q + 1] : oe;
+            two_sum(a, e, lo ? os : v[2 * q]);
+            v[2 * q] = a;
+            v[2 * q + 1] = e + (lo ? oe : v[2 * q + 1]);
+        }
+}
+
+__global__ void __launch_bounds__(GAE_THREADS, 4) gae_scan_kernel(int T, int N, float gamma, float lam,
+                                                                const float* __restrict__ rew,
+                                                                const float* __restrict__ val,
+                                                                const float* __restrict__ last_val,
+                                                                const uint8_t* __restrict__ done,
+                                                                float* __restrict__ adv, float* __restrict__ ret,
+                                                                float4* __restrict__ partials) {
     pdl_wait();
     pdl_trigger();
     const int n = blockIdx.x * GAE_THREADS + threadIdx.x;
-    double s1 = 0.0, s2 = 0.0;
+    float st[4] = {0.f, 0.f, 0.f, 0.f};     // sum, its error, sum of squares, its error
     if (n < N) {
         float next_v = last_val[n];
         float next_a = 0.f;
@@ -72,58 +92,91 @@ __global__ void __launch_bounds__(GAE_THREADS) gae_scan_kernel(int T, int N, flo
                     adv[o] = next_a;
                     ret[o] = next_a + v[i];
                     next_v = v[i];
-                    s1 += (double)next_a;
-                    s2 += (double)next_a * (double)next_a;
+                    two_sum(st[0], st[1], next_a);
+                    // the square's own rounding error (exact by fma) joins the error term, so the
+                    // sums carry A and A^2 to about twice fp32's precision
+                    const float sq = next_a * next_a;
+                    two_sum(st[2], st[3], sq);
+                    st[3] += fmaf(next_a, next_a, -sq);
                 }
             }
         }
     }
     if (partials) {
-        __shared__ double red[2][GAE_THREADS / 32];
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
+        __shared__ float ws[GAE_THREADS / 32][4];
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red[0][warp] = s1; red[1][warp] = s2; }
+        warp_pairs(st, lane);
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ws[warp][i] = st[i];
         __syncthreads();
         if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < GAE_THREADS / 32; ++w) { a += red[0][w]; b += red[1][w]; }
-            partials[2 * blockIdx.x] = a;
-            partials[2 * blockIdx.x + 1] = b;
+            float b[4] = {ws[0][0], ws[0][1], ws[0][2], ws[0][3]};
+            for (int w = 1; w < GAE_THREADS / 32; ++w) {
+                two_sum(b[0], b[1], ws[w][0]);
+                b[1] += ws[w][1];
+                two_sum(b[2], b[3], ws[w][2]);
+                b[3] += ws[w][3];
+            }
+            partials[blockIdx.x] = make_float4(b[0], b[1], b[2], b[3]);
         }
     }
 }
 
-__global__ void gae_normalize_kernel(size_t total, int nparts, const double* __restrict__ partials,
-                                     float* __restrict__ adv, int normalize, float* __restrict__ stats) {
+// One block: the blocks' slots in a fixed order (thread t takes slots t, t + 256, ...; adding a
+// zero slot changes no sum), then the
+// xor tree and the warps in order; mean and population std into slot nparts (and adv_stats).
+__global__ void __launch_bounds__(GAE_THREADS) gae_stats_kernel(int nparts, double total, float4* __restrict__ partials,
+                                                                float* __restrict__ adv_stats) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double red[2][32];
-    __shared__ float ms[2];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        a += partials[2 * i];
-        b += partials[2 * i + 1];
-    }
-    a = warp_sum(a);
-    b = warp_sum(b);
+    __shared__ float ws[GAE_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { sa += red[0][w]; sb += red[1][w]; }
-        const double mean = sa / (double)total;
-        double var = sb / (double)total - mean * mean;
-        var = var > 0.0 ? var : 0.0;
-        ms[0] = (float)mean;
-        ms[1] = (float)sqrt(var);
-        if (blockIdx.x == 0 && stats) { stats[0] = ms[0]; stats[1] = ms[1]; }
+    float st[4] = {0.f, 0.f, 0.f, 0.f};
+    // eight slots' loads in flight per thread before any is added
+    for (int i0 = threadIdx.x; i0 < nparts; i0 += 8 * GAE_THREADS) {
+        float4 q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * GAE_THREADS;
+            q[k] = i < nparts ? partials[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            two_sum(st[0], st[1], q[k].x);
+            st[1] += q[k].y;
+            two_sum(st[2], st[3], q[k].z);
+            st[3] += q[k].w;
+        }
     }
+    warp_pairs(st, lane);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ws[warp][i] = st[i];
     __syncthreads();
-    if (!normalize) return;
-    const float mean = ms[0];
-    const float inv = 1.0f / (ms[1] + 1e-8f);
+    if (threadIdx.x != 0) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < GAE_THREADS / 32; ++w) {
+        s1 += (double)ws[w][0] + (double)ws[w][1];
+        s2 += (double)ws[w][2] + (double)ws[w][3];
+    }
+    const double mean = s1 / total;
+    double var = s2 / total - mean * mean;
+    var = var > 0.0 ? var : 0.0;
+    const float m = (float)mean, sd = (float)sqrt(var);
+    partials[nparts] = make_float4(m, sd, 0.f, 0.f);
+    if (adv_stats) {
+        adv_stats[0] = m;
+        adv_stats[1] = sd;
+    }
+}
+
+__global__ void gae_normalize_kernel(size_t total, const float4* __restrict__ ms, float* __restrict__ adv) {
+    pdl_wait();
+    pdl_trigger();
+    const float4 q = ms[0];
+    const float mean = q.x;
+    const float inv = 1.0f / (q.y + 1e-8f);
     const size_t n4 = total / 4;
     float4* a4 = reinterpret_cast<float4*>(adv);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
@@ -139,7 +192,13 @@ __global__ void gae_normalize_kernel(size_t total, int nparts, const double* __r
 
 int gae_num_partials(int T, int N) { return (N + GAE_THREADS - 1) / GAE_THREADS; }
 
-int gae_noalloc_max_envs() { return NOALLOC_MAX_PARTS * GAE_THREADS; }
+// one slot per block of 256 robots plus the (mean, std) slot
+int gae_noalloc_max_envs() { return (NOALLOC_MAX_SLOTS - 1) * GAE_THREADS; }
+
+size_t gae_workspace_bytes(int T, int N) {
+    if (T <= 0 || N <= 0) return 0;
+    return (size_t)(gae_num_partials(T, N) + 1) * sizeof(float4);
+}
 
 // Device address of the scratch array on the current device.  In host code the array's name is
 // only a host-side stand-in, so the address is looked up with the device current.  Outside stream
@@ -174,18 +233,20 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
                        float* adv_stats, float* partials, int nparts, cudaStream_t s) {
     if (T <= 0 || N <= 0) return cudaSuccess;
     const bool need = normalize || adv_stats;
-    double* part = need ? reinterpret_cast<double*>(partials) : nullptr;
-    cudaError_t e0 = launch_pdl(gae_scan_kernel, dim3(gae_num_partials(T, N)), dim3(GAE_THREADS), 0, s, T, N, gamma, lam,
-                                rew, val, last_val, done, adv, ret, part);
-    if (e0 != cudaSuccess) return e0;
-    cudaError_t e = cudaGetLastError();
+    if (need && (!partials || nparts != gae_num_partials(T, N))) return cudaErrorInvalidValue;
+    float4* part = need ? reinterpret_cast<float4*>(partials) : nullptr;
+    cudaError_t e = launch_pdl(gae_scan_kernel, dim3(gae_num_partials(T, N)), dim3(GAE_THREADS), 0, s, T, N, gamma, lam, rew,
+                               val, last_val, done, adv, ret, part);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess || !need) return e;
     const size_t total = (size_t)T * N;
+    e = launch_pdl(gae_stats_kernel, dim3(1), dim3(GAE_THREADS), 0, s, nparts, (double)total, part, adv_stats);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess || !normalize) return e;
     int blocks = (int)((total / 4 + 255) / 256);
     if (blocks < 1) blocks = 1;
-    if (blocks > 1184) blocks = 1184;   // 8 x 148 SMs
-    e = launch_pdl(gae_normalize_kernel, dim3(blocks), dim3(256), 0, s, total, nparts, (const double*)part, adv, normalize,
-                   adv_stats);
+    if (blocks > 4 * 148) blocks = 4 * 148;     // four blocks of 256 per SM, grid-stride
+    e = launch_pdl(gae_normalize_kernel, dim3(blocks), dim3(256), 0, s, total, (const float4*)(part + nparts), adv);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

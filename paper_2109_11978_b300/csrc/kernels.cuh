@@ -9,7 +9,10 @@ namespace rl {
 cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, const float* val,
                        const float* last_val, const uint8_t* done, float* adv, float* ret,
                        int normalize, float* adv_stats, float* partials, int nparts, cudaStream_t s);
+// partials: device scratch of gae_workspace_bytes (one 16-byte slot per 256 robots and a
+// (mean, std) slot); nparts = gae_num_partials(T, N)
 int gae_num_partials(int T, int N);
+size_t gae_workspace_bytes(int T, int N);
 int gae_noalloc_max_envs();
 cudaError_t gae_noalloc_scratch(cudaStream_t s, void** out);
 

@@ -1546,10 +1546,7 @@ rl_status rl_policy_act(rl_ctx* c, int32_t t, int32_t n, const void* obs, float*
     return act_impl(c, q, t, n, obs, actions, mu, logp, values);
 }
 
-size_t rl_gae_workspace_bytes(int32_t T, int32_t N) {
-    if (T <= 0 || N <= 0) return 0;
-    return (size_t)gae_num_partials(T, N) * 2 * sizeof(double);
-}
+size_t rl_gae_workspace_bytes(int32_t T, int32_t N) { return gae_workspace_bytes(T, N); }
 
 rl_status rl_gae(int32_t T, int32_t N, float gamma, float lam, const float* rew, const float* val, const float* last_val,
                  const uint8_t* done, float* adv_out, float* ret_out, int32_t normalize, float* adv_stats_out,

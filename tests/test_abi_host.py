@@ -91,7 +91,7 @@ def test_null_arguments_rejected(lib):
     assert lib.rl_policy_act(None, 0, 1, None, None, None, None, None, None) == N.RL_ERR_INVALID_ARG
     assert lib.rl_ppo_update(None, None, None, None, None, None, None, None, 1, 1, 0.2, None, None) == N.RL_ERR_INVALID_ARG
     assert lib.rl_gae(0, 5, 0.99, 0.95, None, None, None, None, None, None, 0, None, None, 0, None) == N.RL_ERR_INVALID_ARG
-    assert lib.rl_gae_workspace_bytes(24, 4096) == 64 * 16
+    assert lib.rl_gae_workspace_bytes(24, 4096) == (4096 // 256 + 1) * 16
     assert lib.rl_gae_workspace_bytes(0, 4096) == 0
     assert lib.rl_status_string(N.RL_ERR_TIMEOUT) == b"device wait timed out"
     lib.rl_destroy(None)

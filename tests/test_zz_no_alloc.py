@@ -46,9 +46,15 @@ def test_noalloc_matches_regular_entry_point_twice(T, N):
 
 
 def test_noalloc_rejects_sizes_past_the_static_scratch():
-    T, N = 1, 262144 + 1
-    args = _inputs(T, N, 3)
+    """The array holds 4096 slots: one per block of 256 robots and the (mean, std) slot, so at most
+    1,048,320 robots; one more is refused, the limit itself matches the regular entry point."""
+    T, NMAX = 1, 4095 * 256
+    args = _inputs(T, NMAX + 1, 3)
     with pytest.raises(api.RLError):
-        _run(api.rl_gae_noalloc, T, N, args, True)
-    a, r, s = _run(api.rl_gae_noalloc, T, 262144, tuple(x[..., :262144] .contiguous() for x in args), True)
+        _run(api.rl_gae_noalloc, T, NMAX + 1, args, True)
+    cut = tuple(x[..., :NMAX].contiguous() for x in args)
+    a, r, s = _run(api.rl_gae_noalloc, T, NMAX, cut, True)
+    ws = torch.empty(api.rl_gae_workspace_bytes(T, NMAX) // 4 + 4, device="cuda")
+    a0, r0, s0 = _run(api.rl_gae, T, NMAX, cut, True, workspace=ws)
     assert np.isfinite(a).all()
+    assert rel_err(a, a0) < TOL_FP32 and rel_err(r, r0) < TOL_FP32
