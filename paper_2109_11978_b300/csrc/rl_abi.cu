@@ -86,6 +86,13 @@ struct rl_ctx {
     float* head_part = nullptr;
     int head_blocks = 0;
     AdamParams adam;
+    // the same step split in three, so that most of it leaves the update's critical path: early
+    // (every parameter but W_0, b_0 and W_1: its gradients exist once dW_1 is in flight, and the
+    // last input gradient no longer reads it), mid (W_1, once the last input gradient, which reads
+    // W_1, has run) and late (W_0, b_0, after the last weight gradient dW_0)
+    AdamParams adam_early, adam_mid, adam_late;
+    cudaStream_t aside = nullptr;
+    cudaEvent_t ev_early_fork = nullptr, ev_mid_fork = nullptr, ev_early_join = nullptr;
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
     int bn_fwd[4], bn_dx[4], bn_dw[4], bn_act[4];
@@ -504,7 +511,16 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
             CK(launch_loss_stats(h, c->wside));
             ++c->launches;
         }
-        return dw_layer(c, qw, k, M);
+        rl_status r = dw_layer(c, qw, k, M);
+        if (r != RL_OK || k != 1 || !step) return r;
+        // every gradient but the first hidden layer's is now in flight or done: the early part of
+        // Adam on its own stream, after this weight gradient and beside the last ones
+        CK(cudaEventRecord(c->ev_early_fork, c->wside));
+        CK(cudaStreamWaitEvent(c->aside, c->ev_early_fork, 0));
+        c->adam_early.grad_out = nullptr;
+        CK(launch_adam(c->adam_early, c->aside));
+        ++c->launches;
+        return RL_OK;
     };
     if (overlap_dw) {
         st = fork_dw(c->NH - 1);
@@ -513,6 +529,16 @@ rl_status minibatch_fwd_bwd(rl_ctx* c, Enq& q, int M, const int* idx, const floa
     for (int k = c->NH - 1; k >= 1; --k) {
         st = dx_layer(c, q, k, M);
         if (st != RL_OK) return st;
+        if (overlap_dw && step && k == 1) {
+            // the last input gradient has read W_1: the mid part of Adam (W_1) after it, on the
+            // early part's stream, beside dW_0
+            CK(cudaEventRecord(c->ev_mid_fork, q.s));
+            CK(cudaStreamWaitEvent(c->aside, c->ev_mid_fork, 0));
+            c->adam_mid.grad_out = nullptr;
+            CK(launch_adam(c->adam_mid, c->aside));
+            ++c->launches;
+            CK(cudaEventRecord(c->ev_early_join, c->aside));
+        }
         if (overlap_dw) {
             st = fork_dw(k - 1);
             if (st != RL_OK) return st;
@@ -585,6 +611,30 @@ void build_adam(rl_ctx* c) {
     }
     a.nsegs = ns;
     a.nblocks = blocks;
+    // the early / mid / late parts: the segments keep their order and partial sources, with their
+    // blocks renumbered per part
+    AdamParams* part[3] = {&c->adam_early, &c->adam_mid, &c->adam_late};
+    auto part_of = [&](long long off) {
+        for (int n = 0; n < 2; ++n) {
+            if (off == c->L[n][0].w || off == c->L[n][0].b) return 2;
+            if (c->NH >= 2 && off == c->L[n][1].w) return 1;
+        }
+        return 0;
+    };
+    for (int h = 0; h < 3; ++h) {
+        AdamParams& d = *part[h];
+        d = a;
+        d.nsegs = 0;
+        d.nblocks = 0;
+        for (int k = 0; k < a.nsegs; ++k) {
+            if (part_of(a.seg[k].offset) != h) continue;
+            AdamSeg sg = a.seg[k];
+            sg.block_start = d.nblocks;
+            d.nblocks += (int)((sg.size + adam_per_block(sg.nsplit, sg.vec) - 1) / adam_per_block(sg.nsplit, sg.vec));
+            d.wbf[d.nsegs] = a.wbf[k];
+            d.seg[d.nsegs++] = sg;
+        }
+    }
 }
 
 // Adam's partial-sum pass restricted to the weight matrices of hidden layer l (both networks),
@@ -680,8 +730,16 @@ rl_status update_impl(rl_ctx* c, Enq& q, const void* obs, const float* actions, 
                                          true, c->bf16 ? c->recs : nullptr, overlap,
                                          k == 0 && pack_on_side ? c->ev_pack_join : nullptr, c->trace + 2 * k);
         if (st != RL_OK) return st;
-        c->adam.grad_out = nullptr;
-        CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
+        if (overlap && c->NH >= 2) {
+            // the early and mid parts ran beside the last gradients (minibatch_fwd_bwd); the late
+            // part here, and the next minibatch starts after all three
+            c->adam_late.grad_out = nullptr;
+            CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam_late, s); }));
+            CK(cudaStreamWaitEvent(s, c->ev_early_join, 0));
+        } else {
+            c->adam.grad_out = nullptr;
+            CK(q.run(RL_PROF_ADAM, 1, [&] { return launch_adam(c->adam, s); }));
+        }
         if (k + 1 < nmb && !overlap)
             CK(q.run(RL_PROF_GATHER, 1,
                      [&] { return launch_gather(obs, c->bf16 ? 1 : 0, mb_idx(k + 1), Mb, c->Op, c->X0buf[nxt], s); }));
@@ -1085,6 +1143,10 @@ void rl_destroy(rl_ctx* c) {
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->wside) cudaStreamDestroy(c->wside);
+    if (c->aside) cudaStreamDestroy(c->aside);
+    if (c->ev_early_fork) cudaEventDestroy(c->ev_early_fork);
+    if (c->ev_early_join) cudaEventDestroy(c->ev_early_join);
+    if (c->ev_mid_fork) cudaEventDestroy(c->ev_mid_fork);
     for (cudaEvent_t e : c->ev_dw)
         if (e) cudaEventDestroy(e);
     if (c->ev_dw_join) cudaEventDestroy(c->ev_dw_join);
@@ -1118,6 +1180,10 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->wside, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->aside, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_early_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_early_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_mid_fork, cudaEventDisableTiming));
     for (cudaEvent_t& e : c->ev_dw) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_dw_join, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_perm_fork, cudaEventDisableTiming));
