@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--robots-sweep", action="store_true",
                     help="throughput against the number of parallel robots at three batch sizes (one JSON line per point)")
     ap.add_argument("--tiles-out", default=None, help="write the full autotune report (every trial) to this JSON file")
+    ap.add_argument("--profile-run", type=int, default=0, metavar="K",
+                    help="for profiler captures: build the BF16 learner (tile shapes from --tiles), run K iterations "
+                         "without the graph and without timing, exit")
     ap.add_argument("--tiles", default=None,
                     help="apply the GEMM tile shapes of a saved autotune report instead of autotuning (for profiler runs, "
                          "where serialised launches would distort the autotuner's timings)")
@@ -81,10 +84,11 @@ def read_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum summed over the GEMM launches of one iteration of
-# the rough-terrain workload (ncu, one pass per launch, cold caches); None until the current GEMM
-# build has been captured.
-GEMM_DRAM_BYTES_PER_ITERATION = None
+# dram__bytes_read.sum + dram__bytes_write.sum summed over the 235 GEMM launches of one iteration
+# of the rough-terrain workload (ncu, one pass per launch, cold caches), captured on the current
+# GEMM build (`bench.py --profile-run 1` under ncu); set to None whenever the GEMM kernel changes,
+# until it is captured again.
+GEMM_DRAM_BYTES_PER_ITERATION = 8005.1e6 + 254.6e6
 
 
 def gemm_flops_per_iteration(w, O):
@@ -462,6 +466,19 @@ def main():
         from paper_2109_11978_b300 import api, synth
         robots_sweep(torch, api, synth)
         return 0
+    if args.profile_run:
+        import torch
+        from paper_2109_11978_b300 import api, synth
+        L, _ = make_learner(api, synth, api.RL_BF16, seed=0)
+        if args.tiles:
+            select_tiles(api, L, args)
+        for _ in range(args.profile_run):
+            L.train_iteration(use_graph=False)
+        torch.cuda.synchronize()
+        status = api.rl_last_device_status(L.ctx)
+        L.close()
+        print(json.dumps({"profile_run": args.profile_run, "device_status": status}))
+        return 0 if status == 0 else 1
     rank, world, local = dist_info()
     import torch
     torch.cuda.set_device(local)

@@ -2,16 +2,17 @@
 // plus the batch normalisation of the advantages.
 //
 // Layout: rewards, values, dones, advantages and returns are [T][N] (robot index
-// contiguous), so at every step t a warp touches 32 consecutive robots: 128-byte coalesced
-// loads and stores.  One thread owns one robot and keeps its running A_{t+1}, V_{t+1} in
-// registers; the T steps are processed newest first in chunks of 8 whose loads are issued
-// together.  Each 256-thread block also leaves the sum and the sum of squares of its advantages
-// in a 16-byte scratch slot as compensated fp32 pairs (value, rounding error: Neumaier's
-// two-sum at every addition, a fixed xor tree across the lanes, the warps in order), so that no
-// fp64 arithmetic runs per element (fp64 is slow on this part).  One block then reduces the
-// slots in a fixed order and writes (mean, std) to the slot after them (the last additions and
-// the variance in fp64, a handful of operations); the normalising kernel reads those two
-// numbers and rescales the advantages in place with 16-byte vectors.
+// contiguous), so at every step t a warp touches consecutive robots: coalesced loads and
+// stores.  A thread owns four consecutive robots (16-byte accesses, 512 bytes per warp request;
+// one robot when N is not a multiple of 4 or an array is not 16-byte aligned) and keeps their
+// running A_{t+1}, V_{t+1} in registers; the T steps are processed newest first in chunks whose
+// loads are issued together.  Each 256-thread block also leaves the sum and the sum of squares
+// of its advantages in a 16-byte scratch slot as compensated fp32 pairs (value, rounding error:
+// Neumaier's two-sum at every addition, a fixed xor tree across the lanes, the warps in order),
+// so that no fp64 arithmetic runs per element (fp64 is slow on this part).  One block then
+// reduces the slots in a fixed order and writes (mean, std) to the scratch's first slot (the last
+// additions and the variance in fp64, a handful of operations); the normalising kernel reads
+// those two numbers and rescales the advantages in place with 16-byte vectors.
 #include <mutex>
 
 #include "common.cuh"
@@ -19,10 +20,11 @@
 
 namespace rl {
 
-// Scratch of rl_gae_noalloc: the per-block (sum, error, sum of squares, error) slots of the
-// advantage statistics plus the (mean, std) slot, in a file-scope device array instead of caller-
-// or library-allocated memory.  4096 slots of 16 bytes = 4095 blocks of 256 robots, so at most
-// 1,048,320 robots; 64 KiB held by every device that loads the library, until the process exits.
+// Scratch of rl_gae_noalloc: the (mean, std) slot and the per-block (sum, error, sum of squares,
+// error) slots of the advantage statistics, in a file-scope device array instead of caller- or
+// library-allocated memory.  4096 slots of 16 bytes = the statistics slot and 4095 blocks of 256
+// robots (the one-robot-per-thread form; the four-robot form needs fewer), so at most 1,048,320
+// robots; 64 KiB held by every device that loads the library, until the process exits.
 constexpr int NOALLOC_MAX_SLOTS = 4096;
 static __device__ __align__(256) float4 g_gae_noalloc_scratch[NOALLOC_MAX_SLOTS];
 
@@ -53,51 +55,90 @@ __device__ __forceinline__ void warp_pairs(float (&v)[4], int lane) {
         }
 }
 
-__global__ void __launch_bounds__(GAE_THREADS, 4) gae_scan_kernel(int T, int N, float gamma, float lam,
+// R robots per thread (R = 4: 16-byte loads and stores of four consecutive robots, used when N is
+// a multiple of 4 and the arrays are 16-byte aligned, so that each warp request moves 512 bytes;
+// R = 1 otherwise); the T steps newest first in chunks whose loads are issued together.
+template <int R>
+struct GaeIO;
+template <>
+struct GaeIO<1> {
+    static constexpr int CH = 8;
+    __device__ static void ldf(const float* p, size_t o, float (&x)[1]) { x[0] = __ldg(p + o); }
+    __device__ static void ldd(const uint8_t* p, size_t o, float (&x)[1]) { x[0] = (float)__ldg(p + o); }
+    __device__ static void stf(float* p, size_t o, const float (&x)[1]) { p[o] = x[0]; }
+};
+template <>
+struct GaeIO<4> {
+    static constexpr int CH = 4;
+    __device__ static void ldf(const float* p, size_t o, float (&x)[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p + o));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    __device__ static void ldd(const uint8_t* p, size_t o, float (&x)[4]) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p + o));
+        x[0] = (float)(w & 0xFFu); x[1] = (float)((w >> 8) & 0xFFu); x[2] = (float)((w >> 16) & 0xFFu); x[3] = (float)(w >> 24);
+    }
+    __device__ static void stf(float* p, size_t o, const float (&x)[4]) {
+        *reinterpret_cast<float4*>(p + o) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+
+template <int R>
+__global__ void __launch_bounds__(GAE_THREADS, R == 4 ? 3 : 4) gae_scan_kernel(int T, int N, float gamma, float lam,
                                                                 const float* __restrict__ rew,
                                                                 const float* __restrict__ val,
                                                                 const float* __restrict__ last_val,
                                                                 const uint8_t* __restrict__ done,
                                                                 float* __restrict__ adv, float* __restrict__ ret,
                                                                 float4* __restrict__ partials) {
+    using IO = GaeIO<R>;
+    constexpr int CH = IO::CH;
     pdl_wait();
     pdl_trigger();
-    const int n = blockIdx.x * GAE_THREADS + threadIdx.x;
+    const int n = (blockIdx.x * GAE_THREADS + threadIdx.x) * R;
     float st[4] = {0.f, 0.f, 0.f, 0.f};     // sum, its error, sum of squares, its error
     if (n < N) {
-        float next_v = last_val[n];
-        float next_a = 0.f;
-        const float gl = gamma * lam;
-        for (int t1 = T; t1 > 0; t1 -= CHUNK) {
-            const int t0 = t1 - CHUNK > 0 ? t1 - CHUNK : 0;
-            float r[CHUNK], v[CHUNK], d[CHUNK];
+        float next_v[R], next_a[R];
+        IO::ldf(last_val, (size_t)n, next_v);
 #pragma unroll
-            for (int i = 0; i < CHUNK; ++i) {
+        for (int k = 0; k < R; ++k) next_a[k] = 0.f;
+        const float gl = gamma * lam;
+        for (int t1 = T; t1 > 0; t1 -= CH) {
+            const int t0 = t1 - CH > 0 ? t1 - CH : 0;
+            float r[CH][R], v[CH][R], d[CH][R];
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
                 const int t = t1 - 1 - i;
                 if (t >= t0) {
                     const size_t o = (size_t)t * N + n;
-                    r[i] = __ldg(rew + o);
-                    v[i] = __ldg(val + o);
-                    d[i] = (float)__ldg(done + o);
+                    IO::ldf(rew, o, r[i]);
+                    IO::ldf(val, o, v[i]);
+                    IO::ldd(done, o, d[i]);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < CHUNK; ++i) {
+            for (int i = 0; i < CH; ++i) {
                 const int t = t1 - 1 - i;
                 if (t >= t0) {
-                    const float nonterm = 1.0f - d[i];
-                    const float delta = r[i] + gamma * nonterm * next_v - v[i];
-                    next_a = delta + gl * nonterm * next_a;
+                    float a[R], rt[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const float nonterm = 1.0f - d[i][k];
+                        const float delta = r[i][k] + gamma * nonterm * next_v[k] - v[i][k];
+                        next_a[k] = delta + gl * nonterm * next_a[k];
+                        a[k] = next_a[k];
+                        rt[k] = next_a[k] + v[i][k];
+                        next_v[k] = v[i][k];
+                        two_sum(st[0], st[1], next_a[k]);
+                        // the square's own rounding error (exact by fma) joins the error term, so
+                        // the sums carry A and A^2 to about twice fp32's precision
+                        const float sq = next_a[k] * next_a[k];
+                        two_sum(st[2], st[3], sq);
+                        st[3] += fmaf(next_a[k], next_a[k], -sq);
+                    }
                     const size_t o = (size_t)t * N + n;
-                    adv[o] = next_a;
-                    ret[o] = next_a + v[i];
-                    next_v = v[i];
-                    two_sum(st[0], st[1], next_a);
-                    // the square's own rounding error (exact by fma) joins the error term, so the
-                    // sums carry A and A^2 to about twice fp32's precision
-                    const float sq = next_a * next_a;
-                    two_sum(st[2], st[3], sq);
-                    st[3] += fmaf(next_a, next_a, -sq);
+                    IO::stf(adv, o, a);
+                    IO::stf(ret, o, rt);
                 }
             }
         }
@@ -124,10 +165,10 @@ __global__ void __launch_bounds__(GAE_THREADS, 4) gae_scan_kernel(int T, int N, 
 }
 
 // One block: the blocks' slots in a fixed order (thread t takes slots t, t + 256, ...; adding a
-// zero slot changes no sum), then the
-// xor tree and the warps in order; mean and population std into slot nparts (and adv_stats).
-__global__ void __launch_bounds__(GAE_THREADS) gae_stats_kernel(int nparts, double total, float4* __restrict__ partials,
-                                                                float* __restrict__ adv_stats) {
+// zero slot changes no sum), then the xor tree and the warps in order; mean and population std
+// into ms_slot (and adv_stats).
+__global__ void __launch_bounds__(GAE_THREADS) gae_stats_kernel(int nparts, double total, const float4* __restrict__ partials,
+                                                                float4* __restrict__ ms_slot, float* __restrict__ adv_stats) {
     pdl_wait();
     pdl_trigger();
     __shared__ float ws[GAE_THREADS / 32][4];
@@ -164,7 +205,7 @@ __global__ void __launch_bounds__(GAE_THREADS) gae_stats_kernel(int nparts, doub
     double var = s2 / total - mean * mean;
     var = var > 0.0 ? var : 0.0;
     const float m = (float)mean, sd = (float)sqrt(var);
-    partials[nparts] = make_float4(m, sd, 0.f, 0.f);
+    ms_slot[0] = make_float4(m, sd, 0.f, 0.f);
     if (adv_stats) {
         adv_stats[0] = m;
         adv_stats[1] = sd;
@@ -234,19 +275,30 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
     if (T <= 0 || N <= 0) return cudaSuccess;
     const bool need = normalize || adv_stats;
     if (need && (!partials || nparts != gae_num_partials(T, N))) return cudaErrorInvalidValue;
-    float4* part = need ? reinterpret_cast<float4*>(partials) : nullptr;
-    cudaError_t e = launch_pdl(gae_scan_kernel, dim3(gae_num_partials(T, N)), dim3(GAE_THREADS), 0, s, T, N, gamma, lam, rew,
-                               val, last_val, done, adv, ret, part);
+    // slot 0: (mean, std); slots 1 ..: one per block of the scan
+    float4* ms = need ? reinterpret_cast<float4*>(partials) : nullptr;
+    float4* part = need ? ms + 1 : nullptr;
+    const bool v4 = N % 4 == 0 && ((reinterpret_cast<uintptr_t>(rew) | reinterpret_cast<uintptr_t>(val) |
+                                    reinterpret_cast<uintptr_t>(last_val) | reinterpret_cast<uintptr_t>(adv) |
+                                    reinterpret_cast<uintptr_t>(ret)) & 15u) == 0 &&
+                    (reinterpret_cast<uintptr_t>(done) & 3u) == 0;
+    const int robots_per_block = GAE_THREADS * (v4 ? 4 : 1);
+    const int blocks = (N + robots_per_block - 1) / robots_per_block;
+    cudaError_t e = v4 ? launch_pdl(gae_scan_kernel<4>, dim3(blocks), dim3(GAE_THREADS), 0, s, T, N, gamma, lam, rew, val,
+                                    last_val, done, adv, ret, part)
+                       : launch_pdl(gae_scan_kernel<1>, dim3(blocks), dim3(GAE_THREADS), 0, s, T, N, gamma, lam, rew, val,
+                                    last_val, done, adv, ret, part);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess || !need) return e;
     const size_t total = (size_t)T * N;
-    e = launch_pdl(gae_stats_kernel, dim3(1), dim3(GAE_THREADS), 0, s, nparts, (double)total, part, adv_stats);
+    e = launch_pdl(gae_stats_kernel, dim3(1), dim3(GAE_THREADS), 0, s, blocks, (double)total, (const float4*)part, ms,
+                   adv_stats);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess || !normalize) return e;
-    int blocks = (int)((total / 4 + 255) / 256);
-    if (blocks < 1) blocks = 1;
-    if (blocks > 4 * 148) blocks = 4 * 148;     // four blocks of 256 per SM, grid-stride
-    e = launch_pdl(gae_normalize_kernel, dim3(blocks), dim3(256), 0, s, total, (const float4*)(part + nparts), adv);
+    int nb = (int)((total / 4 + 255) / 256);
+    if (nb < 1) nb = 1;
+    if (nb > 4 * 148) nb = 4 * 148;     // four blocks of 256 per SM, grid-stride
+    e = launch_pdl(gae_normalize_kernel, dim3(nb), dim3(256), 0, s, total, (const float4*)ms, adv);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
