@@ -216,6 +216,8 @@ def grouped_learners(torch, api, synth, steps=5, warmup=2):
         hfs.append(synth.heightfield(32 + i))
         params.append(synth.xavier_params(31 + i, 235, WORKLOAD["hidden"], 12))
     g = api.rl_group_create(cfgs, hfs, params)
+    for i in range(len(GROUP_SIZES)):          # each learner's GEMM tile shapes for its own sizes
+        api.rl_autotune(api.rl_group_learner(g, i))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(warmup):
         api.rl_group_train_iteration(g, use_graph=True)
@@ -236,7 +238,8 @@ def grouped_learners(torch, api, synth, steps=5, warmup=2):
     return {"learners": list(GROUP_SIZES), "env_steps_per_iteration": total, "ms_per_step": sum(times) / len(times),
             "env_steps_per_s": total * len(times) / (sum(times) / 1000.0), "device_status": -status,
             "what": "8 independent BF16 learners (own weights, Adam, alpha, curriculum), obs 235, 512-256-128, "
-                    "24 steps, 5x4 update each, replayed as one CUDA graph with one branch per learner"}
+                    "24 steps, 5x4 update each, tile shapes autotuned per learner, replayed as one CUDA graph with "
+                    "one branch per learner"}
 
 
 def large_config(torch, api, synth, steps=3, warmup=2):

@@ -288,6 +288,42 @@ __device__ __forceinline__ float elu_fast(float x) {
     return fmaxf(x, ex2_ftz(fminf(x, 0.f) * 1.4426950408889634f) - 1.f);
 }
 
+// Two fp32 values as one 64-bit register pair, for the packed (f32x2) add / multiply / fma of
+// sm_100-class SMs: one instruction for two lanes' worth of fp32 arithmetic, same rounding as the
+// scalar forms.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// elu_fast(a + ba), elu_fast(b + bb) with the bias add, the scaling by log2 e and the - 1 done as
+// packed pairs (the same operations and roundings as the scalar form, so the same bits)
+__device__ __forceinline__ void elu_bias2(float& a, float& b, float ba, float bb) {
+    float x0, x1, t0, t1, e0, e1;
+    f2_unpack(f2_add(f2_pack(a, b), f2_pack(ba, bb)), x0, x1);
+    f2_unpack(f2_mul(f2_pack(fminf(x0, 0.f), fminf(x1, 0.f)), f2_pack(1.4426950408889634f, 1.4426950408889634f)), t0, t1);
+    f2_unpack(f2_add(f2_pack(ex2_ftz(t0), ex2_ftz(t1)), f2_pack(-1.f, -1.f)), e0, e1);
+    a = fmaxf(x0, e0);
+    b = fmaxf(x1, e1);
+}
+
 // 16-byte asynchronous copy global -> shared through the load/store unit (cp.async), which leaves
 // the TMA unit to the operand stream; src_bytes 0 fills the 16 bytes with zeros and reads nothing.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
@@ -801,10 +837,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
                         const float4 bb = __ldg(bias4 + j4);
-                        v[4 * j4 + 0] = elu_fast(v[4 * j4 + 0] + bb.x);
-                        v[4 * j4 + 1] = elu_fast(v[4 * j4 + 1] + bb.y);
-                        v[4 * j4 + 2] = elu_fast(v[4 * j4 + 2] + bb.z);
-                        v[4 * j4 + 3] = elu_fast(v[4 * j4 + 3] + bb.w);
+                        elu_bias2(v[4 * j4 + 0], v[4 * j4 + 1], bb.x, bb.y);
+                        elu_bias2(v[4 * j4 + 2], v[4 * j4 + 3], bb.z, bb.w);
                     }
                     uint32_t o[16];
 #pragma unroll
@@ -846,8 +880,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const float y0 = __uint_as_float(hw[j] << 16), y1 = __uint_as_float(hw[j] & 0xFFFF0000u);
-                                v[8 * g + 2 * j] = fmaf(v[8 * g + 2 * j], fminf(y0, 0.f), v[8 * g + 2 * j]);
-                                v[8 * g + 2 * j + 1] = fmaf(v[8 * g + 2 * j + 1], fminf(y1, 0.f), v[8 * g + 2 * j + 1]);
+                                const uint64_t vv = f2_pack(v[8 * g + 2 * j], v[8 * g + 2 * j + 1]);
+                                f2_unpack(f2_fma(vv, f2_pack(fminf(y0, 0.f), fminf(y1, 0.f)), vv), v[8 * g + 2 * j],
+                                          v[8 * g + 2 * j + 1]);
                             }
                         }
                     } else {
