@@ -247,13 +247,15 @@ def large_config(torch, api, synth, steps=3, warmup=2):
     w = dict(WORKLOAD)
     w["num_envs"] = 16384
     L, O = make_learner(api, synth, api.RL_BF16, seed=40, w=w)
+    api.rl_autotune(L.ctx)                     # tile shapes for this learner's own sizes, as the main line
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     L.train_iteration(use_graph=True)
     times = time_iterations(torch, L, steps, warmup, flush)
     status = api.rl_last_device_status(L.ctx)
     L.close()
     return {"num_envs": 16384, "ms_per_step": sum(times) / len(times),
-            "env_steps_per_s": 16384 * 24 * len(times) / (sum(times) / 1000.0), "device_status": status}
+            "env_steps_per_s": 16384 * 24 * len(times) / (sum(times) / 1000.0), "device_status": status,
+            "tiles": "autotuned"}
 
 
 def actuator_lstm(torch, api, reps=5):
