@@ -158,8 +158,30 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         if (ok[0]) act_rows_load<HB, NK, 2>(p.act, mm, ok, true, lane, hc, ha);
         float* Wa = gtab + 2 * GTAB;
         float* Wc = Wa + p.act.A * p.act.H;
-        for (int i = tid; i < p.act.A * p.act.H; i += THREADS) Wa[i] = p.act.Wa[i];
-        for (int i = tid; i < p.act.H; i += THREADS) Wc[i] = p.act.Wc[i];
+        // every load of the staging issued before its stores (16-byte pieces where the layout
+        // allows), so that the block waits for one round trip to L2 instead of one per piece
+        const int nwa = p.act.A * p.act.H, nwc = p.act.H;
+        if (((reinterpret_cast<uintptr_t>(p.act.Wa) | reinterpret_cast<uintptr_t>(p.act.Wc)) & 15u) == 0 && nwa % 4 == 0 &&
+            nwc % 4 == 0) {
+            const float4* wa4 = reinterpret_cast<const float4*>(p.act.Wa);
+            const float4* wc4 = reinterpret_cast<const float4*>(p.act.Wc);
+            float4 ra[4], rc;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = tid + u * THREADS;
+                if (i < nwa / 4) ra[u] = __ldg(wa4 + i);
+            }
+            if (tid < nwc / 4) rc = __ldg(wc4 + tid);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = tid + u * THREADS;
+                if (i < nwa / 4) reinterpret_cast<float4*>(Wa)[i] = ra[u];
+            }
+            if (tid < nwc / 4) reinterpret_cast<float4*>(Wc)[tid] = rc;
+        } else {
+            for (int i = tid; i < nwa; i += THREADS) Wa[i] = p.act.Wa[i];
+            for (int i = tid; i < nwc; i += THREADS) Wc[i] = p.act.Wc[i];
+        }
         __syncthreads();
         {
             float* const as[2] = {act_s[r0], act_s[r1]};
@@ -451,7 +473,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             pxr[q] = R[R_PX]; pyr[q] = R[R_PY]; hcr[q] = R[R_HC]; hsr[q] = R[R_HS]; zr[q] = R[R_Z];
             ibxr[q] = __float_as_int(R[R_BX]); ibyr[q] = __float_as_int(R[R_BY]);
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
