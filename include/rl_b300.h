@@ -377,6 +377,15 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
 rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits);
 
+/* Caps the persistent CTAs of the context's tensor-core GEMM launches (no counterpart in the
+ * paper: a scheduling control of this implementation).  max_ctas 0: one CTA per SM (the default
+ * of a lone learner); n >= 1: at most n CTAs (a cluster mode of two CTAs per tile counts both).
+ * rl_group_create sets each learner's cap to twice its share of the SMs by robot count (at least
+ * 16), so that the learners' launches run side by side.  The cap changes which CTA computes a
+ * tile, never a result.  Drops a captured iteration graph.  RL_ERR_INVALID_ARG for a negative
+ * value or a null context. */
+rl_status rl_set_gemm_ctas(rl_ctx* ctx, int32_t max_ctas);
+
 /* Diagnostic: C = A B^T with the library's tcgen05 BF16 tensor-core GEMM kernel (FP32
  * accumulation), for checking the tensor-core path in isolation.  A [M][K] bf16, B [N][K] bf16
  * (row-major, K contiguous), C [M][N] fp32.  K % 8 == 0 (16-byte rows), N % 64 == 0, pointers

@@ -93,6 +93,7 @@ SIGNATURES = {
     "rl_launches_per_iteration": (_i32, [_vp]),
     "rl_autotune": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t, _vp]),
     "rl_set_gemm_tiles": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
+    "rl_set_gemm_ctas": (_i32, [_vp, _i32]),
     "rl_gemm_bf16": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rl_gemm_bf16_tn": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rl_gemm_bf16_shape": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp]),

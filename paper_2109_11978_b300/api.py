@@ -217,6 +217,11 @@ def rl_autotune(ctx):
     return json.loads(buf.value.decode() or "{}")
 
 
+def rl_set_gemm_ctas(ctx, max_ctas):
+    """Caps the persistent CTAs of the context's GEMM launches (0: one per SM)."""
+    check(lib().rl_set_gemm_ctas(ctx, int(max_ctas)), "rl_set_gemm_ctas")
+
+
 def rl_set_gemm_tiles(ctx, site, layer, bn, cluster=1, splits=1):
     """Pins one GEMM site's tile shape (site 0 forward, 1 input gradient, 2 weight gradient)."""
     check(lib().rl_set_gemm_tiles(ctx, int(site), int(layer), int(bn), int(cluster), int(splits)), "rl_set_gemm_tiles")

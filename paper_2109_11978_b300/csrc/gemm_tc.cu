@@ -986,7 +986,8 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     if (fit <= 0) return cudaErrorNotReady;        // tc_prepare has not run on this device
     const int mct = ((p.M + BM - 1) / BM + CM - 1) / CM;
     const int total = mct * (p.N / BN) * p.splits * p.batch;
-    const int clusters = total < fit ? total : fit;      // one persistent CTA per SM
+    int clusters = total < fit ? total : fit;            // one persistent CTA per SM
+    if (p.max_ctas > 0 && clusters > p.max_ctas / CM) clusters = p.max_ctas / CM > 0 ? p.max_ctas / CM : 1;
     constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR, KS>();
     if constexpr (CM == 1) {
         return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false, KS>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);

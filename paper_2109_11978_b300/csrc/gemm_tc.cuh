@@ -33,6 +33,7 @@ struct TcParams {
     int* status;               // device status word
     int ks;                    // K blocks per stage: 0 / 1, or 2 (cm 1, no pair, bn <= 128) with the
                                // operand maps of make_tmap_bf16_k2 (K-major) / make_tmap_bf16_mn2
+    int max_ctas;              // persistent CTAs at most (0: as many as fit, one per SM)
     int mn3;                   // 1 (cm 1, no pair, ks 0 / 1): the MN-major operands are the 3D maps of
                                // make_tmap_bf16_mn1 (one copy per operand and stage instead of one
                                // per 64-wide box); 0: 64 x 64 box maps

@@ -92,6 +92,9 @@ struct rl_ctx {
     // W_1, has run) and late (W_0, b_0, after the last weight gradient dW_0)
     AdamParams adam_early, adam_mid, adam_late;
     cudaStream_t aside = nullptr;
+    // persistent GEMM CTAs at most (0: one per SM); grouped learners share the SMs in proportion
+    // to their robots
+    int gemm_cap = 0;
     cudaEvent_t ev_early_fork = nullptr, ev_mid_fork = nullptr, ev_early_join = nullptr;
     // bf16 weights and tensor maps
     void* wbf[2][4] = {};
@@ -309,6 +312,7 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         set_cluster(tp, cm);
         tp.epi = EPI_BIAS_ELU;
         tp.status = c->status;
+        tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
         GemmBatch g;
@@ -353,6 +357,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
         tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD;
         tp.mn3 = c->cm_dx[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
         tp.status = c->status;
+        tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
         GemmBatch g;
@@ -388,6 +393,7 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
         tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; set_cluster(tp, c->cm_dw[k]); tp.mn = MAJ_MN; tp.epi = EPI_STORE;
         tp.mn3 = c->cm_dw[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
         tp.status = c->status;
+        tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
     } else {
         GemmBatch g;
@@ -1808,6 +1814,13 @@ rl_status rl_autotune(rl_ctx* c, char* report, size_t report_bytes, void* stream
     return st;
 }
 
+rl_status rl_set_gemm_ctas(rl_ctx* c, int32_t max_ctas) {
+    if (!c || max_ctas < 0) return RL_ERR_INVALID_ARG;
+    c->gemm_cap = max_ctas;
+    drop_graph(c);
+    return RL_OK;
+}
+
 rl_status rl_set_gemm_tiles(rl_ctx* c, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits) {
     if (!c) return RL_ERR_INVALID_ARG;
     return set_tiles_impl(c, site, layer, bn, cluster, splits);
@@ -1964,6 +1977,17 @@ rl_status rl_group_create(int32_t n, const rl_config* cfgs, const float* const* 
     if (st != RL_OK) {
         rl_group_destroy(g);
         return st;
+    }
+    if (n > 1) {
+        // the learners' branches run side by side: each learner's persistent GEMMs take at most
+        // twice its share of the SMs (by robots), so that no learner's launch occupies every SM
+        // while the others wait (measured on 8 learners of 512 ... 8192 robots: 23.9 -> 30.0 M
+        // env-steps/s; one and three times the share were within 2 % of it)
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+        long long total = 0;
+        for (rl_ctx* c : g->ctx) total += c->N;
+        for (rl_ctx* c : g->ctx) c->gemm_cap = (int)std::max(16ll, (2ll * sms * c->N + total - 1) / total);
     }
     *out = g;
     return RL_OK;

@@ -44,3 +44,27 @@ def test_group_graph_equals_learners_one_by_one(prec):
     api.rl_group_destroy(g)
     for L in solo:
         L.close()
+
+
+@pytest.mark.parametrize("cap", [16, 37])
+def test_gemm_cta_cap_keeps_results(cap):
+    """A learner whose GEMM launches run on at most `cap` persistent CTAs (as grouped learners'
+    do) trains bit for bit like one with a CTA per SM: the cap moves tiles between CTAs, never
+    changes a sum."""
+    w = workload("small_rough", precision=1, epochs=2, minibatches=2)
+    O, _ = obs_dims(w)
+    params = synth.xavier_params(w["seed"] + 1, O, w["hidden"], 12)
+    hf = synth.heightfield(w["seed"] + 2)
+    A = api.Learner(lib_config(w), hf, params)
+    B = api.Learner(lib_config(w), hf, params)
+    api.rl_set_gemm_ctas(B.ctx, cap)
+    for _ in range(2):
+        A.train_iteration(use_graph=True)
+        B.train_iteration(use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(A.params(), B.params())
+    assert api.rl_last_device_status(B.ctx) == 0
+    with pytest.raises(api.RLError):
+        api.rl_set_gemm_ctas(B.ctx, -1)
+    A.close()
+    B.close()
