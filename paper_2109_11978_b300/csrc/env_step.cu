@@ -4,13 +4,16 @@
 // observation with bilinear height samples and Table 4 noise.
 //
 // Layout: the env state is a structure of arrays in HBM ([57][N] fp32 + [3][N] int32).  A block
-// owns 16 robots.  Phase 1: the stand-in's independent recurrences of a robot (its 12 joints and
-// three base chains) on separate threads, the feet on a sixteenth, meeting in shared memory for
-// the reward and the reset, leaving a 60-float record per robot in shared memory.  Phase 2: all 8
-// warps assemble the observation rows (one robot per warp at a time, two adjacent columns per
-// lane), so the row of obs_pad floats (or bf16) leaves as full 128-byte lines and the 187 height
-// samples of a robot are gathered by 32 lanes in parallel from the L2-resident heightfield; the
-// rotated sample offsets of the grid come from a per-block table.
+// of 512 threads owns 16 robots.  Phase 0 (policy heads fused in): one warp per robot.  Phase 1:
+// the stand-in's independent recurrences of a robot (its 12 joints and three base chains) on
+// separate threads of the first 256, the feet on a sixteenth, meeting in shared memory for the
+// reward and the reset, leaving a 60-float record per robot in shared memory.  Phase 2: the 16
+// warps assemble the observation rows (a pair of robots per two warps, which take alternate
+// 64-column blocks, two adjacent columns per lane), so the row of obs_pad floats (or bf16) leaves
+// as full 128-byte lines and the height samples of a robot are gathered by many lanes in
+// parallel from the L2-resident heightfield; the rotated sample offsets of the grid come from a
+// per-block table.  At a few thousand robots the kernel is one wave of latency-bound blocks, so
+// the extra threads shorten each block's path rather than add throughput.
 #include "act_row.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -41,8 +44,6 @@ constexpr int SLOT_CMD = 133, SLOT_HEADING = 136, SLOT_EPLEN = 138, SLOT_OBS = 2
 // Foot-contact schedule of the stand-in.
 constexpr int CONTACT_PERIOD = 40, CONTACT_DUTY = 20, CONTACT_ENV_STRIDE = 7;
 
-// Block shapes: 256 threads owning 256 robots (large N, one robot per thread in phase 1), or
-// 256 threads owning 16 robots (small N: every SM gets a block or two).
 constexpr int REC = 64;         // floats per robot record in shared memory
 constexpr int GTAB = 1024;      // height-grid offset table entries (larger grids compute in place)
 
@@ -108,19 +109,20 @@ __device__ __forceinline__ float terrain_height(const float* __restrict__ hf, in
     return (1.f - fu) * (1.f - fv) * h00 + fu * (1.f - fv) * h10 + (1.f - fu) * fv * h01 + fu * fv * h11;
 }
 
-// Phase-1 roles of a block's 256 threads (16 robots): threads 0..191 one (robot, joint) pair
+// Phase-1 roles of the first 256 threads of a block (16 robots): threads 0..191 one (robot, joint) pair
 // each; then 16 threads each for the three independent base chains of the stand-in (planar
 // velocity / yaw / heading / position; vertical and roll / pitch rates; gravity direction and
 // height) and 16 for the feet (from thread 192 on: 16 threads per role).  Each role is a whole
 // number of warps or half-warps.
 constexpr int T_PLANE = 192;
+constexpr int T_ROLES = T_PLANE + 64;   // planar, rates, gravity, feet: 16 threads each
 
 // FUSE: 0, or 16 * bf16 + H / 32 of a fused policy head (its per-row evaluation runs first).
 template <int MODE, int FUSE>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
-__global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
+__global__ void __launch_bounds__(512, 2) env_step_kernel(EnvParams p) {
     pdl_wait();
     pdl_trigger();
-    constexpr int ENVS = 16, THREADS = 256;
+    constexpr int ENVS = 16, THREADS = 512;
     extern __shared__ float rec_raw[];
     float (*rec)[REC] = reinterpret_cast<float (*)[REC]>(rec_raw);       // [ENVS][REC]
     // exchange of phase 1: the joints' reward terms, the rates, the feet, the reset decision
@@ -145,17 +147,16 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     if constexpr (FUSE != 0) {
         // Phase 0 (fused policy head): the head weights into shared memory, then one warp per
         // robot evaluates mu, the sampled action, logp and V exactly as the action-head kernel
-        // does, writing the rollout's records and the block's actions / values for phase 1.
-        // the warp's two robots together (ENVS = 2 x the warps of the block); their hidden rows
-        // are loaded first, so that the loads overlap the staging of the head weights
-        static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
+        // does, writing the rollout's records and the block's actions / values for phase 1.  The
+        // warp's hidden rows are loaded first, so that the loads overlap the staging of the head
+        // weights.
+        static_assert(ENVS == THREADS / 32, "one robot per warp");
         constexpr bool HB = (FUSE >> 4) != 0;
         constexpr int NK = FUSE & 15;
-        const int r0 = warp, r1 = warp + THREADS / 32;
-        const int mm[2] = {env0 + r0, env0 + r1};
-        const bool ok[2] = {env0 + r0 < N, env0 + r1 < N};
-        float hc[2][NK], ha[2][NK];
-        if (ok[0]) act_rows_load<HB, NK, 2>(p.act, mm, ok, true, lane, hc, ha);
+        const int mm[1] = {env0 + warp};
+        const bool ok[1] = {env0 + warp < N};
+        float hc[1][NK], ha[1][NK];
+        if (ok[0]) act_rows_load<HB, NK, 1>(p.act, mm, ok, true, lane, hc, ha);
         float* Wa = gtab + 2 * GTAB;
         float* Wc = Wa + p.act.A * p.act.H;
         // every load of the staging issued before its stores (16-byte pieces where the layout
@@ -165,15 +166,15 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             nwc % 4 == 0) {
             const float4* wa4 = reinterpret_cast<const float4*>(p.act.Wa);
             const float4* wc4 = reinterpret_cast<const float4*>(p.act.Wc);
-            float4 ra[4], rc;
+            float4 ra[2], rc;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 2; ++u) {
                 const int i = tid + u * THREADS;
                 if (i < nwa / 4) ra[u] = __ldg(wa4 + i);
             }
             if (tid < nwc / 4) rc = __ldg(wc4 + tid);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 2; ++u) {
                 const int i = tid + u * THREADS;
                 if (i < nwa / 4) reinterpret_cast<float4*>(Wa)[i] = ra[u];
             }
@@ -184,9 +185,9 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         }
         __syncthreads();
         {
-            float* const as[2] = {act_s[r0], act_s[r1]};
-            float* const vs[2] = {&val_s[r0], &val_s[r1]};
-            if (ok[0]) act_rows_loaded<HB, NK, 2>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs, hc, ha);
+            float* const as[1] = {act_s[warp]};
+            float* const vs[1] = {&val_s[warp]};
+            if (ok[0]) act_rows_loaded<HB, NK, 1>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs, hc, ha);
         }
         __syncthreads();
     }
@@ -195,9 +196,10 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     // and the reset decision meet on the robot's planar thread through shared memory (the joint
     // terms summed in joint order).
     const bool joint = tid < T_PLANE;
+    const bool p1 = tid < T_ROLES;                                     // threads past the roles idle here
     const int lr = joint ? tid / 12 : (tid - T_PLANE) & 15;           // robot of the block
     const int jl = joint ? tid % 12 : 0;
-    const int role = joint ? 0 : 1 + (tid - T_PLANE) / 16;             // 1 planar, 2 rates, 3 grav, 4 feet
+    const int role = joint ? 0 : p1 ? 1 + (tid - T_PLANE) / 16 : 5;   // 1 planar, 2 rates, 3 grav, 4 feet, 5 idle
     const int e = env0 + lr;
     const bool valid = e < N;
     const int ec = valid ? e : N - 1;          // a readable robot for the threads of a missing one
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         vz = F(7); wx = F(8); wy = F(9);
     } else if (role == 3) {
         gx = F(11); gy = F(12); gz = F(13); z = F(RL_F_Z);
-    } else {
+    } else if (role == 4) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) tair[f] = F(RL_F_TAIR + f);
     }
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
                 vz = wx = wy = 0.f;
             } else if (role == 3) {
                 gx = gy = 0.f; gz = -1.f; z = znom(level);
-            } else {
+            } else if (role == 4) {
 #pragma unroll
                 for (int f = 0; f < 4; ++f) tair[f] = 0.f;
             }
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             vz = wx = wy = 0.f;
         } else if (role == 3) {
             gx = gy = 0.f; gz = -1.f; z = znom(0);
-        } else {
+        } else if (role == 4) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) tair[f] = 0.f;
         }
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             F(11) = gx; F(12) = gy; F(13) = gz; F(RL_F_Z) = z;
             R[6] = gx; R[7] = gy; R[8] = gz;
             R[R_Z] = z;
-        } else {
+        } else if (role == 4) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) F(RL_F_TAIR + f) = tair[f];
         }
@@ -451,10 +453,12 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
     }
     __syncthreads();
 
-    // Phase 2: observation rows, two columns per lane; a warp's two robots (warp, warp + 8) go
-    // through the column loop together, so that the height samples' loads of both rows (and of
-    // several column pairs, unrolled) are in flight at once.
-    static_assert(ENVS == 2 * (THREADS / 32), "two robots per warp");
+    // Phase 2: observation rows, two columns per lane; a warp's two robots (w, w + 8 for
+    // w = warp mod 8) go through the column loop together, so that the height samples' loads of
+    // both rows (and of several column pairs, unrolled) are in flight at once, and the two warps
+    // of a robot pair take alternate 64-column blocks of the row.
+    static_assert(ENVS == THREADS / 32, "two warps per robot pair");
+    constexpr int PW = ENVS / 2;                 // warps per column half
     {
         int ev[2];
         bool okr[2];
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
         int ibxr[2], ibyr[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int le = warp + q * (THREADS / 32);
+            const int le = (warp % PW) + q * PW;
             ev[q] = env0 + le;
             okr[q] = ev[q] < N;
             const float* R = rec[le];
@@ -473,8 +477,8 @@ __global__ void __launch_bounds__(256, 2) env_step_kernel(EnvParams p) {
             pxr[q] = R[R_PX]; pyr[q] = R[R_PY]; hcr[q] = R[R_HC]; hsr[q] = R[R_HS]; zr[q] = R[R_Z];
             ibxr[q] = __float_as_int(R[R_BX]); ibyr[q] = __float_as_int(R[R_BY]);
         }
-#pragma unroll 4
-        for (int c0 = 2 * lane; c0 < p.Op; c0 += 64) {
+#pragma unroll 2
+        for (int c0 = 2 * lane + 64 * (warp / PW); c0 < p.Op; c0 += 128) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (!okr[q]) continue;
@@ -523,13 +527,14 @@ template <int MODE, int FUSE>
 static cudaError_t launch_cfg(const EnvParams& p, cudaStream_t s) {
     size_t smem = ((size_t)16 * REC + 2 * GTAB) * sizeof(float);
     if (FUSE != 0) smem += (size_t)(p.act.A * p.act.H + p.act.H) * sizeof(float);
-    cudaError_t e = launch_pdl(env_step_kernel<MODE, FUSE>, dim3((p.N + 15) / 16), dim3(256), smem, s, p);
+    cudaError_t e = launch_pdl(env_step_kernel<MODE, FUSE>, dim3((p.N + 15) / 16), dim3(512), smem, s, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 // Shared memory: 12 KiB per block (16 robot records + the grid table), plus at most 13 KiB of
-// head weights when the policy head is fused: within the default limit, nothing to set.
+// head weights when the policy head is fused: within the default limit, nothing to set.  Blocks
+// of 512 threads, 16 robots each.
 cudaError_t env_prepare() { return cudaSuccess; }
 
 cudaError_t launch_env_step(const EnvParams& p, int mode, cudaStream_t s) {
