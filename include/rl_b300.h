@@ -368,8 +368,11 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * layer: hidden layer index; bn: output tile width 64, 128 or 256 dividing the site's output
  * width; cluster: 1 (one CTA per 128-row tile), 3 (pairs of CTAs run one 256-row tile on the
  * cta_group::2 MMA, each loading half of B) or 4 (one CTA per tile, two K blocks per pipeline
- * stage fetched by one 3D TMA copy per operand); 3 needs at least two 128-row tiles at the site
- * and a tile width of at least 128, 4 a tile width of at most 128 (2, a B tile shared by TMA
+ * stage fetched by one 3D TMA copy per operand) or 5 (weight-stationary, sites 0, 1 and 3: each
+ * CTA keeps one column tile of the layer's weights in shared memory and streams the activations of
+ * its row tiles, two K blocks per stage); 3 needs at least two 128-row tiles at the site and a
+ * tile width of at least 128, 4 a tile width of at most 128, 5 a weight slice (tile width x the
+ * layer's K x 2 bytes) that leaves room for a stage of the ring (2, a B tile shared by TMA
  * multicast, is not offered and returns RL_ERR_INVALID_ARG);
  * splits: weight-gradient split-K count (1 .. the larger of twice the default and two waves of
  * 64-wide tiles over 148 SMs, rounded so every slice is a multiple of 64 rows), ignored for the
@@ -379,7 +382,8 @@ rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn
 
 /* Caps the persistent CTAs of the context's tensor-core GEMM launches (no counterpart in the
  * paper: a scheduling control of this implementation).  max_ctas 0: one CTA per SM (the default
- * of a lone learner); n >= 1: at most n CTAs (a cluster mode of two CTAs per tile counts both).
+ * of a lone learner); n >= 1: at most n CTAs (a cluster mode of two CTAs per tile counts both;
+ * a weight-stationary site runs at least one CTA per (network, column tile) group).
  * rl_group_create sets each learner's cap to twice its share of the SMs by robot count (at least
  * 16), so that the learners' launches run side by side.  The cap changes which CTA computes a
  * tile, never a result.  Drops a captured iteration graph.  RL_ERR_INVALID_ARG for a negative

@@ -35,6 +35,8 @@ namespace {
 constexpr int EPI_WARPS = 16;                      // epilogue warps (four per TMEM lane quarter)
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;    // warp 0: TMA, warp 1: MMA + TMEM owner
 constexpr int BM = 128, BK = 64;
+constexpr int PROD_LANES = 4;                      // producer lanes of the weight-stationary form
+constexpr unsigned PROD_MASK = (1u << PROD_LANES) - 1u;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -384,6 +386,22 @@ struct TileCfg {
     static constexpr int SMEM = STAGES * STAGE + FIXED;
 };
 
+// Weight-stationary layout (tile mode WS, single CTA): the epilogue's staging blocks and a 1 KB
+// barrier block first, then a ring of A stages of two K blocks each (one 3D copy per stage), then
+// the CTA's resident B slice (kblocks x BN rows x 128 bytes, sized at run time), with as many ring
+// stages as fit (at most 8) in the largest dynamic shared memory of a block.
+template <int BN, int EPI>
+struct WsCfg {
+    using C = TileCfg<BN, EPI>;
+    static constexpr int A_STAGE = 2 * C::A_BYTES;
+    static constexpr int FRONT = C::STG_BYTES + 1024;
+    static constexpr int SMEM = 227 * 1024;
+    static constexpr int USABLE = SMEM - 1024;              // after aligning the base to 1 KB
+    __host__ __device__ static constexpr int stages(int kblocks) {
+        return (USABLE - FRONT - kblocks * BN * 128) / A_STAGE > 8 ? 8 : (USABLE - FRONT - kblocks * BN * 128) / A_STAGE;
+    }
+};
+
 // The tile sequence of one persistent CTA, t = t0, t0 + step, ..., with each index decoded as
 // t = tm + mct (ni + nt (sp + splits b)) (cluster row tile, column tile, split, batch entry).  The
 // first index is divided out once; every step then adds the step's own decode with carries, so a
@@ -439,12 +457,14 @@ struct TileSeq {
 // number per K block lifts the narrow tiles' mainloop, which is bound by that per-stage cost rather
 // than by the tensor core.  A split or tile with an odd number of K blocks loads a whole last
 // stage and multiplies only its first half.
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     // PAIR: the cluster's two CTAs run one 256 x BN tile on the pair (cta_group::2) tensor core;
     // each CTA stages its 128 rows of A and half of B, the even CTA issues the MMAs
     static_assert(PAIR ? CM == 2 : CM == 1, "clusters of two run the pair MMA only; every other tile is one CTA's");
     static_assert(KS == 1 || (KS == 2 && CM == 1 && !PAIR && BN <= 128), "two-block stages: single CTA, BN <= 128");
+    static_assert(!WS || (CM == 1 && !PAIR && KS == 1 && MJ != MAJ_MN && EPI != EPI_STORE),
+                  "weight-stationary: single CTA, K-major A, forward or input-gradient epilogue");
     using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>;
     constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
     constexpr bool B_MN = MJ != MAJ_K;                      // B^T [K][N] in memory
@@ -454,18 +474,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     constexpr uint16_t MC_MASK = (uint16_t)((1u << CM) - 1u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* stage_t = smem + C::STAGES * C::STAGE;
-    float* bias_s = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STG_BYTES);
-    (void)bias_s;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
-    // barriers: full[S], empty[S], tfull[NACC], tempty[NACC], drain (the area keeps room for
-    // 2 EPI_WARPS more)
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
+    using W = WsCfg<BN, EPI>;
+    // ring stages (run-time in WS mode, where the resident B slice takes its share first)
+    const int NS = WS ? W::stages(p.kblocks) : C::STAGES;
+    constexpr int NSMAX = WS ? 8 : C::STAGES;               // barrier slots per ring role
+    uint8_t* stage_t = WS ? smem : smem + C::STAGES * C::STAGE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(WS ? smem + C::STG_BYTES : smem + C::STAGES * C::STAGE + C::STG_BYTES + C::BIAS_BYTES);
+    uint8_t* ring = WS ? smem + W::FRONT : smem;             // the operand stages
+    uint8_t* bres = ring + (WS ? NS * W::A_STAGE : 0);       // WS: the resident B slice
+    (void)bres;
+    // barriers: full[S], empty[S], tfull[NACC], tempty[NACC], drain, bfull (WS: the B slice) (the
+    // area keeps room for 2 EPI_WARPS more)
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSMAX);
     constexpr int NACC = C::NACC;
-    const uint32_t tfull0 = smem_u32(bars + 2 * C::STAGES), tempty0 = smem_u32(bars + 2 * C::STAGES + NACC);
-    const uint32_t drain = smem_u32(bars + 2 * C::STAGES + 2 * NACC);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS);
-    static_assert((2 * C::STAGES + 2 * NACC + 1 + 2 * EPI_WARPS) * 8 + 8 <= C::BAR_BYTES, "barrier area");
+    const uint32_t tfull0 = smem_u32(bars + 2 * NSMAX), tempty0 = smem_u32(bars + 2 * NSMAX + NACC);
+    const uint32_t drain = smem_u32(bars + 2 * NSMAX + 2 * NACC);
+    const uint32_t bfull = drain + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSMAX + 2 * NACC + 2 + 2 * EPI_WARPS);
+    static_assert((2 * NSMAX + 2 * NACC + 2 + 2 * EPI_WARPS) * 8 + 8 <= (WS ? 1024 : C::BAR_BYTES), "barrier area");
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     // a pair instantiation launched without its cluster shape would address a CTA that does not
@@ -484,10 +510,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const TileStep tstep{ncl, mct, nt, p.splits, ncl % mct, ncl / mct};
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full0 + 8 * s, PAIR ? 2 : 1);             // pair: one arrival per CTA (even CTA's)
             mbar_init(empty0 + 8 * s, PAIR ? 1 : CM);
         }
+        mbar_init(bfull, 1);
         for (int a = 0; a < NACC; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
             mbar_init(tempty0 + 8 * a, PAIR ? 2 * EPI_WARPS : EPI_WARPS);
@@ -526,7 +553,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     };
 
     if (warp == 0) {
-        if (lane == 0) {
+        if constexpr (WS) {
+            // ---------------- TMA producer, weight-stationary: CTA cid serves the (network, column
+            // tile) group g = cid mod G and its row tiles cid / G, cid / G + ncl / G, ...; its B
+            // slice (every K block of the group's BN weight rows) is loaded once, spread over the
+            // producer lanes, and only A streams through the ring.  Lane 0 waits for each free stage
+            // and posts its byte count; the lanes then take the stages' copies in turn, since one
+            // thread's copies are served one after the other at a fixed cost each.
+            if (lane < PROD_LANES) {
+                const int G = nt * p.batch, gs = ncl / G, g = cid % G, jr = cid / G;
+                const int ni = g % nt, b = g / nt;
+                const CUtensorMap* ma = &p.tmA[b];
+                const CUtensorMap* mb = &p.tmB[b];
+                const bool has = jr < gs && jr < mct;
+                if (has) {
+                    if (lane == 0) mbar_expect_tx(bfull, (uint32_t)(p.kblocks * BN * 128));
+                    for (int kb = lane; kb < p.kblocks; kb += PROD_LANES) {
+                        const uint32_t dst = smem_u32(bres + (size_t)kb * BN * 128);
+                        if (!B_MN) tma_load_2d(dst, mb, bfull, kb * BK, ni * BN);
+                        else tma_load_3d(dst, mb, bfull, 0, kb * BK, ni * BN / 64);
+                    }
+                }
+                const int nst = (p.kblocks + 1) / 2;
+                int it = 0, s = 0;
+                uint32_t ph = 0;
+                bool ok = true;
+                for (int mi = jr; has && ok && mi < mct; mi += gs) {
+                    for (int i = 0; i < nst; ++i, ++it) {
+                        int got = 1;
+                        if (lane == 0) {
+                            got = mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, abort_flag) ? 1 : 0;
+                            if (got) mbar_expect_tx(full0 + 8 * s, (uint32_t)W::A_STAGE);
+                        }
+                        got = __shfl_sync(PROD_MASK, got, 0);
+                        if (!got) {
+                            if (lane == 0) *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        // K blocks 2 i, 2 i + 1 of the row tile (a missing second block reads zeros)
+                        if (lane == it % PROD_LANES) tma_load_3d(smem_u32(ring + s * W::A_STAGE), ma, full0 + 8 * s, 0, mi * BM, 2 * i);
+                        if (++s == NS) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+                if (lane == 0 && has && !ok) {
+                    // the copies issued land before the CTA leaves (bounded): the B slice and the
+                    // last ring stages
+                    mbar_wait(bfull, 0u, p.status);
+                    for (int k = 1; k <= NS && it - k >= 0; ++k) {
+                        const int j = it - k;
+                        mbar_wait(full0 + 8 * (j % NS), (uint32_t)(j / NS) & 1u, p.status);
+                    }
+                }
+            }
+        } else if (lane == 0) {
             // ---------------- TMA producer
             int it = 0;
             bool ok = true;
@@ -548,7 +631,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                         ok = false;
                         break;
                     }
-                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    const uint32_t sa = smem_u32(ring + s * C::STAGE);
                     if constexpr (KS == 2) {
                         // K blocks kb, kb + 1: K-major operands as two 64-column chunks of their rows,
                         // MN-major ones as 128 K rows of their 64-wide M / N chunks
@@ -621,13 +704,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (WS && lane == 0) {
+            // ---------------- MMA issuer, weight-stationary: A from the ring, B from the resident
+            // slice; eight MMAs (two K blocks) per stage hand-off
+            const uint32_t idesc = idesc_bf16<BN, false, B_MN>();
+            const int G = nt * p.batch, gs = ncl / G, jr = cid / G;
+            const uint64_t ad0 = sw128_desc(smem_u32(ring));
+            const uint64_t bd0 = B_MN ? sw128_desc_mn(smem_u32(bres), 8192u) : sw128_desc(smem_u32(bres));
+            constexpr uint64_t KSTEP_B = B_MN ? (2048 >> 4) : (32 >> 4);
+            constexpr uint64_t BKB = (uint64_t)(BN * 128) >> 4;      // one K block of the resident B
+            constexpr uint64_t ASUB = (uint64_t)C::A_BYTES >> 4;     // the stage's second K block
+            const int nst = (p.kblocks + 1) / 2;
+            const bool has = jr < gs && jr < mct;
+            bool ok = !has || mbar_wait(bfull, 0u, p.status, abort_flag);
+            if (!ok) *abort_flag = 1;
+            int local = 0, s = 0;
+            uint32_t ph = 0;
+            for (int mi = jr; has && ok && mi < mct; mi += gs, ++local) {
+                const int a = local % NACC;
+                const uint32_t aph = (uint32_t)(local / NACC) & 1u;
+                if (!mbar_wait(tempty0 + 8 * a, aph ^ 1u, p.status, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * BN);
+                for (int i = 0; i < nst; ++i) {
+                    if (!mbar_wait(full0 + 8 * s, ph, p.status, abort_flag)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = ad0 + (uint64_t)((s * W::A_STAGE) >> 4);
+                    const int nsub = min(2, p.kblocks - 2 * i);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        if (j >= nsub) break;
+                        const uint64_t bd = bd0 + BKB * (uint64_t)(2 * i + j);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16(d, ad + ASUB * j + 2 * kk, bd + KSTEP_B * kk, idesc, (i > 0 || j > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(empty0 + 8 * s);
+                    if (++s == NS) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull0 + 8 * a);
+            }
+            // drain: every MMA issued has finished before the TMEM is freed
+            mma_commit(drain);
+            mbar_wait(drain, 0u, p.status);
+        } else if (!WS && lane == 0) {
             // ---------------- MMA issuer (pair mode: the even CTA only)
             const uint32_t idesc = idesc_bf16<BN, A_MN, B_MN, PAIR ? 2 * BM : BM>();
             int it = 0, local = 0;
             bool ok = true;
             const bool issuer = !PAIR || rank == 0;
-            const uint32_t sa0 = smem_u32(smem);
+            const uint32_t sa0 = smem_u32(ring);
             constexpr uint32_t LBO = KS == 2 ? 16384u : 8192u;   // MN-major: bytes between 64-wide chunks
             const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0, LBO) : sw128_desc(sa0);
             const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + KS * C::A_BYTES, LBO) : sw128_desc(sa0 + KS * C::A_BYTES);
@@ -728,15 +865,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             sp = r % p.splits;
             b = r / p.splits;
         };
+        // the k-th tile of this CTA (false past its last): tile cid + k ncl of the global order, or
+        // in WS mode row tile cid / G + k ncl / G of its group (network, column tile) cid mod G
+        auto tile_at = [&](int k, int& mi, int& ni, int& sp, int& b) -> bool {
+            if constexpr (WS) {
+                const int G = nt * p.batch, gs = ncl / G, g = cid % G;
+                mi = cid / G + k * gs;
+                ni = g % nt;
+                b = g / nt;
+                sp = 0;
+                return cid / G < gs && mi < mct;
+            } else {
+                const int t = cid + k * ncl;
+                if (t >= total) return false;
+                decode(t, mi, ni, sp, b);
+                return true;
+            }
+        };
         auto h_issue = [&](int j) {
-            // chunk j of this warp's sequence: tile cid + (j / CPT) ncl, column chunk j % CPT
-            const int t = cid + (j / CPT) * ncl;
+            // chunk j of this warp's sequence: the CTA's tile j / CPT, column chunk j % CPT
             // the output store that last read the buffer (chunk j - 2) is done reading it
             if (lane == 0) bulk_wait_read<0>();
             __syncwarp();
-            if (t < total) {
-                int mi, ni, sp, b;
-                decode(t, mi, ni, sp, b);
+            int mi, ni, sp, b;
+            if (tile_at(j / CPT, mi, ni, sp, b)) {
                 const int x = ni * BN + slice * C::SLICE_COLS + 32 * (j % CPT);
                 const int y = mi * BM + 32 * q;
                 const uint32_t dst = smem_u32(stg_raw + 2048 * (j & 1));
@@ -754,10 +906,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         };
         if (EPI == EPI_ELU_GRAD && busy) h_issue(0);
         int oj = 0;                                              // bf16 output blocks written (buffer index)
-        int local = 0;
-        for (int t = cid; t < total; t += ncl, ++local) {
+        for (int local = 0;; ++local) {
             int mi, ni, sp, b, kb0;
-            decode(t, mi, ni, sp, b);
+            if (!tile_at(local, mi, ni, sp, b)) break;
             const int nkb = kblocks_of(sp, kb0);
             const int a = local % NACC;
             const uint32_t aph = (uint32_t)(local / NACC) & 1u;
@@ -931,7 +1082,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 // Clusters of CM CTAs that fit on the device at once (one CTA per SM), per instantiation;
 // measured once in tc_prepare (before any stream capture) and used to size the persistent grid.
 struct ClusterFit {
-    int clusters[3][3][3];    // [bn 64/128/256][epi][cm 1/2/4]
+    int clusters[3][3][3];    // [bn 64/128/256][epi][single CTA, weight-stationary, pair]
 };
 static ClusterFit g_fit[64];
 
@@ -939,20 +1090,20 @@ static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 
 // cluster modes of the ABI: 1 single CTA (and 4, its two-K-block form), 3 the cta_group::2 pair
 static int cm_index(int cm) { return cm == 1 || cm == 4 ? 0 : cm == 3 ? 2 : -1; }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false>
 constexpr int smem_of() {
-    return TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>::SMEM;
+    return WS ? WsCfg<BN, EPI>::SMEM : TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>::SMEM;
 }
-// slot of the cluster-fit table: 0 single CTA, 2 pair (slot 1 unused)
-template <int CM, bool PAIR>
+// slot of the cluster-fit table: 0 single CTA, 1 weight-stationary single CTA, 2 pair
+template <int CM, bool PAIR, bool WS = false>
 constexpr int fit_slot() {
-    return PAIR ? 2 : (CM == 1 ? 0 : 1);
+    return PAIR ? 2 : WS ? 1 : 0;
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false>
 cudaError_t set_attr(int dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_of<BN, EPI, CM, MJ, PAIR, KS>());
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS, WS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of<BN, EPI, CM, MJ, PAIR, KS, WS>());
     if (e != cudaSuccess) return e;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -974,21 +1125,29 @@ cudaError_t set_attr(int dev) {
         if (e != cudaSuccess) return e;
         if (fit > 0 && fit < n) n = fit;
     }
-    if (dev >= 0 && dev < 64) g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR>()] = n > 0 ? n : 1;
+    if (dev >= 0 && dev < 64) g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR, WS>()] = n > 0 ? n : 1;
     return cudaSuccess;
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int fit = (dev >= 0 && dev < 64) ? g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR>()] : 0;
+    int fit = (dev >= 0 && dev < 64) ? g_fit[dev].clusters[bn_index(BN)][EPI][fit_slot<CM, PAIR, WS>()] : 0;
     if (fit <= 0) return cudaErrorNotReady;        // tc_prepare has not run on this device
     const int mct = ((p.M + BM - 1) / BM + CM - 1) / CM;
     const int total = mct * (p.N / BN) * p.splits * p.batch;
     int clusters = total < fit ? total : fit;            // one persistent CTA per SM
     if (p.max_ctas > 0 && clusters > p.max_ctas / CM) clusters = p.max_ctas / CM > 0 ? p.max_ctas / CM : 1;
-    constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR, KS>();
+    constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR, KS, WS>();
+    if constexpr (WS) {
+        // a whole number of CTAs per (network, column tile) group, at least one each (a CTA cap
+        // below the group count is raised to it)
+        const int G = (p.N / BN) * p.batch;
+        if (G > fit) return cudaErrorInvalidValue;
+        clusters = clusters < G ? G : clusters / G * G;
+        return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false, 1, true>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);
+    }
     if constexpr (CM == 1) {
         return launch_pdl(tc_gemm_kernel<BN, EPI, 1, MJ, false, KS>, dim3(clusters), dim3(TC_THREADS), SMEM, s, p);
     }
@@ -1016,6 +1175,10 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
 
 template <int BN, int EPI, int MJ>
 cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
+    if (p.ws) {
+        if constexpr (EPI != EPI_STORE && MJ != MAJ_MN) return launch_cfg<BN, EPI, 1, MJ, false, 1, true>(p, s);
+        return cudaErrorInvalidValue;
+    }
     if (p.cm == 1) {
         if (p.ks == 2) {
             if constexpr (BN <= 128) return launch_cfg<BN, EPI, 1, MJ, false, 2>(p, s);
@@ -1062,6 +1225,11 @@ cudaError_t prepare_form(int dev) {
     e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, true>(dev);
     e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 2>(dev);
     e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 2>(dev);
+    if constexpr (EPI != EPI_STORE && MJ != MAJ_MN) {
+        e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 1, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 1, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ, false, 1, true>(dev);
+    }
     return e;
 }
 
@@ -1076,6 +1244,11 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.cm == 2 && !p.pair) return cudaErrorInvalidValue;     // clusters of two run the pair MMA only
     if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
     if (p.mn3 && (p.cm != 1 || p.pair || p.ks == 2 || p.mn == MAJ_K)) return cudaErrorInvalidValue;
+    // weight-stationary: single CTA, no split, forward (B K-major) or input gradient (B by the 3D
+    // MN-major maps), at least one ring stage beside the resident B slice
+    if (p.ws && (p.cm != 1 || p.pair || p.ks == 2 || p.splits != 1 || p.epi == EPI_STORE || (p.mn == MAJ_B_MN && !p.mn3) ||
+                 tc_ws_stages(p.bn, p.epi, p.kblocks) < 1))
+        return cudaErrorInvalidValue;
     if (p.epi == EPI_ELU_GRAD) {
         // activation rows are read as 16-byte pieces
         for (int b = 0; b < p.batch; ++b)
@@ -1203,6 +1376,17 @@ int tc_cluster_fit(int bn, int epi, int cm) {
     const int bi = bn_index(bn), ci = cm_index(cm);
     if (bi < 0 || ci < 0 || epi < 0 || epi > 2) return 0;
     return g_fit[dev].clusters[bi][epi][ci];
+}
+
+int tc_ws_stages(int bn, int epi, int kblocks) {
+    if (kblocks < 1) return 0;
+    const bool g = epi == EPI_ELU_GRAD;
+    switch (bn) {
+        case 64: return g ? WsCfg<64, EPI_ELU_GRAD>::stages(kblocks) : WsCfg<64, EPI_BIAS_ELU>::stages(kblocks);
+        case 128: return g ? WsCfg<128, EPI_ELU_GRAD>::stages(kblocks) : WsCfg<128, EPI_BIAS_ELU>::stages(kblocks);
+        case 256: return g ? WsCfg<256, EPI_ELU_GRAD>::stages(kblocks) : WsCfg<256, EPI_BIAS_ELU>::stages(kblocks);
+    }
+    return 0;
 }
 
 int tc_smem_bytes(int bn, int epi) {

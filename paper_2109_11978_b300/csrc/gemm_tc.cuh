@@ -37,6 +37,12 @@ struct TcParams {
     int mn3;                   // 1 (cm 1, no pair, ks 0 / 1): the MN-major operands are the 3D maps of
                                // make_tmap_bf16_mn1 (one copy per operand and stage instead of one
                                // per 64-wide box); 0: 64 x 64 box maps
+    int ws;                    // 1: weight-stationary (cm 1, no pair, one split; forward or input
+                               // gradient): each CTA keeps one (batch entry, column tile) B slice in
+                               // shared memory and streams its row tiles' A through the ring, A by
+                               // the two-K-block maps of make_tmap_bf16_k2, B by the maps of the
+                               // single-CTA form (K-major box 64 x bn; MN-major make_tmap_bf16_mn1,
+                               // mn3 = 1); the grid is a whole number of CTAs per group
 };
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);
@@ -55,6 +61,9 @@ int tc_stage_blocks(int bn, int cm, int pair);
 bool make_tmap_out(CUtensorMap* map, void* base, bool fp32, uint64_t splits, uint64_t rows, uint64_t cols, uint64_t ld,
                    uint64_t split_ld);
 int tc_smem_bytes(int bn, int epi);
+// ring stages of the weight-stationary form beside a resident B slice of kblocks K blocks (0 or
+// less: the slice does not fit)
+int tc_ws_stages(int bn, int epi, int kblocks);
 int tc_cluster_fit(int bn, int epi, int cm);   // clusters resident at once (after tc_prepare)
 cudaError_t tc_prepare();
 

@@ -211,16 +211,26 @@ struct Enq {
 };
 
 // Tile modes of a GEMM site: 1 one CTA per tile, 3 pairs of CTAs on one 256-row tile
-// (cta_group::2), 4 one CTA per tile with two K blocks per pipeline stage (bn <= 128).  (Mode 2,
-// pairs of row tiles sharing the B tile by TMA multicast, is not offered.)
+// (cta_group::2), 4 one CTA per tile with two K blocks per pipeline stage (bn <= 128), 5
+// weight-stationary (forward and input-gradient sites: each CTA keeps one column tile of the
+// weights in shared memory and streams its row tiles' activations, two K blocks per stage).
+// (Mode 2, pairs of row tiles sharing the B tile by TMA multicast, is not offered.)
 // B rows one CTA loads per K step for a K-major B (tile width bn, mode cm)
 uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 ? bn / 2 : bn); }
 void set_cluster(TcParams& tp, int cm) {
     tp.cm = cm == 3 ? 2 : 1;
     tp.pair = cm == 3 ? 1 : 0;
     tp.ks = cm == 4 ? 2 : 1;
+    tp.ws = cm == 5 ? 1 : 0;
 }
+// two-K-block stages of both operands (mode 4); of the A operand (modes 4 and 5)
 bool two_block(int cm) { return cm == 4; }
+bool a_two_block(int cm) { return cm == 4 || cm == 5; }
+// weight-stationary mode 5 fits a site: a ring stage beside the resident weight slice, and no
+// more (network, column tile) groups than SMs
+bool ws_fits(int bn, int epi, int kblocks, int width) {
+    return tc_ws_stages(bn, epi, kblocks) >= 1 && 2 * (width / bn) <= 148;
+}
 
 int pick_bn(int n) {
     if (n % 128 == 0) return 128;
@@ -238,10 +248,10 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         if (two_block(c->cm_act[l]))
             ok = ok && make_tmap_bf16_k2(&c->tm_actB2[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_act[l]);
         if (l > 0) ok = ok && make_tmap_bf16_k2(&c->tm_fwdA2[n][l], c->H[n][l - 1], c->rows, Li.in, Li.in, 128);
-        if (l > 0 && two_block(c->cm_dx[l])) {
+        if (l > 0 && a_two_block(c->cm_dx[l]))
             ok = ok && make_tmap_bf16_k2(&c->tm_dxA2[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
+        if (l > 0 && two_block(c->cm_dx[l]))
             ok = ok && make_tmap_bf16_mn2(&c->tm_dxB2[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_dx[l]);
-        }
         if (two_block(c->cm_dw[l])) {
             const void* xb2 = l == 0 ? c->X0 : c->H[n][l - 1];
             ok = ok && make_tmap_bf16_mn2(&c->tm_dwA2[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
@@ -258,8 +268,8 @@ bool encode_layer_maps(rl_ctx* c, int l) {
             ok = ok && make_tmap_bf16(&c->tm_dxA[n][l], c->dY[n][l], c->Mb, Li.out, Li.out, 128);
             // input gradient, B read MN-major: W_l [out][in] as it is stored; one 3D copy per stage
             // in single-CTA mode, 64 x 64 boxes otherwise
-            ok = ok && (c->cm_dx[l] == 1 ? make_tmap_bf16_mn1(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in,
-                                                               (uint32_t)c->bn_dx[l])
+            ok = ok && ((c->cm_dx[l] == 1 || c->cm_dx[l] == 5)
+                            ? make_tmap_bf16_mn1(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, (uint32_t)c->bn_dx[l])
                                          : make_tmap_bf16(&c->tm_dxB[n][l], c->wbf[n][l], Li.out, Li.in, Li.in, 64));
         }
         // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in]; one 3D copy per
@@ -286,15 +296,15 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         TcParams tp;
         std::memset(&tp, 0, sizeof(tp));
         const int bn = act ? c->bn_act[l] : c->bn_fwd[l], cm = act ? c->cm_act[l] : c->cm_fwd[l];
-        const bool k2 = two_block(cm);
+        const bool k2 = two_block(cm), ak2 = a_two_block(cm);
         for (int j = 0; j < nnets; ++j) {
             const int n = net0 + j;
             if (l == 0) {
-                const bool mk = k2 ? make_tmap_bf16_k2(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)
+                const bool mk = ak2 ? make_tmap_bf16_k2(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128)
                                    : make_tmap_bf16(&tp.tmA[j], X, (uint64_t)rows, (uint64_t)Li.in, (uint64_t)Li.in, 128);
                 if (!mk) return RL_ERR_CUDA;
             } else {
-                tp.tmA[j] = k2 ? c->tm_fwdA2[n][l] : c->tm_fwdA[n][l];
+                tp.tmA[j] = ak2 ? c->tm_fwdA2[n][l] : c->tm_fwdA[n][l];
             }
             if (k2) tp.tmB[j] = act ? c->tm_actB2[n][l] : c->tm_fwdB2[n][l];
             else tp.tmB[j] = act ? c->tm_actB[n][l] : c->tm_fwdB[n][l];
@@ -346,7 +356,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
         std::memset(&tp, 0, sizeof(tp));
         const bool k2 = two_block(c->cm_dx[k]);
         for (int n = 0; n < 2; ++n) {
-            tp.tmA[n] = k2 ? c->tm_dxA2[n][k] : c->tm_dxA[n][k];
+            tp.tmA[n] = a_two_block(c->cm_dx[k]) ? c->tm_dxA2[n][k] : c->tm_dxA[n][k];
             tp.tmB[n] = k2 ? c->tm_dxB2[n][k] : c->tm_dxB[n][k];
             if (!make_tmap_out(&tp.tmC[n], c->dY[n][k - 1], false, 1, (uint64_t)M, (uint64_t)Li.in, (uint64_t)Li.in, 0))
                 return RL_ERR_CUDA;
@@ -355,7 +365,7 @@ rl_status dx_layer(rl_ctx* c, Enq& q, int k, int M) {
         }
         tp.M = M; tp.N = Li.in; tp.ldh = Li.in; tp.kblocks = Li.out / 64; tp.kb_per_split = tp.kblocks; tp.splits = 1;
         tp.batch = 2; tp.bn = c->bn_dx[k]; set_cluster(tp, c->cm_dx[k]); tp.mn = MAJ_B_MN; tp.epi = EPI_ELU_GRAD;
-        tp.mn3 = c->cm_dx[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
+        tp.mn3 = (c->cm_dx[k] == 1 || c->cm_dx[k] == 5) ? 1 : 0;       // the maps of encode_layer_maps
         tp.status = c->status;
         tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
@@ -867,7 +877,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
         trials += buf;
     };
     const int bns[3] = {64, 128, 256};
-    const int cms[3] = {1, 3, 4};
+    const int cms[4] = {1, 3, 4, 5};
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
         const int row_tiles = (c->Mb + 127) / 128;
@@ -878,7 +888,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
             for (int bn : bns)
                 for (int cm : cms) {
                     if (Li.out % bn || (cm == 3 && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128) ||
-                        st != RL_OK)
+                        (cm == 5 && !ws_fits(bn, EPI_BIAS_ELU, Li.in / 64, Li.out)) || st != RL_OK)
                         continue;
                     c->bn_fwd[l] = bn;
                     c->cm_fwd[l] = cm;
@@ -899,7 +909,8 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 for (int bn : bns)
                     for (int cm : cms) {
                         if (Li.out % bn || (cm == 3 && act_tiles < 2) || (cm == 3 && bn < 128) ||
-                            (cm == 4 && bn > 128) || st != RL_OK)
+                            (cm == 4 && bn > 128) || (cm == 5 && !ws_fits(bn, EPI_BIAS_ELU, Li.in / 64, Li.out)) ||
+                            st != RL_OK)
                             continue;
                         c->bn_act[l] = bn;
                         c->cm_act[l] = cm;
@@ -921,7 +932,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 for (int bn : bns)
                     for (int cm : cms) {
                         if (Li.in % bn || (cm == 3 && (row_tiles < 2 || bn < 128)) || (cm == 4 && bn > 128) ||
-                            st != RL_OK)
+                            (cm == 5 && !ws_fits(bn, EPI_ELU_GRAD, Li.out / 64, Li.in)) || st != RL_OK)
                             continue;
                         c->bn_dx[l] = bn;
                         c->cm_dx[l] = cm;
@@ -946,6 +957,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
                 for (int cm : cms) {
+                    if (cm == 5) continue;                                               // weight gradients stream both operands
                     if (cm == 3 && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
                     if (cm == 4 && (!c->bf16 || bn > 128)) continue;
                     // split counts: one or two waves of this width's tiles over the SMs, and the
@@ -1011,9 +1023,12 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
 // weight-gradient K chunk and split count it implies (the current ones for the other sites).
 rl_status check_tiles(const rl_ctx* c, int site, int l, int bn, int cm, int splits, int* kc_out, int* S_out) {
     if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
-    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 3 && cm != 4)) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 3 && cm != 4 && cm != 5)) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
     const int width = (site == 0 || site == 3) ? Li.out : Li.in;
+    if (cm == 5 && (site == 2 || width % bn ||
+                    !ws_fits(bn, site == 1 ? EPI_ELU_GRAD : EPI_BIAS_ELU, (site == 1 ? Li.out : Li.in) / 64, width)))
+        return RL_ERR_INVALID_ARG;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
     const bool paired = cm == 3;
     if (width % bn || (paired && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128)) return RL_ERR_INVALID_ARG;

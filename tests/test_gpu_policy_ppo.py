@@ -230,11 +230,14 @@ def test_autotune_keeps_results(form):
 
 @pytest.mark.parametrize("bn,cm,splits", [(64, 1, "one"), (64, 1, "most"), (128, 1, "most"), (128, 1, "one"),
                                           (256, 1, "one"), (256, 1, "most"), (128, 3, "one"), (256, 3, "most"),
-                                          (64, 4, "most"), (128, 4, "one"), (128, 4, "most")])
+                                          (64, 4, "most"), (128, 4, "one"), (128, 4, "most"), (64, 5, "one"),
+                                          (128, 5, "one"), (256, 5, "one")])
 def test_gemm_tile_shapes_keep_results(bn, cm, splits):
     """Every tile width and tile mode of the tensor-core GEMM (1: one CTA per tile; 3: CTA pairs
     on the cta_group::2 MMA; 4: two K blocks per pipeline stage, so splits of an odd K-block count
-    end on a half-used stage), pinned at every site where it is valid, gives
+    end on a half-used stage; 5: weight-stationary, the forward and input-gradient sites only, with
+    more CTAs per (network, column tile) group than the rollout site's 4 row tiles, so some CTAs
+    have no tile), pinned at every site where it is valid, gives
     the oracle's gradient within the BF16 tolerance.  2880 minibatch rows = 23 row tiles: the last
     pair of a cluster has one tile past the rows, and the last row tile is ragged."""
     w = workload("rough", num_envs=480, precision=1)
@@ -284,9 +287,11 @@ def test_gemm_tile_shapes_keep_results(bn, cm, splits):
 def test_set_gemm_tiles_rejects_invalid():
     w = workload("tiny", precision=1)
     L, _, _, _ = _setup(w)
-    for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 5, 1), (0, 9, 64, 1, 1),
+    # (site, layer, bn, cluster, splits): the weight-stationary mode 5 is refused at the weight
+    # gradient, mode 6 does not exist
+    for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 6, 1), (0, 9, 64, 1, 1),
                  (2, 0, 64, 1, 0), (3, 0, 128, 1, 1), (0, 0, 64, 3, 1), (0, 0, 256, 4, 1), (0, 0, 64, 2, 1),
-                 (0, 0, 128, 2, 1)):
+                 (0, 0, 128, 2, 1), (2, 0, 64, 5, 1)):
         with pytest.raises(api.RLError):
             api.rl_set_gemm_tiles(L.ctx, *args)
     L.close()
