@@ -84,11 +84,19 @@ def read_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum summed over the 235 GEMM launches of one iteration
-# of the rough-terrain workload (ncu, one pass per launch, cold caches), captured on the current
-# GEMM build (`bench.py --profile-run 1` under ncu); set to None whenever the GEMM kernel changes,
-# until it is captured again.
-GEMM_DRAM_BYTES_PER_ITERATION = 8005.1e6 + 254.6e6
+# dram__bytes_read.sum + dram__bytes_write.sum summed over the GEMM launches of one iteration of
+# the rough-terrain workload (ncu, one pass per launch), with the SHA-1 of the GEMM source it was
+# captured on: the figure is reported only while the kernel source is unchanged (null otherwise,
+# until captured again).
+GEMM_DRAM = {"gemm_tc_sha1": None, "bytes_per_iteration": None, "profile": None}
+
+
+def gemm_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2109_11978_b300", "csrc", "gemm_tc.cu"), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    ok = GEMM_DRAM["gemm_tc_sha1"] == sha and GEMM_DRAM["bytes_per_iteration"] is not None
+    return (GEMM_DRAM["bytes_per_iteration"] if ok else None), sha
 
 
 def gemm_flops_per_iteration(w, O):
@@ -101,6 +109,34 @@ def gemm_flops_per_iteration(w, O):
     dx_row = sum(2 * i * o for i, o in layers[1:])
     rollout = T * N * 2 * fwd_row + N * fwd_row                   # act (actor + critic) + last value
     update = E * MB * Mb * 2 * (fwd_row + dx_row + fwd_row)      # forward, input grads, weight grads
+    return rollout + update
+
+
+def gemm_bytes_per_iteration(w, O, splits):
+    """Algorithmic HBM bytes of the MLP GEMM launches of one iteration: every operand read once and
+    every result written once per launch (bf16 activations, gradients and weights, fp32 split-K
+    partials of the weight gradients, `splits` per hidden layer), nothing kept between launches.
+    The layer-0 input is the padded observation row (both networks read the same rows)."""
+    N, T, E, MB = w["num_envs"], w["num_steps"], w["epochs"], w["minibatches"]
+    Mb = N * T // MB
+    Op = (O + 63) // 64 * 64
+    dims = [Op] + list(w["hidden"])
+    layers = list(zip(dims[:-1], dims[1:]))
+
+    def fwd(rows, nets):
+        b = 0
+        for l, (i, o) in enumerate(layers):
+            a_in = rows * i * 2 * (1 if l == 0 else nets)
+            b += a_in + nets * (o * i * 2 + rows * o * 2)
+        return b
+
+    dx = sum(2 * (Mb * o * 2 + o * i * 2 + Mb * i * 2 + Mb * i * 2) for (i, o) in layers[1:])
+    dw = 0
+    for l, (i, o) in enumerate(layers):
+        x_in = Mb * i * 2 * (1 if l == 0 else 2)
+        dw += 2 * Mb * o * 2 + x_in + 2 * splits[l] * o * i * 4
+    rollout = T * fwd(N, 2) + fwd(N, 1)
+    update = E * MB * (fwd(Mb, 2) + dx + dw)
     return rollout + update
 
 
@@ -526,34 +562,66 @@ def main():
     gemm_ms = breakdown["gemm"]["ms_per_iteration"]
     gemm_n = breakdown["gemm"]["launches_per_iteration"]
     flops_iter = gemm_flops_per_iteration(w, O)
-    achieved = flops_iter / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else None
-    # the GEMM launches last 5-30 us each: the burst peak is the fair denominator (the sustained
-    # one, for seconds-long loops under the power cap, is reported beside it)
+    splits = {s_["layer"]: s_["splits"] for s_ in tuned["sites"] if s_["site"] == "weight_grad"}
+    bytes_iter = gemm_bytes_per_iteration(w, O, [splits.get(l, 1) for l in range(len(w["hidden"]))])
+    gemm_s = gemm_ms / 1000.0 if gemm_ms > 0 else None
+    # the GEMM launches last 5-30 us each: the burst peaks are the fair denominators (the sustained
+    # BF16 figure, for seconds-long loops under the power cap, is reported beside it)
     peak = peaks.get("bf16_tflops", 1800.0)
     peak_sus = peaks.get("bf16_tflops_sustained", 1400.0)
-    roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (all MLP GEMM launches of the iteration)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": GEMM_DRAM_BYTES_PER_ITERATION,
-            "traffic_note": "DRAM bytes (read + write) of the iteration's GEMM launches from one ncu capture of this "
-                            "workload and GEMM build, per iteration like achieved (null until captured)",
-            "peak_source": f"bf16_tflops burst ({peak_src})", "frac_of_sustained": (achieved / peak_sus) if achieved else None,
-            "gemm_launches_per_iteration": gemm_n,
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    t_flop = flops_iter / (peak * 1e12)          # s per iteration at the tensor peak
+    t_byte = bytes_iter / (hbm * 1e9)            # s per iteration at the HBM peak
+    tflops = flops_iter / gemm_s / 1e12 if gemm_s else None
+    gbs = bytes_iter / gemm_s / 1e9 if gemm_s else None
+    traffic, gemm_sha = gemm_traffic()
+    # the roofline binds at the lower ceiling: with the iteration's arithmetic intensity below the
+    # ridge point (every MLP GEMM here: K <= 512, outputs as wide as their inputs) that is HBM
+    hbm_bound = t_byte >= t_flop
+    roof = {"bound": "hbm" if hbm_bound else "tensor",
+            "kernel": "tc_gemm_kernel (all MLP GEMM launches of the iteration)",
+            "achieved": gbs if hbm_bound else tflops, "peak": hbm if hbm_bound else peak,
+            "unit": "GB/s" if hbm_bound else "TFLOP/s",
+            "frac": ((gbs / hbm) if hbm_bound else (tflops / peak)) if gemm_s else None,
+            "traffic": traffic,
+            "traffic_note": "DRAM bytes (read + write) of the iteration's GEMM launches from one ncu capture on this "
+                            "GEMM source (sha1 " + gemm_sha[:12] + "), per iteration like achieved; null when the "
+                            "source has changed since the capture",
+            "peak_source": f"hbm_gbs copy bandwidth / bf16_tflops burst ({peak_src})",
+            "algorithmic_bytes_per_iteration": bytes_iter, "algorithmic_flops_per_iteration": flops_iter,
+            "arithmetic_intensity_flop_per_byte": flops_iter / bytes_iter,
+            "ridge_flop_per_byte": peak * 1e12 / (hbm * 1e9),
+            "roofline_time_ms": max(t_flop, t_byte) * 1e3,
+            "tensor": {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": (tflops / peak) if tflops else None,
+                       "frac_of_sustained": (tflops / peak_sus) if tflops else None},
+            "gemm_ms_per_iteration": gemm_ms, "gemm_launches_per_iteration": gemm_n,
             "gemm_share_of_step": gemm_ms / (total_ms / args.steps) if total_ms else None,
-            "algorithmic_flops_per_iteration": flops_iter,
-            "achieved_note": "algorithmic FLOPs / summed in-graph CUDA-event time of the GEMM launches (profiled run)"}
+            "achieved_note": "algorithmic bytes (every operand read once, every result written once per launch) and "
+                             "FLOPs of the iteration's GEMM launches / their summed in-graph CUDA-event time "
+                             "(profiled run)"}
 
-    # --- end to end through the public API: stats read back to pinned host memory each step
+    # --- end to end through the public API with host buffers: the caller keeps the simulator state
+    # in pinned host memory between iterations; each step passes it in (rl_env_set_state), trains
+    # one iteration (rl_train_iteration, statistics to pinned host memory) and takes the state back
+    # (rl_env_get_state), host-timed with the stream synchronised every step
+    sf_h = torch.empty((api.RL_NF, N), dtype=torch.float32).pin_memory()
+    si_h = torch.empty((api.RL_NI, N), dtype=torch.int32).pin_memory()
     stats_host = torch.empty(api.RL_NSTATS, dtype=torch.float32).pin_memory()
+    api.rl_env_get_state(L.ctx, sf_h, si_h)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        api.rl_env_set_state(L.ctx, sf_h, si_h)
         L.train_iteration(use_graph=True, stats_host=stats_host)
+        api.rl_env_get_state(L.ctx, sf_h, si_h)
+        torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * N * T * args.steps / e2e_s, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": 4 * api.RL_NSTATS,
-           "note": "host-timed rl_train_iteration with the statistics copied to pinned host memory and the stream "
-                   "synchronised every iteration; the method keeps every per-step tensor on the GPU (Sec. 2), so no "
-                   "host input crosses per iteration"}
+    state_bytes = sf_h.numel() * sf_h.element_size() + si_h.numel() * si_h.element_size()
+    e2e = {"value": world * N * T * args.steps / e2e_s, "unit": "env-steps/s", "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes + stats_host.numel() * stats_host.element_size(),
+           "note": "host-timed through the C ABI with pinned host buffers: per iteration the env state in "
+                   "(rl_env_set_state), rl_train_iteration with its statistics copied out, the env state out "
+                   "(rl_env_get_state), stream synchronised"}
     L.close()
     del flush
 

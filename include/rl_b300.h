@@ -197,7 +197,13 @@ int64_t rl_checkpoint_bytes(rl_ctx* ctx);
 rl_status rl_checkpoint_save(rl_ctx* ctx, void* dst, size_t bytes, void* stream);
 rl_status rl_checkpoint_load(rl_ctx* ctx, const void* src, size_t bytes, void* stream);
 
-/* Env state access (layout above).  state_f: [RL_NF][num_envs] fp32, state_i: [RL_NI][num_envs]. */
+/* Env state access (layout above).  state_f: [RL_NF][num_envs] fp32, state_i: [RL_NI][num_envs],
+ * in device or host memory (the copy direction follows from the unified address space; a pinned
+ * host buffer keeps the copy asynchronous on stream, a pageable one makes it synchronous).  Both
+ * enqueue on stream and return without synchronising it: a host buffer may be read or reused only
+ * after the stream has reached the copy.  A caller that keeps the simulator state in host memory
+ * between iterations passes it in with rl_env_set_state before rl_train_iteration and takes it back
+ * with rl_env_get_state after it. */
 rl_status rl_env_get_state(rl_ctx* ctx, float* state_f, int32_t* state_i, void* stream);
 rl_status rl_env_set_state(rl_ctx* ctx, const float* state_f, const int32_t* state_i, void* stream);
 

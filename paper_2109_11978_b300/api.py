@@ -27,6 +27,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _ptr_any(t):
+    """A contiguous CUDA or host tensor (the env-state calls take either)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise RLError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -114,11 +123,11 @@ def rl_checkpoint_load(ctx, image):
 
 
 def rl_env_get_state(ctx, sf, si):
-    check(lib().rl_env_get_state(ctx, _ptr(sf), _ptr(si), _stream()), "rl_env_get_state")
+    check(lib().rl_env_get_state(ctx, _ptr_any(sf), _ptr_any(si), _stream()), "rl_env_get_state")
 
 
 def rl_env_set_state(ctx, sf, si):
-    check(lib().rl_env_set_state(ctx, _ptr(sf), _ptr(si), _stream()), "rl_env_set_state")
+    check(lib().rl_env_set_state(ctx, _ptr_any(sf), _ptr_any(si), _stream()), "rl_env_set_state")
 
 
 def rl_env_reset_all(ctx, obs_out=None):

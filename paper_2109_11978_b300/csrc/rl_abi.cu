@@ -1581,17 +1581,18 @@ rl_status rl_set_scalars(rl_ctx* c, double alpha, int64_t iteration, int64_t ada
     return RL_OK;
 }
 
+// host or device buffers: the copy direction follows from the unified address space
 rl_status rl_env_get_state(rl_ctx* c, float* sf, int32_t* si, void* stream) {
     if (!c || !sf || !si) return RL_ERR_INVALID_ARG;
-    CK(cudaMemcpyAsync(sf, c->sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
-    CK(cudaMemcpyAsync(si, c->si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(sf, c->sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDefault, S_(stream)));
+    CK(cudaMemcpyAsync(si, c->si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDefault, S_(stream)));
     return RL_OK;
 }
 
 rl_status rl_env_set_state(rl_ctx* c, const float* sf, const int32_t* si, void* stream) {
     if (!c || !sf || !si) return RL_ERR_INVALID_ARG;
-    CK(cudaMemcpyAsync(c->sf, sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
-    CK(cudaMemcpyAsync(c->si, si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDeviceToDevice, S_(stream)));
+    CK(cudaMemcpyAsync(c->sf, sf, sizeof(float) * (size_t)RL_NF * c->N, cudaMemcpyDefault, S_(stream)));
+    CK(cudaMemcpyAsync(c->si, si, sizeof(int) * (size_t)RL_NI * c->N, cudaMemcpyDefault, S_(stream)));
     return RL_OK;
 }
 

@@ -123,3 +123,40 @@ def test_damaged_tile_record_leaves_the_context_as_it_was():
     assert torch.equal(api.rl_checkpoint_save(B.ctx), before)
     A.close()
     B.close()
+
+
+def test_env_state_through_host_buffers_is_exact():
+    """The env-state calls take pinned host buffers as well as device ones: the state read into
+    host memory equals the one read on the device, and a training run whose state makes the round
+    trip through host memory every iteration (in before, out after) repeats the device-resident
+    run bit for bit (parameters, env state, the update's statistics; the mean reward sums
+    per-block partials with float atomics and matches to rounding)."""
+    w = workload("small_rough", precision=1)
+    La, Lb = _learner(w), _learner(w)
+    N = w["num_envs"]
+    sf_h = torch.empty((api.RL_NF, N), dtype=torch.float32).pin_memory()
+    si_h = torch.empty((api.RL_NI, N), dtype=torch.int32).pin_memory()
+    api.rl_env_get_state(Lb.ctx, sf_h, si_h)
+    torch.cuda.synchronize()
+    sf_d, si_d = Lb.get_state()
+    assert torch.equal(sf_h, sf_d.cpu()) and torch.equal(si_h, si_d.cpu())
+    ref = _run(La, 2)
+    got = []
+    for _ in range(2):
+        api.rl_env_set_state(Lb.ctx, sf_h, si_h)
+        s = torch.zeros(api.RL_NSTATS, dtype=torch.float32).pin_memory()
+        api.rl_train_iteration(Lb.ctx, True, s)
+        api.rl_env_get_state(Lb.ctx, sf_h, si_h)
+        torch.cuda.synchronize()
+        got.append(s.clone())
+    a, b = _snapshot(La), _snapshot(Lb)
+    assert torch.equal(a["params"], b["params"])
+    assert torch.equal(a["sf"], sf_h) and torch.equal(a["si"], si_h)
+    for x, y in zip(ref, got):
+        keep = torch.ones_like(x, dtype=torch.bool)
+        keep[7] = False
+        assert torch.equal(x[keep], y[keep])
+        assert abs(float(x[7]) - float(y[7])) <= 1e-6 * max(1.0, abs(float(x[7])))
+    assert api.rl_last_device_status(Lb.ctx) == 0
+    La.close()
+    Lb.close()
