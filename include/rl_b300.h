@@ -376,8 +376,13 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * cta_group::2 MMA, each loading half of B) or 4 (one CTA per tile, two K blocks per pipeline
  * stage fetched by one 3D TMA copy per operand) or 5 (weight-stationary, sites 0, 1 and 3: each
  * CTA keeps one column tile of the layer's weights in shared memory and streams the activations of
- * its row tiles, two K blocks per stage); 3 needs at least two 128-row tiles at the site and a
- * tile width of at least 128, 4 a tile width of at most 128, 5 a weight slice (tile width x the
+ * its row tiles, two K blocks per stage), or, at the weight gradient (site 2) only, 6 and 7
+ * (modes 1 and 4 with the split-K partials reduced inside the GEMM: the partials of a tile are
+ * computed by a cluster of c CTAs, c the largest divisor of the split count in 2 .. 8, which sum
+ * them in rank order through distributed shared memory, so that Adam sums splits / c partials;
+ * one CTA per tile and split, and no reduction for a learner whose GEMM CTAs are capped below that
+ * count); 3 needs at least two 128-row tiles at the site and a
+ * tile width of at least 128, 4 and 7 a tile width of at most 128, 5 a weight slice (tile width x the
  * layer's K x 2 bytes) that leaves room for a stage of the ring (2, a B tile shared by TMA
  * multicast, is not offered and returns RL_ERR_INVALID_ARG);
  * splits: weight-gradient split-K count (1 .. the larger of twice the default and two waves of

@@ -186,6 +186,12 @@ __device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t cbar, uint32_t b
     asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(cbar), "r"(bytes)
                  : "memory");
 }
+// 16 bytes of a cluster peer's shared memory (address from mapa_rank)
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t caddr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(caddr) : "memory");
+    return v;
+}
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
 }
@@ -457,7 +463,7 @@ struct TileSeq {
 // number per K block lifts the narrow tiles' mainloop, which is bound by that per-stage cost rather
 // than by the tensor core.  A split or tile with an odd number of K blocks loads a whole last
 // stage and multiplies only its first half.
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false, bool SR = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     // PAIR: the cluster's two CTAs run one 256 x BN tile on the pair (cta_group::2) tensor core;
     // each CTA stages its 128 rows of A and half of B, the even CTA issues the MMAs
@@ -465,6 +471,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     static_assert(KS == 1 || (KS == 2 && CM == 1 && !PAIR && BN <= 128), "two-block stages: single CTA, BN <= 128");
     static_assert(!WS || (CM == 1 && !PAIR && KS == 1 && MJ != MAJ_MN && EPI != EPI_STORE),
                   "weight-stationary: single CTA, K-major A, forward or input-gradient epilogue");
+    // SR: split-K reduction in a cluster.  Each CTA computes one tile; the p.sred CTAs of a cluster
+    // hold consecutive splits of the same tile, stage their fp32 partials in their own (idle) ring
+    // memory, and after a cluster barrier each sums a share of the tile's rows over the cluster's
+    // partials in rank order, writing one partial per cluster (split group) to p.sr_out.
+    static_assert(!SR || (EPI == EPI_STORE && CM == 1 && !PAIR && !WS), "split reduction: split-K partials, single CTA");
+    static_assert(!SR || TileCfg<BN, EPI, BN, KS>::STAGES * TileCfg<BN, EPI, BN, KS>::STAGE >= BM * (BN + 4) * 4,
+                  "the ring holds a padded fp32 tile");
     using C = TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>;
     constexpr bool A_MN = MJ == MAJ_MN;                     // A^T [K][M] in memory
     constexpr bool B_MN = MJ != MAJ_K;                      // B^T [K][N] in memory
@@ -508,6 +521,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int cid = CM > 1 ? (int)cluster_id_x() : (int)blockIdx.x;
     const int ncl = CM > 1 ? (int)nclusters_x() : (int)gridDim.x;
     const TileStep tstep{ncl, mct, nt, p.splits, ncl % mct, ncl / mct};
+    // SR: the CTA's one tile, t = r + sred (tm + mct (ni + nt (sg + SG b))) with r its rank in the
+    // cluster and split sg sred + r (ncl = total, so every role's tile loop runs once)
+    auto sr_tile = [&](TileSeq& ts) {
+        const int sred = p.sred, r = cid % sred;
+        int u = cid / sred;
+        ts.tm = u % mct;
+        u /= mct;
+        ts.ni = u % nt;
+        u /= nt;
+        const int SG = p.splits / sred;
+        ts.sp = (u % SG) * sred + r;
+        ts.b = u / SG;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -613,7 +639,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             // ---------------- TMA producer
             int it = 0;
             bool ok = true;
-            for (TileSeq ts(cid, tstep); ts.t < total && ok; ts.next(tstep)) {
+            TileSeq ts0(cid, tstep);
+            if (SR) sr_tile(ts0);
+            for (TileSeq ts = ts0; ts.t < total && ok; ts.next(tstep)) {
                 const int mi = ts.tm * CM + rank, ni = ts.ni, sp = ts.sp, b = ts.b;
                 int kb0;
                 const int nkb = kblocks_of(sp, kb0);
@@ -768,7 +796,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             constexpr uint32_t LBO = KS == 2 ? 16384u : 8192u;   // MN-major: bytes between 64-wide chunks
             const uint64_t ad0 = A_MN ? sw128_desc_mn(sa0, LBO) : sw128_desc(sa0);
             const uint64_t bd0 = B_MN ? sw128_desc_mn(sa0 + KS * C::A_BYTES, LBO) : sw128_desc(sa0 + KS * C::A_BYTES);
-            for (TileSeq ts(cid, tstep); issuer && ts.t < total && ok; ts.next(tstep), ++local) {
+            TileSeq ts0(cid, tstep);
+            if (SR) sr_tile(ts0);
+            for (TileSeq ts = ts0; issuer && ts.t < total && ok; ts.next(tstep), ++local) {
                 int kb0;
                 const int nkb = kblocks_of(ts.sp, kb0);
                 const int a = local % NACC;
@@ -878,7 +908,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             } else {
                 const int t = cid + k * ncl;
                 if (t >= total) return false;
-                decode(t, mi, ni, sp, b);
+                if (SR) {
+                    TileSeq ts(cid, tstep);
+                    sr_tile(ts);
+                    mi = ts.tm;
+                    ni = ts.ni;
+                    sp = ts.sp;
+                    b = ts.b;
+                } else {
+                    decode(t, mi, ni, sp, b);
+                }
                 return true;
             }
         };
@@ -962,7 +1001,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 }
                 const int col = n0 + c;
-                if (EPI == EPI_STORE) {
+                if (EPI == EPI_STORE && SR) {
+                    // the partial into this CTA's ring memory, free now that the tile's MMAs are
+                    // done: row 32 q + lane, padded rows (BN + 4 floats: 16-byte stores of 8 lanes
+                    // meet 32 different banks)
+                    float* red = reinterpret_cast<float*>(ring) + (size_t)(32 * q + lane) * (BN + 4) + c;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4)
+                        *reinterpret_cast<float4*>(red + 4 * j4) = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+                } else if (EPI == EPI_STORE) {
                     // two fp32 half blocks of 32 rows x 16 columns through the 2 KB buffer (64-byte
                     // swizzle: 16-byte unit u of row r at unit u ^ ((r >> 1) & 3)), each out by TMA
                     // store once the previous store from the buffer has read it
@@ -1068,6 +1115,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         if (EPI == EPI_ELU_GRAD) cp_async_wait<0>();
         if (lane == 0) bulk_wait_all();
     }
+    if constexpr (SR) {
+        // every CTA of the cluster has staged its partial (the barrier orders the shared-memory
+        // writes before the peers' reads); CTA r then sums rows [r BM / sred, (r + 1) BM / sred) of
+        // the tile over ranks 0 .. sred - 1 in order and writes them to its split group's partial;
+        // the second barrier keeps each CTA's memory until the peers have read it
+        __syncwarp();
+        cluster_sync_all();
+        if (warp >= 2) {
+            TileSeq ts(cid, tstep);
+            sr_tile(ts);
+            const int sred = p.sred, r = cid % sred, sg = ts.sp / sred;
+            const int r0 = r * BM / sred, r1 = (r + 1) * BM / sred;
+            const int m0 = ts.tm * BM, n0 = ts.ni * BN;
+            constexpr int C4 = BN / 4;
+            const uint32_t red0 = smem_u32(ring);
+            float* out = p.sr_out[ts.b] + (size_t)sg * p.sr_split_ld;
+            for (int e = threadIdx.x - 64; e < (r1 - r0) * C4; e += 32 * EPI_WARPS) {
+                const int row = r0 + e / C4, c4 = e % C4;
+                const uint32_t off = (uint32_t)((row * (BN + 4) + 4 * c4) * 4);
+                float4 acc = ld_cluster_f4(mapa_rank(red0 + off, 0));
+                for (int k = 1; k < sred; ++k) {
+                    const float4 x = ld_cluster_f4(mapa_rank(red0 + off, (uint32_t)k));
+                    acc.x += x.x;
+                    acc.y += x.y;
+                    acc.z += x.z;
+                    acc.w += x.w;
+                }
+                if (m0 + row < p.M)
+                    *reinterpret_cast<float4*>(out + (size_t)(m0 + row) * p.sr_ld + n0 + 4 * c4) = acc;
+            }
+        }
+        cluster_sync_all();
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -1090,7 +1170,7 @@ static int bn_index(int bn) { return bn == 64 ? 0 : bn == 128 ? 1 : bn == 256 ? 
 // cluster modes of the ABI: 1 single CTA (and 4, its two-K-block form), 3 the cta_group::2 pair
 static int cm_index(int cm) { return cm == 1 || cm == 4 ? 0 : cm == 3 ? 2 : -1; }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS, bool WS = false, bool SR = false>
 constexpr int smem_of() {
     return WS ? WsCfg<BN, EPI>::SMEM : TileCfg<BN, EPI, PAIR ? BN / 2 : BN, KS>::SMEM;
 }
@@ -1100,10 +1180,11 @@ constexpr int fit_slot() {
     return PAIR ? 2 : WS ? 1 : 0;
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false, bool SR = false>
 cudaError_t set_attr(int dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS, WS>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, CM, MJ, PAIR, KS, WS, SR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of<BN, EPI, CM, MJ, PAIR, KS, WS>());
+    if (SR) return e;                    // grid = the tile count; the fit table belongs to the plain forms
     if (e != cudaSuccess) return e;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1129,7 +1210,7 @@ cudaError_t set_attr(int dev) {
     return cudaSuccess;
 }
 
-template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false>
+template <int BN, int EPI, int CM, int MJ, bool PAIR, int KS = 1, bool WS = false, bool SR = false>
 cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1140,6 +1221,24 @@ cudaError_t launch_cfg(const TcParams& p, cudaStream_t s) {
     int clusters = total < fit ? total : fit;            // one persistent CTA per SM
     if (p.max_ctas > 0 && clusters > p.max_ctas / CM) clusters = p.max_ctas / CM > 0 ? p.max_ctas / CM : 1;
     constexpr int SMEM = smem_of<BN, EPI, CM, MJ, PAIR, KS, WS>();
+    if constexpr (SR) {
+        // one CTA per tile and split, clusters of p.sred consecutive splits of one tile
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)p.sred;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = dim3((unsigned)total);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = SMEM;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, EPI, 1, MJ, false, KS, false, true>, p);
+    }
     if constexpr (WS) {
         // a whole number of CTAs per (network, column tile) group, at least one each (a CTA cap
         // below the group count is raised to it)
@@ -1177,6 +1276,16 @@ template <int BN, int EPI, int MJ>
 cudaError_t launch_cm_mj(const TcParams& p, cudaStream_t s) {
     if (p.ws) {
         if constexpr (EPI != EPI_STORE && MJ != MAJ_MN) return launch_cfg<BN, EPI, 1, MJ, false, 1, true>(p, s);
+        return cudaErrorInvalidValue;
+    }
+    if (p.cm == 1 && p.sred >= 1) {
+        if constexpr (EPI == EPI_STORE && MJ == MAJ_MN) {
+            if (p.ks == 2) {
+                if constexpr (BN <= 128) return launch_cfg<BN, EPI, 1, MJ, false, 2, false, true>(p, s);
+                return cudaErrorInvalidValue;
+            }
+            return launch_cfg<BN, EPI, 1, MJ, false, 1, false, true>(p, s);
+        }
         return cudaErrorInvalidValue;
     }
     if (p.cm == 1) {
@@ -1225,6 +1334,13 @@ cudaError_t prepare_form(int dev) {
     e = e != cudaSuccess ? e : set_attr<256, EPI, 2, MJ, true>(dev);
     e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 2>(dev);
     e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 2>(dev);
+    if constexpr (EPI == EPI_STORE && MJ == MAJ_MN) {
+        e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 1, false, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 1, false, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<256, EPI, 1, MJ, false, 1, false, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 2, false, true>(dev);
+        e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 2, false, true>(dev);
+    }
     if constexpr (EPI != EPI_STORE && MJ != MAJ_MN) {
         e = e != cudaSuccess ? e : set_attr<64, EPI, 1, MJ, false, 1, true>(dev);
         e = e != cudaSuccess ? e : set_attr<128, EPI, 1, MJ, false, 1, true>(dev);
@@ -1244,6 +1360,13 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
     if (p.cm == 2 && !p.pair) return cudaErrorInvalidValue;     // clusters of two run the pair MMA only
     if (p.ks < 0 || p.ks > 2 || (p.ks == 2 && (p.cm != 1 || p.pair || p.bn > 128))) return cudaErrorInvalidValue;
     if (p.mn3 && (p.cm != 1 || p.pair || p.ks == 2 || p.mn == MAJ_K)) return cudaErrorInvalidValue;
+    // split reduction in a cluster: split-K partials of both-MN-major operands, single CTA, a cluster
+    // size of 1..8 dividing the split count, an output for the cluster partials
+    if (p.sred != 0 && (p.sred < 1 || p.sred > 8 || p.splits % p.sred || p.epi != EPI_STORE || p.mn != MAJ_MN || p.cm != 1 ||
+                        p.pair || p.ws || !p.sr_out[0] || (p.batch > 1 && !p.sr_out[1]) || p.sr_ld < p.N || p.sr_ld % 4 ||
+                        p.sr_split_ld % 4 || (reinterpret_cast<uintptr_t>(p.sr_out[0]) & 15u) ||
+                        (p.batch > 1 && (reinterpret_cast<uintptr_t>(p.sr_out[1]) & 15u))))
+        return cudaErrorInvalidValue;
     // weight-stationary: single CTA, no split, forward (B K-major) or input gradient (B by the 3D
     // MN-major maps), at least one ring stage beside the resident B slice
     if (p.ws && (p.cm != 1 || p.pair || p.ks == 2 || p.splits != 1 || p.epi == EPI_STORE || (p.mn == MAJ_B_MN && !p.mn3) ||

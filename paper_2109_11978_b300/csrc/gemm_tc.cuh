@@ -43,6 +43,12 @@ struct TcParams {
                                // the two-K-block maps of make_tmap_bf16_k2, B by the maps of the
                                // single-CTA form (K-major box 64 x bn; MN-major make_tmap_bf16_mn1,
                                // mn3 = 1); the grid is a whole number of CTAs per group
+    int sred;                  // split-K partials (EPI_STORE, MAJ_MN, cm 1): 0 writes every split's
+                               // partial through tmC; 1..8 reduces them in clusters of sred CTAs
+                               // holding consecutive splits of one tile (one CTA per tile and split),
+                               // writing splits / sred partials to sr_out
+    float* sr_out[2];          // per batch entry: partial g of element (m, n) at g sr_split_ld + m sr_ld + n
+    long long sr_ld, sr_split_ld;
 };
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);

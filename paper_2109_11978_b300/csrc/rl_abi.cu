@@ -220,12 +220,32 @@ uint32_t b_rows(int bn, int cm) { return (uint32_t)(cm == 3 ? bn / 2 : bn); }
 void set_cluster(TcParams& tp, int cm) {
     tp.cm = cm == 3 ? 2 : 1;
     tp.pair = cm == 3 ? 1 : 0;
-    tp.ks = cm == 4 ? 2 : 1;
+    tp.ks = (cm == 4 || cm == 7) ? 2 : 1;
     tp.ws = cm == 5 ? 1 : 0;
 }
-// two-K-block stages of both operands (mode 4); of the A operand (modes 4 and 5)
-bool two_block(int cm) { return cm == 4; }
-bool a_two_block(int cm) { return cm == 4 || cm == 5; }
+// two-K-block stages of both operands (modes 4, 7); of the A operand (modes 4, 5, 7)
+bool two_block(int cm) { return cm == 4 || cm == 7; }
+bool a_two_block(int cm) { return cm == 4 || cm == 5 || cm == 7; }
+
+// Cluster size of the in-GEMM split-K reduction of hidden layer l's weight gradient (modes 6, 7):
+// the largest d in 2 .. 8 dividing the split count (one CTA per tile and split, so only when the
+// learner's GEMMs are uncapped or the launch fits its cap); 0: every split's partial goes to Adam.
+int split_cluster(const rl_ctx* c, int l) {
+    if (!c->bf16 || (c->cm_dw[l] != 6 && c->cm_dw[l] != 7)) return 0;
+    const LayerInfo& Li = c->L[0][l];
+    const long long tiles = (long long)((Li.out + 127) / 128) * (Li.in / c->bn_dw[l]) * 2;
+    if (c->gemm_cap > 0 && tiles * c->S[l] > c->gemm_cap) return 0;
+    for (int d = 8; d >= 2; --d)
+        if (c->S[l] % d == 0) return d;
+    return 0;
+}
+// Partials of layer l's weight gradient that Adam sums.
+int weight_partials(const rl_ctx* c, int l) {
+    const int d = split_cluster(c, l);
+    return d ? c->S[l] / d : c->S[l];
+}
+// Weight-gradient sites also take modes 6 and 7: modes 1 and 4 with the split-K partials reduced
+// inside the GEMM by clusters of CTAs (see split_cluster).
 // weight-stationary mode 5 fits a site: a ring stage beside the resident weight slice, and no
 // more (network, column tile) groups than SMs
 bool ws_fits(int bn, int epi, int kblocks, int width) {
@@ -274,7 +294,7 @@ bool encode_layer_maps(rl_ctx* c, int l) {
         }
         // weight gradient, MN-major operands: dY_l [rows][out] and H_{l-1} [rows][in]; one 3D copy per
         // operand and stage in single-CTA mode, 64 x 64 boxes otherwise
-        const bool dw3 = c->cm_dw[l] == 1;
+        const bool dw3 = c->cm_dw[l] == 1 || c->cm_dw[l] == 6;
         auto dw_map = [&](CUtensorMap* m, const void* base, int cols, int tile) {
             return dw3 ? make_tmap_bf16_mn1(m, base, c->Mb, cols, cols, (uint32_t)tile) : make_tmap_bf16(m, base, c->Mb, cols, cols, 64);
         };
@@ -401,7 +421,11 @@ rl_status dw_layer(rl_ctx* c, Enq& q, int k, int M) {
         }
         tp.M = Li.out; tp.N = Li.in; tp.kblocks = (M + 63) / 64; tp.kb_per_split = c->kchunk[k] / 64;
         tp.splits = c->S[k]; tp.batch = 2; tp.bn = c->bn_dw[k]; set_cluster(tp, c->cm_dw[k]); tp.mn = MAJ_MN; tp.epi = EPI_STORE;
-        tp.mn3 = c->cm_dw[k] == 1 ? 1 : 0;       // the maps of encode_layer_maps
+        tp.mn3 = (c->cm_dw[k] == 1 || c->cm_dw[k] == 6) ? 1 : 0;       // the maps of encode_layer_maps
+        tp.sred = split_cluster(c, k);
+        for (int n = 0; n < 2; ++n) tp.sr_out[n] = c->gw[n][k];
+        tp.sr_ld = Li.in;
+        tp.sr_split_ld = (long long)Li.out * Li.in;
         tp.status = c->status;
         tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
@@ -613,7 +637,8 @@ void build_adam(rl_ctx* c) {
         for (int n = 0; n < 2; ++n) {
             for (int l = 0; l < c->NH; ++l) {
                 const LayerInfo& Li = c->L[n][l];
-                add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, c->S[l], c->wbf[n][l], Li.out, Li.in);
+                add(Li.w, (long long)Li.out * Li.in, c->gw[n][l], (long long)Li.out * Li.in, weight_partials(c, l), c->wbf[n][l],
+                    Li.out, Li.in);
                 if (l < c->NH - 1)
                     add(Li.b, Li.out, c->gb[n][l], Li.out, c->gb_parts, nullptr, 0, 0);
                 else
@@ -672,7 +697,7 @@ AdamParams weight_reduce_params(rl_ctx* c, int l) {
         sg.size = (long long)Li.out * Li.in;
         sg.partials = c->gw[n][l];
         sg.stride = sg.size;
-        sg.nsplit = c->S[l];
+        sg.nsplit = weight_partials(c, l);
         sg.block_start = blocks;
         sg.vec = (sg.offset % 4 == 0 && sg.size % 4 == 0) ? 1 : 0;
         const long long per_block = adam_per_block(sg.nsplit, sg.vec);
@@ -878,6 +903,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     };
     const int bns[3] = {64, 128, 256};
     const int cms[4] = {1, 3, 4, 5};
+    const int dw_cms[5] = {1, 3, 4, 6, 7};      // weight gradients: no weight-stationary form
     for (int l = 0; l < c->NH && st == RL_OK; ++l) {
         const LayerInfo& Li = c->L[0][l];
         const int row_tiles = (c->Mb + 127) / 128;
@@ -956,10 +982,10 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
             for (int bi = 0; bi < (c->bf16 ? 3 : 1) && st == RL_OK; ++bi) {
                 const int bn = c->bf16 ? bns[bi] : 64;
                 if (Li.in % bn) continue;
-                for (int cm : cms) {
-                    if (cm == 5) continue;                                               // weight gradients stream both operands
+                for (int cm : dw_cms) {
                     if (cm == 3 && (!c->bf16 || out_tiles < 2 || bn < 128)) continue;   // whole 64-wide B boxes per CTA
-                    if (cm == 4 && (!c->bf16 || bn > 128)) continue;
+                    if ((cm == 4 || cm == 7) && (!c->bf16 || bn > 128)) continue;
+                    if (cm == 6 && !c->bf16) continue;
                     // split counts: one or two waves of this width's tiles over the SMs, and the
                     // default's half and double
                     const long long tl = (long long)out_tiles * (Li.in / bn) * 2;
@@ -1023,7 +1049,8 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
 // weight-gradient K chunk and split count it implies (the current ones for the other sites).
 rl_status check_tiles(const rl_ctx* c, int site, int l, int bn, int cm, int splits, int* kc_out, int* S_out) {
     if (!c->bf16 || l < 0 || l >= c->NH || site < 0 || site > 3 || (site == 1 && l == 0)) return RL_ERR_INVALID_ARG;
-    if ((bn != 64 && bn != 128 && bn != 256) || (cm != 1 && cm != 3 && cm != 4 && cm != 5)) return RL_ERR_INVALID_ARG;
+    if ((bn != 64 && bn != 128 && bn != 256) || cm < 1 || cm > 7 || cm == 2) return RL_ERR_INVALID_ARG;
+    if ((cm == 6 || cm == 7) && site != 2) return RL_ERR_INVALID_ARG;
     const LayerInfo& Li = c->L[0][l];
     const int width = (site == 0 || site == 3) ? Li.out : Li.in;
     if (cm == 5 && (site == 2 || width % bn ||
@@ -1031,7 +1058,8 @@ rl_status check_tiles(const rl_ctx* c, int site, int l, int bn, int cm, int spli
         return RL_ERR_INVALID_ARG;
     const int row_tiles = site == 2 ? (Li.out + 127) / 128 : site == 3 ? (c->N + 127) / 128 : (c->Mb + 127) / 128;
     const bool paired = cm == 3;
-    if (width % bn || (paired && row_tiles < 2) || (cm == 3 && bn < 128) || (cm == 4 && bn > 128)) return RL_ERR_INVALID_ARG;
+    if (width % bn || (paired && row_tiles < 2) || (cm == 3 && bn < 128) || ((cm == 4 || cm == 7) && bn > 128))
+        return RL_ERR_INVALID_ARG;
     if ((site == 1 || site == 2) && paired && bn < 128) return RL_ERR_INVALID_ARG;   // whole 64-wide B boxes per CTA
     int kc = c->kchunk[l], Sr = c->S[l];
     if (site == 2) {
@@ -1833,9 +1861,11 @@ rl_status rl_autotune(rl_ctx* c, char* report, size_t report_bytes, void* stream
 rl_status rl_set_gemm_ctas(rl_ctx* c, int32_t max_ctas) {
     if (!c || max_ctas < 0) return RL_ERR_INVALID_ARG;
     c->gemm_cap = max_ctas;
+    build_adam(c);          // the cap decides which weight gradients reduce their splits in clusters
     drop_graph(c);
     return RL_OK;
 }
+
 
 rl_status rl_set_gemm_tiles(rl_ctx* c, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits) {
     if (!c) return RL_ERR_INVALID_ARG;
@@ -2003,7 +2033,10 @@ rl_status rl_group_create(int32_t n, const rl_config* cfgs, const float* const* 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
         long long total = 0;
         for (rl_ctx* c : g->ctx) total += c->N;
-        for (rl_ctx* c : g->ctx) c->gemm_cap = (int)std::max(16ll, (2ll * sms * c->N + total - 1) / total);
+        for (rl_ctx* c : g->ctx) {
+            c->gemm_cap = (int)std::max(16ll, (2ll * sms * c->N + total - 1) / total);
+            build_adam(c);
+        }
     }
     *out = g;
     return RL_OK;

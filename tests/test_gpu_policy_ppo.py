@@ -288,10 +288,11 @@ def test_set_gemm_tiles_rejects_invalid():
     w = workload("tiny", precision=1)
     L, _, _, _ = _setup(w)
     # (site, layer, bn, cluster, splits): the weight-stationary mode 5 is refused at the weight
-    # gradient, mode 6 does not exist
+    # gradient, the split-reducing modes 6 and 7 everywhere else, mode 7 above a tile width of 128;
+    # mode 8 does not exist
     for args in ((4, 0, 64, 1, 1), (1, 0, 64, 1, 1), (0, 0, 96, 1, 1), (0, 0, 64, 6, 1), (0, 9, 64, 1, 1),
                  (2, 0, 64, 1, 0), (3, 0, 128, 1, 1), (0, 0, 64, 3, 1), (0, 0, 256, 4, 1), (0, 0, 64, 2, 1),
-                 (0, 0, 128, 2, 1), (2, 0, 64, 5, 1)):
+                 (0, 0, 128, 2, 1), (2, 0, 64, 5, 1), (3, 0, 64, 7, 1), (2, 0, 256, 7, 2), (0, 0, 64, 8, 1)):
         with pytest.raises(api.RLError):
             api.rl_set_gemm_tiles(L.ctx, *args)
     L.close()
@@ -323,5 +324,46 @@ def test_profile_classes_count_every_launch():
     L.train_iteration(use_graph=True)
     torch.cuda.synchronize()
     assert api.rl_profile_read(L.ctx)[1] == 0
+    assert api.rl_last_device_status(L.ctx) == 0
+    L.close()
+
+
+@pytest.mark.parametrize("splits,bn,cm", [(8, 128, 6), (12, 128, 7), (6, 64, 6), (9, 128, 7)])
+def test_weight_gradient_split_reduction_in_clusters(splits, bn, cm):
+    """Tile modes 6 and 7 of the weight gradient: the split-K partials reduced inside the GEMM by
+    clusters of CTAs (the largest divisor of the split count up to 8: 8, 6, 6 and 3 here), Adam
+    summing the clusters' partials, give the gradient of the plain modes 1 and 4 to fp32 rounding and
+    the oracle's gradient within the BF16 tolerance; 2880 minibatch rows with splits of whole 64-row
+    blocks (the last split of 8 and 12 ragged)."""
+    w = workload("rough", num_envs=480, precision=1)
+    L, params, O, Op = _setup(w)
+    M = w["num_envs"] * w["num_steps"] // w["minibatches"]
+    hidden = w["hidden"]
+    b, d = _batch(M, O, Op, 12, params, hidden, 43, True, kink_margin=True)
+    d = _own_old_policy(L, b, d, O, params, hidden)
+    grads = {}
+    plain = {6: 1, 7: 4}[cm]
+    for mode in (cm, plain):
+        for layer in range(len(hidden)):
+            api.rl_set_gemm_tiles(L.ctx, 2, layer, bn, mode, splits)
+        g = torch.empty(L.n_params, device="cuda")
+        api.rl_ppo_loss_grad(L.ctx, d["obs"], d["actions"], d["logp_old"], d["mu_old"], d["log_std_old"], d["v_old"],
+                             d["adv"], d["ret"], g)
+        torch.cuda.synchronize()
+        assert api.rl_last_device_status(L.ctx) == 0
+        grads[mode] = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(grads[plain]).max()
+    assert np.abs(grads[cm] - grads[plain]).max() <= 1e-5 * scale
+    p = OM.unflatten(params, O, hidden, 12)
+    _, gr, _ = OP.loss_and_grad(p, b["obs"][:, :O], b["actions"], b["logp_old"], b["mu_old"], b["log_std_old"],
+                                b["v_old"], b["adv"], b["ret"])
+    errs = _per_tensor_err(grads[cm], OP.flat_grad(gr), (O, hidden, 12), rel_err)
+    assert max(errs.values()) < TOL_BF16, errs
+    for layer in range(len(hidden)):
+        api.rl_set_gemm_tiles(L.ctx, 2, layer, bn, cm, splits)
+    with pytest.raises(api.RLError):
+        api.rl_set_gemm_tiles(L.ctx, 0, 0, 128, 6, 1)          # modes 6, 7: weight gradients only
+    L.train_iteration(use_graph=True)
+    torch.cuda.synchronize()
     assert api.rl_last_device_status(L.ctx) == 0
     L.close()
