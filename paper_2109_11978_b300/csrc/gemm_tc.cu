@@ -568,6 +568,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     if (CM > 1) cluster_sync_all();    // both CTAs' barriers exist before the pair's copies and commits land
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if constexpr (WS) {
+        // weights that no kernel in flight writes (b_early): the B slice goes out before the wait
+        if (p.b_early && warp == 0 && lane < PROD_LANES) {
+            const int G = nt * p.batch, gs = ncl / G, g = cid % G, jr = cid / G;
+            if (jr < gs && jr < mct) {
+                const CUtensorMap* mb = &p.tmB[g / nt];
+                if (lane == 0) mbar_expect_tx(bfull, (uint32_t)(p.kblocks * BN * 128));
+                for (int kb = lane; kb < p.kblocks; kb += PROD_LANES) {
+                    const uint32_t dst = smem_u32(bres + (size_t)kb * BN * 128);
+                    if (!B_MN) tma_load_2d(dst, mb, bfull, kb * BK, (g % nt) * BN);
+                    else tma_load_3d(dst, mb, bfull, 0, kb * BK, (g % nt) * BN / 64);
+                }
+            }
+        }
+    }
     // set-up done: wait for the preceding kernel's results, let the next kernel's CTAs be placed
     pdl_wait();
     pdl_trigger();
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 const CUtensorMap* ma = &p.tmA[b];
                 const CUtensorMap* mb = &p.tmB[b];
                 const bool has = jr < gs && jr < mct;
-                if (has) {
+                if (has && !p.b_early) {
                     if (lane == 0) mbar_expect_tx(bfull, (uint32_t)(p.kblocks * BN * 128));
                     for (int kb = lane; kb < p.kblocks; kb += PROD_LANES) {
                         const uint32_t dst = smem_u32(bres + (size_t)kb * BN * 128);
@@ -1369,6 +1384,7 @@ cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s) {
         return cudaErrorInvalidValue;
     // weight-stationary: single CTA, no split, forward (B K-major) or input gradient (B by the 3D
     // MN-major maps), at least one ring stage beside the resident B slice
+    if (p.b_early && !p.ws) return cudaErrorInvalidValue;
     if (p.ws && (p.cm != 1 || p.pair || p.ks == 2 || p.splits != 1 || p.epi == EPI_STORE || (p.mn == MAJ_B_MN && !p.mn3) ||
                  tc_ws_stages(p.bn, p.epi, p.kblocks) < 1))
         return cudaErrorInvalidValue;

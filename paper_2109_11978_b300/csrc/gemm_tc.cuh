@@ -49,6 +49,8 @@ struct TcParams {
                                // writing splits / sred partials to sr_out
     float* sr_out[2];          // per batch entry: partial g of element (m, n) at g sr_split_ld + m sr_ld + n
     long long sr_ld, sr_split_ld;
+    int b_early;               // ws only: no kernel that may still run when this one starts writes B, so
+                               // the B slice is fetched before the wait for the preceding kernel
 };
 
 cudaError_t launch_tc_gemm(const TcParams& p, cudaStream_t s);

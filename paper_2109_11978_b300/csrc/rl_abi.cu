@@ -310,7 +310,10 @@ bool encode_layer_maps(rl_ctx* c, int l) {
 // One hidden layer of the forward pass for `rows` rows (X = layer-0 input), batch = nnets
 // networks starting at net0: 2 (actor + critic) or 1 with net0 = 1 (critic only).  act: the
 // rollout's policy inference (its own tile shapes, tuned for num_envs rows), else the update.
-rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets, bool act) {
+// b_early: no kernel still running when this one starts writes the weights (the rollout's steps
+// after the first, the last value), so a weight-stationary launch fetches its weight slice before
+// it waits for the preceding kernel.
+rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0, int nnets, bool act, bool b_early = false) {
     const LayerInfo& Li = c->L[0][l];
     if (c->bf16) {
         TcParams tp;
@@ -341,6 +344,7 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
         tp.bn = bn;
         set_cluster(tp, cm);
         tp.epi = EPI_BIAS_ELU;
+        tp.b_early = (b_early && tp.ws) ? 1 : 0;
         tp.status = c->status;
         tp.max_ctas = c->gemm_cap;
         CK(q.gemm(&tp, 0, false, false, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr));
@@ -360,9 +364,9 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
 }
 
 // Forward through every hidden layer.
-rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act) {
+rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act, bool b_early = false) {
     for (int l = 0; l < c->NH; ++l) {
-        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, act);
+        rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, act, b_early);
         if (st != RL_OK) return st;
     }
     return RL_OK;
@@ -464,9 +468,9 @@ HeadParams head_common(rl_ctx* c, int rows) {
 }
 
 rl_status act_impl(rl_ctx* c, Enq& q, int t, int n, const void* obs, float* actions, float* mu, float* logp,
-                   float* values) {
+                   float* values, bool b_early = false) {
     const bool critic_only = !actions && !mu && !logp;
-    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2, true);
+    rl_status st = forward_hidden(c, q, obs, n, critic_only ? 1 : 0, critic_only ? 1 : 2, true, b_early);
     if (st != RL_OK) return st;
     HeadParams h = head_common(c, n);
     h.t = t;
@@ -806,7 +810,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
     for (int t = 0; t < c->T; ++t) {
         const size_t o = (size_t)t * c->N;
         // policy inference: the hidden layers here, the output heads fused into the env step
-        rl_status st = forward_hidden(c, q, obs + t * obs_step, c->N, 0, 2, true);
+        rl_status st = forward_hidden(c, q, obs + t * obs_step, c->N, 0, 2, true, t > 0);
         if (st != RL_OK) return st;
         ep.act = head_common(c, c->N);
         ep.act.t = t;
@@ -836,7 +840,7 @@ rl_status train_enqueue(rl_ctx* c, cudaStream_t s, bool profile) {
         ++c->launches;
         CK(cudaEventRecord(c->ev_perm_join, c->side));
     }
-    rl_status st = act_impl(c, q, c->T, c->N, obs + c->T * obs_step, nullptr, nullptr, nullptr, c->last_val);
+    rl_status st = act_impl(c, q, c->T, c->N, obs + c->T * obs_step, nullptr, nullptr, nullptr, c->last_val, true);
     if (st != RL_OK) return st;
     CK(q.run(RL_PROF_OTHER, 2, [&] {
         return launch_gae(c->T, c->N, c->cfg.gamma, c->cfg.lam, c->rew, c->values, c->last_val, c->done, c->adv, c->ret, 1,
@@ -942,7 +946,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
                         c->cm_act[l] = cm;
                         if (!encode_layer_maps(c, l)) return RL_ERR_CUDA;
                         float ms = 0.f;
-                        st = timed([&] { return fwd_layer(c, q, l, c->obs, c->N, 0, 2, true); }, ms);
+                        st = timed([&] { return fwd_layer(c, q, l, c->obs, c->N, 0, 2, true, true); }, ms);
                         if (st == RL_OK) trial("act_forward", l, bn, cm, 1, ms);
                         if (st == RL_OK && ms < abest) { abest = ms; abn = bn; acm = cm; }
                     }

@@ -158,8 +158,9 @@ def _bf16_round(x):
     return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("prec,grid", [(1, (17, 11)), (0, (17, 11)), (1, (12, 9))])
-def test_train_iteration_rough_teacher_forced(prec, grid):
+@pytest.mark.parametrize("prec,grid,act_ws", [(1, (17, 11), False), (0, (17, 11), False), (1, (12, 9), False),
+                                              (1, (17, 11), True)])
+def test_train_iteration_rough_teacher_forced(prec, grid, act_ws):
     """One rl_train_iteration of the rough-terrain form: 17 x 11 (or the paper's 108-point 12 x 9)
     height samples, Table 4 noise, pushes, last hidden width 128, so the rollout runs the env step
     with the policy heads fused in (the kernel form the bench times).  The oracle's rollout is
@@ -167,9 +168,14 @@ def test_train_iteration_rough_teacher_forced(prec, grid):
     bit for bit like the library's: dones, time-outs and levels must match exactly, rewards to
     1e-5, observations within the rounding of their storage type (bf16: half an ulp of the
     oracle's value plus the fp32 path's 1e-5), mu, V, log pi and the sampled actions within the
-    precision's tolerance; GAE on the library's rewards and values to 1e-5."""
+    precision's tolerance; GAE on the library's rewards and values to 1e-5.  act_ws: the rollout's
+    hidden layers in the weight-stationary tile mode, whose launches after the first step fetch
+    their weight slice before waiting for the preceding kernel."""
     w = workload("small_rough", precision=prec, grid=grid, crash_threshold=2 ** 26, epochs=1, minibatches=2)
     L, params, O, Op = _setup(w)
+    if act_ws:
+        for layer in range(len(w["hidden"])):
+            api.rl_set_gemm_tiles(L.ctx, 3, layer, 64, 5, 1)
     T, N = w["num_steps"], w["num_envs"]
     L.train_iteration(use_graph=True)
     torch.cuda.synchronize()
