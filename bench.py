@@ -88,8 +88,7 @@ def read_peaks():
 # the rough-terrain workload (ncu, one pass per launch), with the SHA-1 of the GEMM source it was
 # captured on: the figure is reported only while the kernel source is unchanged (null otherwise,
 # until captured again).
-GEMM_DRAM = {"gemm_tc_sha1": "fbb10d2d74d2028b58af0c69655156ab76447e7b", "bytes_per_iteration": 7982.98e6 + 293.06e6,
-             "profile": "profiles/gemm_rough4096_dram.md"}
+GEMM_DRAM = {"gemm_tc_sha1": "8ca9e60503e8dc9dfcd6850669968b54259c27ab", "bytes_per_iteration": 7983.36e6 + 292.64e6}
 
 
 def gemm_traffic():
