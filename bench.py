@@ -355,6 +355,9 @@ ENV_BYTES = {"bf16": 2 * 240 + 52 + 256 * 2 + 10, "fp32": 2 * 240 + 52 + 256 * 4
 GAE_BYTES_PER_SAMPLE = 17 + 8        # r, V, d read, A, R written + normalisation pass (read + write A)
 
 
+ADAM_BYTES_PER_PARAM = 30     # p, m, v read + written (24), gradient read (4), bf16 copy written (2)
+
+
 def sweep(torch, api, synth, reps=10):
     """Achieved HBM bandwidth of the memory-bound kernels at sizes past the L2 (126 MB)."""
     peaks, src = read_peaks()
@@ -408,6 +411,19 @@ def sweep(torch, api, synth, reps=10):
         lines.append({"kernel": "gae_scan_kernel+gae_normalize_kernel", "T": T, "robots": n, "ms": ms,
                       "bytes_per_sample": GAE_BYTES_PER_SAMPLE, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
                       "peak_source": src})
+        del r, v, lv, d, adv, ret, ws
+    # Adam (rl_adam_step: the update's Adam kernel on one gradient): p, m, v read and written, g read,
+    # the bf16 copy written = 30 B per parameter; the learner's 571,801 parameters, then past the L2
+    for n in (571801, 4 * 2 ** 20, 16 * 2 ** 20, 64 * 2 ** 20):
+        p_ = torch.randn(n, device="cuda") * 1e-3
+        g_ = torch.randn(n, device="cuda") * 1e-2
+        m_, v_ = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+        wb_ = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+        ms = timed(lambda: api.rl_adam_step(p_, g_, m_, v_, 1e-3, 1, 1, wb_))
+        gbs = ADAM_BYTES_PER_PARAM * n / (ms / 1000.0) / 1e9
+        lines.append({"kernel": "adam_kernel", "params": n, "ms": ms, "bytes_per_param": ADAM_BYTES_PER_PARAM,
+                      "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": src})
+        del p_, g_, m_, v_, wb_
     return lines
 
 

@@ -401,6 +401,19 @@ rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn
  * value or a null context. */
 rl_status rl_set_gemm_ctas(rl_ctx* ctx, int32_t max_ctas);
 
+/* One Adam step (Sec. 2.2, Table 3; Kingma & Ba's bias-corrected update with beta1 0.9, beta2
+ * 0.999, eps 1e-8) by the library's Adam kernel, on caller buffers: the optimizer step of the PPO
+ * update exposed on its own for measurement and tests (no entry point of its own in the paper).
+ * n parameters p (fp32, updated in place); the gradient as nsplit >= 1 partial sums, partial q of
+ * element i at g[q n + i], summed in the kernel's fixed order; moments m, v (fp32, in place, zero
+ * before the first step); learning rate lr >= 0; t >= 1 the step count of the bias corrections
+ * 1 - 0.9^t and 1 - 0.999^t; bf16_out (may be NULL): receives the new p rounded to bf16.  All
+ * device pointers; 16-byte aligned buffers and n a multiple of 4 take the 4-wide form.  Enqueues on
+ * stream without synchronising.  RL_ERR_INVALID_ARG for n < 1, nsplit < 1, t < 1, a negative or
+ * NaN lr or a null buffer. */
+rl_status rl_adam_step(int64_t n, float* p, const float* g, int32_t nsplit, float* m, float* v, float lr, int32_t t,
+                       void* bf16_out, void* stream);
+
 /* Diagnostic: C = A B^T with the library's tcgen05 BF16 tensor-core GEMM kernel (FP32
  * accumulation), for checking the tensor-core path in isolation.  A [M][K] bf16, B [N][K] bf16
  * (row-major, K contiguous), C [M][N] fp32.  K % 8 == 0 (16-byte rows), N % 64 == 0, pointers

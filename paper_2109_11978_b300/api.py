@@ -226,6 +226,13 @@ def rl_autotune(ctx):
     return json.loads(buf.value.decode() or "{}")
 
 
+def rl_adam_step(p, g, m, v, lr, t, nsplit=1, bf16_out=None):
+    """One Adam step on device tensors (g holds nsplit partial sums of len(p) each)."""
+    n = p.numel()
+    check(lib().rl_adam_step(ctypes.c_int64(n), _ptr(p), _ptr(g), int(nsplit), _ptr(m), _ptr(v), float(lr), int(t),
+                             _ptr(bf16_out), _stream()), "rl_adam_step")
+
+
 def rl_set_gemm_ctas(ctx, max_ctas):
     """Caps the persistent CTAs of the context's GEMM launches (0: one per SM)."""
     check(lib().rl_set_gemm_ctas(ctx, int(max_ctas)), "rl_set_gemm_ctas")

@@ -165,6 +165,9 @@ struct AdamParams {
     // bf16 weight copies (optional): for segment s, wbf[s] has the segment's layout
     void* wbf[MAX_SEGS];
     float* grad_out;       // optional: reduced gradient (flat internal) instead of a step
+    // without a device scalar block (scal null): the step size alpha / (1 - 0.9^t) and
+    // 1 / sqrt(1 - 0.999^t) given by the host
+    float step_size_host, inv_sqrt_bc2_host;
 };
 constexpr int ADAM_THREADS = 256;
 constexpr int ADAM_WIDE = 64;      // segments with more partials than this: a warp per parameter group

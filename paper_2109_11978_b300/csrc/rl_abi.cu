@@ -1871,6 +1871,48 @@ rl_status rl_set_gemm_ctas(rl_ctx* c, int32_t max_ctas) {
 }
 
 
+rl_status rl_adam_step(int64_t n, float* p, const float* g, int32_t nsplit, float* m, float* v, float lr, int32_t t,
+                       void* bf16_out, void* stream) {
+    if (n < 1 || !p || !g || !m || !v || nsplit < 1 || t < 1 || !(lr >= 0.f)) return RL_ERR_INVALID_ARG;
+    AdamParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = p;
+    a.m = m;
+    a.v = v;
+    const double t_d = (double)t;
+    a.step_size_host = (float)((double)lr / (1.0 - std::pow(0.9, t_d)));
+    a.inv_sqrt_bc2_host = (float)(1.0 / std::sqrt(1.0 - std::pow(0.999, t_d)));
+    // one segment per 2^30 parameters (the segment's block count stays within an int)
+    long long off = 0;
+    int blocks = 0;
+    while (off < n) {
+        if (a.nsegs == MAX_SEGS) return RL_ERR_INVALID_ARG;
+        const long long size = std::min<long long>(n - off, 1ll << 30);
+        AdamSeg& sg = a.seg[a.nsegs];
+        sg.offset = off;
+        sg.size = size;
+        sg.partials = g + off;
+        sg.stride = n;
+        sg.nsplit = nsplit;
+        sg.block_start = blocks;
+        a.wbf[a.nsegs] = bf16_out ? static_cast<void*>(static_cast<__nv_bfloat16*>(bf16_out) + off) : nullptr;
+        sg.vec = (off % 4 == 0 && size % 4 == 0 && n % 4 == 0 && ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(p) |
+                                                                   reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15u) == 0 &&
+                  (reinterpret_cast<uintptr_t>(bf16_out) & 7u) == 0)
+                     ? 1
+                     : 0;
+        const long long per_block = adam_per_block(nsplit, sg.vec);
+        const long long nb = (size + per_block - 1) / per_block;
+        if (blocks + nb > (1ll << 31) - 1) return RL_ERR_INVALID_ARG;
+        blocks += (int)nb;
+        off += size;
+        ++a.nsegs;
+    }
+    a.nblocks = blocks;
+    CK(launch_adam(a, S_(stream)));
+    return RL_OK;
+}
+
 rl_status rl_set_gemm_tiles(rl_ctx* c, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits) {
     if (!c) return RL_ERR_INVALID_ARG;
     return set_tiles_impl(c, site, layer, bn, cluster, splits);

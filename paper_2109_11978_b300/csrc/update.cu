@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(ADAM_THREADS, 4) adam_kernel(AdamParams p) {
     const AdamSeg sg = p.seg[s];
     // step size alpha / (1 - 0.9^t) and 1 / sqrt(1 - 0.999^t), computed once per minibatch by the
     // loss kernel together with Algorithm 1 and the step count
-    const float step_size = p.scal ? p.scal[SC_STEPSIZE] : 0.f;
-    const float inv_sqrt_bc2 = p.scal ? p.scal[SC_INVSQRT_BC2] : 1.f;
+    const float step_size = p.scal ? p.scal[SC_STEPSIZE] : p.step_size_host;
+    const float inv_sqrt_bc2 = p.scal ? p.scal[SC_INVSQRT_BC2] : p.inv_sqrt_bc2_host;
     if (sg.vec) adam_segment<4>(p, sg, s, step_size, inv_sqrt_bc2);
     else adam_segment<1>(p, sg, s, step_size, inv_sqrt_bc2);
 }

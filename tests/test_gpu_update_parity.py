@@ -215,3 +215,35 @@ def test_config_obs_dims_of_the_108_point_grid():
     assert obs_dims(w) == (156, 192)
     cfg = lib_config(w)
     assert cfg.obs_dim == 156 and cfg.obs_pad == 192
+
+
+@pytest.mark.parametrize("n,nsplit", [(10007, 1), (16384, 3), (4099, 70)])
+def test_adam_step_matches_oracle(n, nsplit):
+    """rl_adam_step, the update's Adam kernel on caller buffers: three steps with fresh gradients
+    (given as nsplit partial sums; 70 takes the kernel's warp-per-group form, 16384 its 4-wide form),
+    against the oracle's Adam (Table 3 betas, bias-corrected, float64 state): moments within 1e-6,
+    each step's parameter change within 1e-5 (max-norm relative), and the bf16 copy equal to the new
+    parameters rounded to bf16."""
+    rng = np.random.default_rng(n + nsplit)
+    # parameters of the step's size, so that rounding p to fp32 stays far below the step itself
+    p0 = (rng.normal(size=n) * 1e-3).astype(np.float32)
+    p = torch.from_numpy(p0).cuda()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    wb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    ad = OP.Adam(n)
+    ref = p0.astype(np.float64)
+    for t in (1, 2, 3):
+        parts = (rng.normal(size=(nsplit, n)) * 0.1).astype(np.float32)
+        g = parts.astype(np.float64).sum(0)
+        before = p.cpu().numpy().astype(np.float64)
+        api.rl_adam_step(p, torch.from_numpy(parts).cuda().reshape(-1), m, v, 1e-3, t, nsplit, wb)
+        torch.cuda.synchronize()
+        ref_new = ad.step(ref, g, 1e-3)
+        got = p.cpu().numpy().astype(np.float64)
+        assert rel_err(got - before, ref_new - ref) < 1e-5, t
+        assert rel_err(m.cpu().numpy(), ad.m) < 1e-6 and rel_err(v.cpu().numpy(), ad.v) < 1e-6, t
+        assert torch.equal(wb.cpu(), p.cpu().to(torch.bfloat16))
+        ref = ref_new
+    with pytest.raises(api.RLError):
+        api.rl_adam_step(p, torch.zeros(n, device="cuda"), m, v, 1e-3, 0)
