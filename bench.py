@@ -459,6 +459,50 @@ def cpu_baseline(seconds_budget=20.0, n_envs=256):
                       f"{n_envs * 24 // 4}), FP64 numpy, {dt:.1f} s"}
 
 
+# The two small configurations beside the headline: C1 tiny (64 robots x 24 steps, obs 48, actor /
+# critic 48-64-64, 1 epoch x 2 minibatches) and C2 flat terrain (4096 x 24, obs 48, 512-256-128,
+# 5 x 4), both in the plain FP32 form, with no height samples.
+SMALL_CONFIGS = {
+    "C1 tiny": dict(num_envs=64, num_steps=24, grid=(0, 0), hidden=(64, 64), epochs=1, minibatches=2),
+    "C2 flat": dict(num_envs=4096, num_steps=24, grid=(0, 0), hidden=(512, 256, 128), epochs=5, minibatches=4),
+}
+
+
+def small_configs(torch, api, synth, steps=10, warmup=3, oracle_budget=6.0):
+    """GPU env-steps/s of C1 and C2 (plain FP32 GPU form, graph replay, median) next to the FP64
+    oracle on the host cores (C1 whole iterations, C2 a bounded sample at 256 robots)."""
+    from oracle import config as OC
+    from oracle.train import Learner as OLearner
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for name, w in SMALL_CONFIGS.items():
+        O = 48
+        cfg = api.default_config(num_envs=w["num_envs"], num_steps=w["num_steps"], grid_x=0, grid_y=0, obs_dim=O,
+                                 obs_pad=64, hidden=list(w["hidden"]), epochs=w["epochs"], minibatches=w["minibatches"],
+                                 precision=api.RL_FP32, seed=10)
+        L = api.Learner(cfg, None, synth.xavier_params(11, O, w["hidden"], 12))
+        times = time_iterations(torch, L, steps, warmup, flush)
+        status = api.rl_last_device_status(L.ctx)
+        L.close()
+        ms = statistics.median(times)
+        gpu = w["num_envs"] * w["num_steps"] / (ms / 1000.0)
+        n_or = min(w["num_envs"], 256)
+        ol = OLearner(OC.EnvConfig(num_envs=n_or, grid_x=0, grid_y=0, seed=10),
+                      OC.PPOConfig(epochs=w["epochs"], minibatches=w["minibatches"], seed=10), list(w["hidden"]), None,
+                      synth.xavier_params(11, O, w["hidden"], 12))
+        t0 = time.perf_counter()
+        iters = 0
+        while iters < 1 or (time.perf_counter() - t0 < oracle_budget and iters < 4):
+            ol.iterate(w["num_steps"])
+            iters += 1
+        dt = time.perf_counter() - t0
+        out[name] = {"gpu_fp32_env_steps_per_s": gpu, "gpu_ms_per_iteration": ms, "device_status": status,
+                     "oracle_env_steps_per_s": n_or * w["num_steps"] * iters / dt, "oracle_cores": len(os.sched_getaffinity(0)),
+                     "oracle_sample": f"{iters} iteration(s) at {n_or} robots x {w['num_steps']} steps, {dt:.1f} s",
+                     "config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()}}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -661,6 +705,7 @@ def main():
         extra["robots_16384"] = large_config(torch, api, synth)
         extra["actuator_lstm"] = actuator_lstm(torch, api)
         extra["hbm_sweep"] = sweep(torch, api, synth, reps=5)
+        extra["small_configs"] = small_configs(torch, api, synth)
         extra["robots_sweep"] = robots_sweep(torch, api, synth, quiet=True)
     if rank != 0:
         return 0
