@@ -71,8 +71,10 @@ __device__ __forceinline__ float box_muller(uint64_t w) {
 // Programmatic dependent launch.  The kernels of an iteration are launched with programmatic
 // stream serialization: a kernel's blocks may be scheduled while its predecessor drains, run
 // their set-up, and wait in pdl_wait() until the predecessor grid has completed and its memory
-// is visible; pdl_trigger() lets the successor be scheduled early.  Every kernel calls pdl_wait()
-// before it reads or writes global memory (so completion is transitive along the stream).
+// is visible; pdl_trigger() lets the successor be scheduled early.  Every kernel calls
+// pdl_trigger() only after pdl_wait(), so when a kernel starts, every kernel before its
+// predecessor has completed: it may read what those wrote before its own pdl_wait() (weights,
+// state, records), but reads its predecessor's results and writes global memory only after it.
 // Without the launch attribute both are no-ops.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

@@ -120,8 +120,14 @@ constexpr int T_ROLES = T_PLANE + 64;   // planar, rates, gravity, feet: 16 thre
 // FUSE: 0, or 16 * bf16 + H / 32 of a fused policy head (its per-row evaluation runs first).
 template <int MODE, int FUSE>   // MODE 0 = policy step, 1 = spawn all robots (initial state)
 __global__ void __launch_bounds__(512, 2) env_step_kernel(EnvParams p) {
-    pdl_wait();
-    pdl_trigger();
+    // The fused form follows the rollout's last forward layer, which writes only the hidden rows:
+    // the robot state, the head weights and the iteration counter come from kernels that have
+    // completed when this one starts, so they are read before the wait for that layer.  The plain
+    // form may follow a kernel that writes the state (a reset) and waits first.
+    if constexpr (FUSE == 0) {
+        pdl_wait();
+        pdl_trigger();
+    }
     constexpr int ENVS = 16, THREADS = 512;
     extern __shared__ float rec_raw[];
     float (*rec)[REC] = reinterpret_cast<float (*)[REC]>(rec_raw);       // [ENVS][REC]
@@ -144,57 +150,7 @@ __global__ void __launch_bounds__(512, 2) env_step_kernel(EnvParams p) {
         gtab[k] = ((float)ix - 0.5f * (float)(p.GX - 1)) * p.grid_sp;
         gtab[GTAB + k] = ((float)iy - 0.5f * (float)(p.GY - 1)) * p.grid_sp;
     }
-    if constexpr (FUSE != 0) {
-        // Phase 0 (fused policy head): the head weights into shared memory, then one warp per
-        // robot evaluates mu, the sampled action, logp and V exactly as the action-head kernel
-        // does, writing the rollout's records and the block's actions / values for phase 1.  The
-        // warp's hidden rows are loaded first, so that the loads overlap the staging of the head
-        // weights.
-        static_assert(ENVS == THREADS / 32, "one robot per warp");
-        constexpr bool HB = (FUSE >> 4) != 0;
-        constexpr int NK = FUSE & 15;
-        const int mm[1] = {env0 + warp};
-        const bool ok[1] = {env0 + warp < N};
-        float hc[1][NK], ha[1][NK];
-        if (ok[0]) act_rows_load<HB, NK, 1>(p.act, mm, ok, true, lane, hc, ha);
-        float* Wa = gtab + 2 * GTAB;
-        float* Wc = Wa + p.act.A * p.act.H;
-        // every load of the staging issued before its stores (16-byte pieces where the layout
-        // allows), so that the block waits for one round trip to L2 instead of one per piece
-        const int nwa = p.act.A * p.act.H, nwc = p.act.H;
-        if (((reinterpret_cast<uintptr_t>(p.act.Wa) | reinterpret_cast<uintptr_t>(p.act.Wc)) & 15u) == 0 && nwa % 4 == 0 &&
-            nwc % 4 == 0) {
-            const float4* wa4 = reinterpret_cast<const float4*>(p.act.Wa);
-            const float4* wc4 = reinterpret_cast<const float4*>(p.act.Wc);
-            float4 ra[2], rc;
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = tid + u * THREADS;
-                if (i < nwa / 4) ra[u] = __ldg(wa4 + i);
-            }
-            if (tid < nwc / 4) rc = __ldg(wc4 + tid);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = tid + u * THREADS;
-                if (i < nwa / 4) reinterpret_cast<float4*>(Wa)[i] = ra[u];
-            }
-            if (tid < nwc / 4) reinterpret_cast<float4*>(Wc)[tid] = rc;
-        } else {
-            for (int i = tid; i < nwa; i += THREADS) Wa[i] = p.act.Wa[i];
-            for (int i = tid; i < nwc; i += THREADS) Wc[i] = p.act.Wc[i];
-        }
-        __syncthreads();
-        {
-            float* const as[1] = {act_s[warp]};
-            float* const vs[1] = {&val_s[warp]};
-            if (ok[0]) act_rows_loaded<HB, NK, 1>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs, hc, ha);
-        }
-        __syncthreads();
-    }
-    // Phase 1: the stand-in's joints and base chains are independent recurrences, each on its own
-    // thread with the same fp32 operations as one robot per thread would use; the reward sums
-    // and the reset decision meet on the robot's planar thread through shared memory (the joint
-    // terms summed in joint order).
+    // Phase 1's inputs: each thread's role and its part of the robot state
     const bool joint = tid < T_PLANE;
     const bool p1 = tid < T_ROLES;                                     // threads past the roles idle here
     const int lr = joint ? tid / 12 : (tid - T_PLANE) & 15;           // robot of the block
@@ -227,6 +183,59 @@ __global__ void __launch_bounds__(512, 2) env_step_kernel(EnvParams p) {
     int eplen = si[(size_t)RL_I_EPLEN * N + ec];
     int level = si[(size_t)RL_I_LEVEL * N + ec];
     int contact = si[(size_t)RL_I_CONTACT * N + ec];
+    if constexpr (FUSE != 0) {
+        // Phase 0 (fused policy head): the head weights into shared memory, then one warp per
+        // robot evaluates mu, the sampled action, logp and V exactly as the action-head kernel
+        // does, writing the rollout's records and the block's actions / values for phase 1.  The
+        // head weights are staged before the wait for the forward layer, the warp's hidden rows
+        // loaded after it.
+        static_assert(ENVS == THREADS / 32, "one robot per warp");
+        constexpr bool HB = (FUSE >> 4) != 0;
+        constexpr int NK = FUSE & 15;
+        const int mm[1] = {env0 + warp};
+        const bool ok[1] = {env0 + warp < N};
+        float* Wa = gtab + 2 * GTAB;
+        float* Wc = Wa + p.act.A * p.act.H;
+        // every load of the staging issued before its stores (16-byte pieces where the layout
+        // allows), so that the block waits for one round trip to L2 instead of one per piece
+        const int nwa = p.act.A * p.act.H, nwc = p.act.H;
+        if (((reinterpret_cast<uintptr_t>(p.act.Wa) | reinterpret_cast<uintptr_t>(p.act.Wc)) & 15u) == 0 && nwa % 4 == 0 &&
+            nwc % 4 == 0) {
+            const float4* wa4 = reinterpret_cast<const float4*>(p.act.Wa);
+            const float4* wc4 = reinterpret_cast<const float4*>(p.act.Wc);
+            float4 ra[2], rc;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = tid + u * THREADS;
+                if (i < nwa / 4) ra[u] = __ldg(wa4 + i);
+            }
+            if (tid < nwc / 4) rc = __ldg(wc4 + tid);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = tid + u * THREADS;
+                if (i < nwa / 4) reinterpret_cast<float4*>(Wa)[i] = ra[u];
+            }
+            if (tid < nwc / 4) reinterpret_cast<float4*>(Wc)[tid] = rc;
+        } else {
+            for (int i = tid; i < nwa; i += THREADS) Wa[i] = p.act.Wa[i];
+            for (int i = tid; i < nwc; i += THREADS) Wc[i] = p.act.Wc[i];
+        }
+        pdl_wait();
+        pdl_trigger();
+        float hrc[1][NK], hra[1][NK];
+        if (ok[0]) act_rows_load<HB, NK, 1>(p.act, mm, ok, true, lane, hrc, hra);
+        __syncthreads();
+        {
+            float* const as[1] = {act_s[warp]};
+            float* const vs[1] = {&val_s[warp]};
+            if (ok[0]) act_rows_loaded<HB, NK, 1>(p.act, Wa, Wc, mm, ok, it, true, lane, as, vs, hrc, hra);
+        }
+        __syncthreads();
+    }
+    // Phase 1: the stand-in's joints and base chains are independent recurrences, each on its own
+    // thread with the same fp32 operations as one robot per thread would use; the reward sums
+    // and the reset decision meet on the robot's planar thread through shared memory (the joint
+    // terms summed in joint order).
     uint64_t key;
     float st_r = 0.f, st_d = 0.f, st_l = 0.f;   // per-robot statistics (planar threads)
     if (MODE == 0) {

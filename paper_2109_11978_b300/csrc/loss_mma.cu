@@ -101,8 +101,11 @@ struct Smem {
 template <int H>
 __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma_kernel(HeadParams p) {
     constexpr int NW = warps_of<H>(), THREADS = 32 * NW;
-    pdl_wait();
-    pdl_trigger();
+    // Everything staged before the wait for the preceding kernel (the forward GEMM that writes the
+    // last hidden rows) was written by kernels that have completed when this one starts: the
+    // packed records and permutation (written once per iteration before the update), the head
+    // weights and log-std (Adam of the previous minibatch, which precedes the forward layers).  The
+    // hidden rows are copied after the wait.
     using S = Smem<H>;
     constexpr int HP = S::HP;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -164,19 +167,8 @@ __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma
             R = __ldg(p.ret + s);
         }
     }
-    // ---- stage (asynchronous 16-byte copies): h tiles (zeros past M), the critic head's fp32 weights
-    {
-        const __nv_bfloat16* ga = reinterpret_cast<const __nv_bfloat16*>(p.ha) + (size_t)m0 * H;
-        const __nv_bfloat16* gc = reinterpret_cast<const __nv_bfloat16*>(p.hc) + (size_t)m0 * H;
-        constexpr int VPR = H / 8;                            // 16-byte vectors per row
-        for (int v = tid; v < ROWS * VPR; v += THREADS) {
-            const int r = v / VPR, c = (v % VPR) * 8;
-            const int rr = r < rows ? r : 0;                  // a valid address; zero-filled
-            cp_async16(ha + r * HP + c, ga + (size_t)rr * H + c, r < rows ? 16 : 0);
-            cp_async16(hc + r * HP + c, gc + (size_t)rr * H + c, r < rows ? 16 : 0);
-        }
-        for (int v = tid; v < H / 4; v += THREADS) cp_async16(wcf + 4 * v, p.Wc + 4 * v, 16);
-    }
+    // ---- the critic head's fp32 weights (asynchronous 16-byte copies)
+    for (int v = tid; v < H / 4; v += THREADS) cp_async16(wcf + 4 * v, p.Wc + 4 * v, 16);
     // head weights -> bf16 hi / lo tiles (Wa rows j >= A and Wc rows 1..7 zero), read straight from
     // global memory while the row copies are in flight
     {
@@ -211,6 +203,21 @@ __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma
         // has no cancellation between terms near 1/2 (the KL of a small policy change is small)
         const float dls = lso - ls;
         cst[32 + tid] = 0.5f * expm1f(2.f * dls) - dls;
+    }
+    // the preceding kernel's results (the hidden rows), then the next kernel may be placed
+    pdl_wait();
+    pdl_trigger();
+    // ---- h tiles (asynchronous 16-byte copies, zeros past M)
+    {
+        const __nv_bfloat16* ga = reinterpret_cast<const __nv_bfloat16*>(p.ha) + (size_t)m0 * H;
+        const __nv_bfloat16* gc = reinterpret_cast<const __nv_bfloat16*>(p.hc) + (size_t)m0 * H;
+        constexpr int VPR = H / 8;                            // 16-byte vectors per row
+        for (int v = tid; v < ROWS * VPR; v += THREADS) {
+            const int r = v / VPR, c = (v % VPR) * 8;
+            const int rr = r < rows ? r : 0;                  // a valid address; zero-filled
+            cp_async16(ha + r * HP + c, ga + (size_t)rr * H + c, r < rows ? 16 : 0);
+            cp_async16(hc + r * HP + c, gc + (size_t)rr * H + c, r < rows ? 16 : 0);
+        }
     }
     cp_async_wait_all();
     __syncthreads();
