@@ -362,7 +362,9 @@ rl_status rl_profile_read_class(rl_ctx* ctx, int32_t kernel_class, float* total_
  * (64, 128, 256 output columns), tile modes (one CTA per tile, a CTA pair on the cta_group::2
  * MMA, or one CTA per tile with two K blocks per pipeline stage) and, for weight gradients, split-K counts (one and two waves of the width's tiles over the SMs, half and double the default;
  * timed together with the summation of their partials, which Adam performs) on the context's
- * own buffers, keeps the fastest, and drops a captured iteration graph so the next
+ * own buffers, keeps the fastest, then times the fused forward of the three hidden layers
+ * (rl_set_forward_fused) against the chosen per-layer launches at both forward sites and keeps
+ * the faster, and drops a captured iteration graph so the next
  * rl_train_iteration re-captures with the new shapes.  Synchronises; the buffers it runs on are
  * scratch (parameters, Adam state and env state are untouched).  report (host, may be NULL): a
  * JSON summary of the chosen shapes and their times, truncated to report_bytes. */
@@ -390,6 +392,21 @@ rl_status rl_autotune(rl_ctx* ctx, char* report, size_t report_bytes, void* stre
  * other sites.  Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for any other value or an FP32 context; nothing is changed then. */
 rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits);
+
+/* Runs the forward pass of the three hidden layers (Sec. 2.2's ELU MLPs, actor and critic) as one
+ * fused launch instead of one GEMM launch per layer (no counterpart in the paper: a scheduling
+ * control of this implementation, chosen by rl_autotune).  site: 0 the update's forward (every
+ * layer's activations are written, for the backward), 3 the rollout's (only the last layer's);
+ * on: 1 fused, 0 layer by layer (the default).  Each CTA carries one 128-row tile of one network
+ * through all three layers on the tensor cores, the activations staying in shared memory; the
+ * products are accumulated in the same order and finished by the same epilogue arithmetic as the
+ * per-layer launches, so both forms give the same bits.  Drops a captured iteration graph.
+ * RL_ERR_INVALID_ARG for another site or value, or (on = 1) an FP32 context or widths the fused
+ * form does not take: three hidden layers, input width a multiple of 64 up to 256, first width a
+ * multiple of 128 up to 512, second and third multiples of 128 up to 256. */
+rl_status rl_set_forward_fused(rl_ctx* ctx, int32_t site, int32_t on);
+/* 1 if the site's forward runs fused, 0 if layer by layer, -1 for a null context or another site. */
+int32_t rl_get_forward_fused(rl_ctx* ctx, int32_t site);
 
 /* Caps the persistent CTAs of the context's tensor-core GEMM launches (no counterpart in the
  * paper: a scheduling control of this implementation).  max_ctas 0: one CTA per SM (the default

@@ -94,6 +94,8 @@ SIGNATURES = {
     "rl_autotune": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t, _vp]),
     "rl_set_gemm_tiles": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "rl_set_gemm_ctas": (_i32, [_vp, _i32]),
+    "rl_set_forward_fused": (_i32, [_vp, _i32, _i32]),
+    "rl_get_forward_fused": (_i32, [_vp, _i32]),
     "rl_adam_step": (_i32, [ctypes.c_int64, _vp, _vp, _i32, _vp, _vp, _f32, _i32, _vp, _vp]),
     "rl_gemm_bf16": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rl_gemm_bf16_tn": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),

@@ -243,6 +243,19 @@ def rl_set_gemm_tiles(ctx, site, layer, bn, cluster=1, splits=1):
     check(lib().rl_set_gemm_tiles(ctx, int(site), int(layer), int(bn), int(cluster), int(splits)), "rl_set_gemm_tiles")
 
 
+def rl_set_forward_fused(ctx, site, on):
+    """The three hidden layers' forward as one fused launch (site 0 the update's, 3 the rollout's)."""
+    check(lib().rl_set_forward_fused(ctx, int(site), int(bool(on))), "rl_set_forward_fused")
+
+
+def rl_get_forward_fused(ctx, site):
+    """1 if the site's forward runs fused, 0 if layer by layer."""
+    r = int(lib().rl_get_forward_fused(ctx, int(site)))
+    if r < 0:
+        raise RLError("rl_get_forward_fused: invalid context or site")
+    return r
+
+
 def rl_gemm_bf16(A, B, C):
     """C[M][N] (fp32) = A[M][K] (bf16) @ B[N][K]^T (bf16) on the tcgen05 tensor-core kernel."""
     M, K = A.shape

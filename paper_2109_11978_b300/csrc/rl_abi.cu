@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "gemm_tc.cuh"
+#include "mlp_fused.cuh"
 #include "kernels.cuh"
 
 using namespace rl;
@@ -102,6 +103,9 @@ struct rl_ctx {
     // cluster mode per site: 1 single CTA, 3 pairs of CTAs running one 256-row tile on the
     // cta_group::2 MMA (half of B each), 4 single CTA with two K blocks per pipeline stage
     int cm_fwd[4], cm_dx[4], cm_dw[4], cm_act[4];
+    // the three hidden layers' forward as one fused launch (mlp_fused.cu): the update's (fwd) and
+    // the rollout's (act); set by the autotuner or rl_set_forward_fused
+    bool fuse_fwd = false, fuse_act = false;
     CUtensorMap tm_fwdB[2][4], tm_fwdA[2][4];   // A for l >= 1 (H of layer l-1), A for l == 0 unused
     CUtensorMap tm_actB[2][4];                   // forward B maps of the rollout's policy inference
     CUtensorMap tm_x0;                           // gathered minibatch observations
@@ -363,8 +367,46 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
     return RL_OK;
 }
 
+// The fused forward fits the context: BF16, three hidden layers of the widths mlp_fwd_fits takes.
+bool fused_fits(const rl_ctx* c) {
+    return c->bf16 && c->NH == 3 && mlp_fwd_fits(c->L[0][0].in, c->L[0][0].out, c->L[0][1].out, c->L[0][2].out);
+}
+
+// The three hidden layers in one launch (mlp_fused.cu): every layer's rows are kept for the
+// update's backward, only the last layer's for the rollout.
+rl_status forward_fused(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act, bool b_early) {
+    MlpParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    const LayerInfo* L0 = c->L[0];
+    if (!make_tmap_bf16(&mp.tmX, X, (uint64_t)rows, (uint64_t)L0[0].in, (uint64_t)L0[0].in, 128)) return RL_ERR_CUDA;
+    for (int j = 0; j < nnets; ++j) {
+        const int n = net0 + j;
+        for (int l = 0; l < 3; ++l) {
+            const LayerInfo& Li = c->L[n][l];
+            if (!make_tmap_bf16(&mp.tmW[j][l], c->wbf[n][l], (uint64_t)Li.out, (uint64_t)Li.in, (uint64_t)Li.in, 128))
+                return RL_ERR_CUDA;
+            if ((!act || l == 2) &&
+                !make_tmap_bf16(&mp.tmH[j][l], c->H[n][l], (uint64_t)rows, (uint64_t)Li.out, (uint64_t)Li.out, 128))
+                return RL_ERR_CUDA;
+            mp.bias[j][l] = c->params + Li.b;
+        }
+    }
+    mp.M = rows;
+    mp.K0 = L0[0].in;
+    mp.N0 = L0[0].out;
+    mp.N1 = L0[1].out;
+    mp.N2 = L0[2].out;
+    mp.nnets = nnets;
+    mp.store_hidden = act ? 0 : 1;
+    mp.b_early = b_early ? 1 : 0;
+    mp.status = c->status;
+    CK(q.run(RL_PROF_GEMM, 1, [&] { return launch_mlp_fwd(mp, q.s); }));
+    return RL_OK;
+}
+
 // Forward through every hidden layer.
 rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act, bool b_early = false) {
+    if ((act ? c->fuse_act : c->fuse_fwd) && fused_fits(c)) return forward_fused(c, q, X, rows, net0, nnets, act, b_early);
     for (int l = 0; l < c->NH; ++l) {
         rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, act, b_early);
         if (st != RL_OK) return st;
@@ -1035,6 +1077,28 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
         }
         if (c->bf16 && !encode_layer_maps(c, l)) return RL_ERR_CUDA;
     }
+    // the fused forward of the three hidden layers against the layer-by-layer form with the shapes
+    // just chosen, at both sites (the update's minibatch rows, the rollout's num_envs rows); the
+    // report's cluster field is 1 when the fused form is kept
+    if (st == RL_OK && fused_fits(c)) {
+        for (int site : {0, 3}) {
+            bool& flag = site == 0 ? c->fuse_fwd : c->fuse_act;
+            const char* name = site == 0 ? "forward_fused" : "act_forward_fused";
+            float ms[2] = {0.f, 0.f};
+            for (int f = 0; f < 2 && st == RL_OK; ++f) {
+                flag = f == 1;
+                st = timed(
+                    [&] {
+                        return site == 0 ? forward_hidden(c, q, c->X0, c->Mb, 0, 2, false)
+                                         : forward_hidden(c, q, c->obs, c->N, 0, 2, true, true);
+                    },
+                    ms[f]);
+                if (st == RL_OK) trial(name, 0, 128, f, 1, ms[f]);
+            }
+            flag = st == RL_OK && ms[1] < ms[0];
+            note(name, 0, 128, flag ? 1 : 0, 1, flag ? ms[1] : ms[0]);
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     report += "], \"trials_site_layer_bn_cluster_splits_us\": [" + trials + "]";
@@ -1248,6 +1312,7 @@ static rl_status create_impl(rl_ctx* c, const float* heightfield, const float* i
         CK(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
     }
     CK(tc_prepare());
+    CK(mlp_prepare());
     CK(env_prepare());
     heads_prepare();
 
@@ -1916,6 +1981,18 @@ rl_status rl_adam_step(int64_t n, float* p, const float* g, int32_t nsplit, floa
 rl_status rl_set_gemm_tiles(rl_ctx* c, int32_t site, int32_t layer, int32_t bn, int32_t cluster, int32_t splits) {
     if (!c) return RL_ERR_INVALID_ARG;
     return set_tiles_impl(c, site, layer, bn, cluster, splits);
+}
+
+rl_status rl_set_forward_fused(rl_ctx* c, int32_t site, int32_t on) {
+    if (!c || (site != 0 && site != 3) || (on != 0 && on != 1) || (on && !fused_fits(c))) return RL_ERR_INVALID_ARG;
+    (site == 0 ? c->fuse_fwd : c->fuse_act) = on != 0;
+    drop_graph(c);
+    return RL_OK;
+}
+
+int32_t rl_get_forward_fused(rl_ctx* c, int32_t site) {
+    if (!c || (site != 0 && site != 3)) return -1;
+    return (site == 0 ? c->fuse_fwd : c->fuse_act) ? 1 : 0;
 }
 
 rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {

@@ -158,9 +158,10 @@ def _bf16_round(x):
     return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("prec,grid,act_ws", [(1, (17, 11), False), (0, (17, 11), False), (1, (12, 9), False),
-                                              (1, (17, 11), True)])
-def test_train_iteration_rough_teacher_forced(prec, grid, act_ws):
+@pytest.mark.parametrize("prec,grid,act_ws,fused", [(1, (17, 11), False, False), (0, (17, 11), False, False),
+                                                    (1, (12, 9), False, False), (1, (17, 11), True, False),
+                                                    (1, (17, 11), False, True)])
+def test_train_iteration_rough_teacher_forced(prec, grid, act_ws, fused):
     """One rl_train_iteration of the rough-terrain form: 17 x 11 (or the paper's 108-point 12 x 9)
     height samples, Table 4 noise, pushes, last hidden width 128, so the rollout runs the env step
     with the policy heads fused in (the kernel form the bench times).  The oracle's rollout is
@@ -170,9 +171,15 @@ def test_train_iteration_rough_teacher_forced(prec, grid, act_ws):
     oracle's value plus the fp32 path's 1e-5), mu, V, log pi and the sampled actions within the
     precision's tolerance; GAE on the library's rewards and values to 1e-5.  act_ws: the rollout's
     hidden layers in the weight-stationary tile mode, whose launches after the first step fetch
-    their weight slice before waiting for the preceding kernel."""
-    w = workload("small_rough", precision=prec, grid=grid, crash_threshold=2 ** 26, epochs=1, minibatches=2)
+    their weight slice before waiting for the preceding kernel.  fused: the rough task's 512-256-128
+    networks with the three hidden layers' forward fused into one launch at both sites."""
+    hidden = (512, 256, 128) if fused else (128, 128)
+    w = workload("small_rough", precision=prec, grid=grid, crash_threshold=2 ** 26, epochs=1, minibatches=2,
+                 hidden=hidden)
     L, params, O, Op = _setup(w)
+    if fused:
+        api.rl_set_forward_fused(L.ctx, 0, 1)
+        api.rl_set_forward_fused(L.ctx, 3, 1)
     if act_ws:
         for layer in range(len(w["hidden"])):
             api.rl_set_gemm_tiles(L.ctx, 3, layer, 64, 5, 1)
