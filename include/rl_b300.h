@@ -400,12 +400,16 @@ rl_status rl_set_gemm_tiles(rl_ctx* ctx, int32_t site, int32_t layer, int32_t bn
  * on: 1 fused, 0 layer by layer (the default).  Each CTA carries one 128-row tile of one network
  * through all three layers on the tensor cores, the activations staying in shared memory; the
  * products are accumulated in the same order and finished by the same epilogue arithmetic as the
- * per-layer launches, so both forms give the same bits.  Drops a captured iteration graph.
+ * per-layer launches, so both forms give the same bits.  While the context's GEMM CTAs are capped
+ * (rl_set_gemm_ctas, grouped learners) the forward runs layer by layer whatever the setting, since
+ * the fused launch takes one CTA per row tile and network; rl_autotune then does not time it.
+ * Drops a captured iteration graph.
  * RL_ERR_INVALID_ARG for another site or value, or (on = 1) an FP32 context or widths the fused
  * form does not take: three hidden layers, input width a multiple of 64 up to 256, first width a
  * multiple of 128 up to 512, second and third multiples of 128 up to 256. */
 rl_status rl_set_forward_fused(rl_ctx* ctx, int32_t site, int32_t on);
-/* 1 if the site's forward runs fused, 0 if layer by layer, -1 for a null context or another site. */
+/* 1 if the site's forward runs fused (set, and the GEMM CTAs uncapped), 0 if layer by layer, -1
+ * for a null context or another site. */
 int32_t rl_get_forward_fused(rl_ctx* ctx, int32_t site);
 
 /* Caps the persistent CTAs of the context's tensor-core GEMM launches (no counterpart in the

@@ -371,6 +371,9 @@ rl_status fwd_layer(rl_ctx* c, Enq& q, int l, const void* X, int rows, int net0,
 bool fused_fits(const rl_ctx* c) {
     return c->bf16 && c->NH == 3 && mlp_fwd_fits(c->L[0][0].in, c->L[0][0].out, c->L[0][1].out, c->L[0][2].out);
 }
+// The site's forward runs fused: chosen, fitting, and the context's GEMM CTAs uncapped (the fused
+// launch takes one CTA per row tile and network, so it cannot keep to a learner's share of the SMs).
+bool fused_on(const rl_ctx* c, bool act) { return (act ? c->fuse_act : c->fuse_fwd) && fused_fits(c) && c->gemm_cap == 0; }
 
 // The three hidden layers in one launch (mlp_fused.cu): every layer's rows are kept for the
 // update's backward, only the last layer's for the rollout.
@@ -406,7 +409,7 @@ rl_status forward_fused(rl_ctx* c, Enq& q, const void* X, int rows, int net0, in
 
 // Forward through every hidden layer.
 rl_status forward_hidden(rl_ctx* c, Enq& q, const void* X, int rows, int net0, int nnets, bool act, bool b_early = false) {
-    if ((act ? c->fuse_act : c->fuse_fwd) && fused_fits(c)) return forward_fused(c, q, X, rows, net0, nnets, act, b_early);
+    if (fused_on(c, act)) return forward_fused(c, q, X, rows, net0, nnets, act, b_early);
     for (int l = 0; l < c->NH; ++l) {
         rl_status st = fwd_layer(c, q, l, X, rows, net0, nnets, act, b_early);
         if (st != RL_OK) return st;
@@ -1080,7 +1083,7 @@ rl_status autotune_impl(rl_ctx* c, cudaStream_t s, std::string& report) {
     // the fused forward of the three hidden layers against the layer-by-layer form with the shapes
     // just chosen, at both sites (the update's minibatch rows, the rollout's num_envs rows); the
     // report's cluster field is 1 when the fused form is kept
-    if (st == RL_OK && fused_fits(c)) {
+    if (st == RL_OK && fused_fits(c) && c->gemm_cap == 0) {
         for (int site : {0, 3}) {
             bool& flag = site == 0 ? c->fuse_fwd : c->fuse_act;
             const char* name = site == 0 ? "forward_fused" : "act_forward_fused";
@@ -1992,7 +1995,7 @@ rl_status rl_set_forward_fused(rl_ctx* c, int32_t site, int32_t on) {
 
 int32_t rl_get_forward_fused(rl_ctx* c, int32_t site) {
     if (!c || (site != 0 && site != 3)) return -1;
-    return (site == 0 ? c->fuse_fwd : c->fuse_act) ? 1 : 0;
+    return fused_on(c, site == 3) ? 1 : 0;
 }
 
 rl_status rl_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {

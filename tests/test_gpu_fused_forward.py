@@ -134,3 +134,22 @@ def test_set_forward_fused_rejects_invalid():
     with pytest.raises(api.RLError):
         api.rl_get_forward_fused(L.ctx, 1)
     L.close()
+
+
+def test_fused_forward_not_used_under_a_cta_cap():
+    """A learner whose GEMM CTAs are capped (grouped learners) runs its forward layer by layer: the
+    fused launch takes one CTA per row tile and network."""
+    w = workload("rough", precision=1)
+    L, _, O, Op = _setup(w)
+    api.rl_set_forward_fused(L.ctx, 3, 1)
+    api.rl_set_gemm_ctas(L.ctx, 32)
+    assert api.rl_get_forward_fused(L.ctx, 3) == 0
+    x, xd = _obs(256, O, Op, 7, True)
+    capped = _act(L, xd, 256)
+    api.rl_set_gemm_ctas(L.ctx, 0)
+    assert api.rl_get_forward_fused(L.ctx, 3) == 1
+    fused = _act(L, xd, 256)
+    for a, b in zip(capped, fused):
+        assert torch.equal(a, b)
+    assert api.rl_last_device_status(L.ctx) == 0
+    L.close()
