@@ -17,7 +17,7 @@ struct TcParams {
     int kb_per_split, splits;  // split-K over blockIdx.z
     int batch;                 // 1 or 2 (actor, critic share one launch)
     int bn;                    // 64, 128 or 256
-    int cm;                    // CTAs per cluster along M sharing (multicasting) the B tile: 1 or 2
+    int cm;                    // CTAs per cluster along M: 1, or 2 with pair (no copy is multicast)
     int pair;                  // with cm = 2: the pair runs one 256-row tile on the cta_group::2 MMA,
                                // each CTA loading half of B (B maps: box rows bn / 2); bn 128 / 256
     int mn;                    // operand forms: MAJ_K (A [M][K], B [N][K]), MAJ_MN (A^T [K][M],
