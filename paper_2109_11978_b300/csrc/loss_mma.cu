@@ -93,7 +93,7 @@ struct Smem {
     static constexpr int REC = MU;                            // [ROWS][RP]
     static constexpr int G = MU + ROWS * FP;                  // [ROWS][FP]: g_mu (12) and g_v at 12
     static constexpr int WCF = G + ROWS * FP;                 // [H] Wc fp32
-    static constexpr int CST = WCF + H;                       // [64] log-std constants
+    static constexpr int CST = WCF + H;                       // [64] log-std constants, ba at 48, bc at 60
     static constexpr int FLOATS = CST + 64;
     static constexpr int BYTES = FLOATS * 4;
 };
@@ -203,7 +203,9 @@ __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma
         // has no cancellation between terms near 1/2 (the KL of a small policy change is small)
         const float dls = lso - ls;
         cst[32 + tid] = 0.5f * expm1f(2.f * dls) - dls;
+        cst[48 + tid] = p.ba[tid];                           // the heads' biases, with the constants
     }
+    if (tid == 0) cst[60] = p.bc[0];
     // the preceding kernel's results (the hidden rows), then the next kernel may be placed
     pdl_wait();
     pdl_trigger();
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma
             const int jj = qq + TPR * u;
             diff[u] = 0.f;
             if (jj < A && live) {
-                const float mu = mu_s[r * FP + jj] + p.ba[jj];
+                const float mu = mu_s[r * FP + jj] + cst[48 + jj];
                 const float ls = cst[jj], iv = cst[16 + jj];
                 diff[u] = aold[u] - mu;
                 logp += -0.5f * diff[u] * diff[u] * iv - ls - HALF_LOG_2PI;
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(32 * warps_of<H>(), H >= 128 ? 3 : 4) loss_mma
             logp += __shfl_xor_sync(0xffffffffu, logp, o);
             kl += __shfl_xor_sync(0xffffffffu, kl, o);
         }
-        const float v = mu_s[r * FP + 12] + p.bc[0];
+        const float v = mu_s[r * FP + 12] + cst[60];
         __syncwarp();                   // the row's mu / V are read before its record overwrites them
         const float inv_M = 1.0f / (float)p.M;
         const float ratio = expf(logp - lpo);
