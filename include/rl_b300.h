@@ -335,6 +335,18 @@ rl_status rl_get_storage(rl_ctx* ctx, int32_t which, void** ptr, size_t* bytes);
  * bounded wait that ran out, RL_ERR_STATE for an out-of-range index).  Synchronises. */
 rl_status rl_last_device_status(rl_ctx* ctx);
 
+/* Resets the device status word to RL_OK (enqueued on stream), e.g. after a failure has been
+ * handled; the context's buffers and state are untouched. */
+rl_status rl_clear_device_status(rl_ctx* ctx, void* stream);
+
+/* Forced time-out of the bounded device wait (a test of the failure path; no counterpart in the
+ * paper): one warp initialises an mbarrier that nothing arrives on and waits for it with the bounded
+ * wait of the tensor-core kernels (2 s on the global timer), which records RL_ERR_TIMEOUT in the
+ * context's status word (the first failure recorded wins) and returns, leaving the CUDA context
+ * usable.  Enqueued on stream without synchronising; rl_last_device_status then reports
+ * RL_ERR_TIMEOUT.  RL_ERR_INVALID_ARG for a null context. */
+rl_status rl_diag_forced_timeout(rl_ctx* ctx, void* stream);
+
 /* In-graph timing of the kernels of rl_train_iteration, by class: RL_PROF_GEMM (every MLP GEMM,
  * rollout and update), RL_PROF_LOSS (loss head), RL_PROF_ADAM, RL_PROF_ENV (env step),
  * RL_PROF_ACT (action head), RL_PROF_GATHER (minibatch gather), RL_PROF_OTHER (GAE,

@@ -87,6 +87,8 @@ SIGNATURES = {
     "rl_train_iteration": (_i32, [_vp, _i32, _vp, _vp]),
     "rl_get_storage": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)]),
     "rl_last_device_status": (_i32, [_vp]),
+    "rl_clear_device_status": (_i32, [_vp, _vp]),
+    "rl_diag_forced_timeout": (_i32, [_vp, _vp]),
     "rl_profile_enable": (_i32, [_vp, _i32, _i32]),
     "rl_profile_read": (_i32, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_i32)]),
     "rl_profile_read_class": (_i32, [_vp, _i32, ctypes.POINTER(_f32), ctypes.POINTER(_i32)]),

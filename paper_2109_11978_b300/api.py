@@ -201,6 +201,16 @@ def rl_last_device_status(ctx):
     return int(lib().rl_last_device_status(ctx))
 
 
+def rl_clear_device_status(ctx):
+    """Resets the device status word to RL_OK (on the current stream)."""
+    check(lib().rl_clear_device_status(ctx, _stream()), "rl_clear_device_status")
+
+
+def rl_diag_forced_timeout(ctx):
+    """Launches one warp whose bounded wait runs out (2 s), recording RL_ERR_TIMEOUT."""
+    check(lib().rl_diag_forced_timeout(ctx, _stream()), "rl_diag_forced_timeout")
+
+
 def rl_profile_enable(ctx, kernel_class=0, on=True):
     check(lib().rl_profile_enable(ctx, int(kernel_class), int(bool(on))), "rl_profile_enable")
 

@@ -176,6 +176,8 @@ __host__ __device__ inline long long adam_per_block(int nsplit, int vec) {
     return (long long)(nsplit > ADAM_WIDE ? ADAM_THREADS / 32 : ADAM_THREADS) * (vec ? 4 : 1);
 }
 cudaError_t launch_adam(const AdamParams& p, cudaStream_t s);
+// One warp waiting (bounded) on an mbarrier nothing arrives on: records RL_ERR_TIMEOUT in *status.
+cudaError_t launch_forced_timeout(int* status, cudaStream_t s);
 
 // Minibatch gather: rows idx[i] of obs [B][Op] -> X [M][Op].
 // Batched LSTM actuator cell (actuator.cu): n joints, inputs [n][2], state h, c [n][32] updated in

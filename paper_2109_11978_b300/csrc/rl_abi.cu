@@ -1877,6 +1877,18 @@ rl_status rl_last_device_status(rl_ctx* c) {
     return st;
 }
 
+rl_status rl_clear_device_status(rl_ctx* c, void* stream) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), S_(stream)));
+    return RL_OK;
+}
+
+rl_status rl_diag_forced_timeout(rl_ctx* c, void* stream) {
+    if (!c) return RL_ERR_INVALID_ARG;
+    CK(launch_forced_timeout(c->status, S_(stream)));
+    return RL_OK;
+}
+
 rl_status rl_profile_enable(rl_ctx* c, int32_t kernel_class, int32_t on) {
     if (!c || kernel_class < 0 || kernel_class > RL_PROF_ALL) return RL_ERR_INVALID_ARG;
     const unsigned bits = kernel_class == RL_PROF_ALL ? 0x7Fu : (1u << kernel_class);
