@@ -31,6 +31,7 @@ static __device__ __align__(256) float4 g_gae_noalloc_scratch[NOALLOC_MAX_SLOTS]
 namespace {
 
 constexpr int GAE_THREADS = 256;
+constexpr int GAE_V4_MIN_N = 262144;   // robots from which the scan takes four per thread
 constexpr int CHUNK = 8;
 
 __device__ __forceinline__ void two_sum(float& sum, float& err, float x) {
@@ -278,7 +279,10 @@ cudaError_t launch_gae(int T, int N, float gamma, float lam, const float* rew, c
     // slot 0: (mean, std); slots 1 ..: one per block of the scan
     float4* ms = need ? reinterpret_cast<float4*>(partials) : nullptr;
     float4* part = need ? ms + 1 : nullptr;
-    const bool v4 = N % 4 == 0 && ((reinterpret_cast<uintptr_t>(rew) | reinterpret_cast<uintptr_t>(val) |
+    // four robots per thread (16-byte accesses) where the scan is bandwidth-bound; below that the
+    // launch is a single latency-bound wave, and one robot per thread gives four times the blocks
+    // and half the dependent load rounds (chunks of 8 steps instead of 4)
+    const bool v4 = N >= GAE_V4_MIN_N && N % 4 == 0 && ((reinterpret_cast<uintptr_t>(rew) | reinterpret_cast<uintptr_t>(val) |
                                     reinterpret_cast<uintptr_t>(last_val) | reinterpret_cast<uintptr_t>(adv) |
                                     reinterpret_cast<uintptr_t>(ret)) & 15u) == 0 &&
                     (reinterpret_cast<uintptr_t>(done) & 3u) == 0;
